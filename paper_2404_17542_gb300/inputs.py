@@ -1,0 +1,281 @@
+"""Seeded synthetic inputs shared by the CUDA path, the CPU oracle, the tests and
+the bench.
+
+This module builds problem *data* only: background meshes, discrete-point (DP)
+clouds, boundary ids, manufactured fields and their analytic derivatives.  It
+holds none of the method's arithmetic (no masking, arrangement, MLS fit or
+solve).  Every generator takes an explicit seed and uses numpy's PCG64, so the
+same arrays reach both sides of every parity test.
+
+Conventions (shared with the C-ABI):
+  * cell / DP index  k = i + n_x * (j + n_y * l)  (one DP per cell, Sec. 2.2);
+  * positions are SoA float64 arrays of shape (dim, N);
+  * mask is int8: -1 inner, 0 void, >= 1 boundary id (Sec. 2.2, Eq. (1));
+  * boundary id 1 is the domain wall, ids >= 2 are moving bodies.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+INNER = -1
+VOID = 0
+WALL_ID = 1
+BODY_ID = 2
+
+BC_DIRICHLET = 0
+BC_NEUMANN = 1
+
+
+@dataclass
+class Mesh:
+    """Uniform Cartesian background mesh of width l0 (Sec. 2.1-2.2)."""
+
+    dim: int
+    n: tuple
+    l0: float
+    origin: tuple = (0.0, 0.0, 0.0)
+    periodic: tuple = (0, 0, 0)
+
+    @property
+    def N(self) -> int:
+        out = 1
+        for d in range(self.dim):
+            out *= self.n[d]
+        return out
+
+    def cell_ijk(self):
+        """Integer cell coordinates, shape (dim, N), in index order."""
+        axes = [np.arange(self.n[d]) for d in range(self.dim)]
+        grids = np.meshgrid(*axes, indexing="ij")
+        # index k = i + n_x*(j + n_y*l): i varies fastest -> ravel in Fortran order
+        return np.stack([g.ravel(order="F") for g in grids])
+
+    def centroids(self):
+        ijk = self.cell_ijk().astype(np.float64)
+        org = np.array(self.origin[: self.dim], dtype=np.float64)[:, None]
+        return org + (ijk + 0.5) * self.l0
+
+
+@dataclass
+class Problem:
+    mesh: Mesh
+    pos: np.ndarray            # (dim, N) float64
+    mask: np.ndarray           # (N,) int8
+    rhs: np.ndarray = None     # (N,) float64, interior right-hand side f
+    bnd: np.ndarray = None     # (N,) float64, Dirichlet g / Neumann data
+    exact: np.ndarray = None   # (N,) float64, manufactured solution (if any)
+    normal: np.ndarray = None  # (dim, N) float64 boundary normals (or None)
+    bc_kind: np.ndarray = field(default_factory=lambda: default_bc_kind())
+    meta: dict = field(default_factory=dict)
+
+
+def default_bc_kind(neumann_ids=()):
+    """Per boundary id: 0 Dirichlet, 1 Neumann (128 entries, id 0 unused)."""
+    bc = np.zeros(128, dtype=np.uint8)
+    for i in neumann_ids:
+        bc[i] = BC_NEUMANN
+    return bc
+
+
+def wall_cells(mesh: Mesh):
+    """Boolean (N,) marking cells with a face on a non-periodic domain wall."""
+    ijk = mesh.cell_ijk()
+    on = np.zeros(mesh.N, dtype=bool)
+    for d in range(mesh.dim):
+        if mesh.periodic[d]:
+            continue
+        on |= (ijk[d] == 0) | (ijk[d] == mesh.n[d] - 1)
+    return on
+
+
+def snap_wall_dps(mesh: Mesh, pos: np.ndarray) -> np.ndarray:
+    """DP cloud convention for box walls: a wall cell's DP lies on the wall.
+
+    Each coordinate of a cell touching the lower (upper) wall of a
+    non-periodic axis is set to that wall; corner cells go to the corner.
+    This defines where the synthetic problem's boundary DPs sit; it is input
+    construction, not part of the arrangement algorithm.
+    """
+    ijk = mesh.cell_ijk()
+    out = pos.copy()
+    for d in range(mesh.dim):
+        if mesh.periodic[d]:
+            continue
+        lo = mesh.origin[d]
+        hi = mesh.origin[d] + mesh.n[d] * mesh.l0
+        out[d, ijk[d] == 0] = lo
+        out[d, ijk[d] == mesh.n[d] - 1] = hi
+    return out
+
+
+def jittered_box(n: int, dim: int, seed: int, jitter: float = 0.25,
+                 periodic: bool = False, length: float = 1.0) -> Problem:
+    """Unit box, one DP per cell at the centroid + U[-jitter*l0, jitter*l0]^dim.
+
+    Non-periodic boxes get Dirichlet wall DPs (id 1) snapped onto the walls.
+    """
+    l0 = length / n
+    per = (1, 1, 1) if periodic else (0, 0, 0)
+    mesh = Mesh(dim=dim, n=tuple([n] * dim + [1] * (3 - dim)), l0=l0,
+                origin=(0.0, 0.0, 0.0), periodic=per)
+    rng = np.random.default_rng(seed)
+    pos = mesh.centroids() + rng.uniform(-jitter * l0, jitter * l0,
+                                         size=(dim, mesh.N))
+    mask = np.full(mesh.N, INNER, dtype=np.int8)
+    if not periodic:
+        pos = snap_wall_dps(mesh, pos)
+        mask[wall_cells(mesh)] = WALL_ID
+    return Problem(mesh=mesh, pos=pos, mask=mask)
+
+
+def sin_product(pos: np.ndarray):
+    """u = prod_d sin(pi x_d) and its Laplacian f = -dim pi^2 u."""
+    dim = pos.shape[0]
+    u = np.ones(pos.shape[1])
+    for d in range(dim):
+        u = u * np.sin(math.pi * pos[d])
+    return u, -dim * math.pi ** 2 * u
+
+
+def manufactured_box(n: int, dim: int, seed: int, jitter: float = 0.25) -> Problem:
+    """Poisson problem lap u = f with u = prod sin(pi x), Dirichlet g = u on walls."""
+    pb = jittered_box(n, dim, seed, jitter)
+    u, f = sin_product(pb.pos)
+    pb.rhs = f
+    pb.bnd = np.where(pb.mask >= 1, u, 0.0)
+    pb.exact = u
+    return pb
+
+
+def poly4_coeffs(rng):
+    """Random coefficients c[a, b] (a + b <= 4) of a 2D degree-4 polynomial."""
+    c = np.zeros((5, 5))
+    for a in range(5):
+        for b in range(5 - a):
+            c[a, b] = rng.uniform(-1.0, 1.0)
+    return c
+
+
+def poly4_eval(c, x, y):
+    """u = sum c_ab x^a y^b and its analytic Laplacian."""
+    u = np.zeros_like(x)
+    lap = np.zeros_like(x)
+    for a in range(5):
+        for b in range(5 - a):
+            u += c[a, b] * x ** a * y ** b
+            if a >= 2:
+                lap += c[a, b] * a * (a - 1) * x ** (a - 2) * y ** b
+            if b >= 2:
+                lap += c[a, b] * b * (b - 1) * x ** a * y ** (b - 2)
+    return u, lap
+
+
+def poly4_box(n: int, seed: int, jitter: float = 0.25) -> Problem:
+    """2D Poisson instance with a random degree-4 polynomial solution."""
+    rng = np.random.default_rng(seed)
+    c = poly4_coeffs(rng)
+    pb = jittered_box(n, 2, int(rng.integers(0, 2**31 - 1)), jitter)
+    u, lap = poly4_eval(c, pb.pos[0], pb.pos[1])
+    pb.rhs = lap
+    pb.bnd = np.where(pb.mask >= 1, u, 0.0)
+    pb.exact = u
+    pb.meta["coeffs"] = c
+    return pb
+
+
+def batched_sizes(seed: int, count: int = 256, lo: int = 32, hi: int = 512):
+    """Mesh widths n_k = floor(exp(U(ln lo, ln hi))) for `count` instances."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(math.log(lo), math.log(hi), size=count)
+    return np.floor(np.exp(u)).astype(np.int64)
+
+
+def batched_poly4(seed: int, count: int = 256, lo: int = 32, hi: int = 512):
+    """Independent degree-4 polynomial Poisson instances of log-uniform size."""
+    sizes = batched_sizes(seed, count, lo, hi)
+    rng = np.random.default_rng(seed + 7919)
+    seeds = rng.integers(0, 2**31 - 1, size=count)
+    return [poly4_box(int(n), int(s)) for n, s in zip(sizes, seeds)]
+
+
+@dataclass
+class Cylinder:
+    """Rigid circular body oscillating along x: x_c(t) = x0 - A sin(2 pi f t)."""
+
+    x0: float = 0.5
+    y0: float = 0.5
+    radius: float = 0.05
+    amp: float = 5 * 0.1 / (2 * math.pi)
+    freq: float = 2.0
+    body_id: int = BODY_ID
+
+    def centre(self, t: float):
+        return (self.x0 - self.amp * math.sin(2 * math.pi * self.freq * t), self.y0)
+
+    def velocity(self, t: float):
+        w = 2 * math.pi * self.freq
+        return (-self.amp * w * math.cos(w * t), 0.0)
+
+    def acceleration(self, t: float):
+        w = 2 * math.pi * self.freq
+        return (self.amp * w * w * math.sin(w * t), 0.0)
+
+
+def cylinder_box(n: int, cyl: Cylinder | None = None) -> Problem:
+    """Unit box for the oscillating-cylinder workload before any DP update.
+
+    DPs start at the cell centroids (Sec. 2.3 step (i)); wall cells carry the
+    Dirichlet wall id with their DPs on the wall; every other cell starts as
+    inner until the masking of the DP update runs.
+    """
+    cyl = cyl or Cylinder()
+    l0 = 1.0 / n
+    mesh = Mesh(dim=2, n=(n, n, 1), l0=l0)
+    pos = snap_wall_dps(mesh, mesh.centroids())
+    mask = np.full(mesh.N, INNER, dtype=np.int8)
+    mask[wall_cells(mesh)] = WALL_ID
+    pb = Problem(mesh=mesh, pos=pos, mask=mask,
+                 bc_kind=default_bc_kind(neumann_ids=(cyl.body_id,)))
+    pb.meta["cylinder"] = cyl
+    return pb
+
+
+def tgv_fields(pos: np.ndarray, t: float, nu: float):
+    """Closed-form 2D Taylor-Green vortex on the periodic unit square."""
+    x, y = pos[0], pos[1]
+    F = math.exp(-8.0 * math.pi ** 2 * nu * t)
+    tp = 2.0 * math.pi
+    u = np.sin(tp * x) * np.cos(tp * y) * F
+    v = -np.cos(tp * x) * np.sin(tp * y) * F
+    p = 0.25 * (np.cos(2 * tp * x) + np.cos(2 * tp * y)) * F * F
+    return u, v, p
+
+
+def tgv_box(n: int, seed: int, jitter: float = 0.25, re: float = 100.0) -> Problem:
+    """Periodic TGV at t = 0 on a jittered periodic DP cloud.
+
+    DP 0 carries the Dirichlet id so that its pressure is pinned to the
+    closed form (the periodic pressure system is otherwise singular).
+    """
+    pb = jittered_box(n, 2, seed, jitter, periodic=True)
+    nu = 1.0 / re
+    u, v, p = tgv_fields(pb.pos, 0.0, nu)
+    pb.mask[0] = WALL_ID
+    pb.meta.update(nu=nu, u=u, v=v, p=p)
+    return pb
+
+
+def cnn_weights(seed: int, c_in: int = 6, width: int = 32, layers: int = 4,
+                c_out: int = 1):
+    """He-initialised 3x3 conv weights [(c_out, c_in, 3, 3)] and zero biases."""
+    rng = np.random.default_rng(seed)
+    chans = [c_in] + [width] * (layers - 1) + [c_out]
+    ws, bs = [], []
+    for a, b in zip(chans[:-1], chans[1:]):
+        std = math.sqrt(2.0 / (9 * a))
+        ws.append(rng.normal(0.0, std, size=(b, a, 3, 3)))
+        bs.append(np.zeros(b))
+    return ws, bs
