@@ -1,0 +1,256 @@
+/*
+ * mcd.h - C ABI of the GB300 (sm_103a) library for the data-parallel hot path
+ * of the mesh-constrained discrete point (MCD) method, arXiv 2404.17542:
+ * DP masking and arrangement, chi=1 quadratic MLS stencil weights, and the
+ * Bi-CGSTAB pressure-Poisson solve they drive.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Mesh / DP indexing: one DP per background-mesh cell (Sec. 2.2); cell and
+ *    DP index k = i + n[0] * (j + n[1] * l).  N = n[0] * n[1] (* n[2]).
+ *  - Positions are SoA float64, `dim` rows of N (x then y then z).
+ *  - mask is int8 per DP: -1 inner, 0 void, >= 1 boundary id (Sec. 2.2, Eq. (1)).
+ *    Whether boundary id b is a Dirichlet or a Neumann boundary is given by
+ *    mcd_mls_params.bc_kind[b].
+ *  - Every pointer argument named *_dev is DEVICE memory owned by the caller
+ *    (e.g. a torch tensor); the library never frees it.  Pointers without the
+ *    suffix are host memory.  Opaque handles (mcd_stencils, mcd_net, ...) own
+ *    their device buffers and are released by their *_destroy call.
+ *  - Work is enqueued on `stream` (NULL = legacy default stream).  Only calls
+ *    whose description says "synchronises" wait for the stream.
+ *  - Errors are reported only by the returned mcd_status; mcd_last_error()
+ *    gives a message for the calling thread.  Nothing falls back to the CPU.
+ */
+#ifndef MCD_H
+#define MCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *mcd_stream_t; /* the same type as cudaStream_t */
+
+typedef enum {
+    MCD_OK = 0,
+    MCD_EINVAL = 1,      /* bad argument (NULL, size, unsupported combination) */
+    MCD_ENOMEM = 2,      /* device allocation failed */
+    MCD_ECUDA = 3,       /* a CUDA runtime call failed */
+    MCD_ESINGULAR = 4,   /* an MLS moment matrix is not positive definite */
+    MCD_ENOCONV = 5,     /* the solve hit max_iter before reaching tol */
+    MCD_EBREAKDOWN = 6,  /* Bi-CGSTAB broke down and restarting did not help */
+    MCD_ENONFINITE = 7,  /* NaN or Inf in an input or a residual */
+    MCD_ETIMEOUT = 8,    /* a bounded device wait gave up */
+    MCD_ENOTSUP = 9      /* feature not built (e.g. 3D arrangement) */
+} mcd_status;
+
+enum { MCD_FP64 = 0, MCD_MIXED = 1 };          /* arithmetic of a solve */
+enum { MCD_DT_F64 = 0, MCD_DT_F32 = 1 };       /* element type of a vector */
+enum { MCD_W_GAUSS = 0, MCD_W_COS2 = 1 };      /* MLS weight function */
+enum { MCD_BC_DIRICHLET = 0, MCD_BC_NEUMANN = 1 };
+
+/* Uniform Cartesian background mesh of width l0 (Sec. 2.1-2.2).  dim is 2 or
+ * 3; n[2] = 1 and periodic[2] = 0 when dim = 2. */
+typedef struct {
+    int dim;
+    int n[3];
+    double l0;
+    double origin[3];
+    int periodic[3];
+} mcd_mesh;
+
+/* -------------------------------------------------------------------------
+ * MLS stencil weights (Sec. 3.2, Eqs. (12)-(17))
+ * ---------------------------------------------------------------------- */
+
+/* weight_kind  MCD_W_COS2: w = cos^2(pi r / (2 r_e)) for r <= r_e, else 0
+ *              (Eq. (17); the paper uses r_e = 2.5 l0);
+ *              MCD_W_GAUSS: w = exp(-(r / r_e)^2), no cut-off.
+ * r_s          scaling length of X = (x - x_c) / r_s (Eq. (12); paper: l0).
+ * precision    MCD_FP64 keeps FP64 rows only; MCD_MIXED also keeps an FP32
+ *              copy of the rows for the inner solve of a mixed solve.
+ * want_derivs  1: also keep the per-component derivative weights (gradient
+ *              and Hessian, needed by the projection driver); 0: rows only.
+ * bc_kind[b]   MCD_BC_DIRICHLET or MCD_BC_NEUMANN for boundary id b. */
+typedef struct {
+    int weight_kind;
+    double r_e;
+    double r_s;
+    int precision;
+    int want_derivs;
+    uint8_t bc_kind[128];
+} mcd_mls_params;
+
+typedef struct mcd_stencils mcd_stencils;  /* opaque; owns its device arrays */
+
+/* mcd_build_stencils - chi=1 quadratic MLS weights of every DP and the rows
+ * of the pressure-Poisson system (Sec. 3.2, Eqs. (12)-(17); Sec. 3.3, Eq. (21)).
+ *
+ * For DP i the fit uses the DPs of the 3x3 (3x3x3) cells around cell i.
+ *  inner DP:     Lambda_c = inner and Dirichlet neighbours (values),
+ *                Lambda^N_c = Neumann neighbours (normal-derivative data),
+ *                basis (X, Y, X^2/2, XY, Y^2/2) (3D: 9 terms);
+ *                row = MLS Laplacian; the Neumann data terms move to the RHS.
+ *  Neumann DP:   linear fit over all non-void neighbours; row = n . grad,
+ *                scaled so its diagonal is -1/r_s^2 (right-hand side scaled
+ *                alike).
+ *  Dirichlet DP, void DP: identity row.
+ * Arguments
+ *  mesh        host; periodic axes use the minimum image.
+ *  pos_dev     device float64 [dim][N] DP positions.
+ *  mask_dev    device int8 [N].
+ *  normal_dev  device float64 [dim][N] unit normals of Neumann DPs (others
+ *              ignored); may be NULL when no bc_kind entry is Neumann.
+ *  prm         host parameters (above).
+ *  st          in/out: *st == NULL allocates a new handle; an existing
+ *              handle of the same mesh size and options is refilled.
+ * A DP whose moment matrix is not positive definite is recorded on the
+ * device; mcd_stencils_check() reports it (MCD_ESINGULAR) and
+ * mcd_solve_pressure() refuses to run on such a handle.  Asynchronous. */
+mcd_status mcd_build_stencils(const mcd_mesh *mesh, const double *pos_dev,
+                              const int8_t *mask_dev, const double *normal_dev,
+                              const mcd_mls_params *prm, mcd_stencils **st,
+                              mcd_stream_t stream);
+
+/* Synchronises `stream`; MCD_ESINGULAR (and *first_bad_dp >= 0) if a moment
+ * matrix failed, MCD_OK (and -1) otherwise.  first_bad_dp may be NULL. */
+mcd_status mcd_stencils_check(const mcd_stencils *st, int64_t *first_bad_dp,
+                              mcd_stream_t stream);
+
+void mcd_stencils_destroy(mcd_stencils *st);
+
+/* Device arrays of a handle, for parity tests and drivers (read-only).
+ *  MCD_ARR_ROW64   float64 [S][N] PPE rows (slot-major, S = 3^dim)
+ *  MCD_ARR_ROW32   float32 [S][N] (MCD_MIXED only)
+ *  MCD_ARR_QL64    float64 [S][N] Neumann-data weights of the PPE rows
+ *  MCD_ARR_D64     float64 [nb][S][N] value weights of each derivative
+ *                  (nb = 5 in 2D: d/dx, d/dy, d2/dx2, d2/dxdy, d2/dy2;
+ *                  9 in 3D: x, y, z, xx, yy, zz, xy, yz, xz); want_derivs only
+ *  MCD_ARR_QD64    float64 [nb][S][N] Neumann-data weights of each derivative
+ *  MCD_ARR_RSCALE  float64 [N] right-hand-side factor of boundary rows
+ *  MCD_ARR_KIND    int8 [N]: 0 void, 1 inner, 2 Dirichlet, 3 Neumann
+ * *count receives the number of elements (may be NULL). */
+enum {
+    MCD_ARR_ROW64 = 0, MCD_ARR_ROW32 = 1, MCD_ARR_QL64 = 2, MCD_ARR_D64 = 3,
+    MCD_ARR_QD64 = 4, MCD_ARR_RSCALE = 5, MCD_ARR_KIND = 6
+};
+mcd_status mcd_stencils_array(const mcd_stencils *st, int which,
+                              const void **dev_ptr, int64_t *count);
+
+/* Copy array `which` (as above) into caller device memory dst_dev, which
+ * must hold *count elements of the array's type.  Asynchronous. */
+mcd_status mcd_stencils_copy(const mcd_stencils *st, int which, void *dst_dev,
+                             mcd_stream_t stream);
+
+/* mcd_apply_laplacian - y = A x with the PPE rows of `st` (the matrix-free
+ * stencil SpMV of Eq. (21)).  dtype MCD_DT_F64 uses the FP64 rows and FP64
+ * vectors; MCD_DT_F32 the FP32 rows (MCD_MIXED handles) and FP32 vectors.
+ * x_dev, y_dev: device [N], must not alias.  Asynchronous. */
+mcd_status mcd_apply_laplacian(const mcd_stencils *st, const void *x_dev,
+                               void *y_dev, int dtype, mcd_stream_t stream);
+
+/* mcd_assemble_rhs - right-hand side b of the PPE system (Eq. (21), (23)):
+ * inner DP b = rhs - sum(QL * bnd over Neumann neighbours); Dirichlet DP
+ * b = bnd; Neumann DP b = rscale * bnd; void DP b = 0.  rhs_dev, bnd_dev,
+ * b_dev: device float64 [N].  Asynchronous. */
+mcd_status mcd_assemble_rhs(const mcd_stencils *st, const double *rhs_dev,
+                            const double *bnd_dev, double *b_dev,
+                            mcd_stream_t stream);
+
+/* -------------------------------------------------------------------------
+ * Pressure solve (Sec. 3.3: Bi-CGSTAB on the MLS PPE)
+ * ---------------------------------------------------------------------- */
+typedef struct mcd_net mcd_net;
+
+/* tol          stop when ||b - A p||_2 <= tol ||b||_2 (FP64 residual).
+ * max_iter     cap on Krylov iterations (all refinements together).
+ * mode         MCD_FP64: plain FP64 Bi-CGSTAB;
+ *              MCD_MIXED: FP32 Bi-CGSTAB inner solves, FP64 residual and
+ *              update (iterative refinement); needs an MCD_MIXED handle.
+ * inner_tol    relative tolerance of each inner FP32 solve (MIXED).
+ * max_refine   cap on refinements (MIXED).
+ * net          NULL, or a trained network giving the initial guess.
+ * check_every  Krylov iterations between host convergence checks (0: auto). */
+typedef struct {
+    double tol;
+    int max_iter;
+    int mode;
+    double inner_tol;
+    int max_refine;
+    const mcd_net *net;
+    int check_every;
+} mcd_solve_params;
+
+typedef struct {
+    int iters;          /* Krylov iterations done */
+    int refinements;    /* FP64 residual evaluations after the first (MIXED) */
+    int restarts;       /* Bi-CGSTAB restarts after a rho breakdown */
+    double rel_res;     /* final ||b - A p|| / ||b|| in FP64 */
+    double b_norm;      /* ||b||_2 */
+} mcd_solve_info;
+
+/* mcd_solve_pressure - solve A p = b (b from mcd_assemble_rhs(rhs, bnd)).
+ * p_dev: device float64 [N]; in: initial guess (ignored when a net is
+ * given), out: solution.  Dirichlet entries of the guess are replaced by
+ * their values.  info: host, may be NULL.  Synchronises `stream`.
+ * Returns MCD_ENOCONV if max_iter is reached (p holds the last iterate),
+ * MCD_ENONFINITE if b or a residual is not finite, MCD_ESINGULAR if the
+ * handle recorded a singular stencil. */
+mcd_status mcd_solve_pressure(const mcd_stencils *st, const double *rhs_dev,
+                              const double *bnd_dev, double *p_dev,
+                              const mcd_solve_params *prm, mcd_solve_info *info,
+                              mcd_stream_t stream);
+
+/* -------------------------------------------------------------------------
+ * Moving-boundary DP update (Sec. 2.2-2.4)
+ * ---------------------------------------------------------------------- */
+
+/* A rigid circular body (2D): centre c at the new time, radius, boundary id
+ * (>= 2; id 1 is the domain wall). */
+typedef struct {
+    int id;
+    double c[3];
+    double radius;
+} mcd_body;
+
+/* mcd_update_dps - one DP update for the body positions of the new step.
+ *  1. mask_prev <- mask.
+ *  2. Role reassignment (Sec. 2.4) of every non-wall cell whose centroid is
+ *     within `band` of the boundary (|psi(centroid)| < band; band <= 0: every
+ *     cell): count the cell vertices with psi >= 0, evaluated as
+ *     dx*dx + dy*dy >= R*R with every operation rounded separately, and map
+ *     0/1 -> void, 2/3 -> body id, 4 -> inner (Eq. (1)).  Cells with a face
+ *     on the domain wall keep their mask.
+ *  3. DPs of band cells that became void go to their cell centroid.
+ *  4. n_relax Jacobi sweeps over the non-void band DPs: spring relaxation
+ *     x* = x - kappa l0 sum_j (1 - r_ij/l0^SPG) x~_ij (Eqs. (5)-(8)), body DPs
+ *     relocated onto the circle (Eq. (9)), inner DPs moved by beta psi d^ when
+ *     alpha > 0 (Sec. 4.7, Eqs. (45)-(46), r_e = 5 l0), clamp into the cell.
+ * pos_dev (float64 [2][N]) and mask_dev (int8 [N]) are updated in place;
+ * mask_prev_dev (int8 [N]) receives the old mask.  2D, nbodies = 1 only
+ * (MCD_ENOTSUP otherwise).  Asynchronous. */
+mcd_status mcd_update_dps(const mcd_mesh *mesh, const mcd_body *bodies,
+                          int nbodies, double *pos_dev, int8_t *mask_dev,
+                          int8_t *mask_prev_dev, double kappa, int n_relax,
+                          double band, double alpha, mcd_stream_t stream);
+
+/* mcd_body_normals - unit normal (x - c)/|x - c| of every DP whose mask is
+ * the body's id, 0 elsewhere (the analytic gradient of the circle SDF,
+ * Sec. 2.5).  normal_dev: device float64 [2][N].  Asynchronous. */
+mcd_status mcd_body_normals(const mcd_mesh *mesh, const mcd_body *body,
+                            const double *pos_dev, const int8_t *mask_dev,
+                            double *normal_dev, mcd_stream_t stream);
+
+/* Message of the last error on the calling thread (never NULL). */
+const char *mcd_last_error(void);
+
+/* Library version string. */
+const char *mcd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCD_H */

@@ -1,0 +1,109 @@
+// Internal helpers shared by the translation units of libmcd (not part of
+// the C ABI).  Error plumbing, the stencil handle layout, the slot
+// geometry of the 3x3 / 3x3x3 compact support and block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/mcd.h"
+
+namespace mcd {
+
+void set_error(const std::string &msg);
+
+#define MCD_CUDA_TRY(call)                                                    \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) {                                              \
+            ::mcd::set_error(std::string(#call) + ": " + cudaGetErrorString(e_)); \
+            return MCD_ECUDA;                                                 \
+        }                                                                     \
+    } while (0)
+
+#define MCD_CHECK_ARG(cond, msg)                                              \
+    do {                                                                      \
+        if (!(cond)) {                                                        \
+            ::mcd::set_error(msg);                                            \
+            return MCD_EINVAL;                                                \
+        }                                                                     \
+    } while (0)
+
+#define MCD_LAUNCH_CHECK()                                                    \
+    do {                                                                      \
+        cudaError_t e_ = cudaGetLastError();                                  \
+        if (e_ != cudaSuccess) {                                              \
+            ::mcd::set_error(std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+            return MCD_ECUDA;                                                 \
+        }                                                                     \
+    } while (0)
+
+// Slot s of the compact support: 2D s = (di+1) + 3 (dj+1); 3D adds 9 (dl+1).
+// Kind codes written per DP.
+enum : int8_t { KIND_VOID = 0, KIND_INNER = 1, KIND_DIRICHLET = 2, KIND_NEUMANN = 3 };
+
+// Geometry passed by value to kernels.
+struct Geo {
+    int dim;
+    int n[3];
+    int per[3];
+    double l0;
+    double org[3];
+    double len[3];   // n[d] * l0 (periodic shift)
+    int64_t N;
+};
+
+inline Geo make_geo(const mcd_mesh &m) {
+    Geo g;
+    g.dim = m.dim;
+    g.N = 1;
+    for (int d = 0; d < 3; ++d) {
+        g.n[d] = (d < m.dim) ? m.n[d] : 1;
+        g.per[d] = (d < m.dim) ? (m.periodic[d] ? 1 : 0) : 0;
+        g.org[d] = (d < m.dim) ? m.origin[d] : 0.0;
+        g.len[d] = g.n[d] * m.l0;
+        g.N *= g.n[d];
+    }
+    g.l0 = m.l0;
+    return g;
+}
+
+// Neighbour of cell coordinate c along one axis with offset o: returns the
+// wrapped / validated coordinate and the position shift a periodic wrap
+// implies (x_j + shift is the minimum image seen from the centre cell).
+__device__ __forceinline__ int nb_coord(int c, int o, int n, int per, double len,
+                                        double &shift, bool &valid) {
+    int v = c + o;
+    shift = 0.0;
+    if (v < 0) {
+        if (per) { v += n; shift = -len; } else { valid = false; v = c; }
+    } else if (v >= n) {
+        if (per) { v -= n; shift = len; } else { valid = false; v = c; }
+    }
+    return v;
+}
+
+// Solver workspace attached to a stencil handle (allocated on first solve).
+struct Workspace;
+
+}  // namespace mcd
+
+struct mcd_stencils {
+    mcd_mesh mesh;
+    mcd_mls_params prm;
+    mcd::Geo geo;
+    int S;               // 9 or 27
+    int nb;              // 5 or 9 derivative components
+    int has_neumann;     // any bc_kind entry is Neumann
+    double *row64;       // [S][N]
+    float *row32;        // [S][N] (MIXED)
+    double *ql64;        // [S][N] (has_neumann)
+    double *d64;         // [nb][S][N] (want_derivs)
+    double *qd64;        // [nb][S][N] (want_derivs && has_neumann)
+    double *rscale;      // [N]
+    int8_t *kind;        // [N]
+    unsigned long long *bad_dp;  // device: smallest failing DP, ~0ull if none
+    mcd::Workspace *ws;
+};

@@ -1,0 +1,608 @@
+// MLS stencil weights and the pressure-Poisson rows (arXiv 2404.17542,
+// Sec. 3.2, Eqs. (12)-(17); Sec. 3.3, Eq. (21), (23)).
+//
+// One thread per DP.  Pass 1 gathers the DP's 3x3 (3x3x3) cells, forms the
+// moment matrix M = sum w p p^T (+ Neumann terms w p^N p^N^T) and the vector
+// sum w p, and factors M by Cholesky in registers.  Pass 2 revisits the
+// neighbours and writes, slot by slot, z = M^{-1} (w p) -- the weight that
+// neighbour carries in every derivative -- into slot-major SoA arrays, so a
+// warp's stores for one slot are contiguous.  The centre weight is
+// -M^{-1} sum_j w_j p_j, known before pass 2, which lets Neumann rows be
+// scaled (row equilibration) without buffering the row.
+//
+// FP64 throughout: the FP64 rows are the matrix the refinement residual is
+// judged on; the FP32 copy used by the inner Krylov solve is their rounding.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace mcd {
+
+template <int DIM> struct Basis;
+
+template <> struct Basis<2> {
+    static constexpr int NB = 5;
+    static constexpr int S = 9;
+    // p(X) = (X, Y, X^2/2, XY, Y^2/2)  (Eq. (13))
+    __device__ static void value(const double *X, double *p) {
+        p[0] = X[0]; p[1] = X[1];
+        p[2] = 0.5 * X[0] * X[0]; p[3] = X[0] * X[1]; p[4] = 0.5 * X[1] * X[1];
+    }
+    // p^N = n . grad_X p(X)  (Neumann term of Eq. (15))
+    __device__ static void normal(const double *X, const double *n, double *p) {
+        p[0] = n[0]; p[1] = n[1];
+        p[2] = n[0] * X[0]; p[3] = n[0] * X[1] + n[1] * X[0]; p[4] = n[1] * X[1];
+    }
+    __device__ static int order(int c) { return c < 2 ? 1 : 2; }
+    __device__ static bool is_lap(int c) { return c == 2 || c == 4; }
+};
+
+template <> struct Basis<3> {
+    static constexpr int NB = 9;
+    static constexpr int S = 27;
+    // (X, Y, Z, X^2/2, Y^2/2, Z^2/2, XY, YZ, XZ)
+    __device__ static void value(const double *X, double *p) {
+        p[0] = X[0]; p[1] = X[1]; p[2] = X[2];
+        p[3] = 0.5 * X[0] * X[0]; p[4] = 0.5 * X[1] * X[1]; p[5] = 0.5 * X[2] * X[2];
+        p[6] = X[0] * X[1]; p[7] = X[1] * X[2]; p[8] = X[0] * X[2];
+    }
+    __device__ static void normal(const double *X, const double *n, double *p) {
+        p[0] = n[0]; p[1] = n[1]; p[2] = n[2];
+        p[3] = n[0] * X[0]; p[4] = n[1] * X[1]; p[5] = n[2] * X[2];
+        p[6] = n[0] * X[1] + n[1] * X[0];
+        p[7] = n[1] * X[2] + n[2] * X[1];
+        p[8] = n[0] * X[2] + n[2] * X[0];
+    }
+    __device__ static int order(int c) { return c < 3 ? 1 : 2; }
+    __device__ static bool is_lap(int c) { return c >= 3 && c <= 5; }
+};
+
+struct BuildArgs {
+    Geo g;
+    const double *pos;
+    const int8_t *mask;
+    const double *normal;
+    uint8_t bc[128];
+    int weight_kind;
+    double r_e, r_s;
+    double *row64;
+    float *row32;
+    double *ql64;
+    double *d64;
+    double *qd64;
+    double *rscale;
+    int8_t *kind;
+    unsigned long long *bad;
+};
+
+__device__ __forceinline__ double mls_weight(double r, int kind, double r_e) {
+    if (kind == MCD_W_COS2) {
+        if (r > r_e) return 0.0;
+        double c = cos(M_PI * r / (2.0 * r_e));
+        return c * c;
+    }
+    double q = r / r_e;
+    return exp(-q * q);
+}
+
+// Packed lower-triangular index of (a, b), a >= b.
+__device__ __forceinline__ int tri(int a, int b) { return a * (a + 1) / 2 + b; }
+
+// In-place Cholesky of the packed matrix (first nf rows); false if a pivot is
+// not positive (the matrix is not positive definite) or not finite.
+template <int NB>
+__device__ bool cholesky(double *L, int nf) {
+    for (int j = 0; j < NB; ++j) {
+        if (j >= nf) break;
+        double d = L[tri(j, j)];
+        for (int k = 0; k < j; ++k) d -= L[tri(j, k)] * L[tri(j, k)];
+        if (!(d > 0.0) || !isfinite(d)) return false;
+        d = sqrt(d);
+        L[tri(j, j)] = d;
+        double inv = 1.0 / d;
+        for (int i = j + 1; i < NB; ++i) {
+            if (i >= nf) break;
+            double v = L[tri(i, j)];
+            for (int k = 0; k < j; ++k) v -= L[tri(i, k)] * L[tri(j, k)];
+            L[tri(i, j)] = v * inv;
+        }
+    }
+    return true;
+}
+
+// Solve (L L^T) z = b in place (first nf entries).
+template <int NB>
+__device__ void chol_solve(const double *L, int nf, double *z) {
+    for (int i = 0; i < NB; ++i) {
+        if (i >= nf) break;
+        double v = z[i];
+        for (int k = 0; k < i; ++k) v -= L[tri(i, k)] * z[k];
+        z[i] = v / L[tri(i, i)];
+    }
+    for (int i = NB - 1; i >= 0; --i) {
+        if (i >= nf) continue;
+        double v = z[i];
+        for (int k = i + 1; k < NB; ++k) {
+            if (k >= nf) break;
+            v -= L[tri(k, i)] * z[k];
+        }
+        z[i] = v / L[tri(i, i)];
+    }
+}
+
+template <int DIM>
+struct Nbr {
+    int64_t j;
+    bool valid;
+    double shift[DIM];
+};
+
+template <int DIM>
+__device__ __forceinline__ void decode(const Geo &g, int64_t k, int *c) {
+    c[0] = (int)(k % g.n[0]);
+    int64_t rest = k / g.n[0];
+    if (DIM == 2) {
+        c[1] = (int)rest;
+    } else {
+        c[1] = (int)(rest % g.n[1]);
+        c[2] = (int)(rest / g.n[1]);
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ Nbr<DIM> neighbour(const Geo &g, const int *c, int s) {
+    Nbr<DIM> r;
+    r.valid = true;
+    int o[3] = {s % 3 - 1, (s / 3) % 3 - 1, s / 9 - 1};
+    int v[3];
+    for (int d = 0; d < DIM; ++d) {
+        double sh;
+        v[d] = nb_coord(c[d], o[d], g.n[d], g.per[d], g.len[d], sh, r.valid);
+        r.shift[d] = sh;
+    }
+    r.j = (DIM == 2) ? (int64_t)v[0] + (int64_t)g.n[0] * v[1]
+                     : (int64_t)v[0] + (int64_t)g.n[0] * ((int64_t)v[1] + (int64_t)g.n[1] * v[2]);
+    return r;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
+    using B = Basis<DIM>;
+    constexpr int NB = B::NB;
+    constexpr int S = B::S;
+    constexpr int C = S / 2;
+    const int64_t N = a.g.N;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+
+    const int8_t mk = a.mask[k];
+    int8_t kind;
+    if (mk == 0) kind = KIND_VOID;
+    else if (mk < 0) kind = KIND_INNER;
+    else kind = (a.bc[(uint8_t)mk] == MCD_BC_NEUMANN) ? KIND_NEUMANN : KIND_DIRICHLET;
+
+    auto write_identity = [&]() {
+        for (int s = 0; s < S; ++s) {
+            double v = (s == C) ? 1.0 : 0.0;
+            a.row64[(int64_t)s * N + k] = v;
+            if (a.row32) a.row32[(int64_t)s * N + k] = (float)v;
+            if (a.ql64) a.ql64[(int64_t)s * N + k] = 0.0;
+            if (a.d64)
+                for (int c = 0; c < NB; ++c) a.d64[((int64_t)c * S + s) * N + k] = 0.0;
+            if (a.qd64)
+                for (int c = 0; c < NB; ++c) a.qd64[((int64_t)c * S + s) * N + k] = 0.0;
+        }
+        a.rscale[k] = 1.0;
+    };
+
+    a.kind[k] = kind;
+    if (kind == KIND_VOID || kind == KIND_DIRICHLET) {
+        write_identity();
+        return;
+    }
+
+    int c[3] = {0, 0, 0};
+    decode<DIM>(a.g, k, c);
+    double xi[DIM];
+    for (int d = 0; d < DIM; ++d) xi[d] = a.pos[(int64_t)d * N + k];
+    const double inv_rs = 1.0 / a.r_s;
+    const int nf = (kind == KIND_NEUMANN) ? DIM : NB;
+
+    // ---- pass 1: moment matrix and sum_j w_j p_j over value neighbours ----
+    double L[NB * (NB + 1) / 2];
+    double acc[NB];
+    for (int q = 0; q < NB * (NB + 1) / 2; ++q) L[q] = 0.0;
+    for (int q = 0; q < NB; ++q) acc[q] = 0.0;
+
+    for (int s = 0; s < S; ++s) {
+        if (s == C) continue;
+        Nbr<DIM> nb = neighbour<DIM>(a.g, c, s);
+        if (!nb.valid) continue;
+        const int8_t mj = a.mask[nb.j];
+        if (mj == 0) continue;
+        const bool neu = (kind == KIND_INNER) && mj > 0 && a.bc[(uint8_t)mj] == MCD_BC_NEUMANN;
+        double dx[DIM], X[DIM], r2 = 0.0;
+        for (int d = 0; d < DIM; ++d) {
+            dx[d] = (a.pos[(int64_t)d * N + nb.j] + nb.shift[d]) - xi[d];
+            X[d] = dx[d] * inv_rs;
+            r2 += dx[d] * dx[d];
+        }
+        const double w = mls_weight(sqrt(r2), a.weight_kind, a.r_e);
+        double p[NB];
+        if (neu) {
+            double n[DIM];
+            for (int d = 0; d < DIM; ++d) n[d] = a.normal[(int64_t)d * N + nb.j];
+            B::normal(X, n, p);
+        } else {
+            B::value(X, p);
+            for (int q = 0; q < NB; ++q) acc[q] += w * p[q];
+        }
+        for (int r = 0; r < NB; ++r) {
+            if (r >= nf) break;
+            const double wp = w * p[r];
+            for (int q = 0; q <= r; ++q) L[tri(r, q)] += wp * p[q];
+        }
+    }
+
+    if (!cholesky<NB>(L, nf)) {
+        atomicMin(a.bad, (unsigned long long)k);
+        write_identity();
+        return;
+    }
+
+    // centre: -M^{-1} sum_j w_j p_j (from phi_j - phi_i)
+    double cen[NB];
+    for (int q = 0; q < NB; ++q) cen[q] = (q < nf) ? -acc[q] : 0.0;
+    chol_solve<NB>(L, nf, cen);
+    double scale[NB];
+    for (int q = 0; q < NB; ++q)
+        scale[q] = (B::order(q) == 1) ? inv_rs : inv_rs * inv_rs;
+    for (int q = 0; q < NB; ++q) cen[q] *= scale[q];
+
+    // Neumann DP: row = sigma n . grad, sigma = -1 / (r_s^2 n . grad_centre)
+    double nrm[DIM];
+    double sigma = 1.0;
+    if (kind == KIND_NEUMANN) {
+        double dcen = 0.0;
+        for (int d = 0; d < DIM; ++d) {
+            nrm[d] = a.normal[(int64_t)d * N + k];
+            dcen += nrm[d] * cen[d];
+        }
+        if (!(dcen != 0.0) || !isfinite(dcen)) {
+            atomicMin(a.bad, (unsigned long long)k);
+            write_identity();
+            return;
+        }
+        sigma = -(inv_rs * inv_rs) / dcen;
+    }
+    a.rscale[k] = sigma;
+
+    // ---- pass 2: per-slot weights ----
+    for (int s = 0; s < S; ++s) {
+        double z[NB];
+        double zq[NB];
+        for (int q = 0; q < NB; ++q) { z[q] = 0.0; zq[q] = 0.0; }
+        if (s == C) {
+            for (int q = 0; q < NB; ++q) z[q] = cen[q];
+        } else {
+            Nbr<DIM> nb = neighbour<DIM>(a.g, c, s);
+            int8_t mj = nb.valid ? a.mask[nb.j] : (int8_t)0;
+            if (mj != 0) {
+                const bool neu = (kind == KIND_INNER) && mj > 0 && a.bc[(uint8_t)mj] == MCD_BC_NEUMANN;
+                double dx[DIM], X[DIM], r2 = 0.0;
+                for (int d = 0; d < DIM; ++d) {
+                    dx[d] = (a.pos[(int64_t)d * N + nb.j] + nb.shift[d]) - xi[d];
+                    X[d] = dx[d] * inv_rs;
+                    r2 += dx[d] * dx[d];
+                }
+                const double w = mls_weight(sqrt(r2), a.weight_kind, a.r_e);
+                double p[NB];
+                if (neu) {
+                    double n[DIM];
+                    for (int d = 0; d < DIM; ++d) n[d] = a.normal[(int64_t)d * N + nb.j];
+                    B::normal(X, n, p);
+                    for (int q = 0; q < NB; ++q) zq[q] = (q < nf) ? w * p[q] * a.r_s : 0.0;
+                    chol_solve<NB>(L, nf, zq);
+                    for (int q = 0; q < NB; ++q) zq[q] *= scale[q];
+                } else {
+                    B::value(X, p);
+                    for (int q = 0; q < NB; ++q) z[q] = (q < nf) ? w * p[q] : 0.0;
+                    chol_solve<NB>(L, nf, z);
+                    for (int q = 0; q < NB; ++q) z[q] *= scale[q];
+                }
+            }
+        }
+        double row = 0.0, ql = 0.0;
+        if (kind == KIND_INNER) {
+            for (int q = 0; q < NB; ++q)
+                if (B::is_lap(q)) { row += z[q]; ql += zq[q]; }
+        } else {
+            for (int d = 0; d < DIM; ++d) row += nrm[d] * z[d];
+            row *= sigma;
+        }
+        a.row64[(int64_t)s * N + k] = row;
+        if (a.row32) a.row32[(int64_t)s * N + k] = (float)row;
+        if (a.ql64) a.ql64[(int64_t)s * N + k] = ql;
+        if (a.d64)
+            for (int q = 0; q < NB; ++q) a.d64[((int64_t)q * S + s) * N + k] = z[q];
+        if (a.qd64)
+            for (int q = 0; q < NB; ++q) a.qd64[((int64_t)q * S + s) * N + k] = zq[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// y = A x with the PPE rows: the matrix-free stencil SpMV.
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) spmv_kernel(Geo g, const T *__restrict__ row,
+                                                   const T *__restrict__ x, T *__restrict__ y) {
+    constexpr int S = (DIM == 2) ? 9 : 27;
+    const int64_t N = g.N;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    int c[3] = {0, 0, 0};
+    decode<DIM>(g, k, c);
+    T acc = 0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        Nbr<DIM> nb = neighbour<DIM>(g, c, s);
+        const T w = row[(int64_t)s * N + k];
+        acc += w * x[nb.j];
+    }
+    y[k] = acc;
+}
+
+// b: inner DP f - sum QL * bnd (Neumann neighbours); boundary DP rscale * bnd.
+template <int DIM>
+__global__ void rhs_kernel(Geo g, const int8_t *__restrict__ kind, const double *__restrict__ ql,
+                           const double *__restrict__ rscale, const double *__restrict__ rhs,
+                           const double *__restrict__ bnd, double *__restrict__ b) {
+    constexpr int S = (DIM == 2) ? 9 : 27;
+    const int64_t N = g.N;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int8_t kd = kind[k];
+    double out = 0.0;
+    if (kd == KIND_INNER) {
+        out = rhs[k];
+        if (ql) {
+            int c[3] = {0, 0, 0};
+            decode<DIM>(g, k, c);
+            for (int s = 0; s < S; ++s) {
+                const double q = ql[(int64_t)s * N + k];
+                if (q != 0.0) {
+                    Nbr<DIM> nb = neighbour<DIM>(g, c, s);
+                    out -= q * bnd[nb.j];
+                }
+            }
+        }
+    } else if (kd == KIND_DIRICHLET || kd == KIND_NEUMANN) {
+        out = rscale[k] * bnd[k];
+    }
+    b[k] = out;
+}
+
+template <typename T>
+static cudaError_t dmalloc(T **p, size_t count) {
+    return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+void free_workspace(mcd_stencils *st);
+
+static void free_arrays(mcd_stencils *st) {
+    cudaFree(st->row64);
+    cudaFree(st->row32);
+    cudaFree(st->ql64);
+    cudaFree(st->d64);
+    cudaFree(st->qd64);
+    cudaFree(st->rscale);
+    cudaFree(st->kind);
+    cudaFree(st->bad_dp);
+}
+
+static bool same_layout(const mcd_stencils *st, const mcd_mesh &m, const mcd_mls_params &p) {
+    if (st->mesh.dim != m.dim) return false;
+    for (int d = 0; d < 3; ++d)
+        if (st->mesh.n[d] != m.n[d]) return false;
+    int has_neu = 0;
+    for (int b = 1; b < 128; ++b) has_neu |= (p.bc_kind[b] == MCD_BC_NEUMANN);
+    return st->prm.precision == p.precision && st->prm.want_derivs == p.want_derivs &&
+           st->has_neumann == has_neu;
+}
+
+}  // namespace mcd
+
+using namespace mcd;
+
+static mcd_status validate_mesh(const mcd_mesh *m) {
+    MCD_CHECK_ARG(m != nullptr, "mesh is NULL");
+    MCD_CHECK_ARG(m->dim == 2 || m->dim == 3, "mesh.dim must be 2 or 3");
+    for (int d = 0; d < m->dim; ++d) MCD_CHECK_ARG(m->n[d] >= 3, "mesh.n[d] must be >= 3");
+    if (m->dim == 2) MCD_CHECK_ARG(m->n[2] == 1, "2D mesh needs n[2] = 1");
+    MCD_CHECK_ARG(m->l0 > 0.0, "mesh.l0 must be positive");
+    return MCD_OK;
+}
+
+extern "C" mcd_status mcd_build_stencils(const mcd_mesh *mesh, const double *pos_dev,
+                                         const int8_t *mask_dev, const double *normal_dev,
+                                         const mcd_mls_params *prm, mcd_stencils **st,
+                                         mcd_stream_t stream) {
+    mcd_status v = validate_mesh(mesh);
+    if (v != MCD_OK) return v;
+    MCD_CHECK_ARG(pos_dev && mask_dev && prm && st, "NULL argument");
+    MCD_CHECK_ARG(prm->r_e > 0.0 && prm->r_s > 0.0, "r_e and r_s must be positive");
+    MCD_CHECK_ARG(prm->weight_kind == MCD_W_GAUSS || prm->weight_kind == MCD_W_COS2,
+                  "unknown weight_kind");
+    MCD_CHECK_ARG(prm->precision == MCD_FP64 || prm->precision == MCD_MIXED, "unknown precision");
+    int has_neu = 0;
+    for (int b = 1; b < 128; ++b) has_neu |= (prm->bc_kind[b] == MCD_BC_NEUMANN);
+    MCD_CHECK_ARG(!has_neu || normal_dev, "normals are required when a boundary id is Neumann");
+
+    mcd_stencils *h = *st;
+    if (h && !same_layout(h, *mesh, *prm)) {
+        set_error("existing stencil handle has a different mesh size or options");
+        return MCD_EINVAL;
+    }
+    const Geo g = make_geo(*mesh);
+    const int S = (mesh->dim == 2) ? 9 : 27;
+    const int nb = (mesh->dim == 2) ? 5 : 9;
+    const int64_t N = g.N;
+    if (!h) {
+        h = new mcd_stencils();
+        h->mesh = *mesh;
+        h->prm = *prm;
+        h->geo = g;
+        h->S = S;
+        h->nb = nb;
+        h->has_neumann = has_neu;
+        cudaError_t e = cudaSuccess;
+        auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+        chk(dmalloc(&h->row64, (size_t)S * N));
+        if (prm->precision == MCD_MIXED) chk(dmalloc(&h->row32, (size_t)S * N));
+        if (has_neu) chk(dmalloc(&h->ql64, (size_t)S * N));
+        if (prm->want_derivs) {
+            chk(dmalloc(&h->d64, (size_t)nb * S * N));
+            if (has_neu) chk(dmalloc(&h->qd64, (size_t)nb * S * N));
+        }
+        chk(dmalloc(&h->rscale, (size_t)N));
+        chk(dmalloc(&h->kind, (size_t)N));
+        chk(dmalloc(&h->bad_dp, 1));
+        if (e != cudaSuccess) {
+            free_arrays(h);
+            delete h;
+            set_error(std::string("stencil allocation: ") + cudaGetErrorString(e));
+            return MCD_ENOMEM;
+        }
+        *st = h;
+    }
+    h->mesh = *mesh;
+    h->geo = g;
+    h->prm = *prm;
+    h->has_neumann = has_neu;
+
+    MCD_CUDA_TRY(cudaMemsetAsync(h->bad_dp, 0xff, sizeof(unsigned long long), stream));
+    BuildArgs a;
+    a.g = g;
+    a.pos = pos_dev;
+    a.mask = mask_dev;
+    a.normal = normal_dev;
+    for (int b = 0; b < 128; ++b) a.bc[b] = prm->bc_kind[b];
+    a.weight_kind = prm->weight_kind;
+    a.r_e = prm->r_e;
+    a.r_s = prm->r_s;
+    a.row64 = h->row64;
+    a.row32 = h->row32;
+    a.ql64 = h->ql64;
+    a.d64 = h->d64;
+    a.qd64 = h->qd64;
+    a.rscale = h->rscale;
+    a.kind = h->kind;
+    a.bad = h->bad_dp;
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((N + threads - 1) / threads);
+    if (mesh->dim == 2)
+        build_kernel<2><<<blocks, threads, 0, stream>>>(a);
+    else
+        build_kernel<3><<<blocks, threads, 0, stream>>>(a);
+    MCD_LAUNCH_CHECK();
+    return MCD_OK;
+}
+
+extern "C" mcd_status mcd_stencils_check(const mcd_stencils *st, int64_t *first_bad_dp,
+                                         mcd_stream_t stream) {
+    MCD_CHECK_ARG(st, "NULL handle");
+    unsigned long long bad = 0;
+    MCD_CUDA_TRY(cudaMemcpyAsync(&bad, st->bad_dp, sizeof(bad), cudaMemcpyDeviceToHost, stream));
+    MCD_CUDA_TRY(cudaStreamSynchronize(stream));
+    const bool fail = bad != ~0ull;
+    if (first_bad_dp) *first_bad_dp = fail ? (int64_t)bad : -1;
+    if (fail) {
+        set_error("singular MLS moment matrix at DP " + std::to_string(bad));
+        return MCD_ESINGULAR;
+    }
+    return MCD_OK;
+}
+
+extern "C" void mcd_stencils_destroy(mcd_stencils *st) {
+    if (!st) return;
+    free_workspace(st);
+    free_arrays(st);
+    delete st;
+}
+
+extern "C" mcd_status mcd_stencils_array(const mcd_stencils *st, int which,
+                                         const void **dev_ptr, int64_t *count) {
+    MCD_CHECK_ARG(st && dev_ptr, "NULL argument");
+    const int64_t N = st->geo.N;
+    const void *p = nullptr;
+    int64_t n = 0;
+    switch (which) {
+        case MCD_ARR_ROW64: p = st->row64; n = (int64_t)st->S * N; break;
+        case MCD_ARR_ROW32: p = st->row32; n = st->row32 ? (int64_t)st->S * N : 0; break;
+        case MCD_ARR_QL64: p = st->ql64; n = st->ql64 ? (int64_t)st->S * N : 0; break;
+        case MCD_ARR_D64: p = st->d64; n = st->d64 ? (int64_t)st->nb * st->S * N : 0; break;
+        case MCD_ARR_QD64: p = st->qd64; n = st->qd64 ? (int64_t)st->nb * st->S * N : 0; break;
+        case MCD_ARR_RSCALE: p = st->rscale; n = N; break;
+        case MCD_ARR_KIND: p = st->kind; n = N; break;
+        default: set_error("unknown array id"); return MCD_EINVAL;
+    }
+    *dev_ptr = p;
+    if (count) *count = n;
+    return MCD_OK;
+}
+
+extern "C" mcd_status mcd_stencils_copy(const mcd_stencils *st, int which, void *dst_dev,
+                                        mcd_stream_t stream) {
+    MCD_CHECK_ARG(dst_dev, "NULL destination");
+    const void *src = nullptr;
+    int64_t count = 0;
+    mcd_status s = mcd_stencils_array(st, which, &src, &count);
+    if (s != MCD_OK) return s;
+    MCD_CHECK_ARG(src && count > 0, "array not kept by this handle");
+    size_t elem = 8;
+    if (which == MCD_ARR_ROW32) elem = 4;
+    if (which == MCD_ARR_KIND) elem = 1;
+    MCD_CUDA_TRY(cudaMemcpyAsync(dst_dev, src, (size_t)count * elem, cudaMemcpyDeviceToDevice, stream));
+    return MCD_OK;
+}
+
+extern "C" mcd_status mcd_apply_laplacian(const mcd_stencils *st, const void *x_dev,
+                                          void *y_dev, int dtype, mcd_stream_t stream) {
+    MCD_CHECK_ARG(st && x_dev && y_dev, "NULL argument");
+    MCD_CHECK_ARG(x_dev != y_dev, "x and y must not alias");
+    const int64_t N = st->geo.N;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((N + threads - 1) / threads);
+    if (dtype == MCD_DT_F64) {
+        if (st->mesh.dim == 2)
+            spmv_kernel<double, 2><<<blocks, threads, 0, stream>>>(st->geo, st->row64, (const double *)x_dev, (double *)y_dev);
+        else
+            spmv_kernel<double, 3><<<blocks, threads, 0, stream>>>(st->geo, st->row64, (const double *)x_dev, (double *)y_dev);
+    } else if (dtype == MCD_DT_F32) {
+        MCD_CHECK_ARG(st->row32, "FP32 rows need an MCD_MIXED stencil handle");
+        if (st->mesh.dim == 2)
+            spmv_kernel<float, 2><<<blocks, threads, 0, stream>>>(st->geo, st->row32, (const float *)x_dev, (float *)y_dev);
+        else
+            spmv_kernel<float, 3><<<blocks, threads, 0, stream>>>(st->geo, st->row32, (const float *)x_dev, (float *)y_dev);
+    } else {
+        set_error("unknown dtype");
+        return MCD_EINVAL;
+    }
+    MCD_LAUNCH_CHECK();
+    return MCD_OK;
+}
+
+extern "C" mcd_status mcd_assemble_rhs(const mcd_stencils *st, const double *rhs_dev,
+                                       const double *bnd_dev, double *b_dev, mcd_stream_t stream) {
+    MCD_CHECK_ARG(st && rhs_dev && bnd_dev && b_dev, "NULL argument");
+    const int64_t N = st->geo.N;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((N + threads - 1) / threads);
+    const double *ql = st->has_neumann ? st->ql64 : nullptr;
+    if (st->mesh.dim == 2)
+        rhs_kernel<2><<<blocks, threads, 0, stream>>>(st->geo, st->kind, ql, st->rscale, rhs_dev, bnd_dev, b_dev);
+    else
+        rhs_kernel<3><<<blocks, threads, 0, stream>>>(st->geo, st->kind, ql, st->rscale, rhs_dev, bnd_dev, b_dev);
+    MCD_LAUNCH_CHECK();
+    return MCD_OK;
+}

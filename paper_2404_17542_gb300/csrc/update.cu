@@ -1,0 +1,222 @@
+// Moving-boundary DP update (arXiv 2404.17542, Sec. 2.2-2.4, Sec. 4.7).
+//
+// remask_kernel  one thread per cell: role reassignment inside the band from
+//                the count of cell vertices with SDF >= 0 (Eq. (1)).  The
+//                vertex test and the band test use explicitly rounded FP64
+//                operations (__dmul_rn / __dadd_rn / __dsqrt_rn), so no
+//                multiply-add is fused and the decision is bit-identical to
+//                a plain IEEE evaluation of the same expression.
+// relax_kernel   one thread per cell: one Jacobi sweep of spring relaxation
+//                (Eqs. (5)-(8)), relocation onto the body (Eq. (9)),
+//                optional boundary-fitted inner move (Eqs. (45)-(46)) and the
+//                clamp into the cell; positions ping-pong between two buffers.
+#include <math.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace mcd {
+
+struct Circle {
+    int id;
+    double cx, cy, R;
+};
+
+__device__ __forceinline__ bool vertex_fluid(double ox, double oy, double l0, int i, int j, const Circle &b) {
+    const double vx = __dadd_rn(ox, __dmul_rn((double)i, l0));
+    const double vy = __dadd_rn(oy, __dmul_rn((double)j, l0));
+    const double dx = __dsub_rn(vx, b.cx);
+    const double dy = __dsub_rn(vy, b.cy);
+    const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    return d2 >= __dmul_rn(b.R, b.R);
+}
+
+__device__ __forceinline__ bool cell_in_band(double ox, double oy, double l0, int i, int j,
+                                             const Circle &b, double band) {
+    if (band <= 0.0) return true;
+    const double cx = __dadd_rn(ox, __dmul_rn((double)i + 0.5, l0));
+    const double cy = __dadd_rn(oy, __dmul_rn((double)j + 0.5, l0));
+    const double dx = __dsub_rn(cx, b.cx);
+    const double dy = __dsub_rn(cy, b.cy);
+    const double psi = __dsub_rn(__dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy))), b.R);
+    return fabs(psi) < band;
+}
+
+__global__ void remask_kernel(Geo g, Circle body, double band, double *__restrict__ pos,
+                              int8_t *__restrict__ mask, int8_t *__restrict__ mask_prev) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.N) return;
+    const int nx = g.n[0], ny = g.n[1];
+    const int i = (int)(k % nx), j = (int)(k / nx);
+    const int8_t old = mask[k];
+    mask_prev[k] = old;
+    if (i == 0 || j == 0 || i == nx - 1 || j == ny - 1) return;   // wall cell
+    if (!cell_in_band(g.org[0], g.org[1], g.l0, i, j, body, band)) return;
+    const int cnt = (int)vertex_fluid(g.org[0], g.org[1], g.l0, i, j, body) +
+                    (int)vertex_fluid(g.org[0], g.org[1], g.l0, i + 1, j, body) +
+                    (int)vertex_fluid(g.org[0], g.org[1], g.l0, i, j + 1, body) +
+                    (int)vertex_fluid(g.org[0], g.org[1], g.l0, i + 1, j + 1, body);
+    const int8_t nm = (cnt <= 1) ? (int8_t)0 : (cnt <= 3 ? (int8_t)body.id : (int8_t)-1);
+    mask[k] = nm;
+    if (nm == 0 && old != 0) {
+        pos[k] = g.org[0] + ((double)i + 0.5) * g.l0;
+        pos[g.N + k] = g.org[1] + ((double)j + 0.5) * g.l0;
+    }
+}
+
+__global__ void relax_kernel(Geo g, Circle body, double band, double kappa, double alpha,
+                             const int8_t *__restrict__ mask, const double *__restrict__ pin,
+                             double *__restrict__ pout) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t N = g.N;
+    if (k >= N) return;
+    const int nx = g.n[0], ny = g.n[1];
+    const int i = (int)(k % nx), j = (int)(k / nx);
+    const double xi = pin[k], yi = pin[N + k];
+    const int8_t mk = mask[k];
+    const bool movable = !(i == 0 || j == 0 || i == nx - 1 || j == ny - 1) && mk != 0 &&
+                         cell_in_band(g.org[0], g.org[1], g.l0, i, j, body, band);
+    if (!movable) {
+        pout[k] = xi;
+        pout[N + k] = yi;
+        return;
+    }
+    const double l0 = g.l0;
+    const double sq2l0 = sqrt(2.0) * l0;
+    double fx = 0.0, fy = 0.0;
+    for (int dj = -1; dj <= 1; ++dj) {
+        for (int di = -1; di <= 1; ++di) {
+            if (di == 0 && dj == 0) continue;
+            const int ii = i + di, jj = j + dj;
+            if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) continue;
+            const int64_t kk = (int64_t)ii + (int64_t)nx * jj;
+            if (mask[kk] == 0) continue;
+            const double ex = pin[kk] - xi, ey = pin[N + kk] - yi;      // x_ij = x_j - x_i
+            const double r = sqrt(ex * ex + ey * ey);
+            if (r == 0.0) continue;
+            const double lspg = (di != 0 && dj != 0) ? sq2l0 : l0;       // Eq. (7)
+            const double G = 1.0 - r / lspg;                            // Eq. (6)
+            fx += G * (ex / r);                                         // Eq. (5)
+            fy += G * (ey / r);
+        }
+    }
+    double sx = xi - kappa * l0 * fx;                                   // Eq. (8)
+    double sy = yi - kappa * l0 * fy;
+    const double dxc = sx - body.cx, dyc = sy - body.cy;
+    const double dist = sqrt(dxc * dxc + dyc * dyc);
+    if (dist > 0.0) {
+        const double psi = dist - body.R;
+        const double hx = -dxc / dist, hy = -dyc / dist;                // -grad psi / |grad psi|
+        if (mk == body.id) {
+            sx += psi * hx;                                             // Eq. (9)
+            sy += psi * hy;
+        } else if (mk == -1 && alpha > 0.0) {
+            const double re = 5.0 * l0;
+            if (psi < re) {
+                const double beta = 0.5 * alpha * (1.0 + cos(M_PI * psi / re));   // Eq. (46)
+                sx += beta * psi * hx;                                  // Eq. (45)
+                sy += beta * psi * hy;
+            }
+        }
+    }
+    const double lox = g.org[0] + i * l0, loy = g.org[1] + j * l0;
+    const double hix = g.org[0] + (i + 1) * l0, hiy = g.org[1] + (j + 1) * l0;
+    pout[k] = fmin(fmax(sx, lox), hix);
+    pout[N + k] = fmin(fmax(sy, loy), hiy);
+}
+
+__global__ void normals_kernel(Geo g, Circle body, const double *__restrict__ pos,
+                               const int8_t *__restrict__ mask, double *__restrict__ nrm) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t N = g.N;
+    if (k >= N) return;
+    double nx = 0.0, ny = 0.0;
+    if (mask[k] == body.id) {
+        const double dx = pos[k] - body.cx, dy = pos[N + k] - body.cy;
+        const double d = sqrt(dx * dx + dy * dy);
+        if (d > 0.0) { nx = dx / d; ny = dy / d; }
+    }
+    nrm[k] = nx;
+    nrm[N + k] = ny;
+}
+
+// Position scratch for the Jacobi ping-pong, grown on demand and kept for
+// the life of the process (one per device ordinal).
+struct Scratch {
+    double *buf = nullptr;
+    size_t cap = 0;
+};
+static std::mutex g_scratch_mu;
+static Scratch g_scratch[64];
+
+static double *scratch_positions(size_t count) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    Scratch &s = g_scratch[dev];
+    if (s.cap < count) {
+        cudaFree(s.buf);
+        s.buf = nullptr;
+        s.cap = 0;
+        if (cudaMalloc(&s.buf, count * sizeof(double)) != cudaSuccess) return nullptr;
+        s.cap = count;
+    }
+    return s.buf;
+}
+
+}  // namespace mcd
+
+using namespace mcd;
+
+extern "C" mcd_status mcd_update_dps(const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
+                                     double *pos_dev, int8_t *mask_dev, int8_t *mask_prev_dev,
+                                     double kappa, int n_relax, double band, double alpha,
+                                     mcd_stream_t stream) {
+    MCD_CHECK_ARG(mesh && bodies && pos_dev && mask_dev && mask_prev_dev, "NULL argument");
+    if (mesh->dim != 2 || nbodies != 1) {
+        set_error("mcd_update_dps: 2D with one body only");
+        return MCD_ENOTSUP;
+    }
+    MCD_CHECK_ARG(mesh->n[0] >= 3 && mesh->n[1] >= 3 && mesh->l0 > 0.0, "bad mesh");
+    MCD_CHECK_ARG(bodies[0].id >= 2 && bodies[0].id <= 127, "body id must be in 2..127");
+    MCD_CHECK_ARG(bodies[0].radius > 0.0, "body radius must be positive");
+    MCD_CHECK_ARG(n_relax >= 0 && kappa >= 0.0, "bad relaxation parameters");
+    const Geo g = make_geo(*mesh);
+    Circle c{bodies[0].id, bodies[0].c[0], bodies[0].c[1], bodies[0].radius};
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((g.N + threads - 1) / threads);
+    remask_kernel<<<blocks, threads, 0, stream>>>(g, c, band, pos_dev, mask_dev, mask_prev_dev);
+    MCD_LAUNCH_CHECK();
+    if (n_relax == 0) return MCD_OK;
+    double *tmp = scratch_positions(2 * (size_t)g.N);
+    if (!tmp) {
+        set_error("mcd_update_dps: scratch allocation failed");
+        return MCD_ENOMEM;
+    }
+    double *a = pos_dev, *b = tmp;
+    for (int it = 0; it < n_relax; ++it) {
+        relax_kernel<<<blocks, threads, 0, stream>>>(g, c, band, kappa, alpha, mask_dev, a, b);
+        double *t = a; a = b; b = t;
+    }
+    MCD_LAUNCH_CHECK();
+    if (a != pos_dev)
+        MCD_CUDA_TRY(cudaMemcpyAsync(pos_dev, a, 2 * (size_t)g.N * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, stream));
+    return MCD_OK;
+}
+
+extern "C" mcd_status mcd_body_normals(const mcd_mesh *mesh, const mcd_body *body, const double *pos_dev,
+                                       const int8_t *mask_dev, double *normal_dev, mcd_stream_t stream) {
+    MCD_CHECK_ARG(mesh && body && pos_dev && mask_dev && normal_dev, "NULL argument");
+    if (mesh->dim != 2) {
+        set_error("mcd_body_normals: 2D only");
+        return MCD_ENOTSUP;
+    }
+    const Geo g = make_geo(*mesh);
+    Circle c{body->id, body->c[0], body->c[1], body->radius};
+    const unsigned blocks = (unsigned)((g.N + 255) / 256);
+    normals_kernel<<<blocks, 256, 0, stream>>>(g, c, pos_dev, mask_dev, normal_dev);
+    MCD_LAUNCH_CHECK();
+    return MCD_OK;
+}

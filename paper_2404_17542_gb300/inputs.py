@@ -113,13 +113,16 @@ def snap_wall_dps(mesh: Mesh, pos: np.ndarray) -> np.ndarray:
 
 def jittered_box(n: int, dim: int, seed: int, jitter: float = 0.25,
                  periodic: bool = False, length: float = 1.0) -> Problem:
-    """Unit box, one DP per cell at the centroid + U[-jitter*l0, jitter*l0]^dim.
+    """Box of side `length` along x, one DP per cell at the centroid +
+    U[-jitter*l0, jitter*l0]^dim.  `n` is the cell count per axis (an int, or
+    a tuple for a non-cubic box with the same l0).
 
     Non-periodic boxes get Dirichlet wall DPs (id 1) snapped onto the walls.
     """
-    l0 = length / n
+    ns = tuple(n) if isinstance(n, (tuple, list)) else tuple([n] * dim)
+    l0 = length / ns[0]
     per = (1, 1, 1) if periodic else (0, 0, 0)
-    mesh = Mesh(dim=dim, n=tuple([n] * dim + [1] * (3 - dim)), l0=l0,
+    mesh = Mesh(dim=dim, n=tuple(list(ns) + [1] * (3 - dim)), l0=l0,
                 origin=(0.0, 0.0, 0.0), periodic=per)
     rng = np.random.default_rng(seed)
     pos = mesh.centroids() + rng.uniform(-jitter * l0, jitter * l0,

@@ -1,0 +1,258 @@
+"""Thin ctypes binding of libmcd (include/mcd.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library.  torch supplies device memory and the current stream.  If the
+library is missing or no GPU is present the calls raise; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmcd.so")
+
+# status codes
+OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, ENOCONV, EBREAKDOWN, ENONFINITE, ETIMEOUT, ENOTSUP = range(10)
+STATUS_NAMES = {0: "MCD_OK", 1: "MCD_EINVAL", 2: "MCD_ENOMEM", 3: "MCD_ECUDA", 4: "MCD_ESINGULAR",
+                5: "MCD_ENOCONV", 6: "MCD_EBREAKDOWN", 7: "MCD_ENONFINITE", 8: "MCD_ETIMEOUT",
+                9: "MCD_ENOTSUP"}
+FP64, MIXED = 0, 1
+DT_F64, DT_F32 = 0, 1
+W_GAUSS, W_COS2 = 0, 1
+ARR_ROW64, ARR_ROW32, ARR_QL64, ARR_D64, ARR_QD64, ARR_RSCALE, ARR_KIND = range(7)
+
+
+class McdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class c_mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("l0", C.c_double),
+                ("origin", C.c_double * 3), ("periodic", C.c_int * 3)]
+
+
+class c_mls_params(C.Structure):
+    _fields_ = [("weight_kind", C.c_int), ("r_e", C.c_double), ("r_s", C.c_double),
+                ("precision", C.c_int), ("want_derivs", C.c_int), ("bc_kind", C.c_uint8 * 128)]
+
+
+class c_solve_params(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("mode", C.c_int),
+                ("inner_tol", C.c_double), ("max_refine", C.c_int), ("net", C.c_void_p),
+                ("check_every", C.c_int)]
+
+
+class c_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("restarts", C.c_int),
+                ("rel_res", C.c_double), ("b_norm", C.c_double)]
+
+
+class c_body(C.Structure):
+    _fields_ = [("id", C.c_int), ("c", C.c_double * 3), ("radius", C.c_double)]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "mcd_build_stencils": (C.c_int, [C.POINTER(c_mesh), C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.POINTER(c_mls_params), C.POINTER(C.c_void_p), C.c_void_p]),
+    "mcd_stencils_check": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
+    "mcd_stencils_destroy": (None, [C.c_void_p]),
+    "mcd_stencils_array": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]),
+    "mcd_stencils_copy": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "mcd_apply_laplacian": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "mcd_assemble_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mcd_solve_pressure": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.POINTER(c_solve_params), C.POINTER(c_solve_info), C.c_void_p]),
+    "mcd_update_dps": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_int, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_double, C.c_int, C.c_double, C.c_double, C.c_void_p]),
+    "mcd_body_normals": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p]),
+    "mcd_last_error": (C.c_char_p, []),
+    "mcd_version": (C.c_char_p, []),
+}
+
+
+def exported_symbols():
+    """Names the binding expects the library to export."""
+    return sorted(_SIGS)
+
+
+def lib():
+    """Load libmcd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2404_17542_gb300.build` (there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != OK:
+        raise McdError(status, lib().mcd_last_error().decode())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor, dtype=None, numel=None):
+    if not t.is_cuda:
+        raise ValueError("tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+def make_mesh(mesh) -> c_mesh:
+    """c_mesh from any object with dim, n, l0, origin, periodic."""
+    m = c_mesh()
+    m.dim = int(mesh.dim)
+    for d in range(3):
+        m.n[d] = int(mesh.n[d]) if d < len(mesh.n) else 1
+        m.origin[d] = float(mesh.origin[d]) if d < len(mesh.origin) else 0.0
+        m.periodic[d] = int(mesh.periodic[d]) if d < len(mesh.periodic) else 0
+    m.l0 = float(mesh.l0)
+    return m
+
+
+class Stencils:
+    """Owner of an mcd_stencils handle (MLS weights + PPE rows)."""
+
+    def __init__(self, mesh, pos, mask, normal=None, bc_kind=None, weight_kind=W_GAUSS,
+                 r_e=None, r_s=None, precision=MIXED, want_derivs=False):
+        self.mesh = mesh
+        self.cmesh = make_mesh(mesh)
+        self.N = int(np.prod([mesh.n[d] for d in range(mesh.dim)]))
+        self.dim = mesh.dim
+        self.S = 3 ** mesh.dim
+        self.nb = 5 if mesh.dim == 2 else 9
+        p = c_mls_params()
+        p.weight_kind = int(weight_kind)
+        p.r_e = float(mesh.l0 if r_e is None else r_e)
+        p.r_s = float(mesh.l0 if r_s is None else r_s)
+        p.precision = int(precision)
+        p.want_derivs = int(bool(want_derivs))
+        bc = np.zeros(128, dtype=np.uint8) if bc_kind is None else np.asarray(bc_kind, dtype=np.uint8)
+        for i in range(128):
+            p.bc_kind[i] = int(bc[i])
+        self.prm = p
+        self.handle = C.c_void_p(None)
+        self.rebuild(pos, mask, normal)
+
+    def rebuild(self, pos, mask, normal=None):
+        npos = _ptr(pos, torch.float64, self.dim * self.N)
+        nmask = _ptr(mask, torch.int8, self.N)
+        nn = _ptr(normal, torch.float64, self.dim * self.N) if normal is not None else C.c_void_p(None)
+        _check(lib().mcd_build_stencils(C.byref(self.cmesh), npos, nmask, nn, C.byref(self.prm),
+                                        C.byref(self.handle), _stream()))
+
+    def check(self):
+        bad = C.c_int64(-1)
+        st = lib().mcd_stencils_check(self.handle, C.byref(bad), _stream())
+        return st, bad.value
+
+    def array(self, which):
+        """Copy of a device array of the handle as a torch tensor."""
+        ptr = C.c_void_p()
+        cnt = C.c_int64()
+        _check(lib().mcd_stencils_array(self.handle, which, C.byref(ptr), C.byref(cnt)))
+        if cnt.value == 0:
+            return None
+        dt = {ARR_ROW32: torch.float32, ARR_KIND: torch.int8}.get(which, torch.float64)
+        out = torch.empty(cnt.value, dtype=dt, device="cuda")
+        _check(lib().mcd_stencils_copy(self.handle, which, _ptr(out), _stream()))
+        return out
+
+    def apply(self, x: torch.Tensor, out: torch.Tensor | None = None):
+        dt = DT_F64 if x.dtype == torch.float64 else DT_F32
+        y = torch.empty_like(x) if out is None else out
+        _check(lib().mcd_apply_laplacian(self.handle, _ptr(x, numel=self.N), _ptr(y, x.dtype, self.N),
+                                         dt, _stream()))
+        return y
+
+    def assemble_rhs(self, rhs: torch.Tensor, bnd: torch.Tensor, out=None):
+        b = torch.empty(self.N, dtype=torch.float64, device=rhs.device) if out is None else out
+        _check(lib().mcd_assemble_rhs(self.handle, _ptr(rhs, torch.float64, self.N),
+                                      _ptr(bnd, torch.float64, self.N), _ptr(b, torch.float64, self.N),
+                                      _stream()))
+        return b
+
+    def solve(self, rhs, bnd, p=None, tol=1e-8, mode=MIXED, max_iter=200000, inner_tol=1e-4,
+              max_refine=60, check_every=64, raise_on_error=True):
+        """Solve the PPE; returns (p, info dict).  p is updated in place if given."""
+        if p is None:
+            p = torch.zeros(self.N, dtype=torch.float64, device=rhs.device)
+        sp = c_solve_params(tol=tol, max_iter=max_iter, mode=mode, inner_tol=inner_tol,
+                            max_refine=max_refine, net=None, check_every=check_every)
+        info = c_solve_info()
+        st = lib().mcd_solve_pressure(self.handle, _ptr(rhs, torch.float64, self.N),
+                                      _ptr(bnd, torch.float64, self.N), _ptr(p, torch.float64, self.N),
+                                      C.byref(sp), C.byref(info), _stream())
+        d = dict(status=st, iters=info.iters, refinements=info.refinements, restarts=info.restarts,
+                 rel_res=info.rel_res, b_norm=info.b_norm)
+        if st != OK and raise_on_error:
+            raise McdError(st, lib().mcd_last_error().decode())
+        return p, d
+
+    def close(self):
+        if self.handle and self.handle.value:
+            lib().mcd_stencils_destroy(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def update_dps(mesh, centre, radius, body_id, pos, mask, mask_prev, kappa=0.2, n_relax=10,
+               band=None, alpha=0.0):
+    """One moving-boundary DP update (Sec. 2.2-2.4) in place on pos/mask."""
+    cm = make_mesh(mesh)
+    b = c_body()
+    b.id = int(body_id)
+    b.c[0], b.c[1], b.c[2] = float(centre[0]), float(centre[1]), 0.0
+    b.radius = float(radius)
+    N = mesh.n[0] * mesh.n[1]
+    band = 5.0 * mesh.l0 if band is None else band
+    _check(lib().mcd_update_dps(C.byref(cm), C.byref(b), 1, _ptr(pos, torch.float64, 2 * N),
+                                _ptr(mask, torch.int8, N), _ptr(mask_prev, torch.int8, N),
+                                float(kappa), int(n_relax), float(band), float(alpha), _stream()))
+
+
+def body_normals(mesh, centre, radius, body_id, pos, mask, out=None):
+    cm = make_mesh(mesh)
+    b = c_body()
+    b.id = int(body_id)
+    b.c[0], b.c[1], b.c[2] = float(centre[0]), float(centre[1]), 0.0
+    b.radius = float(radius)
+    N = mesh.n[0] * mesh.n[1]
+    n = torch.empty(2 * N, dtype=torch.float64, device=pos.device) if out is None else out
+    _check(lib().mcd_body_normals(C.byref(cm), C.byref(b), _ptr(pos, torch.float64, 2 * N),
+                                  _ptr(mask, torch.int8, N), _ptr(n, torch.float64, 2 * N), _stream()))
+    return n
+
+
+def version():
+    return lib().mcd_version().decode()
