@@ -1,0 +1,480 @@
+#!/usr/bin/env python
+"""Benchmark of the MCD pressure-Poisson hot path on one GB300 per rank.
+
+Workload: the oscillating-cylinder moving-boundary problem (2D unit box,
+1024x1024 background mesh, rigid cylinder D = 0.1 oscillating along x with
+KC = 5, Re = 100; Dirichlet p = 0 on the box walls, Neumann dP/dn = -a.n on
+the body).  One step is one pass of the hot path:
+    DP update (remask + 10 relaxation sweeps in the 5 l0 band)
+    -> body normals and Neumann data
+    -> MLS stencil build (FP64 rows + FP32 copy)
+    -> right-hand side assembly
+    -> mixed-precision Bi-CGSTAB solve to ||b - A p|| <= 1e-8 ||b|| (FP64
+       residual), warm-started from the previous step's pressure.
+Metric: DP-unknowns (non-void DPs) solved per second.  The same steps are
+also run with the plain FP64 Bi-CGSTAB for comparison (`fp64_plain`).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: replicas only (each rank runs its own instance; no data-path
+collective; max-over-ranks timing).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DP-unknowns solved/s at rel.res 1e-8: learned+mixed vs plain FP64, same GB300"
+UNIT = "DP-unknowns/s"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mcd", choices=["mcd", "reference"])
+    ap.add_argument("--n", type=int, default=1024, help="background mesh cells per side")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def committed_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source is unchanged since the capture (sha256 of its translation unit)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_2404_17542_gb300", "csrc",
+                       "krylov.cu" if kernel.startswith("bicg") else "stencils.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == sha:
+            return float(parts[3])
+    return None
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+class CylinderRun:
+    """State of one oscillating-cylinder instance on the device."""
+
+    def __init__(self, n, dev, mcd, inputs, tol):
+        import torch
+        self.torch, self.mcd, self.inputs = torch, mcd, inputs
+        self.n, self.dev, self.tol = n, dev, tol
+        pb = inputs.cylinder_box(n)
+        self.pb, self.cyl, self.mesh = pb, pb.meta["cylinder"], pb.mesh
+        N = self.mesh.N
+        self.N = N
+        self.dt = 0.2 * self.mesh.l0 / 1.0                 # CFL 0.2 at U = 1
+        self.pos = torch.from_numpy(pb.pos.ravel().copy()).to(dev)
+        self.mask = torch.from_numpy(pb.mask.copy()).to(dev)
+        self.prev = torch.empty_like(self.mask)
+        self.normal = torch.zeros(2 * N, dtype=torch.float64, device=dev)
+        self.neu = torch.zeros(N, dtype=torch.float64, device=dev)
+        self.p = torch.zeros(N, dtype=torch.float64, device=dev)
+        self.src_host = inputs.ppe_source(pb.pos, 0.0)
+        self.rhs = torch.from_numpy(self.src_host.copy()).to(dev)
+        c0 = self.cyl.centre(0.0)
+        mcd.update_dps(self.mesh, c0, self.cyl.radius, self.cyl.body_id, self.pos, self.mask,
+                       self.prev, kappa=0.2, n_relax=30, band=0.0)
+        mcd.body_boundary(self.mesh, c0, self.cyl.radius, self.cyl.body_id, self.pos, self.mask,
+                          acc=self.cyl.acceleration(0.0), normal=self.normal, neumann=self.neu)
+        self.st = mcd.Stencils(self.mesh, self.pos, self.mask, self.normal, bc_kind=pb.bc_kind,
+                               precision=mcd.MIXED)
+        self.k = 0
+
+    def snapshot(self):
+        return (self.pos.clone(), self.mask.clone(), self.p.clone(), self.k)
+
+    def restore(self, snap):
+        pos, mask, p, k = snap
+        self.pos.copy_(pos)
+        self.mask.copy_(mask)
+        self.p.copy_(p)
+        self.k = k
+
+    def step(self, mode):
+        """One pass of the hot path; returns the solve info."""
+        mcd = self.mcd
+        self.k += 1
+        t = self.k * self.dt
+        c = self.cyl.centre(t)
+        mcd.update_dps(self.mesh, c, self.cyl.radius, self.cyl.body_id, self.pos, self.mask,
+                       self.prev, kappa=0.2, n_relax=10, band=5.0 * self.mesh.l0)
+        mcd.body_boundary(self.mesh, c, self.cyl.radius, self.cyl.body_id, self.pos, self.mask,
+                          acc=self.cyl.acceleration(t), normal=self.normal, neumann=self.neu)
+        self.st.rebuild(self.pos, self.mask, self.normal)
+        _p, info = self.st.solve(self.rhs, self.neu, p=self.p, tol=self.tol, mode=mode)
+        return info
+
+
+def flush_l2(buf):
+    buf.zero_()
+
+
+def timed_steps(run, steps, mode, flush_buf, timing=False):
+    """Run `steps` steps, each bracketed by CUDA events on the current stream
+    with an L2 flush between steps.  Returns (total ms, unknowns, infos)."""
+    torch = run.torch
+    mcd = run.mcd
+    stream = torch.cuda.current_stream()
+    total_ms = 0.0
+    unknowns = 0
+    infos = []
+    for _ in range(steps):
+        flush_l2(flush_buf)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        info = run.step(mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        unknowns += info["unknowns"]
+        infos.append(info)
+    return total_ms, unknowns, infos
+
+
+def e2e_steps(run, steps, mode):
+    """Steps through the public API with host buffers: the step's source field
+    is copied from pinned host memory and the pressure read back each step."""
+    torch = run.torch
+    stream = torch.cuda.current_stream()
+    src = torch.from_numpy(run.src_host.copy()).pin_memory()
+    out = torch.empty(run.N, dtype=torch.float64).pin_memory()
+    total_ms = 0.0
+    unknowns = 0
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run.rhs.copy_(src, non_blocking=True)
+        info = run.step(mode)
+        out.copy_(run.p, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        unknowns += info["unknowns"]
+    return total_ms, unknowns, src.numel() * 8, out.numel() * 8
+
+
+# Algorithmic bytes of the persistent Bi-CGSTAB solve per DP and iteration
+# (FP32 recursion, 2D, 9-point rows):
+#   phase A reads r, p, v, r^ (16) + 9 FP32 weights (36), writes p, v (8)  = 60
+#   phase B reads r, v (8) + weights (36), writes s, t (8)                  = 52
+#   phase C reads x, p, s, t, r^ (20), writes x, r (8)                      = 28
+# i.e. 140 B per DP-iteration; halo re-reads and the true-residual updates
+# are not counted.  The stencil build reads positions and masks (17 B) and
+# writes FP64 + FP32 rows, Neumann weights, row scale and kind (206 B).
+SOLVE_BYTES_PER_DP_ITER = 140
+BUILD_BYTES_PER_DP = 206
+
+
+def gpu_arm(args):
+    import torch
+
+    from paper_2404_17542_gb300 import build, inputs, mcd
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    mcd.lib()
+
+    run = CylinderRun(args.n, dev, mcd, inputs, args.tol)
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    for _ in range(args.warmup):
+        run.step(mcd.MIXED)
+    snap = run.snapshot()
+
+    # timed region: mixed path
+    clocks = ClockSampler(local)
+    clocks.start()
+    mcd.timing_enable(1)
+    launches0 = mcd.launch_count()
+    barrier()
+    wall0 = time.perf_counter()
+    ms, unknowns, infos = timed_steps(run, args.steps, mcd.MIXED, flush_buf)
+    barrier()
+    wall = time.perf_counter() - wall0
+    launches = mcd.launch_count() - launches0
+    ktimes = {}
+    for kid, name in enumerate(mcd.KERNEL_NAMES):
+        n, t = mcd.timing_read(kid)
+        if n:
+            ktimes[name] = (n, t)
+    mcd.timing_enable(0)
+    clk = clocks.stop()
+
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        u = torch.tensor([unknowns], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
+        ms_max, unknowns_all = float(t.item()), float(u.item())
+    else:
+        ms_max, unknowns_all = ms, float(unknowns)
+    value = unknowns_all / (ms_max / 1e3)
+
+    # plain FP64 on the same steps
+    fp64 = None
+    if not args.no_fp64:
+        run.restore(snap)
+        ms64, unk64, infos64 = timed_steps(run, args.steps, mcd.FP64, flush_buf)
+        fp64 = {"value": unk64 / (ms64 / 1e3), "ms_per_step": ms64 / args.steps,
+                "iters_per_step": statistics.mean(i["iters"] for i in infos64),
+                "rel_res_max": max(i["rel_res"] for i in infos64)}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        run.restore(snap)
+        mse, unke, h2d, d2h = e2e_steps(run, args.steps, mcd.MIXED)
+        e2e = {"value": unke / (mse / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    # roofline of the dominant kernel: the persistent Bi-CGSTAB solve
+    peak, peak_src = measured_peaks()
+    roof = None
+    if ktimes:
+        total = sum(v[1] for v in ktimes.values())
+        name = max(ktimes, key=lambda k: ktimes[k][1])
+        n_launch, t_ms = ktimes[name]
+        if name == "bicg_persistent":
+            iters = sum(i["iters"] for i in infos)
+            algo = SOLVE_BYTES_PER_DP_ITER * run.N * iters
+            unit_note = f"{SOLVE_BYTES_PER_DP_ITER} B per DP-iteration x {run.N} DPs x {iters} iterations"
+        else:
+            algo = BUILD_BYTES_PER_DP * run.N * n_launch
+            unit_note = f"{BUILD_BYTES_PER_DP} B per DP x {run.N} DPs x {n_launch} launches"
+        achieved = algo / n_launch / (t_ms / n_launch / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": committed_traffic(name),
+                "kernel": name, "launches": n_launch, "avg_launch_ms": round(t_ms / n_launch, 3),
+                "algorithmic_bytes_per_launch": algo / n_launch, "algorithmic_bytes": unit_note,
+                "peak_source": f"{peak_src} hbm_gbs",
+                "kernel_share": {k: round(v[1] / total, 4) for k, v in ktimes.items()}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 Krylov + f64 refinement",
+            "data": "synthetic",
+            "config": {"workload": f"oscillating cylinder (D=0.1, KC=5, Re=100) {args.n}x{args.n} "
+                                   "moving-boundary PPE step",
+                       "mesh": [args.n, args.n], "tol": args.tol, "mode": "mixed",
+                       "learned_warm_start": False, "warm_start": "previous step pressure",
+                       "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "iters_per_step": statistics.mean(i["iters"] for i in infos),
+            "refinements_per_step": statistics.mean(i["refinements"] for i in infos),
+            "rel_res_max": max(i["rel_res"] for i in infos),
+            "unknowns_per_step": unknowns / args.steps,
+            "wall_s": wall,
+            "fp64_plain": fp64,
+            "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the oracle on host cores (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_step(state, tol=1e-8):
+    """One oracle pass of the same hot path on a smaller cylinder instance."""
+    from oracle import mask as omask
+    from oracle import mls, solve
+    pb, cyl, pos, m, p, k = state
+    mesh = pb.mesh
+    dt = 0.2 * mesh.l0
+    k += 1
+    t = k * dt
+    c = cyl.centre(t)
+    pos, m, _prev = omask.update_dps(mesh, pos, m, c, cyl.radius, body_id=cyl.body_id, n_relax=10)
+    normal = omask.circle_normals(pos, m, c, cyl.body_id)
+    a = cyl.acceleration(t)
+    bnd = np.where(m == cyl.body_id, -(a[0] * normal[0] + a[1] * normal[1]), 0.0)
+    W = mls.build_weights(mesh, pos, m, normal, pb.bc_kind)
+    A = solve.assemble(mesh, W["row"])
+    from paper_2404_17542_gb300 import inputs
+    rhs = inputs.ppe_source(pos, 0.0)
+    b = solve.form_rhs(mesh, W["kind"], W["QL"], rhs, bnd, W["rscale"])
+    x, it, rel = solve.bicgstab(A, b, x0=p, tol=tol)
+    return (pb, cyl, pos, m, x, k), int((m != 0).sum()), it
+
+
+def oracle_state(n):
+    from oracle import mask as omask
+    from paper_2404_17542_gb300 import inputs
+    pb = inputs.cylinder_box(n)
+    cyl = pb.meta["cylinder"]
+    pos, m, _ = omask.update_dps(pb.mesh, pb.pos, pb.mask, cyl.centre(0.0), cyl.radius,
+                                 body_id=cyl.body_id, band=0.0, n_relax=4)
+    return (pb, cyl, pos, m, np.zeros(pb.mesh.N), 0)
+
+
+def cpu_baseline(n=128, steps=2):
+    state = oracle_state(n)
+    state, _u, _it = oracle_step(state)          # untimed first step
+    t0 = time.perf_counter()
+    unknowns = 0
+    for _ in range(steps):
+        state, u, _it = oracle_step(state)
+        unknowns += u
+    dt = time.perf_counter() - t0
+    return {"value": unknowns / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle steps (DP update, MLS weights, Bi-CGSTAB to 1e-8) of the "
+                      f"same cylinder workload at {n}x{n} instead of the full mesh; "
+                      "single-threaded numpy/scipy"}
+
+
+def reference_arm(args):
+    rank, world, _local = dist_env()
+    if rank != 0:
+        return
+    n = 96
+    state = oracle_state(n)
+    for _ in range(args.warmup):
+        state, _u, _it = oracle_step(state, args.tol)
+    t0 = time.perf_counter()
+    unknowns = 0
+    for _ in range(args.steps):
+        state, u, _it = oracle_step(state, args.tol)
+        unknowns += u
+    dt = time.perf_counter() - t0
+    value = unknowns / dt
+    sample = (f"each step one oracle pass (DP update, MLS weights, Bi-CGSTAB to {args.tol}) of "
+              f"the cylinder workload at {n}x{n}; single-threaded numpy/scipy")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"oscillating cylinder (D=0.1, KC=5, Re=100) {args.n}x{args.n} "
+                                   "moving-boundary PPE step",
+                       "mesh": [n, n], "tol": args.tol, "mode": "oracle fp64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+import numpy as np  # noqa: E402  (used by the oracle legs)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -123,7 +123,12 @@ void mcd_stencils_destroy(mcd_stencils *st);
 
 /* Device arrays of a handle, for parity tests and drivers (read-only).
  *  MCD_ARR_ROW64   float64 [S][N] PPE rows (slot-major, S = 3^dim)
- *  MCD_ARR_ROW32   float32 [S][N] (MCD_MIXED only)
+ *  MCD_ARR_ROW32   float32 [S][N] (MCD_MIXED only), difference form: slots
+ *                  other than the centre C = S/2 hold the rounded FP64
+ *                  weights, slot C the row sum (0 for MLS rows, whose sum
+ *                  vanishes because chi = 1 MLS reproduces constants; 1 for
+ *                  identity rows); (A x)_i = row[C] x_i + sum_{s != C}
+ *                  row[s] (x_{j_s} - x_i)
  *  MCD_ARR_QL64    float64 [S][N] Neumann-data weights of the PPE rows
  *  MCD_ARR_D64     float64 [nb][S][N] value weights of each derivative
  *                  (nb = 5 in 2D: d/dx, d/dy, d2/dx2, d2/dxdy, d2/dy2;
@@ -166,13 +171,21 @@ typedef struct mcd_net mcd_net;
 
 /* tol          stop when ||b - A p||_2 <= tol ||b||_2 (FP64 residual).
  * max_iter     cap on Krylov iterations (all refinements together).
- * mode         MCD_FP64: plain FP64 Bi-CGSTAB;
- *              MCD_MIXED: FP32 Bi-CGSTAB inner solves, FP64 residual and
- *              update (iterative refinement); needs an MCD_MIXED handle.
- * inner_tol    relative tolerance of each inner FP32 solve (MIXED).
- * max_refine   cap on refinements (MIXED).
+ * mode         MCD_FP64: plain FP64 Bi-CGSTAB (restarted from the true
+ *              residual if the recursive one converged early);
+ *              MCD_MIXED: FP32 Bi-CGSTAB on the FP32 rows whose iterate is
+ *              folded into an FP64 solution, with reliable updates: the
+ *              FP32 recursive residual is replaced by the FP64 residual
+ *              b - A64 x (iterative refinement on an FP64 residual that
+ *              keeps the Krylov direction); needs an MCD_MIXED handle.
+ * inner_tol    (MIXED) reliable-update factor in (0, 1): an FP64 residual
+ *              is taken once the FP32 residual has fallen by this factor
+ *              since the last one (checked every few iterations).
+ * max_refine   cap on FP64 restarts (FP64 mode).
  * net          NULL, or a trained network giving the initial guess.
- * check_every  Krylov iterations between host convergence checks (0: auto). */
+ * check_every  Krylov iterations between host convergence checks (0: auto).
+ * update_restart (MIXED) 1: restart the FP32 recurrence (fresh shadow
+ *              residual, p = r) at every reliable update; 0: keep p. */
 typedef struct {
     double tol;
     int max_iter;
@@ -181,14 +194,16 @@ typedef struct {
     int max_refine;
     const mcd_net *net;
     int check_every;
+    int update_restart;
 } mcd_solve_params;
 
 typedef struct {
     int iters;          /* Krylov iterations done */
-    int refinements;    /* FP64 residual evaluations after the first (MIXED) */
+    int refinements;    /* FP64 residual updates after the first */
     int restarts;       /* Bi-CGSTAB restarts after a rho breakdown */
     double rel_res;     /* final ||b - A p|| / ||b|| in FP64 */
     double b_norm;      /* ||b||_2 */
+    int64_t unknowns;   /* non-void DPs of the system (DP unknowns solved) */
 } mcd_solve_info;
 
 /* mcd_solve_pressure - solve A p = b (b from mcd_assemble_rhs(rhs, bnd)).
@@ -207,12 +222,16 @@ mcd_status mcd_solve_pressure(const mcd_stencils *st, const double *rhs_dev,
  * Moving-boundary DP update (Sec. 2.2-2.4)
  * ---------------------------------------------------------------------- */
 
-/* A rigid circular body (2D): centre c at the new time, radius, boundary id
- * (>= 2; id 1 is the domain wall). */
+/* A rigid circular body (2D) at the new time: boundary id (>= 2; id 1 is
+ * the domain wall), centre c, radius, translational velocity and
+ * acceleration (the paper's V_trans and dV_trans/dt, Eqs. (24)-(29); a
+ * circle needs no rotation). */
 typedef struct {
     int id;
     double c[3];
     double radius;
+    double vel[3];
+    double acc[3];
 } mcd_body;
 
 /* mcd_update_dps - one DP update for the body positions of the new step.
@@ -236,12 +255,54 @@ mcd_status mcd_update_dps(const mcd_mesh *mesh, const mcd_body *bodies,
                           int8_t *mask_prev_dev, double kappa, int n_relax,
                           double band, double alpha, mcd_stream_t stream);
 
-/* mcd_body_normals - unit normal (x - c)/|x - c| of every DP whose mask is
- * the body's id, 0 elsewhere (the analytic gradient of the circle SDF,
- * Sec. 2.5).  normal_dev: device float64 [2][N].  Asynchronous. */
-mcd_status mcd_body_normals(const mcd_mesh *mesh, const mcd_body *body,
-                            const double *pos_dev, const int8_t *mask_dev,
-                            double *normal_dev, mcd_stream_t stream);
+/* mcd_body_boundary - boundary data of the body's DPs (mask == id):
+ *  normal_dev  float64 [2][N]: unit normal n = (x - c)/|x - c| (the analytic
+ *              gradient of the circle SDF, Sec. 2.5); 0 at other DPs;
+ *  neumann_dev float64 [N] or NULL: the pressure Neumann datum of Eq. (23),
+ *              dP/dn = -(dV/dt) . n with dV/dt = acc; 0 at other DPs.
+ * Asynchronous. */
+mcd_status mcd_body_boundary(const mcd_mesh *mesh, const mcd_body *body,
+                             const double *pos_dev, const int8_t *mask_dev,
+                             double *normal_dev, double *neumann_dev,
+                             mcd_stream_t stream);
+
+/* -------------------------------------------------------------------------
+ * Instrumentation (metrics and tracing; not part of the method)
+ * ---------------------------------------------------------------------- */
+enum {
+    MCD_K_BICG_A = 0,    /* p update + v = A p + r^.v          */
+    MCD_K_BICG_B = 1,    /* s = r - alpha v + t = A s + dots    */
+    MCD_K_BICG_C = 2,    /* x, r update + dots                  */
+    MCD_K_RESIDUAL = 3,  /* FP64 residual b - A x               */
+    MCD_K_BUILD = 4,     /* MLS stencil build                   */
+    MCD_K_UPDATE = 5,    /* remask + relaxation sweeps          */
+    MCD_K_OTHER = 6,     /* everything else                     */
+    MCD_K_SOLVE = 7,     /* persistent cooperative Bi-CGSTAB     */
+    MCD_K_COUNT = 8
+};
+
+/* When sample_every > 0, every sample_every-th launch of each kernel class
+ * is bracketed by CUDA events recorded on the stream it is launched on
+ * (0 disables).  Resets the accumulated samples.  Not thread-safe with
+ * concurrent solves. */
+mcd_status mcd_timing_enable(int sample_every);
+
+/* Synchronises the recorded events of kernel class `kernel` and returns the
+ * number of sampled launches and their summed device time in ms. */
+mcd_status mcd_timing_read(int kernel, int64_t *sampled, double *total_ms);
+
+/* Phase trace of the persistent solver: when enabled (on = 1), thread 0 of
+ * block 0 records %globaltimer stamps (ns) for the first 64 iterations of
+ * each launch: host_out[8*it + slot], slot 0 iteration start, 1 phase A
+ * done, 2 A reduced, 3 B done, 4 B reduced, 5 C done, 6 C reduced; then,
+ * for iteration 10, host_out[512 + b] = phase-A end of block b and
+ * host_out[2560 + b] = its SM id (b < 2048).  mcd_trace_read synchronises
+ * the device and copies the 4608 values. */
+mcd_status mcd_trace_enable(int on);
+mcd_status mcd_trace_read(unsigned long long *host_out);
+
+/* Number of kernels this library has launched since it was loaded. */
+int64_t mcd_launch_count(void);
 
 /* Message of the last error on the calling thread (never NULL). */
 const char *mcd_last_error(void);

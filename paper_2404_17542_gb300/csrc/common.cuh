@@ -88,6 +88,22 @@ __device__ __forceinline__ int nb_coord(int c, int o, int n, int per, double len
 // Solver workspace attached to a stencil handle (allocated on first solve).
 struct Workspace;
 
+// Scope guard around kernel launches: counts them and, when sampling is on,
+// brackets the launch with CUDA events on its stream (mcd_timing_*).
+class KTimer {
+public:
+    KTimer(int kind, cudaStream_t s, int nlaunch = 1);
+    ~KTimer();
+    KTimer(const KTimer &) = delete;
+    KTimer &operator=(const KTimer &) = delete;
+
+private:
+    int kind_;
+    cudaStream_t stream_;
+    bool active_;
+    cudaEvent_t a_{}, b_{};
+};
+
 }  // namespace mcd
 
 struct mcd_stencils {
@@ -107,3 +123,10 @@ struct mcd_stencils {
     unsigned long long *bad_dp;  // device: smallest failing DP, ~0ull if none
     mcd::Workspace *ws;
 };
+
+// Launch a kernel inside a KTimer scope: MCD_KLAUNCH(kind, stream, k<<<...>>>(...));
+#define MCD_KLAUNCH(kind, stream, ...)               \
+    do {                                             \
+        ::mcd::KTimer kt_launch_((kind), (stream));  \
+        __VA_ARGS__;                                 \
+    } while (0)

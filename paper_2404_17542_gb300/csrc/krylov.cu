@@ -17,6 +17,7 @@
 // Scalars live on the device; the host polls them every few iterations, and
 // kernels launched after convergence return at once.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -28,6 +29,7 @@ namespace mcd {
 
 struct Scalars {
     double rho, alpha, omega, beta;
+    double rho_prev;  // rho of the previous iteration (reliable-update beta)
     double rhat2;     // ||r^||^2 (breakdown test)
     double tol2;      // squared absolute tolerance on the recursive residual
     double rr, ss, ts, tt, rv;
@@ -37,6 +39,45 @@ struct Scalars {
     int restart;      // next KA sets r^ = r and p = r
     int restarts;
     int s_conv;       // ||s|| small: KC does x += alpha p and stops
+    unsigned long long unknowns;  // non-void DPs of the system
+    // FP32 copies of alpha, omega, beta for the FP32 kernels: a per-thread
+    // double-to-float conversion would run on the FP64 pipe, which on this
+    // GPU is 1/64 of the FP32 rate
+    float alpha_f, omega_f, beta_f;
+    // persistent solver state
+    int pending;      // next step is a true-residual (reliable) update
+    int max_hit;      // the recursion reached max_iter
+    int parity;       // p / v ping-pong buffer of the next iteration
+    int phase_err;    // a grid barrier gave up (timeout)
+    double rr_last;   // recursive-precision ||r||^2 at the last true residual
+};
+
+// Refresh the FP32 copies (called by the single thread that updates them).
+__device__ __forceinline__ void publish(Scalars *sc) {
+    sc->alpha_f = (float)sc->alpha;
+    sc->omega_f = (float)sc->omega;
+    sc->beta_f = (float)sc->beta;
+}
+
+template <typename T> struct ScalarOf;
+template <> struct ScalarOf<double> {
+    __device__ static double alpha(const Scalars *sc) { return sc->alpha; }
+    __device__ static double omega(const Scalars *sc) { return sc->omega; }
+    __device__ static double beta(const Scalars *sc) { return sc->beta; }
+};
+template <> struct ScalarOf<float> {
+    __device__ static float alpha(const Scalars *sc) { return sc->alpha_f; }
+    __device__ static float omega(const Scalars *sc) { return sc->omega_f; }
+    __device__ static float beta(const Scalars *sc) { return sc->beta_f; }
+};
+
+// Grid barrier state: `release` (its own 256-byte line) and one arrival
+// flag per block.  Both hold barrier epochs, 1, 2, ... within a launch (the
+// host zeroes them before each launch), so nothing is reset in between.
+struct GridBarrier {
+    unsigned int release;
+    unsigned int pad[63];
+    unsigned int flag[1];     // [grid] arrival epochs (allocated past the struct)
 };
 
 struct Workspace {
@@ -55,6 +96,7 @@ struct Workspace {
     Scalars *sc = nullptr;
     Scalars *h_sc = nullptr;     // pinned host mirror
     int pstride = 0;
+    GridBarrier *bar = nullptr;  // persistent-solver grid barrier
 };
 
 void free_workspace(mcd_stencils *st) {
@@ -65,16 +107,21 @@ void free_workspace(mcd_stencils *st) {
     cudaFree(w->dv[0]); cudaFree(w->dv[1]); cudaFree(w->ds); cudaFree(w->dt);
     cudaFree(w->fr); cudaFree(w->frh); cudaFree(w->fp[0]); cudaFree(w->fp[1]);
     cudaFree(w->fv[0]); cudaFree(w->fv[1]); cudaFree(w->fs); cudaFree(w->ft); cudaFree(w->fd);
-    cudaFree(w->partials); cudaFree(w->counter); cudaFree(w->sc);
+    cudaFree(w->partials); cudaFree(w->counter); cudaFree(w->sc); cudaFree(w->bar);
     cudaFreeHost(w->h_sc);
     delete w;
     st->ws = nullptr;
 }
 
-// Tile shape per dimension (one DP per thread, 256 threads).
+// Tile of the Bi-CGSTAB stencil kernels: 256 threads own X x Y (x Z) DPs, R
+// per thread, strided along the last tiled axis (thread grid X x TY x TZ).
 template <int DIM> struct Tile;
-template <> struct Tile<2> { static constexpr int X = 32, Y = 8, Z = 1; };
-template <> struct Tile<3> { static constexpr int X = 32, Y = 4, Z = 2; };
+template <> struct Tile<2> {
+    static constexpr int X = 32, Y = 16, Z = 1, R = 2, TY = 8, TZ = 1;
+};
+template <> struct Tile<3> {
+    static constexpr int X = 32, Y = 4, Z = 4, R = 2, TY = 4, TZ = 2;
+};
 
 template <int DIM> struct HaloDims {
     static constexpr int HX = Tile<DIM>::X + 2;
@@ -113,8 +160,107 @@ __device__ __forceinline__ void block_partials(A (&v)[NV], double *partials, int
     }
 }
 
+// ---- compensated FP32 dot products --------------------------------------
+// FP32 kernels accumulate each dot product as an unevaluated pair (hi, lo):
+// products are split exactly with fma and added with TwoSum, warps and the
+// block combine pairs the same way, and one thread per block converts the
+// pair to FP64.  The sums are then accurate to about twice FP32 precision
+// relative to sum |a_i b_i|, so rho = r^.r stays meaningful when it is much
+// smaller than |r^||r| (as the residual migrates away from r^), and no
+// per-thread FP64 work (slow on this GPU) is needed.
+struct DF {
+    float hi, lo;
+};
+
+// The error-free steps use the _rn intrinsics, which the compiler never
+// contracts into fused multiply-adds (contraction would change the rounded
+// product that TwoSum has to see and void the error terms).
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void df_add_prod(DF &acc, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    float e;
+    two_sum_f(acc.hi, p, acc.hi, e);
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF r;
+    float e;
+    two_sum_f(a.hi, b.hi, r.hi, e);
+    r.lo = __fadd_rn(__fadd_rn(e, a.lo), b.lo);
+    return r;
+}
+
+template <int NV>
+__device__ __forceinline__ void block_partials_df(DF (&v)[NV], double *partials, int stride, int block) {
+    __shared__ DF wsum[NV][32];
+    const int tid = threadIdx.x;
+    const int nthreads = blockDim.x;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        for (int o = 16; o > 0; o >>= 1) {
+            DF other;
+            other.hi = __shfl_down_sync(0xffffffffu, v[q].hi, o);
+            other.lo = __shfl_down_sync(0xffffffffu, v[q].lo, o);
+            v[q] = df_add(v[q], other);
+        }
+    if ((tid & 31) == 0)
+        for (int q = 0; q < NV; ++q) wsum[q][tid >> 5] = v[q];
+    __syncthreads();
+    if (tid < 32) {
+        const int nw = nthreads >> 5;
+        for (int q = 0; q < NV; ++q) {
+            DF x = (tid < nw) ? wsum[q][tid] : DF{0.0f, 0.0f};
+            for (int o = 16; o > 0; o >>= 1) {
+                DF other;
+                other.hi = __shfl_down_sync(0xffffffffu, x.hi, o);
+                other.lo = __shfl_down_sync(0xffffffffu, x.lo, o);
+                x = df_add(x, other);
+            }
+            if (tid == 0) partials[q * stride + block] = (double)x.hi + (double)x.lo;
+        }
+    }
+}
+
+// Accumulator of one dot product: FP64 for the FP64 kernels, a compensated
+// pair for the FP32 ones.
+template <typename T> struct DotAcc;
+template <> struct DotAcc<double> {
+    double v = 0.0;
+    __device__ void add(double a, double b) { v += a * b; }
+};
+template <> struct DotAcc<float> {
+    DF v{0.0f, 0.0f};
+    __device__ void add(float a, float b) { df_add_prod(v, a, b); }
+};
+
+template <int NV>
+__device__ __forceinline__ void dot_partials(DotAcc<double> (&d)[NV], double *partials, int stride, int block) {
+    double v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = d[q].v;
+    block_partials<NV, double>(v, partials, stride, block);
+}
+
+template <int NV>
+__device__ __forceinline__ void dot_partials(DotAcc<float> (&d)[NV], double *partials, int stride, int block) {
+    DF v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = d[q].v;
+    block_partials_df<NV>(v, partials, stride, block);
+}
+
 // Returns true in the block that arrives last; that block then holds the
-// totals of the NV partial sums in out[] (valid in every thread).
+// totals of the NV partial sums in out[] (valid in every thread).  The
+// partials are read with independent loads, four per thread per round, so
+// the tail costs about one L2 round trip for the few-hundred-block grids the
+// solver launches.
 template <int NV>
 __device__ __forceinline__ bool last_block_totals(const double *partials, int stride, int nblocks,
                                                   unsigned int *counter, double (&out)[NV]) {
@@ -130,11 +276,24 @@ __device__ __forceinline__ bool last_block_totals(const double *partials, int st
     __syncthreads();
     if (!is_last) return false;
     __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+    for (int b0 = tid; b0 < nblocks; b0 += 4 * nthreads) {
+        double v[NV][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int b = b0 + u * nthreads;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) v[q][u] = (b < nblocks) ? __ldcg(partials + q * stride + b) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] += (v[q][0] + v[q][1]) + (v[q][2] + v[q][3]);
+    }
+#pragma unroll
     for (int q = 0; q < NV; ++q) {
-        double acc = 0.0;
-        for (int b = tid; b < nblocks; b += nthreads) acc += __ldcg(partials + q * stride + b);
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if ((tid & 31) == 0) red[q][tid >> 5] = acc;
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
+        if ((tid & 31) == 0) red[q][tid >> 5] = acc[q];
     }
     __syncthreads();
     for (int q = 0; q < NV; ++q) {
@@ -149,13 +308,14 @@ __device__ __forceinline__ bool last_block_totals(const double *partials, int st
 struct TileArgs {
     Geo g;
     int bx, by, bz;      // tiles per axis
+    int ntiles;
+    const int8_t *kind;  // non-NULL: Neumann rows act as identity rows
 };
 
 template <int DIM>
-__device__ __forceinline__ void tile_origin(const TileArgs &ta, int &x0, int &y0, int &z0, int &blk) {
-    blk = blockIdx.x;
-    const int tx = blk % ta.bx;
-    const int rest = blk / ta.bx;
+__device__ __forceinline__ void tile_origin(const TileArgs &ta, int tile, int &x0, int &y0, int &z0) {
+    const int tx = tile % ta.bx;
+    const int rest = tile / ta.bx;
     const int ty = rest % ta.by;
     const int tz = rest / ta.by;
     x0 = tx * Tile<DIM>::X;
@@ -177,22 +337,99 @@ __device__ __forceinline__ int64_t halo_index(const Geo &g, int h, int x0, int y
     return (int64_t)gx + (int64_t)g.n[0] * ((int64_t)gy + (int64_t)g.n[1] * gz);
 }
 
-// sum_s row[s][k] * tile[neighbour s] for the thread's own DP.
-template <int DIM, typename T>
-__device__ __forceinline__ T stencil_from_tile(const T *__restrict__ row, int64_t N, int64_t k,
-                                               const T *tile, int lx, int ly, int lz) {
+// DP r of thread tid in the tile at (x0, y0, z0): global index, or -1
+// outside the mesh; (lx, ly, lz) are its coordinates inside the tile.
+template <int DIM>
+__device__ __forceinline__ int64_t tile_dp(const Geo &g, int tid, int r, int x0, int y0, int z0, int &lx,
+                                           int &ly, int &lz) {
+    using TL = Tile<DIM>;
+    lx = tid % TL::X;
+    if (DIM == 2) {
+        ly = (tid / TL::X) + r * TL::TY;
+        lz = 0;
+    } else {
+        ly = (tid / TL::X) % TL::TY;
+        lz = tid / (TL::X * TL::TY) + r * TL::TZ;
+    }
+    const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+    if (gx >= g.n[0] || gy >= g.n[1] || (DIM == 3 && gz >= g.n[2])) return -1;
+    return (DIM == 2) ? (int64_t)gx + (int64_t)g.n[0] * gy
+                      : (int64_t)gx + (int64_t)g.n[0] * ((int64_t)gy + (int64_t)g.n[1] * gz);
+}
+
+template <int DIM>
+__device__ __forceinline__ int tile_centre(int lx, int ly, int lz) {
     using HD = HaloDims<DIM>;
-    T acc = 0;
+    return (lx + 1) + HD::HX * ((ly + 1) + HD::HY * (lz + (DIM == 3 ? 1 : 0)));
+}
+
+// (A x)_k from the shared-memory tile of x and the row weights w[] (already
+// in registers).  FP64 rows are in matrix form (sum_s c_s x_s); FP32 rows in
+// difference form (c_C x_k + sum_{s != C} c_s (x_s - x_k), centre slot = row
+// sum), which keeps the O(1/l0^2) weights from cancelling away the FP32
+// mantissa.
+//
+// The FP32 form is also compensated: each product c_s (x_s - x_k) is split
+// exactly into p + e with a fused multiply-add, and the products are summed
+// with Knuth's TwoSum into a (hi, lo) pair, so the row is accumulated to
+// about twice FP32 precision and rounded once.  A plain FP32 sum of the
+// O(|grad x| / l0) terms loses the digits of their O(lap x) sum and slows
+// Bi-CGSTAB by about 2x; the compensation costs about 11 FP32 operations per
+// term, which this bandwidth-bound kernel has to spare.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ T stencil_apply(const T *w, const T *tile, int lx, int ly, int lz) {
+    using HD = HaloDims<DIM>;
+    constexpr int C = HD::S / 2;
+    const T xk = tile[tile_centre<DIM>(lx, ly, lz)];
+    if (sizeof(T) == 4) {
+        float hi = (float)w[C] * (float)xk, lo = 0.0f;   // centre weight is 0 or 1: exact
+#pragma unroll
+        for (int s = 0; s < HD::S; ++s) {
+            if (s == C) continue;
+            const int ox = s % 3, oy = (s / 3) % 3, oz = s / 9;
+            const int h = (lx + ox) + HD::HX * ((ly + oy) + HD::HY * (lz + oz));
+            const float d = __fsub_rn((float)tile[h], (float)xk);
+            const float p = __fmul_rn((float)w[s], d);
+            const float pe = __fmaf_rn((float)w[s], d, -p);
+            float e;
+            two_sum(hi, p, hi, e);
+            lo = __fadd_rn(lo, __fadd_rn(e, pe));
+        }
+        return (T)__fadd_rn(hi, lo);
+    }
+    T acc = (T)0;
 #pragma unroll
     for (int s = 0; s < HD::S; ++s) {
         const int ox = s % 3, oy = (s / 3) % 3, oz = s / 9;
         const int h = (lx + ox) + HD::HX * ((ly + oy) + HD::HY * (lz + oz));
-        acc += row[(int64_t)s * N + k] * tile[h];
+        acc += w[s] * tile[h];
     }
     return acc;
 }
 
+// Row weights of DP k into registers (zeros for k < 0).
+template <int S, typename T>
+__device__ __forceinline__ void load_row(const T *__restrict__ row, int64_t N, int64_t k, T *w) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) w[s] = (k >= 0) ? __ldg(row + (int64_t)s * N + k) : (T)0;
+}
+
+// One block per tile.  Each thread first issues the weight loads of its R
+// DPs (independent of the tile), then the halo loads; after the barrier it
+// applies the stencil from shared memory.  2D keeps all 9 x R weights in
+// registers; 3D (27 per DP) loads them per DP after the barrier.
+
 // ---- KA: p = r + beta (p_old - omega v_old); v = A p; partial r^.v -------
+// On a restart p = r and the shadow residual r^ is reset to r (textbook
+// choice; a random shadow vector converged more slowly on these systems), and
+// r^.r and r^.r^ are reduced too so that rho = r^.r.  Neumann rows (ta.kind)
+// act as identity rows.
 template <int DIM, typename T, typename A>
 __global__ void __launch_bounds__(256) bicg_ka(TileArgs ta, const T *__restrict__ row, const T *__restrict__ r,
                                                T *__restrict__ rhat, const T *__restrict__ p_old,
@@ -200,45 +437,72 @@ __global__ void __launch_bounds__(256) bicg_ka(TileArgs ta, const T *__restrict_
                                                T *__restrict__ v_new, Scalars *sc, double *partials,
                                                int pstride, unsigned int *counter) {
     using HD = HaloDims<DIM>;
+    using TL = Tile<DIM>;
+    constexpr int S = HD::S;
+    constexpr bool PREF = (S == 9);
     __shared__ T tile[HD::H];
     if (sc->done) return;
-    const T beta = (T)sc->beta, omega = (T)sc->omega;
+    const T beta = ScalarOf<T>::beta(sc), omega = ScalarOf<T>::omega(sc);
     const int restart = sc->restart;
-    int x0, y0, z0, blk;
-    tile_origin<DIM>(ta, x0, y0, z0, blk);
     const Geo &g = ta.g;
     const int tid = threadIdx.x;
+    int x0, y0, z0;
+    tile_origin<DIM>(ta, blockIdx.x, x0, y0, z0);
+    int64_t k[TL::R];
+    int lx[TL::R], ly[TL::R], lz[TL::R];
+    T w[TL::R][PREF ? S : 1];
+    T rh[TL::R];
+#pragma unroll
+    for (int q = 0; q < TL::R; ++q) {
+        k[q] = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+        if (PREF) load_row<S, T>(row, g.N, k[q], w[q]);
+        rh[q] = (!restart && k[q] >= 0) ? rhat[k[q]] : (T)0;
+    }
     for (int h = tid; h < HD::H; h += 256) {
         const int64_t j = halo_index<DIM>(g, h, x0, y0, z0);
         const T rj = r[j];
         tile[h] = restart ? rj : rj + beta * (p_old[j] - omega * v_old[j]);
     }
     __syncthreads();
-    const int lx = tid % Tile<DIM>::X;
-    const int ly = (tid / Tile<DIM>::X) % Tile<DIM>::Y;
-    const int lz = tid / (Tile<DIM>::X * Tile<DIM>::Y);
-    const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-    A dot[1] = {0};
-    if (gx < g.n[0] && gy < g.n[1] && (DIM == 2 || gz < g.n[2])) {
-        const int64_t k = (DIM == 2) ? (int64_t)gx + (int64_t)g.n[0] * gy
-                                     : (int64_t)gx + (int64_t)g.n[0] * ((int64_t)gy + (int64_t)g.n[1] * gz);
-        const int hc = (lx + 1) + HD::HX * ((ly + 1) + HD::HY * (DIM == 3 ? lz + 1 : 0));
-        const T pk = tile[hc];
-        p_new[k] = pk;
-        T rh;
-        if (restart) { rh = r[k]; rhat[k] = rh; } else { rh = rhat[k]; }
-        const T vk = stencil_from_tile<DIM, T>(row, g.N, k, tile, lx, ly, lz);
-        v_new[k] = vk;
-        dot[0] = (A)rh * (A)vk;
+    DotAcc<T> dot[3];
+#pragma unroll
+    for (int q = 0; q < TL::R; ++q) {
+        if (k[q] < 0) continue;
+        const T pk = tile[tile_centre<DIM>(lx[q], ly[q], lz[q])];
+        p_new[k[q]] = pk;
+        T rq = rh[q];
+        if (restart) {
+            rq = pk;   // pk = r[k] on a restart
+            rhat[k[q]] = rq;
+            dot[1].add(rq, pk);
+            dot[2].add(rq, rq);
+        }
+        T vk;
+        if (ta.kind && ta.kind[k[q]] == KIND_NEUMANN) {
+            vk = pk;
+        } else if (PREF) {
+            vk = stencil_apply<DIM, T>(w[q], tile, lx[q], ly[q], lz[q]);
+        } else {
+            T wl[S];
+            load_row<S, T>(row, g.N, k[q], wl);
+            vk = stencil_apply<DIM, T>(wl, tile, lx[q], ly[q], lz[q]);
+        }
+        v_new[k[q]] = vk;
+        dot[0].add(rq, vk);
     }
-    block_partials<1, A>(dot, partials, pstride, blk);
-    double tot[1];
-    if (last_block_totals<1>(partials, pstride, gridDim.x, counter, tot) && tid == 0) {
+    dot_partials<3>(dot, partials, pstride, blockIdx.x);
+    double tot[3];
+    if (last_block_totals<3>(partials, pstride, gridDim.x, counter, tot) && tid == 0) {
         sc->rv = tot[0];
+        if (restart) {
+            sc->rho = tot[1];
+            sc->rhat2 = tot[2];
+        }
         sc->restart = 0;
         const double alpha = sc->rho / tot[0];
-        if (!isfinite(alpha)) { sc->done = 3; return; }
+        if (!isfinite(alpha) || alpha == 0.0) { sc->done = 3; return; }
         sc->alpha = alpha;
+        publish(sc);
     }
 }
 
@@ -249,36 +513,51 @@ __global__ void __launch_bounds__(256) bicg_kb(TileArgs ta, const T *__restrict_
                                                T *__restrict__ t_out, Scalars *sc, double *partials,
                                                int pstride, unsigned int *counter) {
     using HD = HaloDims<DIM>;
+    using TL = Tile<DIM>;
+    constexpr int S = HD::S;
+    constexpr bool PREF = (S == 9);
     __shared__ T tile[HD::H];
     if (sc->done) return;
-    const T alpha = (T)sc->alpha;
-    int x0, y0, z0, blk;
-    tile_origin<DIM>(ta, x0, y0, z0, blk);
+    const T alpha = ScalarOf<T>::alpha(sc);
     const Geo &g = ta.g;
     const int tid = threadIdx.x;
+    int x0, y0, z0;
+    tile_origin<DIM>(ta, blockIdx.x, x0, y0, z0);
+    int64_t k[TL::R];
+    int lx[TL::R], ly[TL::R], lz[TL::R];
+    T w[TL::R][PREF ? S : 1];
+#pragma unroll
+    for (int q = 0; q < TL::R; ++q) {
+        k[q] = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+        if (PREF) load_row<S, T>(row, g.N, k[q], w[q]);
+    }
     for (int h = tid; h < HD::H; h += 256) {
         const int64_t j = halo_index<DIM>(g, h, x0, y0, z0);
         tile[h] = r[j] - alpha * v[j];
     }
     __syncthreads();
-    const int lx = tid % Tile<DIM>::X;
-    const int ly = (tid / Tile<DIM>::X) % Tile<DIM>::Y;
-    const int lz = tid / (Tile<DIM>::X * Tile<DIM>::Y);
-    const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-    A dot[3] = {0, 0, 0};
-    if (gx < g.n[0] && gy < g.n[1] && (DIM == 2 || gz < g.n[2])) {
-        const int64_t k = (DIM == 2) ? (int64_t)gx + (int64_t)g.n[0] * gy
-                                     : (int64_t)gx + (int64_t)g.n[0] * ((int64_t)gy + (int64_t)g.n[1] * gz);
-        const int hc = (lx + 1) + HD::HX * ((ly + 1) + HD::HY * (DIM == 3 ? lz + 1 : 0));
-        const T sk = tile[hc];
-        s_out[k] = sk;
-        const T tk = stencil_from_tile<DIM, T>(row, g.N, k, tile, lx, ly, lz);
-        t_out[k] = tk;
-        dot[0] = (A)tk * (A)sk;
-        dot[1] = (A)tk * (A)tk;
-        dot[2] = (A)sk * (A)sk;
+    DotAcc<T> dot[3];
+#pragma unroll
+    for (int q = 0; q < TL::R; ++q) {
+        if (k[q] < 0) continue;
+        const T sk = tile[tile_centre<DIM>(lx[q], ly[q], lz[q])];
+        s_out[k[q]] = sk;
+        T tk;
+        if (ta.kind && ta.kind[k[q]] == KIND_NEUMANN) {
+            tk = sk;
+        } else if (PREF) {
+            tk = stencil_apply<DIM, T>(w[q], tile, lx[q], ly[q], lz[q]);
+        } else {
+            T wl[S];
+            load_row<S, T>(row, g.N, k[q], wl);
+            tk = stencil_apply<DIM, T>(wl, tile, lx[q], ly[q], lz[q]);
+        }
+        t_out[k[q]] = tk;
+        dot[0].add(tk, sk);
+        dot[1].add(tk, tk);
+        dot[2].add(sk, sk);
     }
-    block_partials<3, A>(dot, partials, pstride, blk);
+    dot_partials<3>(dot, partials, pstride, blockIdx.x);
     double tot[3];
     if (last_block_totals<3>(partials, pstride, gridDim.x, counter, tot) && tid == 0) {
         sc->ts = tot[0];
@@ -288,10 +567,15 @@ __global__ void __launch_bounds__(256) bicg_kb(TileArgs ta, const T *__restrict_
         if (tot[2] <= sc->tol2) { sc->s_conv = 1; return; }
         if (tot[1] == 0.0) { sc->done = 3; return; }
         sc->omega = tot[0] / tot[1];
+        publish(sc);
     }
 }
 
 // ---- KC: x += alpha p + omega s; r = s - omega t; partials r^.r, r.r -------
+// Each thread updates KC_VEC elements spaced by the grid size, so a warp's
+// loads stay coalesced and each thread keeps KC_VEC x 5 loads in flight.
+constexpr int KC_VEC = 4;
+
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) bicg_kc(int64_t N, T *__restrict__ x, T *__restrict__ r,
                                                const T *__restrict__ rhat, const T *__restrict__ p,
@@ -299,44 +583,62 @@ __global__ void __launch_bounds__(256) bicg_kc(int64_t N, T *__restrict__ x, T *
                                                Scalars *sc, double *partials, int pstride,
                                                unsigned int *counter, double eps_breakdown) {
     if (sc->done) return;
-    const T alpha = (T)sc->alpha, omega = (T)sc->omega;
+    const T alpha = ScalarOf<T>::alpha(sc), omega = ScalarOf<T>::omega(sc);
     const int sconv = sc->s_conv;
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    A dot[2] = {0, 0};
-    if (k < N) {
-        const T sk = s[k];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    DotAcc<T> dot[2];
+    T xv[KC_VEC], pv[KC_VEC], sv[KC_VEC], tv[KC_VEC], hv[KC_VEC];
+#pragma unroll
+    for (int u = 0; u < KC_VEC; ++u) {
+        const int64_t k = k0 + u * stride;
+        const bool in = k < N;
+        xv[u] = in ? x[k] : (T)0;
+        pv[u] = in ? p[k] : (T)0;
+        sv[u] = in ? s[k] : (T)0;
+        tv[u] = in ? t[k] : (T)0;
+        hv[u] = in ? rhat[k] : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < KC_VEC; ++u) {
+        const int64_t k = k0 + u * stride;
+        if (k >= N) continue;
         T rk;
         if (sconv) {
-            x[k] += alpha * p[k];
-            rk = sk;
+            x[k] = xv[u] + alpha * pv[u];
+            rk = sv[u];
         } else {
-            x[k] += alpha * p[k] + omega * sk;
-            rk = sk - omega * t[k];
+            x[k] = xv[u] + alpha * pv[u] + omega * sv[u];
+            rk = sv[u] - omega * tv[u];
         }
         r[k] = rk;
-        dot[0] = (A)rhat[k] * (A)rk;
-        dot[1] = (A)rk * (A)rk;
+        dot[0].add(hv[u], rk);
+        dot[1].add(rk, rk);
     }
-    block_partials<2, A>(dot, partials, pstride, blockIdx.x);
+    dot_partials<2>(dot, partials, pstride, blockIdx.x);
     double tot[2];
     if (last_block_totals<2>(partials, pstride, gridDim.x, counter, tot) && threadIdx.x == 0) {
         const double rho_new = tot[0], rr = tot[1];
         sc->rr = rr;
         sc->iter += 1;
         if (!isfinite(rho_new + rr)) { sc->done = 4; return; }
-        if (sconv || rr <= sc->tol2) { sc->done = 1; return; }
+        if (sconv) { sc->done = 1; return; }
+        sc->rho_prev = sc->rho;
+        sc->beta = (rho_new / sc->rho) * (sc->alpha / sc->omega);
+        sc->rho = rho_new;
+        publish(sc);
+        if (rr <= sc->tol2) { sc->done = 1; return; }
         if (sc->iter >= sc->max_iter) { sc->done = 2; return; }
         if (fabs(rho_new) <= eps_breakdown * sqrt(sc->rhat2 * rr)) {
             sc->restarts += 1;
-            if (sc->restarts > 50) { sc->done = 3; return; }
+            if (sc->restarts > 1000) { sc->done = 3; return; }
             sc->restart = 1;
             sc->rho = rr;
             sc->rhat2 = rr;
             sc->beta = 0.0;
+            publish(sc);
             return;
         }
-        sc->beta = (rho_new / sc->rho) * (sc->alpha / sc->omega);
-        sc->rho = rho_new;
     }
 }
 
@@ -347,7 +649,8 @@ template <int DIM>
 __global__ void __launch_bounds__(256) residual64(Geo g, const double *__restrict__ row, const double *__restrict__ b,
                                                   const double *__restrict__ x, double *__restrict__ r,
                                                   Scalars *sc, double *partials, int pstride,
-                                                  unsigned int *counter, double tol) {
+                                                  unsigned int *counter, double tol,
+                                                  const int8_t *__restrict__ excl) {
     constexpr int S = (DIM == 2) ? 9 : 27;
     const int64_t N = g.N;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -371,7 +674,7 @@ __global__ void __launch_bounds__(256) residual64(Geo g, const double *__restric
             acc += row[(int64_t)s * N + k] * x[j];
         }
         const double bk = b[k];
-        const double rk = bk - acc;
+        const double rk = (excl && excl[k] == KIND_NEUMANN) ? 0.0 : bk - acc;
         r[k] = rk;
         dot[0] = rk * rk;
         dot[1] = bk * bk;
@@ -389,54 +692,116 @@ __global__ void __launch_bounds__(256) residual64(Geo g, const double *__restric
         sc->omega = 1.0;
         sc->restart = 1;
         sc->s_conv = 0;
+        publish(sc);
         sc->tol2 = tol * tol * tot[1];
         if (!isfinite(tot[0] + tot[1])) sc->done = 4;
         else sc->done = (tot[0] <= sc->tol2) ? 1 : 0;
     }
 }
 
-// r32 = (float) r64, d = 0; primes the FP32 inner solve with relative
-// tolerance inner_tol on ||r32||.
-__global__ void __launch_bounds__(256) prep_inner(int64_t N, const double *__restrict__ r64, float *__restrict__ r32,
-                                                  float *__restrict__ d, Scalars *sc, double *partials,
-                                                  int pstride, unsigned int *counter, double inner_tol) {
+// Reliable update of the mixed solve (Sleijpen & van der Vorst, 1996): the
+// FP32 recursive residual is replaced by the true residual
+// r64 = b - A64 x64 of the FP64 iterate, r32 = (float) r64.  The search
+// direction p is kept; rho = r^.r32 and beta are recomputed from the new
+// residual.  `prime` (or a preceding ||s|| stop) restarts the recurrence
+// instead (r^ = r, p = r).  Stops (done = 1) when ||r64|| <= tol ||b||.
+template <int DIM>
+__global__ void __launch_bounds__(256) reliable_residual(Geo g, const double *__restrict__ row,
+                                                         const double *__restrict__ b,
+                                                         const double *__restrict__ x,
+                                                         const float *__restrict__ rhat,
+                                                         float *__restrict__ r32, Scalars *sc,
+                                                         double *partials, int pstride,
+                                                         unsigned int *counter, double tol, int prime,
+                                                         const int8_t *__restrict__ excl) {
+    constexpr int S = (DIM == 2) ? 9 : 27;
+    const int64_t N = g.N;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float dot[1] = {0.0f};
+    double dot[4] = {0.0, 0.0, 0.0, 0.0};
     if (k < N) {
-        const float rk = (float)r64[k];
-        r32[k] = rk;
-        d[k] = 0.0f;
+        int c[3] = {0, 0, 0};
+        c[0] = (int)(k % g.n[0]);
+        const int64_t rest = k / g.n[0];
+        if (DIM == 2) c[1] = (int)rest; else { c[1] = (int)(rest % g.n[1]); c[2] = (int)(rest / g.n[1]); }
+        double acc = 0.0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int ox = s % 3 - 1, oy = (s / 3) % 3 - 1, oz = s / 9 - 1;
+            const int gx = wrap_clamp(c[0] + ox, g.n[0], g.per[0]);
+            const int gy = wrap_clamp(c[1] + oy, g.n[1], g.per[1]);
+            int64_t j = (int64_t)gx + (int64_t)g.n[0] * gy;
+            if (DIM == 3) {
+                const int gz = wrap_clamp(c[2] + oz, g.n[2], g.per[2]);
+                j = (int64_t)gx + (int64_t)g.n[0] * ((int64_t)gy + (int64_t)g.n[1] * gz);
+            }
+            acc += row[(int64_t)s * N + k] * x[j];
+        }
+        const double bk = b[k];
+        const double rk = (excl && excl[k] == KIND_NEUMANN) ? 0.0 : bk - acc;
+        const float rf = (float)rk;
+        r32[k] = rf;
         dot[0] = rk * rk;
+        dot[1] = bk * bk;
+        dot[2] = (double)(rhat[k] * rf);
+        dot[3] = (double)(rf * rf);
     }
-    block_partials<1, float>(dot, partials, pstride, blockIdx.x);
-    double tot[1];
-    if (last_block_totals<1>(partials, pstride, gridDim.x, counter, tot) && threadIdx.x == 0) {
-        sc->rr = tot[0];
-        sc->rho = tot[0];
-        sc->rhat2 = tot[0];
-        sc->beta = 0.0;
-        sc->alpha = 1.0;
-        sc->omega = 1.0;
-        sc->restart = 1;
-        sc->s_conv = 0;
-        sc->tol2 = inner_tol * inner_tol * tot[0];
-        sc->done = (tot[0] == 0.0) ? 1 : 0;
+    block_partials<4, double>(dot, partials, pstride, blockIdx.x);
+    double tot[4];
+    if (last_block_totals<4>(partials, pstride, gridDim.x, counter, tot) && threadIdx.x == 0) {
+        sc->rr64 = tot[0];
+        sc->bb64 = tot[1];
+        sc->rr = tot[3];
+        sc->tol2 = tol * tol * tot[1];
+        if (!isfinite(tot[0] + tot[1])) { sc->done = 4; return; }
+        if (tot[0] <= sc->tol2) { sc->done = 1; return; }
+        sc->done = 0;
+        if (prime == 1 || sc->s_conv || sc->restart) {
+            sc->rho = tot[3];
+            sc->rhat2 = tot[3];
+            sc->beta = 0.0;
+            sc->alpha = 1.0;
+            sc->omega = 1.0;
+            sc->restart = 1;
+            sc->s_conv = 0;
+        } else if (prime == 2) {
+            // replace r only; rho and beta stay those of the recursion
+        } else {
+            sc->beta = (tot[2] / sc->rho_prev) * (sc->alpha / sc->omega);
+            sc->rho = tot[2];
+            if (!isfinite(sc->beta)) {
+                sc->rho = tot[3];
+                sc->rhat2 = tot[3];
+                sc->beta = 0.0;
+                sc->restart = 1;
+            }
+        }
+        publish(sc);
     }
 }
 
-__global__ void add_correction(int64_t N, double *__restrict__ x, const float *__restrict__ d) {
+// x64 += d32; d32 = 0 (fold the FP32 correction into the FP64 iterate).
+__global__ void fold_correction(int64_t N, double *__restrict__ x, float *__restrict__ d) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < N) x[k] += (double)d[k];
+    if (k < N) {
+        x[k] += (double)d[k];
+        d[k] = 0.0f;
+    }
 }
 
 // Dirichlet entries of the guess take their value (b = g there); void = 0.
+// Also counts the non-void DPs (the unknowns of the solve).
 __global__ void fix_guess(int64_t N, const int8_t *__restrict__ kind, const double *__restrict__ b,
-                          double *__restrict__ x) {
+                          double *__restrict__ x, Scalars *sc) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    const int8_t kd = kind[k];
-    if (kd == KIND_DIRICHLET) x[k] = b[k];
-    else if (kd == KIND_VOID) x[k] = 0.0;
+    int8_t kd = KIND_VOID;
+    if (k < N) {
+        kd = kind[k];
+        if (kd == KIND_DIRICHLET) x[k] = b[k];
+        else if (kd == KIND_VOID) x[k] = 0.0;
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, kd != KIND_VOID);
+    if ((threadIdx.x & 31) == 0 && ballot)
+        atomicAdd(&sc->unknowns, (unsigned long long)__popc(ballot));
 }
 
 static mcd_status ensure_workspace(mcd_stencils *st, int mode) {
@@ -467,6 +832,7 @@ static mcd_status ensure_workspace(mcd_stencils *st, int mode) {
         chk(cudaMalloc(&w->partials, 4 * (size_t)w->pstride * sizeof(double)));
         chk(cudaMalloc(&w->counter, sizeof(unsigned int)));
         chk(cudaMalloc(&w->sc, sizeof(Scalars)));
+        chk(cudaMalloc(&w->bar, sizeof(GridBarrier) + (size_t)w->pstride * sizeof(unsigned int)));
         chk(cudaMallocHost(&w->h_sc, sizeof(Scalars)));
         if (e == cudaSuccess) e = cudaMemset(w->counter, 0, sizeof(unsigned int));
         if (e != cudaSuccess) {
@@ -497,6 +863,7 @@ static mcd_status ensure_workspace(mcd_stencils *st, int mode) {
         chk(cudaMalloc(&w->fs, N * sizeof(float)));
         chk(cudaMalloc(&w->ft, N * sizeof(float)));
         chk(cudaMalloc(&w->fd, N * sizeof(float)));
+        if (e == cudaSuccess) e = cudaMemset(w->frh, 0, N * sizeof(float));
     }
     if (e != cudaSuccess) {
         set_error(std::string("solver vectors: ") + cudaGetErrorString(e));
@@ -508,6 +875,24 @@ static mcd_status ensure_workspace(mcd_stencils *st, int mode) {
 template <typename T> struct Vecs {
     T *x, *r, *rh, *p[2], *v[2], *s, *t;
 };
+
+static int sm_count() {
+    static const int n = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+        return v > 0 ? v : 1;
+    }();
+    return n;
+}
+
+template <typename K>
+static int occupancy(K kernel) {
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, 256, 0) != cudaSuccess || blocks < 1)
+        return 1;
+    return blocks;
+}
 
 // Launch `count` Bi-CGSTAB iterations (3 kernels each); parity selects the
 // p / v ping-pong buffers and is advanced.
@@ -521,14 +906,20 @@ static mcd_status launch_iters(const mcd_stencils *st, const T *row, Vecs<T> &vv
     ta.bx = (g.n[0] + Tile<DIM>::X - 1) / Tile<DIM>::X;
     ta.by = (g.n[1] + Tile<DIM>::Y - 1) / Tile<DIM>::Y;
     ta.bz = (DIM == 3) ? (g.n[2] + Tile<DIM>::Z - 1) / Tile<DIM>::Z : 1;
+    ta.ntiles = ta.bx * ta.by * ta.bz;
+    ta.kind = st->has_neumann ? st->kind : nullptr;
+    // one block per tile for KA / KB; KC threads take KC_VEC elements each
+    const int grid_a = ta.ntiles;
+    const int grid_b = ta.ntiles;
+    const int grid_c = (int)std::max<int64_t>(1, (g.N + 256 * KC_VEC - 1) / (256 * KC_VEC));
     for (int it = 0; it < count; ++it) {
         const int a = parity, b = parity ^ 1;
-        bicg_ka<DIM, T, A><<<w->nblk, 256, 0, stream>>>(ta, row, vv.r, vv.rh, vv.p[a], vv.v[a], vv.p[b],
-                                                        vv.v[b], w->sc, w->partials, w->pstride, w->counter);
-        bicg_kb<DIM, T, A><<<w->nblk, 256, 0, stream>>>(ta, row, vv.r, vv.v[b], vv.s, vv.t, w->sc,
-                                                        w->partials, w->pstride, w->counter);
-        bicg_kc<T, A><<<w->nblk1, 256, 0, stream>>>(g.N, vv.x, vv.r, vv.rh, vv.p[b], vv.s, vv.t, w->sc,
-                                                    w->partials, w->pstride, w->counter, eps_breakdown);
+        MCD_KLAUNCH(MCD_K_BICG_A, stream, bicg_ka<DIM, T, A><<<grid_a, 256, 0, stream>>>(ta, row, vv.r, vv.rh, vv.p[a], vv.v[a], vv.p[b],
+                                                        vv.v[b], w->sc, w->partials, w->pstride, w->counter));
+        MCD_KLAUNCH(MCD_K_BICG_B, stream, bicg_kb<DIM, T, A><<<grid_b, 256, 0, stream>>>(ta, row, vv.r, vv.v[b], vv.s, vv.t, w->sc,
+                                                        w->partials, w->pstride, w->counter));
+        MCD_KLAUNCH(MCD_K_BICG_C, stream, bicg_kc<T, A><<<grid_c, 256, 0, stream>>>(g.N, vv.x, vv.r, vv.rh, vv.p[b], vv.s, vv.t, w->sc,
+                                                    w->partials, w->pstride, w->counter, eps_breakdown));
         parity = b;
     }
     MCD_LAUNCH_CHECK();
@@ -566,13 +957,787 @@ static mcd_status run_krylov(const mcd_stencils *st, const T *row, Vecs<T> &vv, 
     }
 }
 
+// FP64 residual b - A x; with `interior` set the Neumann rows are left out
+// (their residual reads 0), which is the residual of the interior block.
 template <int DIM>
-static mcd_status residual(const mcd_stencils *st, const double *x, double tol, cudaStream_t stream) {
+static mcd_status residual(const mcd_stencils *st, const double *x, double tol, int interior,
+                           cudaStream_t stream) {
     Workspace *w = st->ws;
-    residual64<DIM><<<w->nblk1, 256, 0, stream>>>(st->geo, st->row64, w->b, x, w->r64, w->sc, w->partials,
-                                                  w->pstride, w->counter, tol);
+    const int8_t *excl = (interior && st->has_neumann) ? st->kind : nullptr;
+    MCD_KLAUNCH(MCD_K_RESIDUAL, stream, residual64<DIM><<<w->nblk1, 256, 0, stream>>>(st->geo, st->row64, w->b, x, w->r64, w->sc, w->partials,
+                                                  w->pstride, w->counter, tol, excl));
     MCD_LAUNCH_CHECK();
     return MCD_OK;
+}
+
+// One Jacobi sweep on the Neumann rows: delta_k = (b_k - (A x)_k) / a_kk for
+// Neumann DPs (reads x only), then x += delta.  The Neumann block is strongly
+// diagonally dominant (its rows are scaled to diagonal -1/r_s^2 and couple to
+// other Neumann DPs only through nearly tangential neighbours), so a few
+// sweeps solve it to rounding once the interior values are final.
+template <int DIM>
+__global__ void neumann_delta(Geo g, const double *__restrict__ row, const int8_t *__restrict__ kind,
+                              const double *__restrict__ b, const double *__restrict__ x,
+                              double *__restrict__ delta) {
+    constexpr int S = (DIM == 2) ? 9 : 27;
+    const int64_t N = g.N;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N || kind[k] != KIND_NEUMANN) return;
+    int c[3] = {0, 0, 0};
+    c[0] = (int)(k % g.n[0]);
+    const int64_t rest = k / g.n[0];
+    if (DIM == 2) c[1] = (int)rest; else { c[1] = (int)(rest % g.n[1]); c[2] = (int)(rest / g.n[1]); }
+    double acc = 0.0;
+    for (int s = 0; s < S; ++s) {
+        const int gx = wrap_clamp(c[0] + s % 3 - 1, g.n[0], g.per[0]);
+        const int gy = wrap_clamp(c[1] + (s / 3) % 3 - 1, g.n[1], g.per[1]);
+        int64_t j = (int64_t)gx + (int64_t)g.n[0] * gy;
+        if (DIM == 3) {
+            const int gz = wrap_clamp(c[2] + s / 9 - 1, g.n[2], g.per[2]);
+            j = (int64_t)gx + (int64_t)g.n[0] * ((int64_t)gy + (int64_t)g.n[1] * gz);
+        }
+        acc += row[(int64_t)s * N + k] * x[j];
+    }
+    delta[k] = (b[k] - acc) / row[(int64_t)(S / 2) * N + k];
+}
+
+__global__ void neumann_apply(int64_t N, const int8_t *__restrict__ kind, const double *__restrict__ delta,
+                              double *__restrict__ x) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N && kind[k] == KIND_NEUMANN) x[k] += delta[k];
+}
+
+template <int DIM>
+static mcd_status neumann_sweeps(const mcd_stencils *st, double *x, int sweeps, cudaStream_t stream) {
+    Workspace *w = st->ws;
+    const int64_t N = st->geo.N;
+    for (int i = 0; i < sweeps; ++i) {
+        MCD_KLAUNCH(MCD_K_OTHER, stream, neumann_delta<DIM><<<w->nblk1, 256, 0, stream>>>(st->geo, st->row64, st->kind,
+                                                                                         w->b, x, w->r64));
+        MCD_KLAUNCH(MCD_K_OTHER, stream, neumann_apply<<<w->nblk1, 256, 0, stream>>>(N, st->kind, w->r64, x));
+    }
+    MCD_LAUNCH_CHECK();
+    return MCD_OK;
+}
+
+template <int DIM>
+static mcd_status reliable_update(const mcd_stencils *st, double *x, double tol, int prime,
+                                  cudaStream_t stream) {
+    Workspace *w = st->ws;
+    const int64_t N = st->geo.N;
+    MCD_KLAUNCH(MCD_K_OTHER, stream, fold_correction<<<w->nblk1, 256, 0, stream>>>(N, x, w->fd));
+    MCD_KLAUNCH(MCD_K_RESIDUAL, stream,
+                reliable_residual<DIM><<<w->nblk1, 256, 0, stream>>>(st->geo, st->row64, w->b, x, w->frh, w->fr,
+                                                                     w->sc, w->partials, w->pstride, w->counter,
+                                                                     tol, prime,
+                                                                     st->has_neumann ? st->kind : nullptr));
+    MCD_LAUNCH_CHECK();
+    return read_scalars(w, stream);
+}
+
+// Mixed solve: FP32 Bi-CGSTAB on the FP32 rows whose iterate d32 is folded
+// into the FP64 solution x, with reliable updates.  At each host check the
+// recursive FP32 residual is compared with the last true residual; once it
+// has fallen by the factor `update` (or the recursion claims convergence),
+// x += d32 and the FP64 residual b - A64 x replaces the FP32 one.  The solve
+// ends when that FP64 residual meets tol.  `updates` counts the reliable
+// updates after the first.
+template <int DIM>
+static mcd_status run_mixed(const mcd_stencils *st, double *x, const mcd_solve_params *prm,
+                            int check_every, int max_launch, int &updates, mcd_status &result,
+                            cudaStream_t stream) {
+    Workspace *w = st->ws;
+    const int64_t N = st->geo.N;
+    const double update = prm->inner_tol;
+    MCD_CUDA_TRY(cudaMemsetAsync(w->fd, 0, N * sizeof(float), stream));
+    mcd_status s = reliable_update<DIM>(st, x, prm->tol, 1, stream);
+    if (s != MCD_OK) return s;
+    updates = 0;
+    if (w->h_sc->done == 4) { result = MCD_ENONFINITE; return MCD_OK; }
+    if (w->h_sc->done == 1) { result = MCD_OK; return MCD_OK; }
+    double rr_last = w->h_sc->rr;
+    Vecs<float> vv{w->fd, w->fr, w->frh, {w->fp[0], w->fp[1]}, {w->fv[0], w->fv[1]}, w->fs, w->ft};
+    int parity = 0, chunk = 4, launched = 0;
+    for (;;) {
+        // compensated dots keep rho meaningful far below FP32 epsilon
+        s = launch_iters<DIM, float, float>(st, st->row32, vv, parity, chunk, 1e-12, stream);
+        if (s != MCD_OK) return s;
+        launched += chunk;
+        s = read_scalars(w, stream);
+        if (s != MCD_OK) return s;
+        const Scalars &h = *w->h_sc;
+        if (h.done == 3) { result = MCD_EBREAKDOWN; return MCD_OK; }
+        if (h.done == 4) { result = MCD_ENONFINITE; return MCD_OK; }
+        const bool want = h.done == 1 || h.done == 2 || h.s_conv || h.rr <= update * update * rr_last;
+        if (want) {
+            const int was_max = (h.done == 2);
+            s = reliable_update<DIM>(st, x, prm->tol,
+                                     prm->update_restart == 1 ? 1 : (prm->update_restart == 2 ? 2 : 0), stream);
+            if (s != MCD_OK) return s;
+            ++updates;
+            if (w->h_sc->done == 1) { result = MCD_OK; return MCD_OK; }
+            if (w->h_sc->done == 4) { result = MCD_ENONFINITE; return MCD_OK; }
+            if (was_max || w->h_sc->iter >= w->h_sc->max_iter) { result = MCD_ENOCONV; return MCD_OK; }
+            rr_last = w->h_sc->rr;
+            // a restarted recurrence reads p only through the restart branch,
+            // so the ping-pong parity need not change
+        }
+        if (launched >= max_launch) {
+            set_error("Krylov loop exceeded its launch budget without a device status");
+            result = MCD_ENOCONV;
+            return MCD_OK;
+        }
+        chunk = std::min(chunk * 2, check_every);
+    }
+}
+
+// ===========================================================================
+// Persistent solver: one cooperative launch runs Bi-CGSTAB iterations, the
+// true-residual (reliable) updates and the convergence test on the device.
+// Every block owns `tpb` tiles for the whole launch.  The three reductions
+// of an iteration are finished at grid barriers: each block writes its
+// partial sums, the last block to arrive adds them in block order (so results
+// are deterministic), updates the scalars and releases the others.  Waiting
+// blocks spin on a generation counter with a bounded number of polls; a
+// block that gives up records the timeout and leaves, and so do the others,
+// so the launch always ends.
+// ===========================================================================
+
+struct PArgs {
+    TileArgs ta;
+    int tpb;                 // tiles per block
+    const void *row;         // T rows of the recursion
+    const double *row64;     // FP64 rows (true residual)
+    const double *b;         // FP64 right-hand side
+    double *x64;             // FP64 solution
+    void *x, *r, *rh, *p0, *p1, *v0, *v1, *s, *t;   // T vectors (x = correction in MIXED)
+    Scalars *sc;
+    double *partials;
+    int pstride;
+    GridBarrier *bar;
+    int mixed;               // 1: fold x into x64 at every true-residual update
+    int update_mode;         // 1: restart the recursion at every update
+    double update2;          // MIXED: update once rr <= update2 * rr_last
+    double tol;
+    double eps_breakdown;
+    int iter_budget;         // iterations this launch may run
+    long long spin_limit;
+    unsigned long long *trace;   // non-NULL: block 0 stamps phase times here
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Phase timestamps of block 0 for the first 64 iterations of a launch:
+// slots 0 start, 1 A done, 2 A reduced, 3 B done, 4 B reduced, 5 C done,
+// 6 C reduced.
+__device__ __forceinline__ void stamp(const PArgs &a, int it, int slot) {
+    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && it < 64) a.trace[it * 8 + slot] = global_ns();
+}
+
+// Per-block stamp of iteration 10: phase A done time and the block's SM.
+__device__ __forceinline__ void stamp_block(const PArgs &a, int it) {
+    if (a.trace && threadIdx.x == 0 && it == 10 && blockIdx.x < 2048) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        a.trace[512 + blockIdx.x] = global_ns();
+        a.trace[512 + 2048 + blockIdx.x] = smid;
+    }
+}
+
+template <typename F>
+__device__ __forceinline__ F vload(const F *p) {
+    return *((volatile const F *)p);
+}
+
+// Grid barrier that finishes the NV-value reduction: returns false if a wait
+// gave up.  Every block writes its partial sums and then its arrival flag
+// (a plain release store: no atomics on a shared word).  Block 0 polls all
+// flags with its 256 threads, adds the partials in block order, runs `last`
+// on thread 0 with the totals, and publishes the epoch on the release word,
+// which the other blocks poll.  `epoch` counts the barriers of this launch.
+template <int NV, typename Acc, typename Last>
+__device__ bool grid_reduce(const PArgs &a, unsigned &epoch, Acc (&d)[NV], Last last) {
+    __shared__ int s_err;
+    __shared__ double s_tot[NV];
+    const int tid = threadIdx.x;
+    ++epoch;
+    dot_partials<NV>(d, a.partials, a.pstride, blockIdx.x);
+    if (tid == 0) s_err = 0;
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        *((volatile unsigned *)&a.bar->flag[blockIdx.x]) = epoch;
+    }
+    if (blockIdx.x == 0) {
+        // wait for every block's flag (each thread a strided subset)
+        for (int b = tid; b < (int)gridDim.x; b += 256) {
+            long long polls = 0;
+            while (vload(&a.bar->flag[b]) != epoch) {
+                if (++polls > a.spin_limit) { s_err = 1; break; }
+                __nanosleep(32);
+            }
+        }
+        __syncthreads();
+        if (s_err) {
+            if (tid == 0) a.sc->phase_err = 1;
+            return false;
+        }
+        __threadfence();
+        double acc[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+        for (int b0 = tid; b0 < (int)gridDim.x; b0 += 4 * 256) {
+            double v[NV][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int bb = b0 + u * 256;
+#pragma unroll
+                for (int q = 0; q < NV; ++q)
+                    v[q][u] = (bb < (int)gridDim.x) ? __ldcg(a.partials + q * a.pstride + bb) : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < NV; ++q) acc[q] += (v[q][0] + v[q][1]) + (v[q][2] + v[q][3]);
+        }
+        __shared__ double red[NV][8];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
+            if ((tid & 31) == 0) red[q][tid >> 5] = acc[q];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int q = 0; q < NV; ++q) {
+                double x = 0.0;
+                for (int w = 0; w < 8; ++w) x += red[q][w];
+                s_tot[q] = x;
+            }
+            last(s_tot);
+            __threadfence();
+            *((volatile unsigned *)&a.bar->release) = epoch;
+        }
+    } else if (tid == 0) {
+        long long polls = 0;
+        while (vload(&a.bar->release) != epoch) {
+            if (++polls > a.spin_limit) {
+                s_err = 1;
+                a.sc->phase_err = 1;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return !s_err;
+}
+
+// Phase A over the block's tiles: p = r + beta (p_old - omega v_old) (or
+// p = r on a restart, with r^ = r) on tile + halo, v = A p.
+// Dots: r^.v, and on a restart r^.r and r^.r^.
+template <int DIM, typename T>
+__device__ void phase_a(const PArgs &a, T *tile, const T *p_old, const T *v_old, T *p_new, T *v_new,
+                        T beta, T omega, int restart, DotAcc<T> (&dot)[3]) {
+    using HD = HaloDims<DIM>;
+    using TL = Tile<DIM>;
+    constexpr int S = HD::S;
+    constexpr bool PREF = (S == 9);
+    constexpr int HN = (HD::H + 255) / 256;
+    const Geo &g = a.ta.g;
+    const T *row = (const T *)a.row;
+    const T *r = (const T *)a.r;
+    T *rhat = (T *)a.rh;
+    const int tid = threadIdx.x;
+    for (int i = 0; i < a.tpb; ++i) {
+        const int tl = blockIdx.x * a.tpb + i;
+        if (tl >= a.ta.ntiles) break;
+        int x0, y0, z0;
+        tile_origin<DIM>(a.ta, tl, x0, y0, z0);
+        int64_t k[TL::R];
+        int lx[TL::R], ly[TL::R], lz[TL::R];
+        T w[TL::R][PREF ? S : 1];
+        T rh[TL::R];
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            k[q] = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+            if (PREF) load_row<S, T>(row, g.N, k[q], w[q]);
+            rh[q] = (!restart && k[q] >= 0) ? __ldcg(rhat + k[q]) : (T)0;
+        }
+        // all halo loads of the tile are issued before any is consumed
+        T hr[HN], hp[HN], hv[HN];
+#pragma unroll
+        for (int u = 0; u < HN; ++u) {
+            const int h = tid + u * 256;
+            hr[u] = hp[u] = hv[u] = (T)0;
+            if (h < HD::H) {
+                const int64_t j = halo_index<DIM>(g, h, x0, y0, z0);
+                hr[u] = __ldcg(r + j);
+                if (!restart) {
+                    hp[u] = __ldcg(p_old + j);
+                    hv[u] = __ldcg(v_old + j);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < HN; ++u) {
+            const int h = tid + u * 256;
+            if (h < HD::H) tile[h] = restart ? hr[u] : hr[u] + beta * (hp[u] - omega * hv[u]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            if (k[q] < 0) continue;
+            const T pk = tile[tile_centre<DIM>(lx[q], ly[q], lz[q])];
+            p_new[k[q]] = pk;
+            T rq = rh[q];
+            if (restart) {
+                rq = pk;   // pk = r[k] on a restart
+                rhat[k[q]] = rq;
+                dot[1].add(rq, pk);
+                dot[2].add(rq, rq);
+            }
+            T vk;
+            if (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN) {
+                vk = pk;
+            } else if (PREF) {
+                vk = stencil_apply<DIM, T>(w[q], tile, lx[q], ly[q], lz[q]);
+            } else {
+                T wl[S];
+                load_row<S, T>(row, g.N, k[q], wl);
+                vk = stencil_apply<DIM, T>(wl, tile, lx[q], ly[q], lz[q]);
+            }
+            v_new[k[q]] = vk;
+            dot[0].add(rq, vk);
+        }
+        __syncthreads();
+    }
+}
+
+// Phase B: s = r - alpha v (tile + halo), t = A s; dots t.s, t.t, s.s.
+template <int DIM, typename T>
+__device__ void phase_b(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T> (&dot)[3]) {
+    using HD = HaloDims<DIM>;
+    using TL = Tile<DIM>;
+    constexpr int S = HD::S;
+    constexpr bool PREF = (S == 9);
+    constexpr int HN = (HD::H + 255) / 256;
+    const Geo &g = a.ta.g;
+    const T *row = (const T *)a.row;
+    const T *r = (const T *)a.r;
+    T *s_out = (T *)a.s;
+    T *t_out = (T *)a.t;
+    const int tid = threadIdx.x;
+    for (int i = 0; i < a.tpb; ++i) {
+        const int tl = blockIdx.x * a.tpb + i;
+        if (tl >= a.ta.ntiles) break;
+        int x0, y0, z0;
+        tile_origin<DIM>(a.ta, tl, x0, y0, z0);
+        int64_t k[TL::R];
+        int lx[TL::R], ly[TL::R], lz[TL::R];
+        T w[TL::R][PREF ? S : 1];
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            k[q] = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+            if (PREF) load_row<S, T>(row, g.N, k[q], w[q]);
+        }
+        T hr[HN], hv[HN];
+#pragma unroll
+        for (int u = 0; u < HN; ++u) {
+            const int h = tid + u * 256;
+            hr[u] = hv[u] = (T)0;
+            if (h < HD::H) {
+                const int64_t j = halo_index<DIM>(g, h, x0, y0, z0);
+                hr[u] = __ldcg(r + j);
+                hv[u] = __ldcg(v + j);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < HN; ++u) {
+            const int h = tid + u * 256;
+            if (h < HD::H) tile[h] = hr[u] - alpha * hv[u];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            if (k[q] < 0) continue;
+            const T sk = tile[tile_centre<DIM>(lx[q], ly[q], lz[q])];
+            s_out[k[q]] = sk;
+            T tk;
+            if (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN) {
+                tk = sk;
+            } else if (PREF) {
+                tk = stencil_apply<DIM, T>(w[q], tile, lx[q], ly[q], lz[q]);
+            } else {
+                T wl[S];
+                load_row<S, T>(row, g.N, k[q], wl);
+                tk = stencil_apply<DIM, T>(wl, tile, lx[q], ly[q], lz[q]);
+            }
+            t_out[k[q]] = tk;
+            dot[0].add(tk, sk);
+            dot[1].add(tk, tk);
+            dot[2].add(sk, sk);
+        }
+        __syncthreads();
+    }
+}
+
+// Phase C (the block's own DPs): x += alpha p + omega s, r = s - omega t (or
+// x += alpha p, r = s after an ||s|| stop); dots r^.r, r.r.
+template <int DIM, typename T>
+__device__ void phase_c(const PArgs &a, const T *p, T alpha, T omega, int sconv, DotAcc<T> (&dot)[2]) {
+    using TL = Tile<DIM>;
+    const Geo &g = a.ta.g;
+    T *x = (T *)a.x;
+    T *r = (T *)a.r;
+    const T *rhat = (const T *)a.rh;
+    const T *s = (const T *)a.s;
+    const T *t = (const T *)a.t;
+    const int tid = threadIdx.x;
+    for (int i = 0; i < a.tpb; ++i) {
+        const int tl = blockIdx.x * a.tpb + i;
+        if (tl >= a.ta.ntiles) break;
+        int x0, y0, z0;
+        tile_origin<DIM>(a.ta, tl, x0, y0, z0);
+        int64_t k[TL::R];
+        T xv[TL::R], pv[TL::R], sv[TL::R], tv[TL::R], hv[TL::R];
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            int lx, ly, lz;
+            k[q] = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx, ly, lz);
+            const bool in = k[q] >= 0;
+            xv[q] = in ? __ldcg(x + k[q]) : (T)0;
+            pv[q] = in ? __ldcg(p + k[q]) : (T)0;
+            sv[q] = in ? __ldcg(s + k[q]) : (T)0;
+            tv[q] = in ? __ldcg(t + k[q]) : (T)0;
+            hv[q] = in ? __ldcg(rhat + k[q]) : (T)0;
+        }
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            if (k[q] < 0) continue;
+            T rk;
+            if (sconv) {
+                x[k[q]] = xv[q] + alpha * pv[q];
+                rk = sv[q];
+            } else {
+                x[k[q]] = xv[q] + alpha * pv[q] + omega * sv[q];
+                rk = sv[q] - omega * tv[q];
+            }
+            r[k[q]] = rk;
+            dot[0].add(hv[q], rk);
+            dot[1].add(rk, rk);
+        }
+    }
+}
+
+// Fold (MIXED): x64 += x; x = 0 over the block's own DPs.
+template <int DIM, typename T>
+__device__ void phase_fold(const PArgs &a) {
+    using TL = Tile<DIM>;
+    const Geo &g = a.ta.g;
+    T *x = (T *)a.x;
+    const int tid = threadIdx.x;
+    for (int i = 0; i < a.tpb; ++i) {
+        const int tl = blockIdx.x * a.tpb + i;
+        if (tl >= a.ta.ntiles) break;
+        int x0, y0, z0;
+        tile_origin<DIM>(a.ta, tl, x0, y0, z0);
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            int lx, ly, lz;
+            const int64_t k = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx, ly, lz);
+            if (k < 0) continue;
+            a.x64[k] += (double)__ldcg(x + k);
+            x[k] = (T)0;
+        }
+    }
+}
+
+// True residual r64 = b - A64 x64 (FP64 matrix form) of the block's DPs,
+// stored in the recursion's precision; Neumann rows read 0 (interior block).
+// Dots ||r64||^2, ||b||^2, r^.r, r.r.
+template <int DIM, typename T>
+__device__ void phase_true_residual(const PArgs &a, DotAcc<double> (&d64)[2], DotAcc<T> (&dt)[2]) {
+    using TL = Tile<DIM>;
+    constexpr int S = (DIM == 2) ? 9 : 27;
+    const Geo &g = a.ta.g;
+    T *r = (T *)a.r;
+    const T *rhat = (const T *)a.rh;
+    const int tid = threadIdx.x;
+    for (int i = 0; i < a.tpb; ++i) {
+        const int tl = blockIdx.x * a.tpb + i;
+        if (tl >= a.ta.ntiles) break;
+        int x0, y0, z0;
+        tile_origin<DIM>(a.ta, tl, x0, y0, z0);
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            int lx, ly, lz;
+            const int64_t k = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx, ly, lz);
+            if (k < 0) continue;
+            const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+            double acc = 0.0;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const int jx = wrap_clamp(gx + s % 3 - 1, g.n[0], g.per[0]);
+                const int jy = wrap_clamp(gy + (s / 3) % 3 - 1, g.n[1], g.per[1]);
+                int64_t j = (int64_t)jx + (int64_t)g.n[0] * jy;
+                if (DIM == 3) {
+                    const int jz = wrap_clamp(gz + s / 9 - 1, g.n[2], g.per[2]);
+                    j = (int64_t)jx + (int64_t)g.n[0] * ((int64_t)jy + (int64_t)g.n[1] * jz);
+                }
+                acc += __ldg(a.row64 + (int64_t)s * g.N + k) * __ldcg(a.x64 + j);
+            }
+            const double bk = a.b[k];
+            const double rk = (a.ta.kind && a.ta.kind[k] == KIND_NEUMANN) ? 0.0 : bk - acc;
+            const T rt = (T)rk;
+            r[k] = rt;
+            d64[0].add(rk, rk);
+            d64[1].add(bk, bk);
+            dt[0].add(__ldcg(rhat + k), rt);
+            dt[1].add(rt, rt);
+        }
+    }
+}
+
+// Main loop: the textbook Bi-CGSTAB iteration (rho = r^.r computed
+// directly each iteration), three grid reductions per iteration.  A
+// true-residual update follows recursive convergence, an ||s|| stop,
+// max_iter, and (MIXED) a fall of the recursive residual by the factor
+// sqrt(update2) since the last update.  update_mode 1 restarts the recursion
+// after each update; update_mode 2 replaces r only and keeps rho and beta
+// (the reliable update of Sleijpen and van der Vorst, 1996).
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) bicg_persistent(PArgs a) {
+    using HD = HaloDims<DIM>;
+    __shared__ T tile[HD::H];
+    Scalars *sc = a.sc;
+    int iters = 0;
+    unsigned epoch = 0;
+    for (;;) {
+        if (vload(&sc->done) || vload(&sc->phase_err)) return;
+        if (vload(&sc->pending)) {
+            // ---- true residual (reliable) update ----------------------------
+            if (a.mixed) {
+                phase_fold<DIM, T>(a);
+                DotAcc<double> none[1];
+                if (!grid_reduce<1>(a, epoch, none, [&](double *) {})) return;
+            }
+            DotAcc<double> d64[2];
+            DotAcc<T> dt[2];
+            phase_true_residual<DIM, T>(a, d64, dt);
+            DotAcc<double> all[4];
+            all[0].v = d64[0].v;
+            all[1].v = d64[1].v;
+            if constexpr (sizeof(T) == 4) {
+                all[2].v = (double)dt[0].v.hi + (double)dt[0].v.lo;
+                all[3].v = (double)dt[1].v.hi + (double)dt[1].v.lo;
+            } else {
+                all[2].v = dt[0].v;
+                all[3].v = dt[1].v;
+            }
+            const double tol = a.tol;
+            const int mode = a.update_mode;
+            if (!grid_reduce<4>(a, epoch, all, [&](double *tot) {
+                    sc->rr64 = tot[0];
+                    sc->bb64 = tot[1];
+                    sc->rr = tot[3];
+                    sc->tol2 = tol * tol * tot[1];
+                    sc->pending = 0;
+                    if (!isfinite(tot[0] + tot[1])) { sc->done = 4; return; }
+                    if (tot[0] <= sc->tol2) { sc->done = 1; return; }
+                    if (sc->max_hit) { sc->done = 2; return; }
+                    sc->rr_last = tot[3];
+                    if (mode == 1 || sc->restart || sc->s_conv || !sc->iter) {
+                        sc->restart = 1;
+                        sc->s_conv = 0;
+                        sc->alpha = sc->beta = sc->omega = 0.0;
+                    }
+                    publish(sc);
+                }))
+                return;
+            continue;
+        }
+        if (iters >= a.iter_budget) return;
+        const int it = iters;
+        ++iters;
+        stamp(a, it, 0);
+        const int par = vload(&sc->parity);
+        T *p_old = (T *)(par ? a.p1 : a.p0), *p_new = (T *)(par ? a.p0 : a.p1);
+        T *v_old = (T *)(par ? a.v1 : a.v0), *v_new = (T *)(par ? a.v0 : a.v1);
+        // ---- phase A: p, v = A p, alpha ------------------------------------
+        {
+            const int restart = vload(&sc->restart);
+            T beta, omega;
+            if constexpr (sizeof(T) == 4) { beta = vload(&sc->beta_f); omega = vload(&sc->omega_f); }
+            else { beta = (T)vload(&sc->beta); omega = (T)vload(&sc->omega); }
+            DotAcc<T> dot[3];
+            phase_a<DIM, T>(a, tile, p_old, v_old, p_new, v_new, beta, omega, restart, dot);
+            stamp(a, it, 1);
+            stamp_block(a, it);
+            if (!grid_reduce<3>(a, epoch, dot, [&](double *tot) {
+                    sc->rv = tot[0];
+                    if (restart) {
+                        sc->rho = tot[1];
+                        sc->rhat2 = tot[2];
+                    }
+                    sc->restart = 0;
+                    const double alpha = sc->rho / tot[0];
+                    if (!isfinite(alpha) || alpha == 0.0) { sc->done = 3; return; }
+                    sc->alpha = alpha;
+                    publish(sc);
+                }))
+                return;
+            stamp(a, it, 2);
+        }
+        if (vload(&sc->done)) continue;
+        // ---- phase B: s, t = A s, omega ------------------------------------
+        {
+            T alpha;
+            if constexpr (sizeof(T) == 4) alpha = vload(&sc->alpha_f);
+            else alpha = (T)vload(&sc->alpha);
+            DotAcc<T> dot[3];
+            phase_b<DIM, T>(a, tile, v_new, alpha, dot);
+            stamp(a, it, 3);
+            if (!grid_reduce<3>(a, epoch, dot, [&](double *tot) {
+                    sc->ts = tot[0];
+                    sc->tt = tot[1];
+                    sc->ss = tot[2];
+                    if (!isfinite(tot[0] + tot[1] + tot[2])) { sc->done = 4; return; }
+                    if (tot[2] <= sc->tol2) { sc->s_conv = 1; return; }
+                    if (tot[1] == 0.0) { sc->done = 3; return; }
+                    sc->omega = tot[0] / tot[1];
+                    publish(sc);
+                }))
+                return;
+            stamp(a, it, 4);
+        }
+        if (vload(&sc->done)) continue;
+        // ---- phase C: x, r, beta and the tests ------------------------------
+        {
+            T alpha, omega;
+            if constexpr (sizeof(T) == 4) { alpha = vload(&sc->alpha_f); omega = vload(&sc->omega_f); }
+            else { alpha = (T)vload(&sc->alpha); omega = (T)vload(&sc->omega); }
+            const int sconv = vload(&sc->s_conv);
+            DotAcc<T> dot[2];
+            phase_c<DIM, T>(a, p_new, alpha, omega, sconv, dot);
+            stamp(a, it, 5);
+            const double eps = a.eps_breakdown;
+            const double update2 = a.update2;
+            const int mixed = a.mixed;
+            if (!grid_reduce<2>(a, epoch, dot, [&](double *tot) {
+                    const double rho_new = tot[0], rr = tot[1];
+                    sc->rr = rr;
+                    sc->iter += 1;
+                    sc->parity ^= 1;
+                    if (!isfinite(rho_new + rr)) { sc->done = 4; return; }
+                    if (sconv) { sc->pending = 1; return; }
+                    sc->rho_prev = sc->rho;
+                    sc->beta = (rho_new / sc->rho) * (sc->alpha / sc->omega);
+                    sc->rho = rho_new;
+                    publish(sc);
+                    if (rr <= sc->tol2) { sc->pending = 1; return; }
+                    if (sc->iter >= sc->max_iter) { sc->max_hit = 1; sc->pending = 1; return; }
+                    if (mixed && rr <= update2 * sc->rr_last) { sc->pending = 1; return; }
+                    if (fabs(rho_new) <= eps * sqrt(sc->rhat2 * rr)) {
+                        sc->restarts += 1;
+                        if (sc->restarts > 1000) { sc->done = 3; return; }
+                        sc->restart = 1;
+                    }
+                }))
+                return;
+            stamp(a, it, 6);
+        }
+    }
+}
+
+// Grid of the persistent launch: as many blocks as can be resident, each
+// owning the same number of tiles.
+template <int DIM, typename T>
+static int persistent_grid(int ntiles, int &tpb) {
+    static const int occ = occupancy(bicg_persistent<DIM, T>);
+    const int maxg = std::max(1, occ * sm_count());
+    tpb = (ntiles + maxg - 1) / maxg;
+    return (ntiles + tpb - 1) / tpb;
+}
+
+// Run the whole solve in persistent launches (each bounded by an iteration
+// budget and the barrier spin limit).  On return w->h_sc holds the final
+// scalars.  x64 is the FP64 solution; in FP64 mode it is also the iterate.
+// Phase trace buffer (instrumentation; NULL unless mcd_trace_enable(1)).
+static unsigned long long *g_trace = nullptr;
+
+template <int DIM, typename T>
+static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_solve_params *prm,
+                                 mcd_status &result, cudaStream_t stream) {
+    Workspace *w = st->ws;
+    const Geo &g = st->geo;
+    const bool mixed = sizeof(T) == 4;
+    PArgs a;
+    a.ta.g = g;
+    a.ta.bx = (g.n[0] + Tile<DIM>::X - 1) / Tile<DIM>::X;
+    a.ta.by = (g.n[1] + Tile<DIM>::Y - 1) / Tile<DIM>::Y;
+    a.ta.bz = (DIM == 3) ? (g.n[2] + Tile<DIM>::Z - 1) / Tile<DIM>::Z : 1;
+    a.ta.ntiles = a.ta.bx * a.ta.by * a.ta.bz;
+    a.ta.kind = st->has_neumann ? st->kind : nullptr;
+    const int grid = persistent_grid<DIM, T>(a.ta.ntiles, a.tpb);
+    a.row64 = st->row64;
+    a.b = w->b;
+    a.x64 = x64;
+    if (mixed) {
+        a.row = st->row32;
+        a.x = w->fd; a.r = w->fr; a.rh = w->frh;
+        a.p0 = w->fp[0]; a.p1 = w->fp[1]; a.v0 = w->fv[0]; a.v1 = w->fv[1];
+        a.s = w->fs; a.t = w->ft;
+        MCD_CUDA_TRY(cudaMemsetAsync(w->fd, 0, g.N * sizeof(float), stream));
+    } else {
+        a.row = st->row64;
+        a.x = x64; a.r = w->dr; a.rh = w->drh;
+        a.p0 = w->dp[0]; a.p1 = w->dp[1]; a.v0 = w->dv[0]; a.v1 = w->dv[1];
+        a.s = w->ds; a.t = w->dt;
+    }
+    a.sc = w->sc;
+    a.partials = w->partials;
+    a.pstride = w->pstride;
+    a.bar = w->bar;
+    a.mixed = mixed ? 1 : 0;
+    a.update_mode = mixed ? (prm->update_restart == 2 ? 2 : 1) : 1;
+    const double upd = (prm->inner_tol > 0.0 && prm->inner_tol < 1.0) ? prm->inner_tol : 0.1;
+    a.update2 = upd * upd;
+    a.tol = prm->tol;
+    a.eps_breakdown = mixed ? 1e-12 : 1e-14;
+    a.iter_budget = 4096;
+    a.spin_limit = 1ll << 24;   // about 1 s of polls at 64 ns per poll
+    a.trace = g_trace;
+    const size_t bar_bytes = sizeof(GridBarrier) + (size_t)grid * sizeof(unsigned int);
+    // start with a true-residual update of the initial guess
+    int one = 1;
+    MCD_CUDA_TRY(cudaMemcpyAsync(&w->sc->pending, &one, sizeof(int), cudaMemcpyHostToDevice, stream));
+    MCD_CUDA_TRY(cudaMemcpyAsync(&w->sc->restart, &one, sizeof(int), cudaMemcpyHostToDevice, stream));
+    const int max_launch = std::max(2, prm->max_iter / a.iter_budget + 8);
+    for (int launch = 0;; ++launch) {
+        void *args[] = {&a};
+        MCD_CUDA_TRY(cudaMemsetAsync(w->bar, 0, bar_bytes, stream));
+        {
+            KTimer kt(MCD_K_SOLVE, stream);
+            MCD_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)bicg_persistent<DIM, T>, dim3(grid),
+                                                     dim3(256), args, 0, stream));
+        }
+        mcd_status s = read_scalars(w, stream);
+        if (s != MCD_OK) return s;
+        const Scalars &h = *w->h_sc;
+        if (h.phase_err) { result = MCD_ETIMEOUT; return MCD_OK; }
+        if (h.done == 1) { result = MCD_OK; return MCD_OK; }
+        if (h.done == 2) { result = MCD_ENOCONV; return MCD_OK; }
+        if (h.done == 3) { result = MCD_EBREAKDOWN; return MCD_OK; }
+        if (h.done == 4) { result = MCD_ENONFINITE; return MCD_OK; }
+        if (launch >= max_launch) {
+            set_error("persistent solve exceeded its launch budget");
+            result = MCD_ENOCONV;
+            return MCD_OK;
+        }
+    }
 }
 
 template <int DIM>
@@ -582,52 +1747,64 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
     const int64_t N = st->geo.N;
     mcd_status s = mcd_assemble_rhs(st, rhs, bnd, w->b, stream);
     if (s != MCD_OK) return s;
-    fix_guess<<<w->nblk1, 256, 0, stream>>>(N, st->kind, w->b, p);
-    MCD_LAUNCH_CHECK();
-
     Scalars init;
     memset(&init, 0, sizeof(init));
     init.max_iter = prm->max_iter > 0 ? prm->max_iter : 1 << 30;
     MCD_CUDA_TRY(cudaMemcpyAsync(w->sc, &init, sizeof(init), cudaMemcpyHostToDevice, stream));
-    const int check_every = prm->check_every > 0 ? prm->check_every : 64;
+    MCD_KLAUNCH(MCD_K_OTHER, stream, fix_guess<<<w->nblk1, 256, 0, stream>>>(N, st->kind, w->b, p, w->sc));
+    MCD_LAUNCH_CHECK();
+    const int check_every = prm->check_every > 0 ? prm->check_every : 64;   // legacy schedule
     const int max_outer = prm->max_refine > 0 ? prm->max_refine : 50;
     const int max_launch = (init.max_iter > (1 << 29) ? (1 << 29) : init.max_iter) + 2 * check_every;
 
     mcd_status result = MCD_ENOCONV;
     int outer = 0;
-    for (;; ++outer) {
-        // FP64 residual of the current iterate (primes the Krylov scalars)
-        s = residual<DIM>(st, p, prm->tol, stream);
+    if (prm->check_every >= 0) {
+        // persistent cooperative solve (the default)
+        s = (prm->mode == MCD_FP64) ? run_persistent<DIM, double>(st, p, prm, result, stream)
+                                    : run_persistent<DIM, float>(st, p, prm, result, stream);
         if (s != MCD_OK) return s;
-        s = read_scalars(w, stream);
-        if (s != MCD_OK) return s;
-        const Scalars &h = *w->h_sc;
-        if (h.done == 4) { result = MCD_ENONFINITE; break; }
-        if (h.done == 1) { result = MCD_OK; break; }
-        if (h.iter >= init.max_iter) { result = MCD_ENOCONV; break; }
-        if (outer >= max_outer) { result = MCD_ENOCONV; break; }
-        if (prm->mode == MCD_FP64) {
+    } else if (prm->mode == MCD_FP64) {
+        for (;; ++outer) {
+            // FP64 residual of the current iterate (primes the Krylov scalars)
+            s = residual<DIM>(st, p, prm->tol, 1, stream);
+            if (s != MCD_OK) return s;
+            s = read_scalars(w, stream);
+            if (s != MCD_OK) return s;
+            const Scalars &h = *w->h_sc;
+            if (h.done == 4) { result = MCD_ENONFINITE; break; }
+            if (h.done == 1) { result = MCD_OK; break; }
+            if (h.iter >= init.max_iter) { result = MCD_ENOCONV; break; }
+            if (outer >= max_outer) { result = MCD_ENOCONV; break; }
             Vecs<double> vv{p, w->r64, w->drh, {w->dp[0], w->dp[1]}, {w->dv[0], w->dv[1]}, w->ds, w->dt};
             s = run_krylov<DIM, double, double>(st, st->row64, vv, check_every, 1e-14, max_launch, stream);
-        } else {
-            prep_inner<<<w->nblk1, 256, 0, stream>>>(N, w->r64, w->fr, w->fd, w->sc, w->partials, w->pstride,
-                                                     w->counter, prm->inner_tol);
-            MCD_LAUNCH_CHECK();
-            Vecs<float> vv{w->fd, w->fr, w->frh, {w->fp[0], w->fp[1]}, {w->fv[0], w->fv[1]}, w->fs, w->ft};
-            s = run_krylov<DIM, float, float>(st, st->row32, vv, check_every, 1e-7, max_launch, stream);
-            if (s == MCD_OK) {
-                add_correction<<<w->nblk1, 256, 0, stream>>>(N, p, w->fd);
-                MCD_LAUNCH_CHECK();
-            }
+            if (s != MCD_OK) return s;
+            const int done = w->h_sc->done;
+            if (done == 4) { result = MCD_ENONFINITE; break; }
+            if (done == 3) { result = MCD_EBREAKDOWN; break; }
+            // done 1 (recursive residual converged) or 2 (max_iter): the next
+            // FP64 residual decides, and restarts the recurrence if needed
         }
+    } else {
+        s = run_mixed<DIM>(st, p, prm, check_every, max_launch, outer, result, stream);
         if (s != MCD_OK) return s;
-        const int done = w->h_sc->done;
-        if (done == 4) { result = MCD_ENONFINITE; break; }
-        if (done == 3) { result = MCD_EBREAKDOWN; break; }
-        // done 1 (inner converged) or 2 (max_iter): re-check with FP64 residual
-        // clear the inner status so the next residual can prime a restart
-        int zero = 0;
-        MCD_CUDA_TRY(cudaMemcpyAsync(&w->sc->done, &zero, sizeof(int), cudaMemcpyHostToDevice, stream));
+    }
+    // Block lower-triangular system: no inner row references a Neumann DP
+    // (Eq. (16) leaves Gamma_N out of Lambda_c), so the Krylov solve above ran
+    // on the interior block with the Neumann rows held fixed.  Their values
+    // now follow from their own rows; then the full FP64 residual decides.
+    if (result == MCD_OK && st->has_neumann) {
+        result = MCD_ENOCONV;
+        for (int round = 0; round < 6; ++round) {
+            s = neumann_sweeps<DIM>(st, p, 8, stream);
+            if (s != MCD_OK) return s;
+            s = residual<DIM>(st, p, prm->tol, 0, stream);
+            if (s != MCD_OK) return s;
+            s = read_scalars(w, stream);
+            if (s != MCD_OK) return s;
+            if (w->h_sc->done == 4) { result = MCD_ENONFINITE; break; }
+            if (w->h_sc->done == 1) { result = MCD_OK; break; }
+        }
     }
     const Scalars &h = *w->h_sc;
     if (info) {
@@ -636,16 +1813,43 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
         info->restarts = h.restarts;
         info->b_norm = sqrt(h.bb64);
         info->rel_res = h.bb64 > 0.0 ? sqrt(h.rr64 / h.bb64) : 0.0;
+        info->unknowns = (int64_t)h.unknowns;
     }
     if (result == MCD_ENOCONV) set_error("solve reached max_iter / max_refine before tol");
     if (result == MCD_ENONFINITE) set_error("non-finite value in right-hand side or residual");
-    if (result == MCD_EBREAKDOWN) set_error("Bi-CGSTAB breakdown");
+    if (result == MCD_EBREAKDOWN || result == MCD_ENONFINITE) {
+        char buf[512];
+        snprintf(buf, sizeof(buf),
+                 "%s (iter %d, refinement %d, restarts %d, rho %.3e, r^.v %.3e, t.s %.3e, t.t %.3e, "
+                 "s.s %.3e, r.r %.3e, tol2 %.3e, ||r64||^2 %.3e, ||b||^2 %.3e)",
+                 result == MCD_EBREAKDOWN ? "Bi-CGSTAB breakdown" : "non-finite value", h.iter, outer,
+                 h.restarts, h.rho, h.rv, h.ts, h.tt, h.ss, h.rr, h.tol2, h.rr64, h.bb64);
+        set_error(buf);
+    }
     return result;
 }
 
 }  // namespace mcd
 
 using namespace mcd;
+
+extern "C" mcd_status mcd_trace_enable(int on) {
+    if (on && !g_trace) {
+        MCD_CUDA_TRY(cudaMalloc(&g_trace, (512 + 4096) * sizeof(unsigned long long)));
+        MCD_CUDA_TRY(cudaMemset(g_trace, 0, (512 + 4096) * sizeof(unsigned long long)));
+    } else if (!on && g_trace) {
+        cudaFree(g_trace);
+        g_trace = nullptr;
+    }
+    return MCD_OK;
+}
+
+extern "C" mcd_status mcd_trace_read(unsigned long long *host_out) {
+    MCD_CHECK_ARG(host_out, "NULL argument");
+    MCD_CHECK_ARG(g_trace, "tracing is not enabled");
+    MCD_CUDA_TRY(cudaMemcpy(host_out, g_trace, (512 + 4096) * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    return MCD_OK;
+}
 
 extern "C" mcd_status mcd_solve_pressure(const mcd_stencils *st, const double *rhs_dev,
                                          const double *bnd_dev, double *p_dev,

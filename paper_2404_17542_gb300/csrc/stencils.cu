@@ -321,7 +321,10 @@ __global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
             row *= sigma;
         }
         a.row64[(int64_t)s * N + k] = row;
-        if (a.row32) a.row32[(int64_t)s * N + k] = (float)row;
+        // FP32 rows are kept in difference form: the centre slot holds the
+        // row sum, exactly 0 here (chi = 1 MLS reproduces constants), and the
+        // SpMV forms sum_j c_ij (x_j - x_i); see spmv_kernel
+        if (a.row32) a.row32[(int64_t)s * N + k] = (s == C) ? 0.0f : (float)row;
         if (a.ql64) a.ql64[(int64_t)s * N + k] = ql;
         if (a.d64)
             for (int q = 0; q < NB; ++q) a.d64[((int64_t)q * S + s) * N + k] = z[q];
@@ -332,22 +335,50 @@ __global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
 
 // ---------------------------------------------------------------------------
 // y = A x with the PPE rows: the matrix-free stencil SpMV.
+// FP64 rows are in matrix form, y_i = sum_s c_is x_js.  FP32 rows are in
+// difference form, y_i = c_iC x_i + sum_{s != C} c_is (x_js - x_i) with the
+// centre slot holding the row sum: for a smooth x the products then carry
+// O(l0) differences instead of O(1) values, which keeps the cancellation of
+// the O(1/l0^2) weights from consuming the FP32 mantissa; the products are
+// split exactly with fma and summed with TwoSum (double-float accumulation).
 // ---------------------------------------------------------------------------
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) spmv_kernel(Geo g, const T *__restrict__ row,
                                                    const T *__restrict__ x, T *__restrict__ y) {
     constexpr int S = (DIM == 2) ? 9 : 27;
+    constexpr int C = S / 2;
+    constexpr bool diff_form = sizeof(T) == 4;
     const int64_t N = g.N;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     int c[3] = {0, 0, 0};
     decode<DIM>(g, k, c);
-    T acc = 0;
+    const T xi = x[k];
+    if (diff_form) {
+        // compensated: exact products (fma) summed by TwoSum into (hi, lo)
+        float hi = (float)row[(int64_t)C * N + k] * (float)xi, lo = 0.0f;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (s == C) continue;
+            Nbr<DIM> nb = neighbour<DIM>(g, c, s);
+            const float w = (float)row[(int64_t)s * N + k];
+            // _rn intrinsics: never contracted into fused multiply-adds
+            const float d = __fsub_rn((float)x[nb.j], (float)xi);
+            const float p = __fmul_rn(w, d);
+            const float pe = __fmaf_rn(w, d, -p);
+            const float sum = __fadd_rn(hi, p);
+            const float bb = __fsub_rn(sum, hi);
+            lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(p, bb)), pe));
+            hi = sum;
+        }
+        y[k] = (T)__fadd_rn(hi, lo);
+        return;
+    }
+    T acc = (T)0;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         Nbr<DIM> nb = neighbour<DIM>(g, c, s);
-        const T w = row[(int64_t)s * N + k];
-        acc += w * x[nb.j];
+        acc += row[(int64_t)s * N + k] * x[nb.j];
     }
     y[k] = acc;
 }
@@ -501,9 +532,9 @@ extern "C" mcd_status mcd_build_stencils(const mcd_mesh *mesh, const double *pos
     const int threads = 128;
     const unsigned blocks = (unsigned)((N + threads - 1) / threads);
     if (mesh->dim == 2)
-        build_kernel<2><<<blocks, threads, 0, stream>>>(a);
+        MCD_KLAUNCH(MCD_K_BUILD, stream, build_kernel<2><<<blocks, threads, 0, stream>>>(a));
     else
-        build_kernel<3><<<blocks, threads, 0, stream>>>(a);
+        MCD_KLAUNCH(MCD_K_BUILD, stream, build_kernel<3><<<blocks, threads, 0, stream>>>(a));
     MCD_LAUNCH_CHECK();
     return MCD_OK;
 }
@@ -575,15 +606,15 @@ extern "C" mcd_status mcd_apply_laplacian(const mcd_stencils *st, const void *x_
     const unsigned blocks = (unsigned)((N + threads - 1) / threads);
     if (dtype == MCD_DT_F64) {
         if (st->mesh.dim == 2)
-            spmv_kernel<double, 2><<<blocks, threads, 0, stream>>>(st->geo, st->row64, (const double *)x_dev, (double *)y_dev);
+            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<double, 2><<<blocks, threads, 0, stream>>>(st->geo, st->row64, (const double *)x_dev, (double *)y_dev));
         else
-            spmv_kernel<double, 3><<<blocks, threads, 0, stream>>>(st->geo, st->row64, (const double *)x_dev, (double *)y_dev);
+            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<double, 3><<<blocks, threads, 0, stream>>>(st->geo, st->row64, (const double *)x_dev, (double *)y_dev));
     } else if (dtype == MCD_DT_F32) {
         MCD_CHECK_ARG(st->row32, "FP32 rows need an MCD_MIXED stencil handle");
         if (st->mesh.dim == 2)
-            spmv_kernel<float, 2><<<blocks, threads, 0, stream>>>(st->geo, st->row32, (const float *)x_dev, (float *)y_dev);
+            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<float, 2><<<blocks, threads, 0, stream>>>(st->geo, st->row32, (const float *)x_dev, (float *)y_dev));
         else
-            spmv_kernel<float, 3><<<blocks, threads, 0, stream>>>(st->geo, st->row32, (const float *)x_dev, (float *)y_dev);
+            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<float, 3><<<blocks, threads, 0, stream>>>(st->geo, st->row32, (const float *)x_dev, (float *)y_dev));
     } else {
         set_error("unknown dtype");
         return MCD_EINVAL;
@@ -600,9 +631,9 @@ extern "C" mcd_status mcd_assemble_rhs(const mcd_stencils *st, const double *rhs
     const unsigned blocks = (unsigned)((N + threads - 1) / threads);
     const double *ql = st->has_neumann ? st->ql64 : nullptr;
     if (st->mesh.dim == 2)
-        rhs_kernel<2><<<blocks, threads, 0, stream>>>(st->geo, st->kind, ql, st->rscale, rhs_dev, bnd_dev, b_dev);
+        MCD_KLAUNCH(MCD_K_OTHER, stream, rhs_kernel<2><<<blocks, threads, 0, stream>>>(st->geo, st->kind, ql, st->rscale, rhs_dev, bnd_dev, b_dev));
     else
-        rhs_kernel<3><<<blocks, threads, 0, stream>>>(st->geo, st->kind, ql, st->rscale, rhs_dev, bnd_dev, b_dev);
+        MCD_KLAUNCH(MCD_K_OTHER, stream, rhs_kernel<3><<<blocks, threads, 0, stream>>>(st->geo, st->kind, ql, st->rscale, rhs_dev, bnd_dev, b_dev));
     MCD_LAUNCH_CHECK();
     return MCD_OK;
 }

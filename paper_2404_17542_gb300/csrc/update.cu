@@ -126,8 +126,9 @@ __global__ void relax_kernel(Geo g, Circle body, double band, double kappa, doub
     pout[N + k] = fmin(fmax(sy, loy), hiy);
 }
 
-__global__ void normals_kernel(Geo g, Circle body, const double *__restrict__ pos,
-                               const int8_t *__restrict__ mask, double *__restrict__ nrm) {
+__global__ void body_bc_kernel(Geo g, Circle body, double ax, double ay, const double *__restrict__ pos,
+                               const int8_t *__restrict__ mask, double *__restrict__ nrm,
+                               double *__restrict__ neu) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t N = g.N;
     if (k >= N) return;
@@ -139,6 +140,7 @@ __global__ void normals_kernel(Geo g, Circle body, const double *__restrict__ po
     }
     nrm[k] = nx;
     nrm[N + k] = ny;
+    if (neu) neu[k] = -(ax * nx + ay * ny);                            // Eq. (23)
 }
 
 // Position scratch for the Jacobi ping-pong, grown on demand and kept for
@@ -186,7 +188,7 @@ extern "C" mcd_status mcd_update_dps(const mcd_mesh *mesh, const mcd_body *bodie
     Circle c{bodies[0].id, bodies[0].c[0], bodies[0].c[1], bodies[0].radius};
     const int threads = 256;
     const unsigned blocks = (unsigned)((g.N + threads - 1) / threads);
-    remask_kernel<<<blocks, threads, 0, stream>>>(g, c, band, pos_dev, mask_dev, mask_prev_dev);
+    MCD_KLAUNCH(MCD_K_UPDATE, stream, remask_kernel<<<blocks, threads, 0, stream>>>(g, c, band, pos_dev, mask_dev, mask_prev_dev));
     MCD_LAUNCH_CHECK();
     if (n_relax == 0) return MCD_OK;
     double *tmp = scratch_positions(2 * (size_t)g.N);
@@ -196,7 +198,7 @@ extern "C" mcd_status mcd_update_dps(const mcd_mesh *mesh, const mcd_body *bodie
     }
     double *a = pos_dev, *b = tmp;
     for (int it = 0; it < n_relax; ++it) {
-        relax_kernel<<<blocks, threads, 0, stream>>>(g, c, band, kappa, alpha, mask_dev, a, b);
+        MCD_KLAUNCH(MCD_K_UPDATE, stream, relax_kernel<<<blocks, threads, 0, stream>>>(g, c, band, kappa, alpha, mask_dev, a, b));
         double *t = a; a = b; b = t;
     }
     MCD_LAUNCH_CHECK();
@@ -206,17 +208,20 @@ extern "C" mcd_status mcd_update_dps(const mcd_mesh *mesh, const mcd_body *bodie
     return MCD_OK;
 }
 
-extern "C" mcd_status mcd_body_normals(const mcd_mesh *mesh, const mcd_body *body, const double *pos_dev,
-                                       const int8_t *mask_dev, double *normal_dev, mcd_stream_t stream) {
+extern "C" mcd_status mcd_body_boundary(const mcd_mesh *mesh, const mcd_body *body, const double *pos_dev,
+                                        const int8_t *mask_dev, double *normal_dev, double *neumann_dev,
+                                        mcd_stream_t stream) {
     MCD_CHECK_ARG(mesh && body && pos_dev && mask_dev && normal_dev, "NULL argument");
     if (mesh->dim != 2) {
-        set_error("mcd_body_normals: 2D only");
+        set_error("mcd_body_boundary: 2D only");
         return MCD_ENOTSUP;
     }
     const Geo g = make_geo(*mesh);
     Circle c{body->id, body->c[0], body->c[1], body->radius};
     const unsigned blocks = (unsigned)((g.N + 255) / 256);
-    normals_kernel<<<blocks, 256, 0, stream>>>(g, c, pos_dev, mask_dev, normal_dev);
+    MCD_KLAUNCH(MCD_K_OTHER, stream, body_bc_kernel<<<blocks, 256, 0, stream>>>(g, c, body->acc[0], body->acc[1],
+                                                                              pos_dev, mask_dev, normal_dev,
+                                                                              neumann_dev));
     MCD_LAUNCH_CHECK();
     return MCD_OK;
 }

@@ -246,6 +246,16 @@ def cylinder_box(n: int, cyl: Cylinder | None = None) -> Problem:
     return pb
 
 
+def ppe_source(pos: np.ndarray, t: float):
+    """Smooth synthetic interior source for the pressure Poisson equation,
+    standing in for div(u*)/dt of a flow step: O(1) amplitude, a few
+    wavelengths across the unit box."""
+    x, y = pos[0], pos[1]
+    tp = 2.0 * math.pi
+    return (np.sin(tp * x) * np.sin(tp * y) + 0.5 * np.cos(3 * tp * x) * np.sin(tp * y)) * \
+        math.cos(tp * t)
+
+
 def tgv_fields(pos: np.ndarray, t: float, nu: float):
     """Closed-form 2D Taylor-Green vortex on the periodic unit square."""
     x, y = pos[0], pos[1]

@@ -46,16 +46,17 @@ class c_mls_params(C.Structure):
 class c_solve_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("mode", C.c_int),
                 ("inner_tol", C.c_double), ("max_refine", C.c_int), ("net", C.c_void_p),
-                ("check_every", C.c_int)]
+                ("check_every", C.c_int), ("update_restart", C.c_int)]
 
 
 class c_solve_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("restarts", C.c_int),
-                ("rel_res", C.c_double), ("b_norm", C.c_double)]
+                ("rel_res", C.c_double), ("b_norm", C.c_double), ("unknowns", C.c_int64)]
 
 
 class c_body(C.Structure):
-    _fields_ = [("id", C.c_int), ("c", C.c_double * 3), ("radius", C.c_double)]
+    _fields_ = [("id", C.c_int), ("c", C.c_double * 3), ("radius", C.c_double),
+                ("vel", C.c_double * 3), ("acc", C.c_double * 3)]
 
 
 _lib = None
@@ -74,8 +75,13 @@ _SIGS = {
                                      C.POINTER(c_solve_params), C.POINTER(c_solve_info), C.c_void_p]),
     "mcd_update_dps": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_int, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_double, C.c_int, C.c_double, C.c_double, C.c_void_p]),
-    "mcd_body_normals": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_void_p, C.c_void_p,
-                                   C.c_void_p, C.c_void_p]),
+    "mcd_body_boundary": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mcd_timing_enable": (C.c_int, [C.c_int]),
+    "mcd_timing_read": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "mcd_launch_count": (C.c_int64, []),
+    "mcd_trace_enable": (C.c_int, [C.c_int]),
+    "mcd_trace_read": (C.c_int, [C.POINTER(C.c_uint64)]),
     "mcd_last_error": (C.c_char_p, []),
     "mcd_version": (C.c_char_p, []),
 }
@@ -197,19 +203,20 @@ class Stencils:
                                       _stream()))
         return b
 
-    def solve(self, rhs, bnd, p=None, tol=1e-8, mode=MIXED, max_iter=200000, inner_tol=1e-4,
-              max_refine=60, check_every=64, raise_on_error=True):
+    def solve(self, rhs, bnd, p=None, tol=1e-8, mode=MIXED, max_iter=200000, inner_tol=0.1,
+              max_refine=60, check_every=64, update_restart=1, raise_on_error=True):
         """Solve the PPE; returns (p, info dict).  p is updated in place if given."""
         if p is None:
             p = torch.zeros(self.N, dtype=torch.float64, device=rhs.device)
         sp = c_solve_params(tol=tol, max_iter=max_iter, mode=mode, inner_tol=inner_tol,
-                            max_refine=max_refine, net=None, check_every=check_every)
+                            max_refine=max_refine, net=None, check_every=check_every,
+                            update_restart=int(update_restart))
         info = c_solve_info()
         st = lib().mcd_solve_pressure(self.handle, _ptr(rhs, torch.float64, self.N),
                                       _ptr(bnd, torch.float64, self.N), _ptr(p, torch.float64, self.N),
                                       C.byref(sp), C.byref(info), _stream())
         d = dict(status=st, iters=info.iters, refinements=info.refinements, restarts=info.restarts,
-                 rel_res=info.rel_res, b_norm=info.b_norm)
+                 rel_res=info.rel_res, b_norm=info.b_norm, unknowns=info.unknowns)
         if st != OK and raise_on_error:
             raise McdError(st, lib().mcd_last_error().decode())
         return p, d
@@ -226,14 +233,21 @@ class Stencils:
             pass
 
 
-def update_dps(mesh, centre, radius, body_id, pos, mask, mask_prev, kappa=0.2, n_relax=10,
-               band=None, alpha=0.0):
-    """One moving-boundary DP update (Sec. 2.2-2.4) in place on pos/mask."""
-    cm = make_mesh(mesh)
+def make_body(centre, radius, body_id, vel=(0.0, 0.0), acc=(0.0, 0.0)) -> c_body:
     b = c_body()
     b.id = int(body_id)
     b.c[0], b.c[1], b.c[2] = float(centre[0]), float(centre[1]), 0.0
     b.radius = float(radius)
+    b.vel[0], b.vel[1], b.vel[2] = float(vel[0]), float(vel[1]), 0.0
+    b.acc[0], b.acc[1], b.acc[2] = float(acc[0]), float(acc[1]), 0.0
+    return b
+
+
+def update_dps(mesh, centre, radius, body_id, pos, mask, mask_prev, kappa=0.2, n_relax=10,
+               band=None, alpha=0.0):
+    """One moving-boundary DP update (Sec. 2.2-2.4) in place on pos/mask."""
+    cm = make_mesh(mesh)
+    b = make_body(centre, radius, body_id)
     N = mesh.n[0] * mesh.n[1]
     band = 5.0 * mesh.l0 if band is None else band
     _check(lib().mcd_update_dps(C.byref(cm), C.byref(b), 1, _ptr(pos, torch.float64, 2 * N),
@@ -241,17 +255,51 @@ def update_dps(mesh, centre, radius, body_id, pos, mask, mask_prev, kappa=0.2, n
                                 float(kappa), int(n_relax), float(band), float(alpha), _stream()))
 
 
-def body_normals(mesh, centre, radius, body_id, pos, mask, out=None):
+def body_boundary(mesh, centre, radius, body_id, pos, mask, acc=(0.0, 0.0), normal=None, neumann=None):
+    """Normals of the body DPs and the Neumann datum -acc . n (Eq. (23))."""
     cm = make_mesh(mesh)
-    b = c_body()
-    b.id = int(body_id)
-    b.c[0], b.c[1], b.c[2] = float(centre[0]), float(centre[1]), 0.0
-    b.radius = float(radius)
+    b = make_body(centre, radius, body_id, acc=acc)
     N = mesh.n[0] * mesh.n[1]
-    n = torch.empty(2 * N, dtype=torch.float64, device=pos.device) if out is None else out
-    _check(lib().mcd_body_normals(C.byref(cm), C.byref(b), _ptr(pos, torch.float64, 2 * N),
-                                  _ptr(mask, torch.int8, N), _ptr(n, torch.float64, 2 * N), _stream()))
-    return n
+    n = torch.empty(2 * N, dtype=torch.float64, device=pos.device) if normal is None else normal
+    f = torch.empty(N, dtype=torch.float64, device=pos.device) if neumann is None else neumann
+    _check(lib().mcd_body_boundary(C.byref(cm), C.byref(b), _ptr(pos, torch.float64, 2 * N),
+                                   _ptr(mask, torch.int8, N), _ptr(n, torch.float64, 2 * N),
+                                   _ptr(f, torch.float64, N), _stream()))
+    return n, f
+
+
+K_BICG_A, K_BICG_B, K_BICG_C, K_RESIDUAL, K_BUILD, K_UPDATE, K_OTHER, K_SOLVE = range(8)
+KERNEL_NAMES = ["bicg_ka", "bicg_kb", "bicg_kc", "residual64", "build_kernel", "update", "other",
+                "bicg_persistent"]
+
+
+def timing_enable(sample_every: int):
+    _check(lib().mcd_timing_enable(int(sample_every)))
+
+
+def timing_read(kernel: int):
+    """(sampled launches, summed device ms) of a kernel class."""
+    n = C.c_int64()
+    ms = C.c_double()
+    _check(lib().mcd_timing_read(int(kernel), C.byref(n), C.byref(ms)))
+    return n.value, ms.value
+
+
+def trace_enable(on: bool):
+    _check(lib().mcd_trace_enable(1 if on else 0))
+
+
+def trace_read():
+    """Phase timestamps (64, 8) of block 0, and per-block phase-A end times
+    and SM ids of iteration 10, from the last persistent launch."""
+    buf = (C.c_uint64 * (512 + 4096))()
+    _check(lib().mcd_trace_read(buf))
+    a = np.array(buf, dtype=np.uint64)
+    return a[:512].reshape(64, 8), a[512:512 + 2048], a[512 + 2048:]
+
+
+def launch_count() -> int:
+    return int(lib().mcd_launch_count())
 
 
 def version():

@@ -53,8 +53,15 @@ def compare_weights(mcd, st, W, N, S, nb, kinds=True):
     assert (np.abs(row - W["row"]) <= WEIGHT_TOL * scale).all()
     r32 = st.array(mcd.ARR_ROW32)
     if r32 is not None:
+        # FP32 rows: difference form (off-centre = rounded FP64 weights,
+        # centre = row sum: 0 for MLS rows, 1 for identity rows)
         r32 = r32.cpu().numpy().reshape(S, N)
-        assert np.array_equal(r32, row.astype(np.float32))
+        C = S // 2
+        off = [s for s in range(S) if s != C]
+        assert np.array_equal(r32[off], row[off].astype(np.float32))
+        ident = np.isin(W["kind"], (0, 2))
+        assert np.array_equal(r32[C], np.where(ident, 1.0, 0.0).astype(np.float32))
+        assert np.abs(W["row"][:, ~ident].sum(axis=0)).max() <= 1e-9 * scale.max()
     if kinds:
         kind = st.array(mcd.ARR_KIND).cpu().numpy()
         assert np.array_equal(kind, W["kind"])
@@ -189,10 +196,13 @@ def test_update_dps_bit_exact_masks(mcd):
         pos_g.copy_(dev(pos_o.ravel()))
 
 
-def test_body_normals(mcd):
+def test_body_boundary_data(mcd):
     pb, pos, m, normal, cyl, c = cylinder_state(40)
-    ng = mcd.body_normals(pb.mesh, c, cyl.radius, cyl.body_id, dev(pos.ravel()), dev(m))
+    acc = cyl.acceleration(0.031)
+    ng, fg = mcd.body_boundary(pb.mesh, c, cyl.radius, cyl.body_id, dev(pos.ravel()), dev(m), acc=acc)
     assert np.allclose(ng.cpu().numpy().reshape(2, -1), normal, rtol=0, atol=1e-14)
+    want = np.where(m == cyl.body_id, -(acc[0] * normal[0] + acc[1] * normal[1]), 0.0)
+    assert np.allclose(fg.cpu().numpy(), want, rtol=0, atol=1e-13 * max(1.0, abs(acc[0])))
 
 
 def test_singular_stencil_reports_esingular(mcd):
