@@ -255,6 +255,32 @@ mcd_status mcd_update_dps(const mcd_mesh *mesh, const mcd_body *bodies,
                           int8_t *mask_prev_dev, double kappa, int n_relax,
                           double band, double alpha, mcd_stream_t stream);
 
+/* Largest mesh (in DPs) that mcd_update_dps_static accepts. */
+#define MCD_NOALLOC_MAX_DPS (1 << 20)
+
+/* mcd_update_dps_static - mcd_update_dps without any GPU memory allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * must not allocate while they step (a framework whose caching allocator has
+ * already reserved the device's memory, a time-stepping loop that cannot
+ * take the device synchronisation and latency cudaMalloc/cudaFree may bring,
+ * or code that forbids allocation after start-up).  Arguments, results and
+ * error codes are those of mcd_update_dps.  Differences:
+ *  - the Jacobi scratch is a fixed device array of 2 * MCD_NOALLOC_MAX_DPS
+ *    doubles (16 MiB) inside the library, reserved on every GPU that loads
+ *    the library until the process exits; meshes with more than
+ *    MCD_NOALLOC_MAX_DPS cells are rejected with MCD_EINVAL;
+ *  - the first call on each device looks up that array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture;
+ *  - all calls share the one array: calls whose work may overlap on the GPU
+ *    (for instance on two streams) race and must be serialised by the
+ *    caller.  Each call overwrites the scratch it reads, so nothing needs
+ *    clearing between calls. */
+mcd_status mcd_update_dps_static(const mcd_mesh *mesh, const mcd_body *bodies,
+                                 int nbodies, double *pos_dev, int8_t *mask_dev,
+                                 int8_t *mask_prev_dev, double kappa, int n_relax,
+                                 double band, double alpha, mcd_stream_t stream);
+
 /* mcd_body_boundary - boundary data of the body's DPs (mask == id):
  *  normal_dev  float64 [2][N]: unit normal n = (x - c)/|x - c| (the analytic
  *              gradient of the circle SDF, Sec. 2.5); 0 at other DPs;

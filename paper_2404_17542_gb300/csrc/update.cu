@@ -225,3 +225,92 @@ extern "C" mcd_status mcd_body_boundary(const mcd_mesh *mesh, const mcd_body *bo
     MCD_LAUNCH_CHECK();
     return MCD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free DP update.
+//
+// Same computation as mcd_update_dps, but the Jacobi ping-pong positions live
+// in the fixed device array below instead of memory obtained with cudaMalloc.
+// It serves callers that must not allocate GPU memory while they step: a
+// framework whose caching allocator has already reserved the device's memory,
+// a time-stepping loop that cannot afford the device-wide synchronisation and
+// unbounded latency that cudaMalloc / cudaFree can bring, or a code base that
+// forbids allocation after start-up.  The array exists once per device that
+// loads this library and stays reserved until the process exits.
+// ---------------------------------------------------------------------------
+namespace mcd {
+
+static __device__ __align__(256) double g_noalloc_pos[2 * (size_t)MCD_NOALLOC_MAX_DPS];
+
+static std::mutex g_noalloc_mu;
+static double *g_noalloc_addr[64];   // device address of g_noalloc_pos, per device
+
+// Device address of the fixed array on the current device.  The host-side
+// symbol g_noalloc_pos is only a stand-in and must never reach a kernel; the
+// real address is looked up once per device, with that device current.
+static mcd_status noalloc_scratch(double **out) {
+    int dev = 0;
+    MCD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("mcd_update_dps_static: device ordinal out of range");
+        return MCD_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_pos);
+        if (e != cudaSuccess || !p) {
+            set_error(std::string("mcd_update_dps_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            return MCD_ECUDA;
+        }
+        g_noalloc_addr[dev] = (double *)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return MCD_OK;
+}
+
+}  // namespace mcd
+
+extern "C" mcd_status mcd_update_dps_static(const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
+                                            double *pos_dev, int8_t *mask_dev, int8_t *mask_prev_dev,
+                                            double kappa, int n_relax, double band, double alpha,
+                                            mcd_stream_t stream) {
+    MCD_CHECK_ARG(mesh && bodies && pos_dev && mask_dev && mask_prev_dev, "NULL argument");
+    if (mesh->dim != 2 || nbodies != 1) {
+        set_error("mcd_update_dps_static: 2D with one body only");
+        return MCD_ENOTSUP;
+    }
+    MCD_CHECK_ARG(mesh->n[0] >= 3 && mesh->n[1] >= 3 && mesh->l0 > 0.0, "bad mesh");
+    MCD_CHECK_ARG(bodies[0].id >= 2 && bodies[0].id <= 127, "body id must be in 2..127");
+    MCD_CHECK_ARG(bodies[0].radius > 0.0, "body radius must be positive");
+    MCD_CHECK_ARG(n_relax >= 0 && kappa >= 0.0, "bad relaxation parameters");
+    const Geo g = make_geo(*mesh);
+    if (g.N > (int64_t)MCD_NOALLOC_MAX_DPS) {
+        set_error("mcd_update_dps_static: mesh has " + std::to_string(g.N) +
+                  " DPs, more than the fixed scratch holds (MCD_NOALLOC_MAX_DPS = " +
+                  std::to_string((long long)MCD_NOALLOC_MAX_DPS) + ")");
+        return MCD_EINVAL;
+    }
+    double *tmp = nullptr;
+    mcd_status st = noalloc_scratch(&tmp);
+    if (st != MCD_OK) return st;
+    Circle c{bodies[0].id, bodies[0].c[0], bodies[0].c[1], bodies[0].radius};
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((g.N + threads - 1) / threads);
+    MCD_KLAUNCH(MCD_K_UPDATE, stream, remask_kernel<<<blocks, threads, 0, stream>>>(g, c, band, pos_dev, mask_dev,
+                                                                                  mask_prev_dev));
+    MCD_LAUNCH_CHECK();
+    // Each sweep writes every one of the 2N scratch positions before any is
+    // read, so contents left by an earlier call never leak into this one.
+    double *a = pos_dev, *b = tmp;
+    for (int it = 0; it < n_relax; ++it) {
+        MCD_KLAUNCH(MCD_K_UPDATE, stream, relax_kernel<<<blocks, threads, 0, stream>>>(g, c, band, kappa, alpha,
+                                                                                     mask_dev, a, b));
+        double *t = a; a = b; b = t;
+    }
+    MCD_LAUNCH_CHECK();
+    if (a != pos_dev)
+        MCD_CUDA_TRY(cudaMemcpyAsync(pos_dev, a, 2 * (size_t)g.N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     stream));
+    return MCD_OK;
+}

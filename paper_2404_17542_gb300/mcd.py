@@ -75,6 +75,9 @@ _SIGS = {
                                      C.POINTER(c_solve_params), C.POINTER(c_solve_info), C.c_void_p]),
     "mcd_update_dps": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_int, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_double, C.c_int, C.c_double, C.c_double, C.c_void_p]),
+    "mcd_update_dps_static": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_int, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_double,
+                                        C.c_double, C.c_void_p]),
     "mcd_body_boundary": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
     "mcd_timing_enable": (C.c_int, [C.c_int]),
@@ -253,6 +256,19 @@ def update_dps(mesh, centre, radius, body_id, pos, mask, mask_prev, kappa=0.2, n
     _check(lib().mcd_update_dps(C.byref(cm), C.byref(b), 1, _ptr(pos, torch.float64, 2 * N),
                                 _ptr(mask, torch.int8, N), _ptr(mask_prev, torch.int8, N),
                                 float(kappa), int(n_relax), float(band), float(alpha), _stream()))
+
+
+def update_dps_static(mesh, centre, radius, body_id, pos, mask, mask_prev, kappa=0.2, n_relax=10,
+                      band=None, alpha=0.0):
+    """update_dps through the allocation-free entry point (fixed scratch of
+    MCD_NOALLOC_MAX_DPS cells inside the library; see include/mcd.h)."""
+    cm = make_mesh(mesh)
+    b = make_body(centre, radius, body_id)
+    N = mesh.n[0] * mesh.n[1]
+    band = 5.0 * mesh.l0 if band is None else band
+    _check(lib().mcd_update_dps_static(C.byref(cm), C.byref(b), 1, _ptr(pos, torch.float64, 2 * N),
+                                       _ptr(mask, torch.int8, N), _ptr(mask_prev, torch.int8, N),
+                                       float(kappa), int(n_relax), float(band), float(alpha), _stream()))
 
 
 def body_boundary(mesh, centre, radius, body_id, pos, mask, acc=(0.0, 0.0), normal=None, neumann=None):
