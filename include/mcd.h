@@ -219,6 +219,39 @@ mcd_status mcd_solve_pressure(const mcd_stencils *st, const double *rhs_dev,
                               mcd_stream_t stream);
 
 /* -------------------------------------------------------------------------
+ * Fractional-step driver (Sec. 3.3, Eqs. (20)-(22)), 2D
+ * ---------------------------------------------------------------------- */
+
+/* mcd_flow_predict - intermediate velocity and PPE source of one step with
+ * the DPs held in place.  For every inner DP
+ *   u* = F_MOC + nu dt lap u                                      (Eq. (20))
+ * where F_MOC = u + d.grad u + 1/2 d^T H d, d = -u dt, is the second-order
+ * Taylor value at the departure point, built like Eq. (19) from the MLS
+ * derivative weights (Eq. (14)); then src = (1/dt) div u* (Eq. (21)).
+ * Non-inner DPs: u* = (ubc, vbc) (0 at void DPs), src = 0.
+ *  vel         stencil handle built with want_derivs = 1; its boundary ids
+ *              should all be Dirichlet (velocity values are prescribed there).
+ *  u, v, ubc, vbc   device float64 [N] (current and boundary velocity).
+ *  us, vs, src      device float64 [N] outputs; us/vs must not alias u/v.
+ * Asynchronous.  MCD_ENOTSUP for 3D meshes. */
+mcd_status mcd_flow_predict(const mcd_stencils *vel, const double *u_dev,
+                            const double *v_dev, const double *ubc_dev,
+                            const double *vbc_dev, double nu, double dt,
+                            double *us_dev, double *vs_dev, double *src_dev,
+                            mcd_stream_t stream);
+
+/* mcd_flow_project - u = u* - dt grad P at inner DPs (Eq. (22)); grad P is
+ * the MLS gradient of the pressure stencils `pst` (want_derivs = 1), with
+ * the Neumann-data terms of Eq. (15) taken from bnd (the same array passed
+ * to mcd_solve_pressure).  Non-inner DPs: (ubc, vbc), 0 at void DPs.
+ * All arrays device float64 [N].  Asynchronous. */
+mcd_status mcd_flow_project(const mcd_stencils *pst, const double *P_dev,
+                            const double *bnd_dev, const double *us_dev,
+                            const double *vs_dev, const double *ubc_dev,
+                            const double *vbc_dev, double dt, double *u_dev,
+                            double *v_dev, mcd_stream_t stream);
+
+/* -------------------------------------------------------------------------
  * Moving-boundary DP update (Sec. 2.2-2.4)
  * ---------------------------------------------------------------------- */
 

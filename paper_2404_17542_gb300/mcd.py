@@ -80,6 +80,10 @@ _SIGS = {
                                         C.c_double, C.c_void_p]),
     "mcd_body_boundary": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mcd_flow_predict": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_double, C.c_double]
+                         + [C.c_void_p] * 3 + [C.c_void_p]),
+    "mcd_flow_project": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.c_double]
+                         + [C.c_void_p] * 2 + [C.c_void_p]),
     "mcd_timing_enable": (C.c_int, [C.c_int]),
     "mcd_timing_read": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "mcd_launch_count": (C.c_int64, []),
@@ -223,6 +227,29 @@ class Stencils:
         if st != OK and raise_on_error:
             raise McdError(st, lib().mcd_last_error().decode())
         return p, d
+
+    def flow_predict(self, u, v, ubc, vbc, nu, dt, us=None, vs=None, src=None):
+        """u*, v* and (1/dt) div u* (Eqs. (20)-(21)); needs want_derivs=True."""
+        us = torch.empty_like(u) if us is None else us
+        vs = torch.empty_like(v) if vs is None else vs
+        src = torch.empty_like(u) if src is None else src
+        f64 = torch.float64
+        _check(lib().mcd_flow_predict(self.handle, _ptr(u, f64, self.N), _ptr(v, f64, self.N),
+                                      _ptr(ubc, f64, self.N), _ptr(vbc, f64, self.N), float(nu),
+                                      float(dt), _ptr(us, f64, self.N), _ptr(vs, f64, self.N),
+                                      _ptr(src, f64, self.N), _stream()))
+        return us, vs, src
+
+    def flow_project(self, P, bnd, us, vs, ubc, vbc, dt, u=None, v=None):
+        """u = u* - dt grad P (Eq. (22)) with this handle's gradient weights."""
+        u = torch.empty_like(us) if u is None else u
+        v = torch.empty_like(vs) if v is None else v
+        f64 = torch.float64
+        _check(lib().mcd_flow_project(self.handle, _ptr(P, f64, self.N), _ptr(bnd, f64, self.N),
+                                      _ptr(us, f64, self.N), _ptr(vs, f64, self.N),
+                                      _ptr(ubc, f64, self.N), _ptr(vbc, f64, self.N), float(dt),
+                                      _ptr(u, f64, self.N), _ptr(v, f64, self.N), _stream()))
+        return u, v
 
     def close(self):
         if self.handle and self.handle.value:
