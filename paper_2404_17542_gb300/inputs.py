@@ -281,14 +281,36 @@ def tgv_box(n: int, seed: int, jitter: float = 0.25, re: float = 100.0) -> Probl
     return pb
 
 
-def cnn_weights(seed: int, c_in: int = 6, width: int = 32, layers: int = 4,
+def cnn_weights(seed: int, c_in: int = 7, width: int = 32, layers: int = 4,
                 c_out: int = 1):
-    """He-initialised 3x3 conv weights [(c_out, c_in, 3, 3)] and zero biases."""
+    """He-initialised 3x3 conv weights [(c_out, c_in, 3, 3)] and zero biases,
+    rounded to float32 (the precision of the network's master copy)."""
     rng = np.random.default_rng(seed)
     chans = [c_in] + [width] * (layers - 1) + [c_out]
     ws, bs = [], []
     for a, b in zip(chans[:-1], chans[1:]):
         std = math.sqrt(2.0 / (9 * a))
-        ws.append(rng.normal(0.0, std, size=(b, a, 3, 3)))
+        ws.append(rng.normal(0.0, std, size=(b, a, 3, 3)).astype(np.float32).astype(np.float64))
         bs.append(np.zeros(b))
+    return ws, bs
+
+
+def cnn_flatten(ws, bs):
+    """Flat float32 parameter vector: per layer W[o][c][dj][di], then b[o]."""
+    parts = []
+    for w, b in zip(ws, bs):
+        parts += [np.asarray(w, np.float32).ravel(), np.asarray(b, np.float32).ravel()]
+    return np.concatenate(parts)
+
+
+def cnn_unflatten(flat, c_in: int = 7, width: int = 32, layers: int = 4, c_out: int = 1):
+    """Inverse of cnn_flatten (float64 arrays)."""
+    chans = [c_in] + [width] * (layers - 1) + [c_out]
+    ws, bs, at = [], [], 0
+    for a, b in zip(chans[:-1], chans[1:]):
+        n = b * a * 9
+        ws.append(np.asarray(flat[at:at + n], np.float64).reshape(b, a, 3, 3))
+        at += n
+        bs.append(np.asarray(flat[at:at + b], np.float64))
+        at += b
     return ws, bs
