@@ -167,7 +167,7 @@ mcd_status mcd_assemble_rhs(const mcd_stencils *st, const double *rhs_dev,
 /* -------------------------------------------------------------------------
  * Pressure solve (Sec. 3.3: Bi-CGSTAB on the MLS PPE)
  * ---------------------------------------------------------------------- */
-typedef struct mcd_net mcd_net;
+typedef struct mcd_net mcd_net;   /* learned warm start, declared below */
 
 /* tol          stop when ||b - A p||_2 <= tol ||b||_2 (FP64 residual).
  * max_iter     cap on Krylov iterations (all refinements together).
@@ -182,10 +182,13 @@ typedef struct mcd_net mcd_net;
  *              is taken once the FP32 residual has fallen by this factor
  *              since the last one (checked every few iterations).
  * max_refine   cap on FP64 restarts (FP64 mode).
- * net          NULL, or a trained network giving the initial guess.
+ * net          NULL, or a network whose correction is added to the guess
+ *              before the Krylov solve (mcd_net_warm_start; 2D only).
  * check_every  Krylov iterations between host convergence checks (0: auto).
  * update_restart (MIXED) 1: restart the FP32 recurrence (fresh shadow
- *              residual, p = r) at every reliable update; 0: keep p. */
+ *              residual, p = r) at every reliable update; 0: keep p.
+ * net_dprev    with net: device float64 [N], the last pressure increment
+ *              (p of the previous step minus the one before), or NULL. */
 typedef struct {
     double tol;
     int max_iter;
@@ -195,6 +198,7 @@ typedef struct {
     const mcd_net *net;
     int check_every;
     int update_restart;
+    const double *net_dprev;
 } mcd_solve_params;
 
 typedef struct {
@@ -204,12 +208,14 @@ typedef struct {
     double rel_res;     /* final ||b - A p|| / ||b|| in FP64 */
     double b_norm;      /* ||b||_2 */
     int64_t unknowns;   /* non-void DPs of the system (DP unknowns solved) */
+    double rel_res_guess;  /* with a net: ||b - A p|| / ||b|| of the guess, else -1 */
+    double rel_res_start;  /* with a net: the same after the warm start, else -1 */
 } mcd_solve_info;
 
 /* mcd_solve_pressure - solve A p = b (b from mcd_assemble_rhs(rhs, bnd)).
- * p_dev: device float64 [N]; in: initial guess (ignored when a net is
- * given), out: solution.  Dirichlet entries of the guess are replaced by
- * their values.  info: host, may be NULL.  Synchronises `stream`.
+ * p_dev: device float64 [N]; in: initial guess (with a net, the point the
+ * warm start corrects), out: solution.  Dirichlet entries of the guess are
+ * replaced by their values.  info: host, may be NULL.  Synchronises `stream`.
  * Returns MCD_ENOCONV if max_iter is reached (p holds the last iterate),
  * MCD_ENONFINITE if b or a residual is not finite, MCD_ESINGULAR if the
  * handle recorded a singular stencil. */
@@ -326,6 +332,81 @@ mcd_status mcd_body_boundary(const mcd_mesh *mesh, const mcd_body *body,
                              mcd_stream_t stream);
 
 /* -------------------------------------------------------------------------
+ * Learned warm start (an addition: the paper has no network)
+ *
+ * A stack of `layers` 3x3 convolutions on the 2D background-mesh grid (zero
+ * padding, stride 1, cross-correlation), `width` channels, ReLU between
+ * layers, one output channel.  bf16 weights and activations on the tensor
+ * cores, FP32 accumulation, FP32 master parameters and Adam moments.
+ *
+ * Parameters (host float32, flat): for each layer W[o][c][dj][di]
+ * (o output, c input channel, dj/di the row/column tap 0..2; input cell
+ * (i + di - 1, j + dj - 1) feeds output cell (i, j)), then b[o].
+ *
+ * Features (device bf16 [N][8], cell index k = i + n0 j, raw uint16 bits):
+ * 0 r / s_r, with r = b - A p the residual of the guess and s_r its rms over
+ * non-void DPs; 1, 2, 3 one-hot role (inner, boundary, void); 4, 5 the DP
+ * offset (x - x_cell) / l0; 6 dprev / s_d, dprev the last pressure increment
+ * and s_d its rms (0 without one); 7 zero.  Channels 0, 4, 5, 6 are 0 at
+ * void DPs.  The network output y is a correction in units of
+ * s_out = s_d if s_d > 0, else s_r l0^2.
+ * ---------------------------------------------------------------------- */
+enum { MCD_NET_PARAMS = 0, MCD_NET_GRADS = 1, MCD_NET_ADAM_M = 2, MCD_NET_ADAM_V = 3 };
+
+/* Number of parameters, or -1 for an unsupported shape (supported: c_in in
+ * [1, 8], width 32, layers in [2, 8]). */
+int64_t mcd_net_param_count(int c_in, int width, int layers);
+
+/* mcd_net_create - network with the given host parameters (copied); Adam
+ * moments zero.  Returns MCD_ENOTSUP for an unsupported shape, MCD_EINVAL if
+ * n_params does not match.  Synchronises the device. */
+mcd_status mcd_net_create(int c_in, int width, int layers, const float *params,
+                          int64_t n_params, mcd_net **net);
+void mcd_net_destroy(mcd_net *net);
+
+/* Copy the FP32 parameters (MCD_NET_PARAMS), the gradients of the last
+ * training step (MCD_NET_GRADS) or an Adam moment to host_out [count];
+ * count must equal the parameter count.  Synchronises the device. */
+mcd_status mcd_net_read(const mcd_net *net, int which, float *host_out, int64_t count);
+
+/* mcd_net_features - features of the system of `st` at the guess p:
+ * r = b - A p (b the assembled right-hand side, mcd_assemble_rhs), written
+ * to x_dev (bf16 [N][8], layout above).  dprev_dev: device float64 [N] or
+ * NULL.  With p_true_dev (device float64 [N], the converged solution) also
+ * the training target (p_true - p) / s_out and weight 1 on unknown DPs
+ * (inner and Neumann; 0 and 0 elsewhere) into target_dev / weight_dev
+ * (device float32 [N]).  2D stencil handles only (else MCD_ENOTSUP).
+ * Asynchronous; uses the network's scratch (one call at a time per net). */
+mcd_status mcd_net_features(mcd_net *net, const mcd_stencils *st, const double *b_dev,
+                            const double *p_dev, const double *dprev_dev,
+                            const double *p_true_dev, uint16_t *x_dev, float *target_dev,
+                            float *weight_dev, mcd_stream_t stream);
+
+/* mcd_net_forward - y_dev (device float32 [nx*ny]) = network(x_dev) with
+ * x_dev the bf16 features [nx*ny][8].  Asynchronous. */
+mcd_status mcd_net_forward(mcd_net *net, const uint16_t *x_dev, int nx, int ny,
+                           float *y_dev, mcd_stream_t stream);
+
+/* mcd_net_train_step - one Adam step (lr, beta = 0.9 / 0.999, eps = 1e-8)
+ * on the loss sum_k w_k (y_k - target_k)^2 / sum_k w_k of one sample
+ * (x_dev bf16 [nx*ny][8]; target_dev, weight_dev float32 [nx*ny]).
+ * loss_dev: device float64 [1] receiving the loss before the step, or NULL.
+ * Asynchronous. */
+mcd_status mcd_net_train_step(mcd_net *net, const uint16_t *x_dev, const float *target_dev,
+                              const float *weight_dev, int nx, int ny, float lr,
+                              double *loss_dev, mcd_stream_t stream);
+
+/* mcd_net_warm_start - p <- p + s e, e = y s_out on unknown DPs (0 elsewhere),
+ * y = network(features of (b, p, dprev)), s = <r, A e> / <A e, A e> the step
+ * that minimises ||b - A (p + s e)||_2 (0 if A e = 0): the residual never
+ * grows.  b_dev: assembled right-hand side; p_dev updated in place.
+ * stats: host double [3] or NULL; when given (synchronises the stream) it
+ * receives ||r|| / ||b|| before and after and the step s. */
+mcd_status mcd_net_warm_start(mcd_net *net, const mcd_stencils *st, const double *b_dev,
+                              const double *dprev_dev, double *p_dev, double *stats,
+                              mcd_stream_t stream);
+
+/* -------------------------------------------------------------------------
  * Instrumentation (metrics and tracing; not part of the method)
  * ---------------------------------------------------------------------- */
 enum {
@@ -337,7 +418,8 @@ enum {
     MCD_K_UPDATE = 5,    /* remask + relaxation sweeps          */
     MCD_K_OTHER = 6,     /* everything else                     */
     MCD_K_SOLVE = 7,     /* persistent cooperative Bi-CGSTAB     */
-    MCD_K_COUNT = 8
+    MCD_K_CNN = 8,       /* network: convolutions, features, training */
+    MCD_K_COUNT = 9
 };
 
 /* When sample_every > 0, every sample_every-th launch of each kernel class

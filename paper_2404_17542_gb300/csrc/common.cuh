@@ -120,9 +120,19 @@ struct mcd_stencils {
     double *qd64;        // [nb][S][N] (want_derivs && has_neumann)
     double *rscale;      // [N]
     int8_t *kind;        // [N]
+    uint16_t *off16;     // [N][2] bf16 DP offsets (x - x_cell) / l0 (2D; network features)
     unsigned long long *bad_dp;  // device: smallest failing DP, ~0ull if none
     mcd::Workspace *ws;
 };
+
+namespace mcd {
+// Fill st->off16 from the DP positions (cnn.cu; no-op in 3D).
+cudaError_t cnn_store_offsets(const mcd_stencils *st, const double *pos, const int8_t *mask,
+                              cudaStream_t stream);
+// Network warm start of a solve: p <- p + s e on the assembled system (cnn.cu).
+mcd_status net_warm_start(const mcd_net *net, const mcd_stencils *st, const double *b,
+                          const double *dprev, double *p, double *host_sc, cudaStream_t stream);
+}  // namespace mcd
 
 // Launch a kernel inside a KTimer scope: MCD_KLAUNCH(kind, stream, k<<<...>>>(...));
 #define MCD_KLAUNCH(kind, stream, ...)               \

@@ -1753,6 +1753,11 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
     MCD_CUDA_TRY(cudaMemcpyAsync(w->sc, &init, sizeof(init), cudaMemcpyHostToDevice, stream));
     MCD_KLAUNCH(MCD_K_OTHER, stream, fix_guess<<<w->nblk1, 256, 0, stream>>>(N, st->kind, w->b, p, w->sc));
     MCD_LAUNCH_CHECK();
+    double ws_sc[8] = {0.0};
+    if (prm->net) {
+        s = net_warm_start(prm->net, st, w->b, prm->net_dprev, p, ws_sc, stream);
+        if (s != MCD_OK) return s;
+    }
     const int check_every = prm->check_every > 0 ? prm->check_every : 64;   // legacy schedule
     const int max_outer = prm->max_refine > 0 ? prm->max_refine : 50;
     const int max_launch = (init.max_iter > (1 << 29) ? (1 << 29) : init.max_iter) + 2 * check_every;
@@ -1814,6 +1819,12 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
         info->b_norm = sqrt(h.bb64);
         info->rel_res = h.bb64 > 0.0 ? sqrt(h.rr64 / h.bb64) : 0.0;
         info->unknowns = (int64_t)h.unknowns;
+        info->rel_res_guess = -1.0;
+        info->rel_res_start = -1.0;
+        if (prm->net && ws_sc[4] > 0.0) {
+            info->rel_res_guess = sqrt(ws_sc[3] / ws_sc[4]);
+            info->rel_res_start = sqrt(ws_sc[6] / ws_sc[4]);
+        }
     }
     if (result == MCD_ENOCONV) set_error("solve reached max_iter / max_refine before tol");
     if (result == MCD_ENONFINITE) set_error("non-finite value in right-hand side or residual");
@@ -1861,7 +1872,6 @@ extern "C" mcd_status mcd_solve_pressure(const mcd_stencils *st, const double *r
     MCD_CHECK_ARG(prm->mode != MCD_MIXED || st->row32, "MIXED solve needs an MCD_MIXED stencil handle");
     MCD_CHECK_ARG(prm->mode != MCD_MIXED || (prm->inner_tol > 0.0 && prm->inner_tol < 1.0),
                   "inner_tol must be in (0, 1)");
-    MCD_CHECK_ARG(prm->net == nullptr, "network warm start is not available in this build");
     mcd_status s = mcd_stencils_check(st, nullptr, stream);
     if (s != MCD_OK) return s;
     s = ensure_workspace(const_cast<mcd_stencils *>(st), prm->mode);

@@ -428,6 +428,7 @@ static void free_arrays(mcd_stencils *st) {
     cudaFree(st->qd64);
     cudaFree(st->rscale);
     cudaFree(st->kind);
+    cudaFree(st->off16);
     cudaFree(st->bad_dp);
 }
 
@@ -497,6 +498,7 @@ extern "C" mcd_status mcd_build_stencils(const mcd_mesh *mesh, const double *pos
         }
         chk(dmalloc(&h->rscale, (size_t)N));
         chk(dmalloc(&h->kind, (size_t)N));
+        if (mesh->dim == 2) chk(dmalloc(&h->off16, (size_t)2 * N));
         chk(dmalloc(&h->bad_dp, 1));
         if (e != cudaSuccess) {
             free_arrays(h);
@@ -536,6 +538,7 @@ extern "C" mcd_status mcd_build_stencils(const mcd_mesh *mesh, const double *pos
     else
         MCD_KLAUNCH(MCD_K_BUILD, stream, build_kernel<3><<<blocks, threads, 0, stream>>>(a));
     MCD_LAUNCH_CHECK();
+    MCD_CUDA_TRY(cnn_store_offsets(h, pos_dev, mask_dev, stream));
     return MCD_OK;
 }
 

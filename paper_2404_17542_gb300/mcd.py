@@ -46,12 +46,13 @@ class c_mls_params(C.Structure):
 class c_solve_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("mode", C.c_int),
                 ("inner_tol", C.c_double), ("max_refine", C.c_int), ("net", C.c_void_p),
-                ("check_every", C.c_int), ("update_restart", C.c_int)]
+                ("check_every", C.c_int), ("update_restart", C.c_int), ("net_dprev", C.c_void_p)]
 
 
 class c_solve_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("restarts", C.c_int),
-                ("rel_res", C.c_double), ("b_norm", C.c_double), ("unknowns", C.c_int64)]
+                ("rel_res", C.c_double), ("b_norm", C.c_double), ("unknowns", C.c_int64),
+                ("rel_res_guess", C.c_double), ("rel_res_start", C.c_double)]
 
 
 class c_body(C.Structure):
@@ -84,6 +85,15 @@ _SIGS = {
                          + [C.c_void_p] * 3 + [C.c_void_p]),
     "mcd_flow_project": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.c_double]
                          + [C.c_void_p] * 2 + [C.c_void_p]),
+    "mcd_net_param_count": (C.c_int64, [C.c_int, C.c_int, C.c_int]),
+    "mcd_net_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
+    "mcd_net_destroy": (None, [C.c_void_p]),
+    "mcd_net_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
+    "mcd_net_features": (C.c_int, [C.c_void_p] * 9 + [C.c_void_p]),
+    "mcd_net_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "mcd_net_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                     C.c_float, C.c_void_p, C.c_void_p]),
+    "mcd_net_warm_start": (C.c_int, [C.c_void_p] * 6 + [C.c_void_p]),
     "mcd_timing_enable": (C.c_int, [C.c_int]),
     "mcd_timing_read": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "mcd_launch_count": (C.c_int64, []),
@@ -211,19 +221,24 @@ class Stencils:
         return b
 
     def solve(self, rhs, bnd, p=None, tol=1e-8, mode=MIXED, max_iter=200000, inner_tol=0.1,
-              max_refine=60, check_every=64, update_restart=1, raise_on_error=True):
-        """Solve the PPE; returns (p, info dict).  p is updated in place if given."""
+              max_refine=60, check_every=64, update_restart=1, raise_on_error=True, net=None,
+              dprev=None):
+        """Solve the PPE; returns (p, info dict).  p is updated in place if given.
+        net (a Net) adds its warm-start correction to p first; dprev is the
+        last pressure increment it reads (or None)."""
         if p is None:
             p = torch.zeros(self.N, dtype=torch.float64, device=rhs.device)
         sp = c_solve_params(tol=tol, max_iter=max_iter, mode=mode, inner_tol=inner_tol,
-                            max_refine=max_refine, net=None, check_every=check_every,
-                            update_restart=int(update_restart))
+                            max_refine=max_refine, net=None if net is None else net.handle,
+                            check_every=check_every, update_restart=int(update_restart),
+                            net_dprev=None if dprev is None else _ptr(dprev, torch.float64, self.N))
         info = c_solve_info()
         st = lib().mcd_solve_pressure(self.handle, _ptr(rhs, torch.float64, self.N),
                                       _ptr(bnd, torch.float64, self.N), _ptr(p, torch.float64, self.N),
                                       C.byref(sp), C.byref(info), _stream())
         d = dict(status=st, iters=info.iters, refinements=info.refinements, restarts=info.restarts,
-                 rel_res=info.rel_res, b_norm=info.b_norm, unknowns=info.unknowns)
+                 rel_res=info.rel_res, b_norm=info.b_norm, unknowns=info.unknowns,
+                 rel_res_guess=info.rel_res_guess, rel_res_start=info.rel_res_start)
         if st != OK and raise_on_error:
             raise McdError(st, lib().mcd_last_error().decode())
         return p, d
@@ -261,6 +276,86 @@ class Stencils:
             self.close()
         except Exception:
             pass
+
+
+NET_PARAMS, NET_GRADS, NET_ADAM_M, NET_ADAM_V = range(4)
+N_CHANNELS = 8
+
+
+class Net:
+    """Owner of an mcd_net handle: the learned warm start (conv network)."""
+
+    def __init__(self, params, c_in=7, width=32, layers=4):
+        flat = np.ascontiguousarray(params, dtype=np.float32)
+        self.c_in, self.width, self.layers = c_in, width, layers
+        self.n_params = int(lib().mcd_net_param_count(c_in, width, layers))
+        if self.n_params < 0:
+            raise McdError(ENOTSUP, "unsupported network shape")
+        self.handle = C.c_void_p(None)
+        _check(lib().mcd_net_create(c_in, width, layers, flat.ctypes.data_as(C.c_void_p),
+                                    flat.size, C.byref(self.handle)))
+
+    def read(self, which=NET_PARAMS):
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().mcd_net_read(self.handle, int(which), out.ctypes.data_as(C.c_void_p), out.size))
+        return out
+
+    def features(self, st: Stencils, b, p, dprev=None, p_true=None):
+        """bf16 features [N][8] (int16 storage of the bf16 bits); with p_true
+        also (target, weight) float32 [N]."""
+        N = st.N
+        f64 = torch.float64
+        x = torch.empty((N, N_CHANNELS), dtype=torch.int16, device=b.device)
+        tgt = wt = None
+        if p_true is not None:
+            tgt = torch.empty(N, dtype=torch.float32, device=b.device)
+            wt = torch.empty(N, dtype=torch.float32, device=b.device)
+        _check(lib().mcd_net_features(
+            self.handle, st.handle, _ptr(b, f64, N), _ptr(p, f64, N),
+            None if dprev is None else _ptr(dprev, f64, N),
+            None if p_true is None else _ptr(p_true, f64, N), _ptr(x),
+            None if tgt is None else _ptr(tgt), None if wt is None else _ptr(wt), _stream()))
+        return x if p_true is None else (x, tgt, wt)
+
+    def forward(self, x, nx, ny, y=None):
+        y = torch.empty(nx * ny, dtype=torch.float32, device=x.device) if y is None else y
+        _check(lib().mcd_net_forward(self.handle, _ptr(x, torch.int16, nx * ny * N_CHANNELS), int(nx),
+                                     int(ny), _ptr(y, torch.float32, nx * ny), _stream()))
+        return y
+
+    def train_step(self, x, target, weight, nx, ny, lr, loss=None):
+        """One Adam step; loss (float64 [1] on the device) receives the loss."""
+        N = nx * ny
+        _check(lib().mcd_net_train_step(self.handle, _ptr(x, torch.int16, N * N_CHANNELS),
+                                        _ptr(target, torch.float32, N), _ptr(weight, torch.float32, N),
+                                        int(nx), int(ny), float(lr),
+                                        None if loss is None else _ptr(loss, torch.float64, 1),
+                                        _stream()))
+
+    def warm_start(self, st: Stencils, b, p, dprev=None):
+        """p <- p + s e in place; returns (rel. residual before, after, s)."""
+        stats = (C.c_double * 3)()
+        f64 = torch.float64
+        _check(lib().mcd_net_warm_start(self.handle, st.handle, _ptr(b, f64, st.N),
+                                        None if dprev is None else _ptr(dprev, f64, st.N),
+                                        _ptr(p, f64, st.N), stats, _stream()))
+        return stats[0], stats[1], stats[2]
+
+    def close(self):
+        if self.handle and self.handle.value:
+            lib().mcd_net_destroy(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bf16_bits_to_float(x: torch.Tensor) -> torch.Tensor:
+    """float32 values of bf16 bit patterns held in an int16 tensor."""
+    return (x.to(torch.int32) << 16).view(torch.float32)
 
 
 def make_body(centre, radius, body_id, vel=(0.0, 0.0), acc=(0.0, 0.0)) -> c_body:
@@ -311,9 +406,9 @@ def body_boundary(mesh, centre, radius, body_id, pos, mask, acc=(0.0, 0.0), norm
     return n, f
 
 
-K_BICG_A, K_BICG_B, K_BICG_C, K_RESIDUAL, K_BUILD, K_UPDATE, K_OTHER, K_SOLVE = range(8)
+K_BICG_A, K_BICG_B, K_BICG_C, K_RESIDUAL, K_BUILD, K_UPDATE, K_OTHER, K_SOLVE, K_CNN = range(9)
 KERNEL_NAMES = ["bicg_ka", "bicg_kb", "bicg_kc", "residual64", "build_kernel", "update", "other",
-                "bicg_persistent"]
+                "bicg_persistent", "cnn"]
 
 
 def timing_enable(sample_every: int):

@@ -1,0 +1,340 @@
+"""GPU parity of the learned warm start (bf16 tensor-core network).
+
+Compared with the FP64 oracle (oracle/cnn.py):
+  * features of a PPE system: role and offset channels bit-exact (up to a
+    rounding tie), residual and increment channels to half a bf16 ulp;
+  * forward pass on ragged grids (sizes not multiples of the 16 x 16 tile):
+    against the oracle with the kernel's bf16 rounding applied at the same
+    points (weights, hidden activations) to 2e-3 relative L2 -- FP32
+    accumulation order and the bf16 rounding of an FP32 (not exact) value
+    are the only differences -- and against plain FP64 to 3e-2
+    (about 8 bf16 roundings along the path, u = 2^-9 each);
+  * gradients of one training step per layer tensor to 2e-2 relative L2
+    (the kernel rounds the backpropagated gradient to bf16 at every layer);
+  * Adam: parameters after two steps equal the oracle's Adam applied to the
+    gradients the GPU used, to one FP32 ulp of the stored parameter plus
+    1e-5 lr (the update itself is FP32 arithmetic);
+  * warm start: the step s and the residual after it match the oracle's line
+    search on the oracle's own network output to 2e-2, and the residual
+    never grows.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import cnn, mls, solve  # noqa: E402
+from paper_2404_17542_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mcd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_17542_gb300 import build
+    build.build()
+    from paper_2404_17542_gb300 import mcd as m
+    m.lib()
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def net_params(seed, layers=4):
+    ws, bs = inputs.cnn_weights(seed, layers=layers)
+    rng = np.random.default_rng(seed + 100)
+    bs = [rng.normal(0.0, 0.05, size=b.shape).astype(np.float32).astype(np.float64) for b in bs]
+    return ws, bs
+
+
+def gpu_to_chw(mcd, x, nx, ny):
+    """[N][8] bf16 bits (int16) -> float64 (8, ny, nx)."""
+    f = mcd.bf16_bits_to_float(x).cpu().numpy().astype(np.float64)
+    return f.reshape(ny, nx, 8).transpose(2, 0, 1)
+
+
+def random_features(nx, ny, seed):
+    """bf16-representable inputs shaped like the real channels."""
+    rng = np.random.default_rng(seed)
+    role = rng.integers(0, 3, size=(ny, nx))
+    x = np.zeros((8, ny, nx))
+    x[0] = rng.normal(size=(ny, nx))
+    x[1:4] = np.stack([role == 0, role == 1, role == 2]).astype(float)
+    x[4:6] = rng.uniform(-0.5, 0.5, size=(2, ny, nx))
+    x[6] = rng.normal(size=(ny, nx))
+    x[[0, 4, 5, 6]] *= (role != 2)
+    return cnn.bf16_round(x)
+
+
+def to_gpu_features(x):
+    """(8, ny, nx) float64 (bf16-representable) -> [N][8] int16 bf16 bits."""
+    f32 = np.ascontiguousarray(x.transpose(1, 2, 0).reshape(-1, 8), dtype=np.float32)
+    bits = (f32.view(np.uint32) >> 16).astype(np.uint16).view(np.int16)
+    return dev(bits)
+
+
+@pytest.mark.parametrize("nx,ny", [(45, 37), (70, 33), (16, 16), (5, 3)])
+def test_forward_parity(mcd, nx, ny):
+    ws, bs = net_params(1)
+    x = random_features(nx, ny, seed=nx)
+    net = mcd.Net(inputs.cnn_flatten(ws, bs))
+    y = net.forward(to_gpu_features(x), nx, ny).cpu().numpy().reshape(ny, nx)
+    wr = [cnn.bf16_round(w) for w in ws]
+    emu = cnn.forward(wr, bs, x[:7], rnd=cnn.bf16_round)[-1][0]
+    plain = cnn.forward(ws, bs, x[:7])[-1][0]
+    assert rel(y, emu) <= 2e-3
+    assert rel(y, plain) <= 3e-2
+
+
+def test_features_parity(mcd):
+    from oracle import mask as omask
+    pb = inputs.cylinder_box(64)
+    cyl = pb.meta["cylinder"]
+    c = cyl.centre(0.0)
+    pos, m, _ = omask.update_dps(pb.mesh, pb.pos, pb.mask, c, cyl.radius, band=0.0, n_relax=4)
+    normal = omask.circle_normals(pos, m, c, cyl.body_id)
+    W = mls.build_weights(pb.mesh, pos, m, normal, pb.bc_kind)
+    rng = np.random.default_rng(3)
+    N = pb.mesh.N
+    rhs = inputs.ppe_source(pos, 0.1)
+    bnd = np.where(m == cyl.body_id, rng.normal(size=N), 0.0)
+    A = solve.assemble(pb.mesh, W["row"])
+    b = solve.form_rhs(pb.mesh, W["kind"], W["QL"], rhs, bnd, W["rscale"])
+    p = np.where(W["kind"] == 2, b / W["rscale"], rng.normal(size=N))
+    dprev = np.where(m != 0, rng.normal(size=N), 0.0)
+    p_true = solve.direct_solve(A, b)
+
+    st = mcd.Stencils(pb.mesh, dev(pos.ravel()), dev(m), dev(normal.ravel()), bc_kind=pb.bc_kind,
+                      precision=mcd.FP64)
+    net = mcd.Net(inputs.cnn_flatten(*net_params(2)))
+    b_g = st.assemble_rhs(dev(rhs), dev(bnd))
+    x, tgt, wt = net.features(st, b_g, dev(p), dev(dprev), dev(p_true))
+    got = gpu_to_chw(mcd, x, 64, 64)
+    r = b - A @ p
+    want, (s_r, s_d, s_out) = cnn.features(pb.mesh, r, m, pos, dprev)
+    want = cnn.bf16_round(want)
+    exact = [1, 2, 3, 4, 5, 7]
+    assert np.mean(got[exact] == want[exact]) >= 0.9999
+    assert np.all(np.abs(got[exact] - want[exact]) <= 2.0 ** -8 * np.abs(want[exact]))
+    for ch in (0, 6):
+        assert np.all(np.abs(got[ch] - want[ch]) <= 2.0 ** -8 * np.abs(want[ch]) + 1e-30)
+    unknown = (W["kind"] == 1) | (W["kind"] == 3)
+    t_want, w_want = cnn.target(p_true, p, unknown, s_out)
+    assert np.array_equal(wt.cpu().numpy(), w_want.astype(np.float32))
+    assert np.allclose(tgt.cpu().numpy(), t_want, rtol=1e-6, atol=1e-6 * np.abs(t_want).max())
+
+
+def test_train_step_gradients_and_adam(mcd):
+    nx, ny = 41, 35
+    ws, bs = net_params(4)
+    x = random_features(nx, ny, seed=9)
+    rng = np.random.default_rng(5)
+    target = rng.normal(size=(1, ny, nx)).astype(np.float32).astype(np.float64)
+    weight = (x[1] > 0).astype(float)[None]
+    flat0 = inputs.cnn_flatten(ws, bs)
+    net = mcd.Net(flat0)
+    xg = to_gpu_features(x)
+    lr = 1e-3
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    net.train_step(xg, dev(target.ravel().astype(np.float32)), dev(weight.ravel().astype(np.float32)),
+                   nx, ny, lr, loss)
+    g1 = net.read(mcd.NET_GRADS)
+    p1 = net.read(mcd.NET_PARAMS)
+
+    # gradients vs the oracle on the same (bf16) weights and activations
+    wr = [cnn.bf16_round(w) for w in ws]
+    acts = cnn.forward(wr, bs, x[:7], rnd=cnn.bf16_round)
+    l_want, dy = cnn.loss(acts[-1], target, weight)
+    assert float(loss.item()) == pytest.approx(l_want, rel=1e-3)
+    dws, dbs = cnn.backward(wr, bs, acts, dy)
+    gw, gb = inputs.cnn_unflatten(g1)
+    for li in range(4):
+        assert rel(gw[li], dws[li]) <= 2e-2, li
+        assert rel(gb[li], dbs[li]) <= 2e-2, li
+
+    # Adam: the oracle's update applied to the gradients the GPU used
+    params = [np.asarray(a, np.float64) for a in inputs.cnn_unflatten(flat0)[0]]
+    params += [np.asarray(a, np.float64) for a in inputs.cnn_unflatten(flat0)[1]]
+    m = [np.zeros_like(a) for a in params]
+    v = [np.zeros_like(a) for a in params]
+    grads = list(gw) + list(gb)
+    cnn.adam(params, grads, m, v, 1, lr)
+    want1 = inputs.cnn_flatten(params[:4], params[4:])
+    ulp = np.spacing(np.abs(want1).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(p1.astype(np.float64) - want1) <= ulp + 1e-5 * lr)
+
+    net.train_step(xg, dev(target.ravel().astype(np.float32)), dev(weight.ravel().astype(np.float32)),
+                   nx, ny, lr)
+    g2 = net.read(mcd.NET_GRADS)
+    gw2, gb2 = inputs.cnn_unflatten(g2)
+    cnn.adam(params, list(gw2) + list(gb2), m, v, 2, lr)
+    want2 = inputs.cnn_flatten(params[:4], params[4:])
+    ulp = np.spacing(np.abs(want2).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(net.read(mcd.NET_PARAMS).astype(np.float64) - want2) <= 2 * ulp + 2e-5 * lr)
+
+
+def test_training_fits_a_teacher(mcd):
+    """Loss falls when the target is another network of the same shape."""
+    nx, ny = 64, 48
+    x = random_features(nx, ny, seed=11)
+    tw, tb = net_params(20)
+    target = cnn.forward(tw, tb, x[:7])[-1].astype(np.float32)
+    weight = np.ones((1, ny, nx), np.float32)
+    net = mcd.Net(inputs.cnn_flatten(*net_params(21)))
+    xg = to_gpu_features(x)
+    tg, wg = dev(target.ravel()), dev(weight.ravel())
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    hist = []
+    for it in range(300):
+        net.train_step(xg, tg, wg, nx, ny, 2e-3, loss)
+        if it in (0, 299):
+            hist.append(float(loss.item()))
+    assert hist[1] < 0.2 * hist[0]
+
+
+def test_warm_start_parity_and_solve(mcd):
+    from oracle import mask as omask
+    pb = inputs.cylinder_box(48)
+    cyl = pb.meta["cylinder"]
+    c = cyl.centre(0.0)
+    pos, m, _ = omask.update_dps(pb.mesh, pb.pos, pb.mask, c, cyl.radius, band=0.0, n_relax=4)
+    normal = omask.circle_normals(pos, m, c, cyl.body_id)
+    W = mls.build_weights(pb.mesh, pos, m, normal, pb.bc_kind)
+    N = pb.mesh.N
+    rng = np.random.default_rng(8)
+    rhs = inputs.ppe_source(pos, 0.2)
+    bnd = np.where(m == cyl.body_id, rng.normal(size=N) * 0.1, 0.0)
+    A = solve.assemble(pb.mesh, W["row"])
+    b = solve.form_rhs(pb.mesh, W["kind"], W["QL"], rhs, bnd, W["rscale"])
+    p_true = solve.direct_solve(A, b)
+    # a guess with a smooth and a rough error, and an increment close to it
+    X, Y = pos
+    err = 0.05 * np.sin(3 * X) * np.cos(2 * Y) + 1e-3 * rng.normal(size=N)
+    unknown = (W["kind"] == 1) | (W["kind"] == 3)
+    p0 = np.where(unknown, p_true - err, b / np.where(W["rscale"] != 0, W["rscale"], 1.0))
+    p0 = np.where(W["kind"] == 0, 0.0, p0)
+    dprev = np.where(m != 0, err * 0.9, 0.0)
+
+    ws, bs = net_params(6)
+    net = mcd.Net(inputs.cnn_flatten(ws, bs))
+    st = mcd.Stencils(pb.mesh, dev(pos.ravel()), dev(m), dev(normal.ravel()), bc_kind=pb.bc_kind,
+                      precision=mcd.MIXED)
+    b_g = st.assemble_rhs(dev(rhs), dev(bnd))
+    p_g = dev(p0)
+    before, after, s = net.warm_start(st, b_g, p_g, dev(dprev))
+
+    x, (s_r, s_d, s_out) = cnn.features(pb.mesh, b - A @ p0, m, pos, dprev)
+    y = cnn.forward([cnn.bf16_round(w) for w in ws], bs, cnn.bf16_round(x)[:7],
+                    rnd=cnn.bf16_round)[-1][0].ravel()
+    e = np.where(unknown, y * s_out, 0.0)
+    q, s_want = cnn.warm_start(A, b, p0, e)
+    nb = np.linalg.norm(b)
+    assert before == pytest.approx(np.linalg.norm(b - A @ p0) / nb, rel=1e-9)
+    assert s == pytest.approx(s_want, rel=2e-2)
+    assert after == pytest.approx(np.linalg.norm(b - A @ q) / nb, rel=2e-2)
+    assert after <= before
+    got = p_g.cpu().numpy()
+    assert np.linalg.norm(b - A @ got) / nb == pytest.approx(after, rel=1e-6)
+
+    # the same warm start inside the solve, then convergence to tol
+    p_s = dev(p0)
+    p_s, info = st.solve(dev(rhs), dev(bnd), p=p_s, tol=1e-10, net=net, dprev=dev(dprev))
+    assert info["rel_res_guess"] == pytest.approx(before, rel=1e-9)
+    assert info["rel_res_start"] == pytest.approx(after, rel=1e-6)
+    assert info["rel_res"] <= 1e-10
+    assert rel(p_s.cpu().numpy(), p_true) <= 1e-8
+
+
+def test_net_rejects_bad_shapes(mcd):
+    with pytest.raises(mcd.McdError):
+        mcd.Net(np.zeros(10, np.float32), width=16)
+    with pytest.raises(mcd.McdError):
+        mcd.Net(np.zeros(10, np.float32))
+
+
+def cylinder_sequence(mcd, n, steps, net=None, train=None):
+    """Run the oscillating-cylinder pressure sequence on the GPU (DP update,
+    stencil build, mixed solve warm-started from the previous pressure).
+    With `train` (a list) it appends (x, target, weight) of every step; with
+    `net` it returns the warm-start statistics of every step instead of
+    solving without it."""
+    pb = inputs.cylinder_box(n)
+    cyl, mesh = pb.meta["cylinder"], pb.mesh
+    N = mesh.N
+    dt = 0.2 * mesh.l0
+    pos = dev(pb.pos.ravel().copy())
+    mask = dev(pb.mask.copy())
+    prev = torch.empty_like(mask)
+    normal = torch.zeros(2 * N, dtype=torch.float64, device="cuda")
+    neu = torch.zeros(N, dtype=torch.float64, device="cuda")
+    rhs = dev(inputs.ppe_source(pb.pos, 0.0))
+    mcd.update_dps(mesh, cyl.centre(0.0), cyl.radius, cyl.body_id, pos, mask, prev, n_relax=30, band=0.0)
+    mcd.body_boundary(mesh, cyl.centre(0.0), cyl.radius, cyl.body_id, pos, mask,
+                      acc=cyl.acceleration(0.0), normal=normal, neumann=neu)
+    st = mcd.Stencils(mesh, pos, mask, normal, bc_kind=pb.bc_kind, precision=mcd.MIXED)
+    p = torch.zeros(N, dtype=torch.float64, device="cuda")
+    p_m1 = p.clone()
+    stats = []
+    for k in range(1, steps + 1):
+        t = k * dt
+        c = cyl.centre(t)
+        mcd.update_dps(mesh, c, cyl.radius, cyl.body_id, pos, mask, prev, band=5.0 * mesh.l0)
+        mcd.body_boundary(mesh, c, cyl.radius, cyl.body_id, pos, mask, acc=cyl.acceleration(t),
+                          normal=normal, neumann=neu)
+        st.rebuild(pos, mask, normal)
+        dprev = p - p_m1
+        p_prev = p.clone()
+        if net is not None:
+            p, info = st.solve(rhs, neu, p=p, net=net, dprev=dprev)
+            stats.append((info["rel_res_guess"], info["rel_res_start"], info["iters"]))
+        else:
+            p, info = st.solve(rhs, neu, p=p)
+        if train is not None and k > 2:
+            b = st.assemble_rhs(rhs, neu)
+            train.append(net_features(mcd, st, b, p_prev, dprev, p))
+        p_m1 = p_prev
+    return stats
+
+
+_FEATURE_NET = {}
+
+
+def net_features(mcd, st, b, p_prev, dprev, p_true):
+    if "net" not in _FEATURE_NET:
+        _FEATURE_NET["net"] = mcd.Net(inputs.cnn_flatten(*net_params(0)))
+    return _FEATURE_NET["net"].features(st, b, p_prev, dprev, p_true)
+
+
+def test_trained_net_gains_over_untrained_and_plain(mcd):
+    """The gain the trained network brings on the cylinder sequence: the
+    residual of the warm-started guess relative to the plain warm start
+    (the previous pressure).  The line search guarantees a ratio <= 1; an
+    untrained network gets only what a random direction gives, the trained
+    one must cut the residual at least in half on steps it has not seen."""
+    n = 128
+    data = []
+    cylinder_sequence(mcd, n, 40, train=data)
+    net = mcd.Net(inputs.cnn_flatten(*net_params(30)))
+    untrained = mcd.Net(inputs.cnn_flatten(*net_params(30)))
+    rng = np.random.default_rng(0)
+    for _ep in range(25):
+        for i in rng.permutation(len(data)):
+            x, tg, wt = data[i]
+            net.train_step(x, tg, wt, n, n, 1e-3)
+    trained = cylinder_sequence(mcd, n, 48, net=net)[40:]
+    random_net = cylinder_sequence(mcd, n, 48, net=untrained)[40:]
+    r_tr = np.mean([after / before for before, after, _ in trained])
+    r_un = np.mean([after / before for before, after, _ in random_net])
+    it_tr = np.mean([it for *_r, it in trained])
+    it_un = np.mean([it for *_r, it in random_net])
+    print(f"residual ratio trained {r_tr:.3f} untrained {r_un:.3f}; iterations {it_tr:.0f} / {it_un:.0f}")
+    assert r_tr <= 0.5
+    assert r_tr < 0.75 * r_un
