@@ -332,6 +332,80 @@ mcd_status mcd_body_boundary(const mcd_mesh *mesh, const mcd_body *body,
                              mcd_stream_t stream);
 
 /* -------------------------------------------------------------------------
+ * Batched systems (an addition: the paper solves one system at a time)
+ *
+ * `count` independent 2D systems (Sec. 2.2 meshes, Dirichlet boundary ids
+ * only) built and solved together.  They are stored back to back: system i
+ * owns DPs [off_i, off_i + N_i) (off_i = mcd_batch_offset(bt, i)) of every
+ * per-DP device array (mask, rhs, bnd, p: [total N]); its positions are the
+ * [2][N_i] block starting at element 2 off_i of pos.  In mcd_mls_params the
+ * radii r_e and r_s are multiples of each system's own l0.
+ * ---------------------------------------------------------------------- */
+typedef struct mcd_batch mcd_batch;
+
+/* Tiling of the batched solve: tiles of 32 x (8 rows) DPs per CTA step, and
+ * CTAs per SM of the persistent launch (0: the default, 2). */
+typedef struct {
+    int rows;          /* 1, 2 or 4 */
+    int ctas_per_sm;   /* 0 .. 4 */
+} mcd_batch_tuning;
+
+typedef struct {
+    int status;        /* MCD_OK, MCD_ENOCONV, MCD_EBREAKDOWN or MCD_ENONFINITE */
+    int iters;         /* Bi-CGSTAB iterations of this system */
+    int updates;       /* true-residual updates after the first */
+    double rel_res;    /* ||b - A p|| / ||b|| (FP64) at the last update */
+} mcd_batch_result;
+
+/* meshes: host [count], each 2D.  Returns MCD_ENOTSUP for a 3D mesh or a
+ * Neumann boundary id.  Allocates the stencil arrays of all systems. */
+mcd_status mcd_batch_create(const mcd_mesh *meshes, int count, const mcd_mls_params *prm,
+                            mcd_batch **bt);
+void mcd_batch_destroy(mcd_batch *bt);
+
+/* DP offset of system i (i = count gives the total), or -1. */
+int64_t mcd_batch_offset(const mcd_batch *bt, int i);
+
+/* MLS stencils of every system (one launch; same rules as
+ * mcd_build_stencils).  Asynchronous. */
+mcd_status mcd_batch_build(mcd_batch *bt, const double *pos_dev, const int8_t *mask_dev,
+                           mcd_stream_t stream);
+
+/* MCD_ESINGULAR (and the first failing DP, batch-global index) if a moment
+ * matrix was singular in the last build.  Synchronises the stream. */
+mcd_status mcd_batch_check(const mcd_batch *bt, int64_t *first_bad_dp, mcd_stream_t stream);
+
+/* mcd_batch_solve - solve every system A_i p_i = b_i (b from rhs / bnd as in
+ * mcd_assemble_rhs) in one persistent cooperative launch: Bi-CGSTAB in
+ * lockstep sweeps with per-system scalars and convergence, the work of the
+ * systems still running spread over all CTAs each sweep.  prm: tol (per
+ * system, ||b_i - A_i p_i|| <= tol ||b_i||), max_iter (per system), mode
+ * (MCD_MIXED: FP32 recursion with FP64 true-residual updates, inner_tol as
+ * in mcd_solve_pressure; MCD_FP64), net must be NULL.  p_dev: initial guess
+ * in, solutions out.  use_graph: capture the launches in a CUDA graph on the
+ * first call and replay it while the arguments and tuning stay the same.
+ * results: host [count] or NULL.  Synchronises the stream.  Returns MCD_OK
+ * if every system converged, else the first failure status. */
+mcd_status mcd_batch_solve(mcd_batch *bt, const double *rhs_dev, const double *bnd_dev,
+                           double *p_dev, const mcd_solve_params *prm, int use_graph,
+                           mcd_batch_result *results, mcd_stream_t stream);
+
+mcd_status mcd_batch_set_tuning(mcd_batch *bt, const mcd_batch_tuning *t);
+mcd_status mcd_batch_get_tuning(const mcd_batch *bt, mcd_batch_tuning *t);
+
+/* mcd_batch_autotune - time `sweeps` sweeps of the solve for every tiling
+ * (rows 1, 2, 4 x 1 .. 4 CTAs per SM within the kernel's occupancy) and keep
+ * the fastest per sweep.  cache_path (may be NULL): a text file of
+ * "<device, sizes and mode key> | rows ctas_per_sm ms" lines; a matching
+ * line is used without timing, a new result is appended.  p_dev is
+ * overwritten (it is the iterate of the trial solves).  best_ms_per_sweep:
+ * host, may be NULL.  Synchronises the device. */
+mcd_status mcd_batch_autotune(mcd_batch *bt, const double *rhs_dev, const double *bnd_dev,
+                              double *p_dev, const mcd_solve_params *prm, int sweeps,
+                              const char *cache_path, double *best_ms_per_sweep,
+                              mcd_stream_t stream);
+
+/* -------------------------------------------------------------------------
  * Learned warm start (an addition: the paper has no network)
  *
  * A stack of `layers` 3x3 convolutions on the 2D background-mesh grid (zero
@@ -419,7 +493,8 @@ enum {
     MCD_K_OTHER = 6,     /* everything else                     */
     MCD_K_SOLVE = 7,     /* persistent cooperative Bi-CGSTAB     */
     MCD_K_CNN = 8,       /* network: convolutions, features, training */
-    MCD_K_COUNT = 9
+    MCD_K_BATCH = 9,     /* batched solve (persistent launch or graph replay) */
+    MCD_K_COUNT = 10
 };
 
 /* When sample_every > 0, every sample_every-th launch of each kernel class

@@ -85,6 +85,9 @@ __device__ __forceinline__ int nb_coord(int c, int o, int n, int per, double len
     return v;
 }
 
+// Add n to the launch counter (launches made by a CUDA graph replay).
+void count_launches(long long n);
+
 // Solver workspace attached to a stencil handle (allocated on first solve).
 struct Workspace;
 
@@ -132,6 +135,27 @@ cudaError_t cnn_store_offsets(const mcd_stencils *st, const double *pos, const i
 // Network warm start of a solve: p <- p + s e on the assembled system (cnn.cu).
 mcd_status net_warm_start(const mcd_net *net, const mcd_stencils *st, const double *b,
                           const double *dprev, double *p, double *host_sc, cudaStream_t stream);
+}  // namespace mcd
+
+namespace mcd {
+// Batched stencil build over systems stored back to back (stencils.cu):
+// system i has geometry geo[i], DP offset off[i] and its 128-thread blocks
+// start at blk_start[i]; r_e and r_s of prm are multiples of each l0.
+struct BatchBuildDesc {
+    const Geo *geo;
+    const int64_t *off;
+    const int *blk_start;
+    int nsys, nblocks;
+    const double *pos;
+    const int8_t *mask;
+    const mcd_mls_params *prm;
+    double *row64;
+    float *row32;
+    double *rscale;
+    int8_t *kind;
+    unsigned long long *bad;
+};
+cudaError_t launch_build_batch(const BatchBuildDesc &d, cudaStream_t stream);
 }  // namespace mcd
 
 // Launch a kernel inside a KTimer scope: MCD_KLAUNCH(kind, stream, k<<<...>>>(...));

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "krylov_common.cuh"
 
 namespace mcd {
 
@@ -71,15 +72,6 @@ template <> struct ScalarOf<float> {
     __device__ static float beta(const Scalars *sc) { return sc->beta_f; }
 };
 
-// Grid barrier state: `release` (its own 256-byte line) and one arrival
-// flag per block.  Both hold barrier epochs, 1, 2, ... within a launch (the
-// host zeroes them before each launch), so nothing is reset in between.
-struct GridBarrier {
-    unsigned int release;
-    unsigned int pad[63];
-    unsigned int flag[1];     // [grid] arrival epochs (allocated past the struct)
-};
-
 struct Workspace {
     int64_t N = 0;
     int nblk = 0;        // blocks of the tiled kernels
@@ -111,313 +103,6 @@ void free_workspace(mcd_stencils *st) {
     cudaFreeHost(w->h_sc);
     delete w;
     st->ws = nullptr;
-}
-
-// Tile of the Bi-CGSTAB stencil kernels: 256 threads own X x Y (x Z) DPs, R
-// per thread, strided along the last tiled axis (thread grid X x TY x TZ).
-template <int DIM> struct Tile;
-template <> struct Tile<2> {
-    static constexpr int X = 32, Y = 16, Z = 1, R = 2, TY = 8, TZ = 1;
-};
-template <> struct Tile<3> {
-    static constexpr int X = 32, Y = 4, Z = 4, R = 2, TY = 4, TZ = 2;
-};
-
-template <int DIM> struct HaloDims {
-    static constexpr int HX = Tile<DIM>::X + 2;
-    static constexpr int HY = Tile<DIM>::Y + 2;
-    static constexpr int HZ = (DIM == 3) ? Tile<DIM>::Z + 2 : 1;
-    static constexpr int H = HX * HY * HZ;
-    static constexpr int S = (DIM == 2) ? 9 : 27;
-};
-
-__device__ __forceinline__ int wrap_clamp(int v, int n, int per) {
-    if (v < 0) return per ? v + n : 0;
-    if (v >= n) return per ? v - n : n - 1;
-    return v;
-}
-
-// Deterministic block reduction of NV values; thread 0 writes them to
-// partials[q * stride + block].
-template <int NV, typename A>
-__device__ __forceinline__ void block_partials(A (&v)[NV], double *partials, int stride, int block) {
-    __shared__ double wsum[NV][32];
-    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
-#pragma unroll
-    for (int q = 0; q < NV; ++q)
-        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
-    if ((tid & 31) == 0)
-        for (int q = 0; q < NV; ++q) wsum[q][tid >> 5] = (double)v[q];
-    __syncthreads();
-    if (tid < 32) {
-        const int nw = nthreads >> 5;
-        for (int q = 0; q < NV; ++q) {
-            double x = (tid < nw) ? wsum[q][tid] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (tid == 0) partials[q * stride + block] = x;
-        }
-    }
-}
-
-// ---- compensated FP32 dot products --------------------------------------
-// FP32 kernels accumulate each dot product as an unevaluated pair (hi, lo):
-// products are split exactly with fma and added with TwoSum, warps and the
-// block combine pairs the same way, and one thread per block converts the
-// pair to FP64.  The sums are then accurate to about twice FP32 precision
-// relative to sum |a_i b_i|, so rho = r^.r stays meaningful when it is much
-// smaller than |r^||r| (as the residual migrates away from r^), and no
-// per-thread FP64 work (slow on this GPU) is needed.
-struct DF {
-    float hi, lo;
-};
-
-// The error-free steps use the _rn intrinsics, which the compiler never
-// contracts into fused multiply-adds (contraction would change the rounded
-// product that TwoSum has to see and void the error terms).
-__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-__device__ __forceinline__ void df_add_prod(DF &acc, float a, float b) {
-    const float p = __fmul_rn(a, b);
-    const float pe = __fmaf_rn(a, b, -p);
-    float e;
-    two_sum_f(acc.hi, p, acc.hi, e);
-    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, pe));
-}
-
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-    DF r;
-    float e;
-    two_sum_f(a.hi, b.hi, r.hi, e);
-    r.lo = __fadd_rn(__fadd_rn(e, a.lo), b.lo);
-    return r;
-}
-
-template <int NV>
-__device__ __forceinline__ void block_partials_df(DF (&v)[NV], double *partials, int stride, int block) {
-    __shared__ DF wsum[NV][32];
-    const int tid = threadIdx.x;
-    const int nthreads = blockDim.x;
-#pragma unroll
-    for (int q = 0; q < NV; ++q)
-        for (int o = 16; o > 0; o >>= 1) {
-            DF other;
-            other.hi = __shfl_down_sync(0xffffffffu, v[q].hi, o);
-            other.lo = __shfl_down_sync(0xffffffffu, v[q].lo, o);
-            v[q] = df_add(v[q], other);
-        }
-    if ((tid & 31) == 0)
-        for (int q = 0; q < NV; ++q) wsum[q][tid >> 5] = v[q];
-    __syncthreads();
-    if (tid < 32) {
-        const int nw = nthreads >> 5;
-        for (int q = 0; q < NV; ++q) {
-            DF x = (tid < nw) ? wsum[q][tid] : DF{0.0f, 0.0f};
-            for (int o = 16; o > 0; o >>= 1) {
-                DF other;
-                other.hi = __shfl_down_sync(0xffffffffu, x.hi, o);
-                other.lo = __shfl_down_sync(0xffffffffu, x.lo, o);
-                x = df_add(x, other);
-            }
-            if (tid == 0) partials[q * stride + block] = (double)x.hi + (double)x.lo;
-        }
-    }
-}
-
-// Accumulator of one dot product: FP64 for the FP64 kernels, a compensated
-// pair for the FP32 ones.
-template <typename T> struct DotAcc;
-template <> struct DotAcc<double> {
-    double v = 0.0;
-    __device__ void add(double a, double b) { v += a * b; }
-};
-template <> struct DotAcc<float> {
-    DF v{0.0f, 0.0f};
-    __device__ void add(float a, float b) { df_add_prod(v, a, b); }
-};
-
-template <int NV>
-__device__ __forceinline__ void dot_partials(DotAcc<double> (&d)[NV], double *partials, int stride, int block) {
-    double v[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] = d[q].v;
-    block_partials<NV, double>(v, partials, stride, block);
-}
-
-template <int NV>
-__device__ __forceinline__ void dot_partials(DotAcc<float> (&d)[NV], double *partials, int stride, int block) {
-    DF v[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] = d[q].v;
-    block_partials_df<NV>(v, partials, stride, block);
-}
-
-// Returns true in the block that arrives last; that block then holds the
-// totals of the NV partial sums in out[] (valid in every thread).  The
-// partials are read with independent loads, four per thread per round, so
-// the tail costs about one L2 round trip for the few-hundred-block grids the
-// solver launches.
-template <int NV>
-__device__ __forceinline__ bool last_block_totals(const double *partials, int stride, int nblocks,
-                                                  unsigned int *counter, double (&out)[NV]) {
-    __shared__ bool is_last;
-    __shared__ double red[NV][32];
-    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
-    if (tid == 0) {
-        __threadfence();
-        const unsigned t = atomicAdd(counter, 1u);
-        is_last = (t == (unsigned)nblocks - 1u);
-    }
-    __syncthreads();
-    if (!is_last) return false;
-    __threadfence();
-    double acc[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) acc[q] = 0.0;
-    for (int b0 = tid; b0 < nblocks; b0 += 4 * nthreads) {
-        double v[NV][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int b = b0 + u * nthreads;
-#pragma unroll
-            for (int q = 0; q < NV; ++q) v[q][u] = (b < nblocks) ? __ldcg(partials + q * stride + b) : 0.0;
-        }
-#pragma unroll
-        for (int q = 0; q < NV; ++q) acc[q] += (v[q][0] + v[q][1]) + (v[q][2] + v[q][3]);
-    }
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
-        if ((tid & 31) == 0) red[q][tid >> 5] = acc[q];
-    }
-    __syncthreads();
-    for (int q = 0; q < NV; ++q) {
-        double x = 0.0;
-        for (int w = 0; w < (nthreads >> 5); ++w) x += red[q][w];
-        out[q] = x;
-    }
-    if (tid == 0) *counter = 0u;
-    return true;
-}
-
-struct TileArgs {
-    Geo g;
-    int bx, by, bz;      // tiles per axis
-    int ntiles;
-    const int8_t *kind;  // non-NULL: Neumann rows act as identity rows
-};
-
-template <int DIM>
-__device__ __forceinline__ void tile_origin(const TileArgs &ta, int tile, int &x0, int &y0, int &z0) {
-    const int tx = tile % ta.bx;
-    const int rest = tile / ta.bx;
-    const int ty = rest % ta.by;
-    const int tz = rest / ta.by;
-    x0 = tx * Tile<DIM>::X;
-    y0 = ty * Tile<DIM>::Y;
-    z0 = tz * Tile<DIM>::Z;
-}
-
-// Global index of halo element h of the tile at (x0, y0, z0).
-template <int DIM>
-__device__ __forceinline__ int64_t halo_index(const Geo &g, int h, int x0, int y0, int z0) {
-    using HD = HaloDims<DIM>;
-    const int hx = h % HD::HX;
-    const int hy = (h / HD::HX) % HD::HY;
-    const int hz = h / (HD::HX * HD::HY);
-    const int gx = wrap_clamp(x0 + hx - 1, g.n[0], g.per[0]);
-    const int gy = wrap_clamp(y0 + hy - 1, g.n[1], g.per[1]);
-    if (DIM == 2) return (int64_t)gx + (int64_t)g.n[0] * gy;
-    const int gz = wrap_clamp(z0 + hz - 1, g.n[2], g.per[2]);
-    return (int64_t)gx + (int64_t)g.n[0] * ((int64_t)gy + (int64_t)g.n[1] * gz);
-}
-
-// DP r of thread tid in the tile at (x0, y0, z0): global index, or -1
-// outside the mesh; (lx, ly, lz) are its coordinates inside the tile.
-template <int DIM>
-__device__ __forceinline__ int64_t tile_dp(const Geo &g, int tid, int r, int x0, int y0, int z0, int &lx,
-                                           int &ly, int &lz) {
-    using TL = Tile<DIM>;
-    lx = tid % TL::X;
-    if (DIM == 2) {
-        ly = (tid / TL::X) + r * TL::TY;
-        lz = 0;
-    } else {
-        ly = (tid / TL::X) % TL::TY;
-        lz = tid / (TL::X * TL::TY) + r * TL::TZ;
-    }
-    const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-    if (gx >= g.n[0] || gy >= g.n[1] || (DIM == 3 && gz >= g.n[2])) return -1;
-    return (DIM == 2) ? (int64_t)gx + (int64_t)g.n[0] * gy
-                      : (int64_t)gx + (int64_t)g.n[0] * ((int64_t)gy + (int64_t)g.n[1] * gz);
-}
-
-template <int DIM>
-__device__ __forceinline__ int tile_centre(int lx, int ly, int lz) {
-    using HD = HaloDims<DIM>;
-    return (lx + 1) + HD::HX * ((ly + 1) + HD::HY * (lz + (DIM == 3 ? 1 : 0)));
-}
-
-// (A x)_k from the shared-memory tile of x and the row weights w[] (already
-// in registers).  FP64 rows are in matrix form (sum_s c_s x_s); FP32 rows in
-// difference form (c_C x_k + sum_{s != C} c_s (x_s - x_k), centre slot = row
-// sum), which keeps the O(1/l0^2) weights from cancelling away the FP32
-// mantissa.
-//
-// The FP32 form is also compensated: each product c_s (x_s - x_k) is split
-// exactly into p + e with a fused multiply-add, and the products are summed
-// with Knuth's TwoSum into a (hi, lo) pair, so the row is accumulated to
-// about twice FP32 precision and rounded once.  A plain FP32 sum of the
-// O(|grad x| / l0) terms loses the digits of their O(lap x) sum and slows
-// Bi-CGSTAB by about 2x; the compensation costs about 11 FP32 operations per
-// term, which this bandwidth-bound kernel has to spare.
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-template <int DIM, typename T>
-__device__ __forceinline__ T stencil_apply(const T *w, const T *tile, int lx, int ly, int lz) {
-    using HD = HaloDims<DIM>;
-    constexpr int C = HD::S / 2;
-    const T xk = tile[tile_centre<DIM>(lx, ly, lz)];
-    if (sizeof(T) == 4) {
-        float hi = (float)w[C] * (float)xk, lo = 0.0f;   // centre weight is 0 or 1: exact
-#pragma unroll
-        for (int s = 0; s < HD::S; ++s) {
-            if (s == C) continue;
-            const int ox = s % 3, oy = (s / 3) % 3, oz = s / 9;
-            const int h = (lx + ox) + HD::HX * ((ly + oy) + HD::HY * (lz + oz));
-            const float d = __fsub_rn((float)tile[h], (float)xk);
-            const float p = __fmul_rn((float)w[s], d);
-            const float pe = __fmaf_rn((float)w[s], d, -p);
-            float e;
-            two_sum(hi, p, hi, e);
-            lo = __fadd_rn(lo, __fadd_rn(e, pe));
-        }
-        return (T)__fadd_rn(hi, lo);
-    }
-    T acc = (T)0;
-#pragma unroll
-    for (int s = 0; s < HD::S; ++s) {
-        const int ox = s % 3, oy = (s / 3) % 3, oz = s / 9;
-        const int h = (lx + ox) + HD::HX * ((ly + oy) + HD::HY * (lz + oz));
-        acc += w[s] * tile[h];
-    }
-    return acc;
-}
-
-// Row weights of DP k into registers (zeros for k < 0).
-template <int S, typename T>
-__device__ __forceinline__ void load_row(const T *__restrict__ row, int64_t N, int64_t k, T *w) {
-#pragma unroll
-    for (int s = 0; s < S; ++s) w[s] = (k >= 0) ? __ldg(row + (int64_t)s * N + k) : (T)0;
 }
 
 // One block per tile.  Each thread first issues the weight loads of its R
@@ -1146,11 +831,6 @@ __device__ __forceinline__ void stamp_block(const PArgs &a, int it) {
         a.trace[512 + blockIdx.x] = global_ns();
         a.trace[512 + 2048 + blockIdx.x] = smid;
     }
-}
-
-template <typename F>
-__device__ __forceinline__ F vload(const F *p) {
-    return *((volatile const F *)p);
 }
 
 // Grid barrier that finishes the NV-value reduction: returns false if a wait

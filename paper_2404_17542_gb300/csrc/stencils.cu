@@ -14,6 +14,8 @@
 // judged on; the FP32 copy used by the inner Krylov solve is their rounding.
 #include <math.h>
 
+#include <string.h>
+
 #include "common.cuh"
 
 namespace mcd {
@@ -165,17 +167,29 @@ __device__ __forceinline__ Nbr<DIM> neighbour(const Geo &g, const int *c, int s)
     return r;
 }
 
+// Weights of DP k of the system with geometry g whose arrays start at DP
+// offset `off` in the arrays of `a` (a batch of systems stored back to back,
+// each in its own [slot][N] layout; off = 0 for a single system).
 template <int DIM>
-__global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
+__device__ __forceinline__ void build_dp(const BuildArgs &a, const Geo &g, int64_t off, int64_t k,
+                                         double r_e, double r_s) {
     using B = Basis<DIM>;
     constexpr int NB = B::NB;
     constexpr int S = B::S;
     constexpr int C = S / 2;
-    const int64_t N = a.g.N;
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
+    const int64_t N = g.N;
+    const double *pos = a.pos + DIM * off;
+    const int8_t *mask = a.mask + off;
+    const double *normal = a.normal ? a.normal + DIM * off : nullptr;
+    double *row64 = a.row64 + S * off;
+    float *row32 = a.row32 ? a.row32 + S * off : nullptr;
+    double *ql64 = a.ql64 ? a.ql64 + S * off : nullptr;
+    double *d64 = a.d64 ? a.d64 + (int64_t)NB * S * off : nullptr;
+    double *qd64 = a.qd64 ? a.qd64 + (int64_t)NB * S * off : nullptr;
+    double *rscale = a.rscale + off;
+    int8_t *kind_out = a.kind + off;
 
-    const int8_t mk = a.mask[k];
+    const int8_t mk = mask[k];
     int8_t kind;
     if (mk == 0) kind = KIND_VOID;
     else if (mk < 0) kind = KIND_INNER;
@@ -184,28 +198,28 @@ __global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
     auto write_identity = [&]() {
         for (int s = 0; s < S; ++s) {
             double v = (s == C) ? 1.0 : 0.0;
-            a.row64[(int64_t)s * N + k] = v;
-            if (a.row32) a.row32[(int64_t)s * N + k] = (float)v;
-            if (a.ql64) a.ql64[(int64_t)s * N + k] = 0.0;
-            if (a.d64)
-                for (int c = 0; c < NB; ++c) a.d64[((int64_t)c * S + s) * N + k] = 0.0;
-            if (a.qd64)
-                for (int c = 0; c < NB; ++c) a.qd64[((int64_t)c * S + s) * N + k] = 0.0;
+            row64[(int64_t)s * N + k] = v;
+            if (row32) row32[(int64_t)s * N + k] = (float)v;
+            if (ql64) ql64[(int64_t)s * N + k] = 0.0;
+            if (d64)
+                for (int c = 0; c < NB; ++c) d64[((int64_t)c * S + s) * N + k] = 0.0;
+            if (qd64)
+                for (int c = 0; c < NB; ++c) qd64[((int64_t)c * S + s) * N + k] = 0.0;
         }
-        a.rscale[k] = 1.0;
+        rscale[k] = 1.0;
     };
 
-    a.kind[k] = kind;
+    kind_out[k] = kind;
     if (kind == KIND_VOID || kind == KIND_DIRICHLET) {
         write_identity();
         return;
     }
 
     int c[3] = {0, 0, 0};
-    decode<DIM>(a.g, k, c);
+    decode<DIM>(g, k, c);
     double xi[DIM];
-    for (int d = 0; d < DIM; ++d) xi[d] = a.pos[(int64_t)d * N + k];
-    const double inv_rs = 1.0 / a.r_s;
+    for (int d = 0; d < DIM; ++d) xi[d] = pos[(int64_t)d * N + k];
+    const double inv_rs = 1.0 / r_s;
     const int nf = (kind == KIND_NEUMANN) ? DIM : NB;
 
     // ---- pass 1: moment matrix and sum_j w_j p_j over value neighbours ----
@@ -216,22 +230,22 @@ __global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
 
     for (int s = 0; s < S; ++s) {
         if (s == C) continue;
-        Nbr<DIM> nb = neighbour<DIM>(a.g, c, s);
+        Nbr<DIM> nb = neighbour<DIM>(g, c, s);
         if (!nb.valid) continue;
-        const int8_t mj = a.mask[nb.j];
+        const int8_t mj = mask[nb.j];
         if (mj == 0) continue;
         const bool neu = (kind == KIND_INNER) && mj > 0 && a.bc[(uint8_t)mj] == MCD_BC_NEUMANN;
         double dx[DIM], X[DIM], r2 = 0.0;
         for (int d = 0; d < DIM; ++d) {
-            dx[d] = (a.pos[(int64_t)d * N + nb.j] + nb.shift[d]) - xi[d];
+            dx[d] = (pos[(int64_t)d * N + nb.j] + nb.shift[d]) - xi[d];
             X[d] = dx[d] * inv_rs;
             r2 += dx[d] * dx[d];
         }
-        const double w = mls_weight(sqrt(r2), a.weight_kind, a.r_e);
+        const double w = mls_weight(sqrt(r2), a.weight_kind, r_e);
         double p[NB];
         if (neu) {
             double n[DIM];
-            for (int d = 0; d < DIM; ++d) n[d] = a.normal[(int64_t)d * N + nb.j];
+            for (int d = 0; d < DIM; ++d) n[d] = normal[(int64_t)d * N + nb.j];
             B::normal(X, n, p);
         } else {
             B::value(X, p);
@@ -245,7 +259,7 @@ __global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
     }
 
     if (!cholesky<NB>(L, nf)) {
-        atomicMin(a.bad, (unsigned long long)k);
+        atomicMin(a.bad, (unsigned long long)(off + k));
         write_identity();
         return;
     }
@@ -265,17 +279,17 @@ __global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
     if (kind == KIND_NEUMANN) {
         double dcen = 0.0;
         for (int d = 0; d < DIM; ++d) {
-            nrm[d] = a.normal[(int64_t)d * N + k];
+            nrm[d] = normal[(int64_t)d * N + k];
             dcen += nrm[d] * cen[d];
         }
         if (!(dcen != 0.0) || !isfinite(dcen)) {
-            atomicMin(a.bad, (unsigned long long)k);
+            atomicMin(a.bad, (unsigned long long)(off + k));
             write_identity();
             return;
         }
         sigma = -(inv_rs * inv_rs) / dcen;
     }
-    a.rscale[k] = sigma;
+    rscale[k] = sigma;
 
     // ---- pass 2: per-slot weights ----
     for (int s = 0; s < S; ++s) {
@@ -285,23 +299,23 @@ __global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
         if (s == C) {
             for (int q = 0; q < NB; ++q) z[q] = cen[q];
         } else {
-            Nbr<DIM> nb = neighbour<DIM>(a.g, c, s);
-            int8_t mj = nb.valid ? a.mask[nb.j] : (int8_t)0;
+            Nbr<DIM> nb = neighbour<DIM>(g, c, s);
+            int8_t mj = nb.valid ? mask[nb.j] : (int8_t)0;
             if (mj != 0) {
                 const bool neu = (kind == KIND_INNER) && mj > 0 && a.bc[(uint8_t)mj] == MCD_BC_NEUMANN;
                 double dx[DIM], X[DIM], r2 = 0.0;
                 for (int d = 0; d < DIM; ++d) {
-                    dx[d] = (a.pos[(int64_t)d * N + nb.j] + nb.shift[d]) - xi[d];
+                    dx[d] = (pos[(int64_t)d * N + nb.j] + nb.shift[d]) - xi[d];
                     X[d] = dx[d] * inv_rs;
                     r2 += dx[d] * dx[d];
                 }
-                const double w = mls_weight(sqrt(r2), a.weight_kind, a.r_e);
+                const double w = mls_weight(sqrt(r2), a.weight_kind, r_e);
                 double p[NB];
                 if (neu) {
                     double n[DIM];
-                    for (int d = 0; d < DIM; ++d) n[d] = a.normal[(int64_t)d * N + nb.j];
+                    for (int d = 0; d < DIM; ++d) n[d] = normal[(int64_t)d * N + nb.j];
                     B::normal(X, n, p);
-                    for (int q = 0; q < NB; ++q) zq[q] = (q < nf) ? w * p[q] * a.r_s : 0.0;
+                    for (int q = 0; q < NB; ++q) zq[q] = (q < nf) ? w * p[q] * r_s : 0.0;
                     chol_solve<NB>(L, nf, zq);
                     for (int q = 0; q < NB; ++q) zq[q] *= scale[q];
                 } else {
@@ -320,17 +334,64 @@ __global__ void __launch_bounds__(128) build_kernel(BuildArgs a) {
             for (int d = 0; d < DIM; ++d) row += nrm[d] * z[d];
             row *= sigma;
         }
-        a.row64[(int64_t)s * N + k] = row;
+        row64[(int64_t)s * N + k] = row;
         // FP32 rows are kept in difference form: the centre slot holds the
         // row sum, exactly 0 here (chi = 1 MLS reproduces constants), and the
         // SpMV forms sum_j c_ij (x_j - x_i); see spmv_kernel
-        if (a.row32) a.row32[(int64_t)s * N + k] = (s == C) ? 0.0f : (float)row;
-        if (a.ql64) a.ql64[(int64_t)s * N + k] = ql;
-        if (a.d64)
-            for (int q = 0; q < NB; ++q) a.d64[((int64_t)q * S + s) * N + k] = z[q];
-        if (a.qd64)
-            for (int q = 0; q < NB; ++q) a.qd64[((int64_t)q * S + s) * N + k] = zq[q];
+        if (row32) row32[(int64_t)s * N + k] = (s == C) ? 0.0f : (float)row;
+        if (ql64) ql64[(int64_t)s * N + k] = ql;
+        if (d64)
+            for (int q = 0; q < NB; ++q) d64[((int64_t)q * S + s) * N + k] = z[q];
+        if (qd64)
+            for (int q = 0; q < NB; ++q) qd64[((int64_t)q * S + s) * N + k] = zq[q];
     }
+}
+
+
+template <int DIM>
+__global__ void __launch_bounds__(128) build_kernel(const __grid_constant__ BuildArgs a) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.g.N) return;
+    build_dp<DIM>(a, a.g, 0, k, a.r_e, a.r_s);
+}
+
+// Batched build: the blocks of system i start at blk_start[i]; geo[i] and
+// off[i] give its geometry and DP offset; r_e and r_s are multiples of its l0.
+template <int DIM>
+__global__ void __launch_bounds__(128) build_batch_kernel(const __grid_constant__ BuildArgs a,
+                                                          const Geo *__restrict__ geo,
+                                                          const int64_t *__restrict__ off,
+                                                          const int *__restrict__ blk_start, int nsys) {
+    int lo = 0, hi = nsys - 1;
+    const int blk = (int)blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (blk_start[mid] <= blk) lo = mid; else hi = mid - 1;
+    }
+    const Geo g = geo[lo];
+    const int64_t k = (int64_t)(blk - blk_start[lo]) * blockDim.x + threadIdx.x;
+    if (k >= g.N) return;
+    build_dp<DIM>(a, g, off[lo], k, a.r_e * g.l0, a.r_s * g.l0);
+}
+
+cudaError_t launch_build_batch(const BatchBuildDesc &d, cudaStream_t stream) {
+    BuildArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pos = d.pos;
+    a.mask = d.mask;
+    a.normal = nullptr;
+    for (int b = 0; b < 128; ++b) a.bc[b] = d.prm->bc_kind[b];
+    a.weight_kind = d.prm->weight_kind;
+    a.r_e = d.prm->r_e;
+    a.r_s = d.prm->r_s;
+    a.row64 = d.row64;
+    a.row32 = d.row32;
+    a.rscale = d.rscale;
+    a.kind = d.kind;
+    a.bad = d.bad;
+    MCD_KLAUNCH(MCD_K_BUILD, stream, build_batch_kernel<2><<<d.nblocks, 128, 0, stream>>>(
+        a, d.geo, d.off, d.blk_start, d.nsys));
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -55,6 +55,14 @@ class c_solve_info(C.Structure):
                 ("rel_res_guess", C.c_double), ("rel_res_start", C.c_double)]
 
 
+class c_batch_tuning(C.Structure):
+    _fields_ = [("rows", C.c_int), ("ctas_per_sm", C.c_int)]
+
+
+class c_batch_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("updates", C.c_int), ("rel_res", C.c_double)]
+
+
 class c_body(C.Structure):
     _fields_ = [("id", C.c_int), ("c", C.c_double * 3), ("radius", C.c_double),
                 ("vel", C.c_double * 3), ("acc", C.c_double * 3)]
@@ -94,6 +102,17 @@ _SIGS = {
     "mcd_net_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                      C.c_float, C.c_void_p, C.c_void_p]),
     "mcd_net_warm_start": (C.c_int, [C.c_void_p] * 6 + [C.c_void_p]),
+    "mcd_batch_create": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(c_mls_params), C.POINTER(C.c_void_p)]),
+    "mcd_batch_destroy": (None, [C.c_void_p]),
+    "mcd_batch_offset": (C.c_int64, [C.c_void_p, C.c_int]),
+    "mcd_batch_build": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mcd_batch_check": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
+    "mcd_batch_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(c_solve_params),
+                                  C.c_int, C.c_void_p, C.c_void_p]),
+    "mcd_batch_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(c_batch_tuning)]),
+    "mcd_batch_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(c_batch_tuning)]),
+    "mcd_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(c_solve_params),
+                                     C.c_int, C.c_char_p, C.POINTER(C.c_double), C.c_void_p]),
     "mcd_timing_enable": (C.c_int, [C.c_int]),
     "mcd_timing_read": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "mcd_launch_count": (C.c_int64, []),
@@ -278,6 +297,98 @@ class Stencils:
             pass
 
 
+class Batch:
+    """Owner of an mcd_batch handle: independent 2D systems stored back to
+    back (system i owns DPs offsets[i] .. offsets[i+1] of every per-DP array;
+    its positions are the [2][N_i] block at 2 offsets[i]).  r_e and r_s are
+    multiples of each system's l0."""
+
+    def __init__(self, meshes, weight_kind=W_GAUSS, r_e=1.0, r_s=1.0, precision=MIXED, bc_kind=None):
+        self.meshes = list(meshes)
+        n = len(self.meshes)
+        arr = (c_mesh * n)(*[make_mesh(m) for m in self.meshes])
+        p = c_mls_params()
+        p.weight_kind = int(weight_kind)
+        p.r_e = float(r_e)
+        p.r_s = float(r_s)
+        p.precision = int(precision)
+        p.want_derivs = 0
+        bc = np.zeros(128, dtype=np.uint8) if bc_kind is None else np.asarray(bc_kind, dtype=np.uint8)
+        for i in range(128):
+            p.bc_kind[i] = int(bc[i])
+        self.prm = p
+        self.handle = C.c_void_p(None)
+        _check(lib().mcd_batch_create(C.cast(arr, C.c_void_p), n, C.byref(p), C.byref(self.handle)))
+        self.offsets = np.array([lib().mcd_batch_offset(self.handle, i) for i in range(n + 1)], dtype=np.int64)
+        self.N = int(self.offsets[-1])
+
+    @staticmethod
+    def pack_positions(pos_list):
+        """Host array of the per-system [2][N_i] position blocks, back to back."""
+        return np.concatenate([np.asarray(p, np.float64).reshape(2, -1).ravel() for p in pos_list])
+
+    def build(self, pos, mask):
+        _check(lib().mcd_batch_build(self.handle, _ptr(pos, torch.float64, 2 * self.N),
+                                     _ptr(mask, torch.int8, self.N), _stream()))
+
+    def check(self):
+        bad = C.c_int64(-1)
+        st = lib().mcd_batch_check(self.handle, C.byref(bad), _stream())
+        return st, bad.value
+
+    def solve(self, rhs, bnd, p=None, tol=1e-8, mode=MIXED, max_iter=200000, inner_tol=0.1, graph=False,
+              raise_on_error=True):
+        """Solve every system; returns (p, dict of per-system arrays status,
+        iters, updates, rel_res)."""
+        if p is None:
+            p = torch.zeros(self.N, dtype=torch.float64, device=rhs.device)
+        sp = c_solve_params(tol=tol, max_iter=max_iter, mode=mode, inner_tol=inner_tol, max_refine=0,
+                            net=None, check_every=0, update_restart=1, net_dprev=None)
+        n = len(self.meshes)
+        res = (c_batch_result * n)()
+        f64 = torch.float64
+        st = lib().mcd_batch_solve(self.handle, _ptr(rhs, f64, self.N), _ptr(bnd, f64, self.N),
+                                   _ptr(p, f64, self.N), C.byref(sp), 1 if graph else 0,
+                                   C.cast(res, C.c_void_p), _stream())
+        out = {k: np.array([getattr(r, k) for r in res]) for k in ("status", "iters", "updates", "rel_res")}
+        out["return"] = st
+        if st != OK and raise_on_error:
+            raise McdError(st, lib().mcd_last_error().decode())
+        return p, out
+
+    def set_tuning(self, rows, ctas_per_sm):
+        t = c_batch_tuning(rows=int(rows), ctas_per_sm=int(ctas_per_sm))
+        _check(lib().mcd_batch_set_tuning(self.handle, C.byref(t)))
+
+    def tuning(self):
+        t = c_batch_tuning()
+        _check(lib().mcd_batch_get_tuning(self.handle, C.byref(t)))
+        return t.rows, t.ctas_per_sm
+
+    def autotune(self, rhs, bnd, p, tol=1e-8, mode=MIXED, sweeps=40, cache_path=None):
+        """Pick the fastest tiling; returns ms per sweep of the choice."""
+        sp = c_solve_params(tol=tol, max_iter=200000, mode=mode, inner_tol=0.1, max_refine=0, net=None,
+                            check_every=0, update_restart=1, net_dprev=None)
+        ms = C.c_double(0.0)
+        f64 = torch.float64
+        _check(lib().mcd_batch_autotune(self.handle, _ptr(rhs, f64, self.N), _ptr(bnd, f64, self.N),
+                                        _ptr(p, f64, self.N), C.byref(sp), int(sweeps),
+                                        None if cache_path is None else str(cache_path).encode(),
+                                        C.byref(ms), _stream()))
+        return ms.value
+
+    def close(self):
+        if self.handle and self.handle.value:
+            lib().mcd_batch_destroy(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 NET_PARAMS, NET_GRADS, NET_ADAM_M, NET_ADAM_V = range(4)
 N_CHANNELS = 8
 
@@ -406,9 +517,9 @@ def body_boundary(mesh, centre, radius, body_id, pos, mask, acc=(0.0, 0.0), norm
     return n, f
 
 
-K_BICG_A, K_BICG_B, K_BICG_C, K_RESIDUAL, K_BUILD, K_UPDATE, K_OTHER, K_SOLVE, K_CNN = range(9)
+K_BICG_A, K_BICG_B, K_BICG_C, K_RESIDUAL, K_BUILD, K_UPDATE, K_OTHER, K_SOLVE, K_CNN, K_BATCH = range(10)
 KERNEL_NAMES = ["bicg_ka", "bicg_kb", "bicg_kc", "residual64", "build_kernel", "update", "other",
-                "bicg_persistent", "cnn"]
+                "bicg_persistent", "cnn", "bicg_batch"]
 
 
 def timing_enable(sample_every: int):
