@@ -9,10 +9,15 @@ the body).  One step is one pass of the hot path:
     -> body normals and Neumann data
     -> MLS stencil build (FP64 rows + FP32 copy)
     -> right-hand side assembly
+    -> learned warm start: the previous step's pressure corrected by the
+       bf16 convolutional network (trained beforehand, untimed, on the
+       first steps of the same run) along its residual-minimising step
     -> mixed-precision Bi-CGSTAB solve to ||b - A p|| <= 1e-8 ||b|| (FP64
-       residual), warm-started from the previous step's pressure.
+       residual).
 Metric: DP-unknowns (non-void DPs) solved per second.  The same steps are
-also run with the plain FP64 Bi-CGSTAB for comparison (`fp64_plain`).
+also run with the plain FP64 Bi-CGSTAB warm-started from the previous
+pressure (`fp64_plain`) and with the mixed solve without the network
+(`mixed_no_net`).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -51,6 +56,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="time the mixed solve without the network")
+    ap.add_argument("--train-steps", type=int, default=48, help="steps whose solves train the network")
+    ap.add_argument("--train-epochs", type=int, default=10)
     return ap.parse_args()
 
 
@@ -158,6 +166,7 @@ class CylinderRun:
         self.normal = torch.zeros(2 * N, dtype=torch.float64, device=dev)
         self.neu = torch.zeros(N, dtype=torch.float64, device=dev)
         self.p = torch.zeros(N, dtype=torch.float64, device=dev)
+        self.dprev = torch.zeros(N, dtype=torch.float64, device=dev)   # last increment (network input)
         self.src_host = inputs.ppe_source(pb.pos, 0.0)
         self.rhs = torch.from_numpy(self.src_host.copy()).to(dev)
         c0 = self.cyl.centre(0.0)
@@ -170,17 +179,19 @@ class CylinderRun:
         self.k = 0
 
     def snapshot(self):
-        return (self.pos.clone(), self.mask.clone(), self.p.clone(), self.k)
+        return (self.pos.clone(), self.mask.clone(), self.p.clone(), self.dprev.clone(), self.k)
 
     def restore(self, snap):
-        pos, mask, p, k = snap
+        pos, mask, p, dprev, k = snap
         self.pos.copy_(pos)
         self.mask.copy_(mask)
         self.p.copy_(p)
+        self.dprev.copy_(dprev)
         self.k = k
 
-    def step(self, mode):
-        """One pass of the hot path; returns the solve info."""
+    def step(self, mode, net=None):
+        """One pass of the hot path; returns the solve info.  With a network
+        the solve starts from its warm start and updates self.dprev."""
         mcd = self.mcd
         self.k += 1
         t = self.k * self.dt
@@ -190,15 +201,55 @@ class CylinderRun:
         mcd.body_boundary(self.mesh, c, self.cyl.radius, self.cyl.body_id, self.pos, self.mask,
                           acc=self.cyl.acceleration(t), normal=self.normal, neumann=self.neu)
         self.st.rebuild(self.pos, self.mask, self.normal)
-        _p, info = self.st.solve(self.rhs, self.neu, p=self.p, tol=self.tol, mode=mode)
+        _p, info = self.st.solve(self.rhs, self.neu, p=self.p, tol=self.tol, mode=mode, net=net,
+                                 dprev=self.dprev if net is not None else None)
         return info
+
+
+def train_warm_start(run, steps, epochs, lr=1e-3, seed=3):
+    """Network of the learned warm start, trained on the solves of the next
+    `steps` steps of the run (plain mixed solves from the previous pressure):
+    features of (b, p_prev, p_prev - p_prev2), target p_new - p_prev.
+    Leaves run.dprev set to the last increment.  Returns (net, info)."""
+    torch, mcd, inputs = run.torch, run.mcd, run.inputs
+    t0 = time.perf_counter()
+    net = mcd.Net(inputs.cnn_flatten(*inputs.cnn_weights(seed)))
+    samples = []
+    p_m1 = run.p.clone()
+    for k in range(steps):
+        p_prev = run.p.clone()
+        dprev = p_prev - p_m1
+        run.step(mcd.MIXED)
+        b = run.st.assemble_rhs(run.rhs, run.neu)
+        if k >= 2:
+            samples.append(net.features(run.st, b, p_prev, dprev, run.p))
+        p_m1 = p_prev
+    run.dprev.copy_(run.p - p_m1)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    loss = torch.zeros(1, dtype=torch.float64, device=run.dev)
+    rng = np.random.default_rng(seed)
+    hist = []
+    t1 = time.perf_counter()
+    for ep in range(epochs):
+        tot = 0.0
+        for i in rng.permutation(len(samples)):
+            x, tg, wt = samples[i]
+            net.train_step(x, tg, wt, run.n, run.n, lr, loss)
+            tot += float(loss.item()) if ep in (0, epochs - 1) else 0.0
+        if ep in (0, epochs - 1):
+            hist.append(tot / max(1, len(samples)))
+    torch.cuda.synchronize()
+    return net, {"train_steps": steps, "samples": len(samples), "epochs": epochs, "lr": lr,
+                 "data_s": round(t_data, 2), "train_s": round(time.perf_counter() - t1, 2),
+                 "loss_first_epoch": hist[0] if hist else None, "loss_last_epoch": hist[-1] if hist else None}
 
 
 def flush_l2(buf):
     buf.zero_()
 
 
-def timed_steps(run, steps, mode, flush_buf, timing=False):
+def timed_steps(run, steps, mode, flush_buf, net=None):
     """Run `steps` steps, each bracketed by CUDA events on the current stream
     with an L2 flush between steps.  Returns (total ms, unknowns, infos)."""
     torch = run.torch
@@ -213,7 +264,7 @@ def timed_steps(run, steps, mode, flush_buf, timing=False):
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        info = run.step(mode)
+        info = run.step(mode, net)
         e1.record(stream)
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
@@ -222,7 +273,7 @@ def timed_steps(run, steps, mode, flush_buf, timing=False):
     return total_ms, unknowns, infos
 
 
-def e2e_steps(run, steps, mode):
+def e2e_steps(run, steps, mode, net=None):
     """Steps through the public API with host buffers: the step's source field
     is copied from pinned host memory and the pressure read back each step."""
     torch = run.torch
@@ -237,7 +288,7 @@ def e2e_steps(run, steps, mode):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         run.rhs.copy_(src, non_blocking=True)
-        info = run.step(mode)
+        info = run.step(mode, net)
         out.copy_(run.p, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -280,9 +331,14 @@ def gpu_arm(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    # the learned warm start: trained (untimed) on the first steps of the run
+    net, learned = None, None
+    if not args.no_learned:
+        net, learned = train_warm_start(run, args.train_steps, args.train_epochs)
+
     # warm-up
     for _ in range(args.warmup):
-        run.step(mcd.MIXED)
+        run.step(mcd.MIXED, net)
     snap = run.snapshot()
 
     # timed region: mixed path
@@ -292,7 +348,7 @@ def gpu_arm(args):
     launches0 = mcd.launch_count()
     barrier()
     wall0 = time.perf_counter()
-    ms, unknowns, infos = timed_steps(run, args.steps, mcd.MIXED, flush_buf)
+    ms, unknowns, infos = timed_steps(run, args.steps, mcd.MIXED, flush_buf, net)
     barrier()
     wall = time.perf_counter() - wall0
     launches = mcd.launch_count() - launches0
@@ -323,11 +379,22 @@ def gpu_arm(args):
                 "iters_per_step": statistics.mean(i["iters"] for i in infos64),
                 "rel_res_max": max(i["rel_res"] for i in infos64)}
 
+    # the mixed solve without the network on the same steps
+    no_net = None
+    if net is not None:
+        run.restore(snap)
+        msn, unkn, infosn = timed_steps(run, args.steps, mcd.MIXED, flush_buf)
+        no_net = {"value": unkn / (msn / 1e3), "ms_per_step": msn / args.steps,
+                  "iters_per_step": statistics.mean(i["iters"] for i in infosn)}
+        learned["iters_per_step"] = statistics.mean(i["iters"] for i in infos)
+        learned["rel_res_guess_mean"] = statistics.mean(i["rel_res_guess"] for i in infos)
+        learned["rel_res_start_mean"] = statistics.mean(i["rel_res_start"] for i in infos)
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
         run.restore(snap)
-        mse, unke, h2d, d2h = e2e_steps(run, args.steps, mcd.MIXED)
+        mse, unke, h2d, d2h = e2e_steps(run, args.steps, mcd.MIXED, net)
         e2e = {"value": unke / (mse / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
@@ -366,7 +433,9 @@ def gpu_arm(args):
             "config": {"workload": f"oscillating cylinder (D=0.1, KC=5, Re=100) {args.n}x{args.n} "
                                    "moving-boundary PPE step",
                        "mesh": [args.n, args.n], "tol": args.tol, "mode": "mixed",
-                       "learned_warm_start": False, "warm_start": "previous step pressure",
+                       "learned_warm_start": net is not None,
+                       "warm_start": ("previous step pressure + network correction" if net is not None
+                                      else "previous step pressure"),
                        "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
             "iters_per_step": statistics.mean(i["iters"] for i in infos),
@@ -376,6 +445,7 @@ def gpu_arm(args):
             "wall_s": wall,
             "fp64_plain": fp64,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
+            "mixed_no_net": no_net, "learned": learned,
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
             "clocks": clk,
         }

@@ -187,8 +187,10 @@ typedef struct mcd_net mcd_net;   /* learned warm start, declared below */
  * check_every  Krylov iterations between host convergence checks (0: auto).
  * update_restart (MIXED) 1: restart the FP32 recurrence (fresh shadow
  *              residual, p = r) at every reliable update; 0: keep p.
- * net_dprev    with net: device float64 [N], the last pressure increment
- *              (p of the previous step minus the one before), or NULL. */
+ * net_dprev    with net: device float64 [N] or NULL, in and out: the
+ *              increment the warm start reads (the pressure of the last
+ *              step minus the one before); after a converged solve it
+ *              holds this solve's increment, p(out) - p(in), for the next. */
 typedef struct {
     double tol;
     int max_iter;
@@ -198,7 +200,7 @@ typedef struct {
     const mcd_net *net;
     int check_every;
     int update_restart;
-    const double *net_dprev;
+    double *net_dprev;
 } mcd_solve_params;
 
 typedef struct {
@@ -210,6 +212,7 @@ typedef struct {
     int64_t unknowns;   /* non-void DPs of the system (DP unknowns solved) */
     double rel_res_guess;  /* with a net: ||b - A p|| / ||b|| of the guess, else -1 */
     double rel_res_start;  /* with a net: the same after the warm start, else -1 */
+    int fallback;       /* MIXED: 1 if the FP32 recursion failed and FP64 finished */
 } mcd_solve_info;
 
 /* mcd_solve_pressure - solve A p = b (b from mcd_assemble_rhs(rhs, bnd)).

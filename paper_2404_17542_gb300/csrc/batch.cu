@@ -61,7 +61,7 @@ struct BScal {
     int done;      // 0 running, 1 converged, 2 max_iter, 3 breakdown, 4 nonfinite
     int restart, restarts, s_conv, pending, max_hit, parity, mode;
     int updates;   // true-residual updates after the first
-    int pad_i;
+    int it_last;   // iteration of the last true residual
 };
 
 struct BState {
@@ -91,6 +91,7 @@ struct BArgs {
     int mixed;
     double tol2_factor;       // tol^2
     double update2;           // MIXED: update once rr <= update2 rr_last
+    int stall;                // MIXED: update after this many iterations without one
     double eps_breakdown;
     int budget;               // sweeps this launch may run
     long long spin_limit;
@@ -587,6 +588,7 @@ __global__ void __launch_bounds__(256) bicg_batch(const __grid_constant__ BArgs 
                         else if (c->max_hit) c->done = 2;
                         else {
                             c->rr_last = rr;
+                            c->it_last = c->iter;
                             c->restart = 1;
                             c->s_conv = 0;
                             c->alpha = c->beta = c->omega = 0.0;
@@ -635,6 +637,12 @@ __global__ void __launch_bounds__(256) bicg_batch(const __grid_constant__ BArgs 
                             if (rr <= c->tol2) c->pending = 1;
                             else if (c->iter >= c->max_iter) { c->max_hit = 1; c->pending = 1; }
                             else if (a.mixed && rr <= a.update2 * c->rr_last) c->pending = 1;
+                            // MIXED guards (as in the single-system solve): a
+                            // residual grown by 1e4 since the last true residual
+                            // is a diverged recursion; no update for `stall`
+                            // iterations forces one
+                            else if (a.mixed && rr > 1e8 * c->rr_last) c->done = 3;
+                            else if (a.mixed && c->iter - c->it_last >= a.stall) c->pending = 1;
                             else if (fabs(rho_new) <= a.eps_breakdown * sqrt(c->rhat2 * rr)) {
                                 c->restarts += 1;
                                 if (c->restarts > 1000) c->done = 3;
@@ -882,8 +890,9 @@ mcd_status make_launch(mcd_batch *bt, double *p, const mcd_solve_params *prm, La
     a.bar = bt->bar;
     a.mixed = mixed ? 1 : 0;
     a.tol2_factor = prm->tol * prm->tol;
-    const double upd = (prm->inner_tol > 0.0 && prm->inner_tol < 1.0) ? prm->inner_tol : 0.1;
+    const double upd = (prm->inner_tol > 0.0 && prm->inner_tol < 1.0) ? prm->inner_tol : 0.3;
     a.update2 = upd * upd;
+    a.stall = 1024;
     a.eps_breakdown = mixed ? 1e-12 : 1e-14;
     const long long mi = prm->max_iter > 0 ? prm->max_iter : (1 << 30);
     a.budget = (int)std::min<long long>(mi * 2 + 64, 1 << 30);

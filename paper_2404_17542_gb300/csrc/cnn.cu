@@ -571,6 +571,14 @@ __global__ void step_kernel(const double *__restrict__ part, int nblk, double *_
     }
 }
 
+// d = p - p_in (the increment of a solve).
+__global__ void increment_kernel(int64_t N, const double *__restrict__ p, const double *__restrict__ pin,
+                                 double *__restrict__ d) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    d[k] = p[k] - pin[k];
+}
+
 __global__ void axpy_step_kernel(int64_t N, const double *__restrict__ sc, const double *__restrict__ e,
                                  double *__restrict__ p) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -608,6 +616,7 @@ struct mcd_net {
     bf16 *x = nullptr;            // features [cap][8]
     float *y = nullptr;           // [cap]
     double *r0 = nullptr, *ap = nullptr, *e = nullptr;   // [cap]
+    double *pin = nullptr;        // [cap] guess of the last solve (increment)
     double *part = nullptr;       // [RED_BLOCKS][NRED]
     double *sc = nullptr;         // [8]
     double *stat = nullptr;       // [4]
@@ -632,9 +641,10 @@ void free_scratch(mcd_net *n) {
     cudaFree(n->r0);
     cudaFree(n->ap);
     cudaFree(n->e);
+    cudaFree(n->pin);
     n->ga = n->gb = n->dy = n->x = nullptr;
     n->y = nullptr;
-    n->r0 = n->ap = n->e = nullptr;
+    n->r0 = n->ap = n->e = n->pin = nullptr;
     n->cap = 0;
 }
 
@@ -652,6 +662,7 @@ mcd_status ensure_scratch(mcd_net *n, int64_t N) {
     chk(cudaMalloc(&n->r0, (size_t)N * sizeof(double)));
     chk(cudaMalloc(&n->ap, (size_t)N * sizeof(double)));
     chk(cudaMalloc(&n->e, (size_t)N * sizeof(double)));
+    chk(cudaMalloc(&n->pin, (size_t)N * sizeof(double)));
     if (e != cudaSuccess) {
         free_scratch(n);
         cudaGetLastError();
@@ -807,6 +818,25 @@ mcd_status net_warm_start(const mcd_net *cnet, const mcd_stencils *st, const dou
         MCD_CUDA_TRY(cudaMemcpyAsync(host_sc, n->sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
         MCD_CUDA_TRY(cudaStreamSynchronize(s));
     }
+    return MCD_OK;
+}
+
+// Keep the guess of a solve (before its Dirichlet values and warm start).
+mcd_status net_save_guess(const mcd_net *cnet, const mcd_stencils *st, const double *p, cudaStream_t s) {
+    mcd_net *n = const_cast<mcd_net *>(cnet);
+    mcd_status r = ensure_scratch(n, st->geo.N);
+    if (r != MCD_OK) return r;
+    MCD_CUDA_TRY(cudaMemcpyAsync(n->pin, p, st->geo.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return MCD_OK;
+}
+
+// dprev = p - (the saved guess): the increment the next warm start reads.
+mcd_status net_store_increment(const mcd_net *cnet, const mcd_stencils *st, const double *p, double *dprev,
+                               cudaStream_t s) {
+    const int64_t N = st->geo.N;
+    const unsigned eb = (unsigned)((N + 255) / 256);
+    MCD_KLAUNCH(MCD_K_CNN, s, increment_kernel<<<eb, 256, 0, s>>>(N, p, cnet->pin, dprev));
+    MCD_LAUNCH_CHECK();
     return MCD_OK;
 }
 

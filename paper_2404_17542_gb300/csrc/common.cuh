@@ -135,6 +135,10 @@ cudaError_t cnn_store_offsets(const mcd_stencils *st, const double *pos, const i
 // Network warm start of a solve: p <- p + s e on the assembled system (cnn.cu).
 mcd_status net_warm_start(const mcd_net *net, const mcd_stencils *st, const double *b,
                           const double *dprev, double *p, double *host_sc, cudaStream_t stream);
+// Save the guess of a solve / write its increment p - guess (cnn.cu).
+mcd_status net_save_guess(const mcd_net *net, const mcd_stencils *st, const double *p, cudaStream_t stream);
+mcd_status net_store_increment(const mcd_net *net, const mcd_stencils *st, const double *p, double *dprev,
+                               cudaStream_t stream);
 }  // namespace mcd
 
 namespace mcd {

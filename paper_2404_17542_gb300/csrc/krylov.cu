@@ -51,6 +51,8 @@ struct Scalars {
     int parity;       // p / v ping-pong buffer of the next iteration
     int phase_err;    // a grid barrier gave up (timeout)
     double rr_last;   // recursive-precision ||r||^2 at the last true residual
+    int it_last;      // iteration of the last true residual
+    int diverged;     // MIXED: the FP32 recursion diverged (its correction dropped)
 };
 
 // Refresh the FP32 copies (called by the single thread that updates them).
@@ -779,7 +781,9 @@ static mcd_status run_mixed(const mcd_stencils *st, double *x, const mcd_solve_p
 // ===========================================================================
 // Persistent solver: one cooperative launch runs Bi-CGSTAB iterations, the
 // true-residual (reliable) updates and the convergence test on the device.
-// Every block owns `tpb` tiles for the whole launch.  The three reductions
+// Block b owns tiles [b T / G, (b + 1) T / G) for the whole launch (T tiles,
+// G blocks: the grid fills every resident slot, and the tile counts of the
+// blocks differ by at most one).  The three reductions
 // of an iteration are finished at grid barriers: each block writes its
 // partial sums, the last block to arrive adds them in block order (so results
 // are deterministic), updates the scalars and releases the others.  Waiting
@@ -790,7 +794,7 @@ static mcd_status run_mixed(const mcd_stencils *st, double *x, const mcd_solve_p
 
 struct PArgs {
     TileArgs ta;
-    int tpb;                 // tiles per block
+    int grid;                // blocks of the launch
     const void *row;         // T rows of the recursion
     const double *row64;     // FP64 rows (true residual)
     const double *b;         // FP64 right-hand side
@@ -803,12 +807,17 @@ struct PArgs {
     int mixed;               // 1: fold x into x64 at every true-residual update
     int update_mode;         // 1: restart the recursion at every update
     double update2;          // MIXED: update once rr <= update2 * rr_last
+    int stall;               // MIXED: update after this many iterations without one
     double tol;
     double eps_breakdown;
     int iter_budget;         // iterations this launch may run
     long long spin_limit;
     unsigned long long *trace;   // non-NULL: block 0 stamps phase times here
 };
+
+__device__ __forceinline__ int tile_first(const PArgs &a, int block) {
+    return (int)((int64_t)block * a.ta.ntiles / a.grid);
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -931,9 +940,8 @@ __device__ void phase_a(const PArgs &a, T *tile, const T *p_old, const T *v_old,
     const T *r = (const T *)a.r;
     T *rhat = (T *)a.rh;
     const int tid = threadIdx.x;
-    for (int i = 0; i < a.tpb; ++i) {
-        const int tl = blockIdx.x * a.tpb + i;
-        if (tl >= a.ta.ntiles) break;
+    const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
+    for (int tl = tb; tl < te; ++tl) {
         int x0, y0, z0;
         tile_origin<DIM>(a.ta, tl, x0, y0, z0);
         int64_t k[TL::R];
@@ -1010,9 +1018,8 @@ __device__ void phase_b(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T> 
     T *s_out = (T *)a.s;
     T *t_out = (T *)a.t;
     const int tid = threadIdx.x;
-    for (int i = 0; i < a.tpb; ++i) {
-        const int tl = blockIdx.x * a.tpb + i;
-        if (tl >= a.ta.ntiles) break;
+    const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
+    for (int tl = tb; tl < te; ++tl) {
         int x0, y0, z0;
         tile_origin<DIM>(a.ta, tl, x0, y0, z0);
         int64_t k[TL::R];
@@ -1076,9 +1083,8 @@ __device__ void phase_c(const PArgs &a, const T *p, T alpha, T omega, int sconv,
     const T *s = (const T *)a.s;
     const T *t = (const T *)a.t;
     const int tid = threadIdx.x;
-    for (int i = 0; i < a.tpb; ++i) {
-        const int tl = blockIdx.x * a.tpb + i;
-        if (tl >= a.ta.ntiles) break;
+    const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
+    for (int tl = tb; tl < te; ++tl) {
         int x0, y0, z0;
         tile_origin<DIM>(a.ta, tl, x0, y0, z0);
         int64_t k[TL::R];
@@ -1119,9 +1125,8 @@ __device__ void phase_fold(const PArgs &a) {
     const Geo &g = a.ta.g;
     T *x = (T *)a.x;
     const int tid = threadIdx.x;
-    for (int i = 0; i < a.tpb; ++i) {
-        const int tl = blockIdx.x * a.tpb + i;
-        if (tl >= a.ta.ntiles) break;
+    const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
+    for (int tl = tb; tl < te; ++tl) {
         int x0, y0, z0;
         tile_origin<DIM>(a.ta, tl, x0, y0, z0);
 #pragma unroll
@@ -1146,9 +1151,8 @@ __device__ void phase_true_residual(const PArgs &a, DotAcc<double> (&d64)[2], Do
     T *r = (T *)a.r;
     const T *rhat = (const T *)a.rh;
     const int tid = threadIdx.x;
-    for (int i = 0; i < a.tpb; ++i) {
-        const int tl = blockIdx.x * a.tpb + i;
-        if (tl >= a.ta.ntiles) break;
+    const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
+    for (int tl = tb; tl < te; ++tl) {
         int x0, y0, z0;
         tile_origin<DIM>(a.ta, tl, x0, y0, z0);
 #pragma unroll
@@ -1229,6 +1233,7 @@ __global__ void __launch_bounds__(256) bicg_persistent(PArgs a) {
                     if (tot[0] <= sc->tol2) { sc->done = 1; return; }
                     if (sc->max_hit) { sc->done = 2; return; }
                     sc->rr_last = tot[3];
+                    sc->it_last = sc->iter;
                     if (mode == 1 || sc->restart || sc->s_conv || !sc->iter) {
                         sc->restart = 1;
                         sc->s_conv = 0;
@@ -1306,6 +1311,7 @@ __global__ void __launch_bounds__(256) bicg_persistent(PArgs a) {
             const double eps = a.eps_breakdown;
             const double update2 = a.update2;
             const int mixed = a.mixed;
+            const int stall = a.stall;
             if (!grid_reduce<2>(a, epoch, dot, [&](double *tot) {
                     const double rho_new = tot[0], rr = tot[1];
                     sc->rr = rr;
@@ -1320,6 +1326,13 @@ __global__ void __launch_bounds__(256) bicg_persistent(PArgs a) {
                     if (rr <= sc->tol2) { sc->pending = 1; return; }
                     if (sc->iter >= sc->max_iter) { sc->max_hit = 1; sc->pending = 1; return; }
                     if (mixed && rr <= update2 * sc->rr_last) { sc->pending = 1; return; }
+                    // MIXED guards: a recursion whose residual grew by 1e4
+                    // since the last true residual has diverged (stop before
+                    // its correction reaches x64); one that has not fallen
+                    // by the update factor for `stall` iterations takes a
+                    // fresh true residual and restarts
+                    if (mixed && rr > 1e8 * sc->rr_last) { sc->diverged = 1; sc->done = 3; return; }
+                    if (mixed && sc->iter - sc->it_last >= stall) { sc->pending = 1; return; }
                     if (fabs(rho_new) <= eps * sqrt(sc->rhat2 * rr)) {
                         sc->restarts += 1;
                         if (sc->restarts > 1000) { sc->done = 3; return; }
@@ -1332,14 +1345,13 @@ __global__ void __launch_bounds__(256) bicg_persistent(PArgs a) {
     }
 }
 
-// Grid of the persistent launch: as many blocks as can be resident, each
-// owning the same number of tiles.
+// Grid of the persistent launch: every resident slot (at most one block per
+// tile).
 template <int DIM, typename T>
-static int persistent_grid(int ntiles, int &tpb) {
+static int persistent_grid(int ntiles) {
     static const int occ = occupancy(bicg_persistent<DIM, T>);
     const int maxg = std::max(1, occ * sm_count());
-    tpb = (ntiles + maxg - 1) / maxg;
-    return (ntiles + tpb - 1) / tpb;
+    return std::min(ntiles, maxg);
 }
 
 // Run the whole solve in persistent launches (each bounded by an iteration
@@ -1361,7 +1373,8 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
     a.ta.bz = (DIM == 3) ? (g.n[2] + Tile<DIM>::Z - 1) / Tile<DIM>::Z : 1;
     a.ta.ntiles = a.ta.bx * a.ta.by * a.ta.bz;
     a.ta.kind = st->has_neumann ? st->kind : nullptr;
-    const int grid = persistent_grid<DIM, T>(a.ta.ntiles, a.tpb);
+    const int grid = persistent_grid<DIM, T>(a.ta.ntiles);
+    a.grid = grid;
     a.row64 = st->row64;
     a.b = w->b;
     a.x64 = x64;
@@ -1383,8 +1396,9 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
     a.bar = w->bar;
     a.mixed = mixed ? 1 : 0;
     a.update_mode = mixed ? (prm->update_restart == 2 ? 2 : 1) : 1;
-    const double upd = (prm->inner_tol > 0.0 && prm->inner_tol < 1.0) ? prm->inner_tol : 0.1;
+    const double upd = (prm->inner_tol > 0.0 && prm->inner_tol < 1.0) ? prm->inner_tol : 0.3;
     a.update2 = upd * upd;
+    a.stall = 1024;
     a.tol = prm->tol;
     a.eps_breakdown = mixed ? 1e-12 : 1e-14;
     a.iter_budget = 4096;
@@ -1427,6 +1441,10 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
     const int64_t N = st->geo.N;
     mcd_status s = mcd_assemble_rhs(st, rhs, bnd, w->b, stream);
     if (s != MCD_OK) return s;
+    if (prm->net && prm->net_dprev) {
+        s = net_save_guess(prm->net, st, p, stream);
+        if (s != MCD_OK) return s;
+    }
     Scalars init;
     memset(&init, 0, sizeof(init));
     init.max_iter = prm->max_iter > 0 ? prm->max_iter : 1 << 30;
@@ -1444,11 +1462,29 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
 
     mcd_status result = MCD_ENOCONV;
     int outer = 0;
+    int mixed_iters = 0, fallback = 0;
     if (prm->check_every >= 0) {
         // persistent cooperative solve (the default)
         s = (prm->mode == MCD_FP64) ? run_persistent<DIM, double>(st, p, prm, result, stream)
                                     : run_persistent<DIM, float>(st, p, prm, result, stream);
         if (s != MCD_OK) return s;
+        if (prm->mode == MCD_MIXED && result != MCD_OK && result != MCD_ETIMEOUT) {
+            // the FP32 recursion failed (diverged or broke down): finish in
+            // FP64 from the last folded iterate, which the failed cycle
+            // never touched
+            const Scalars &hm = *w->h_sc;
+            mixed_iters = hm.iter;
+            fallback = 1;
+            Scalars re;
+            memset(&re, 0, sizeof(re));
+            re.max_iter = std::max(1, init.max_iter - hm.iter);
+            re.unknowns = hm.unknowns;
+            MCD_CUDA_TRY(cudaMemcpyAsync(w->sc, &re, sizeof(re), cudaMemcpyHostToDevice, stream));
+            s = ensure_workspace(const_cast<mcd_stencils *>(st), MCD_FP64);
+            if (s != MCD_OK) return s;
+            s = run_persistent<DIM, double>(st, p, prm, result, stream);
+            if (s != MCD_OK) return s;
+        }
     } else if (prm->mode == MCD_FP64) {
         for (;; ++outer) {
             // FP64 residual of the current iterate (primes the Krylov scalars)
@@ -1491,10 +1527,15 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
             if (w->h_sc->done == 1) { result = MCD_OK; break; }
         }
     }
+    if (result == MCD_OK && prm->net && prm->net_dprev) {
+        s = net_store_increment(prm->net, st, p, prm->net_dprev, stream);
+        if (s != MCD_OK) return s;
+    }
     const Scalars &h = *w->h_sc;
     if (info) {
-        info->iters = h.iter;
+        info->iters = h.iter + mixed_iters;
         info->refinements = outer;
+        info->fallback = fallback;
         info->restarts = h.restarts;
         info->b_norm = sqrt(h.bb64);
         info->rel_res = h.bb64 > 0.0 ? sqrt(h.rr64 / h.bb64) : 0.0;

@@ -52,7 +52,7 @@ class c_solve_params(C.Structure):
 class c_solve_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("restarts", C.c_int),
                 ("rel_res", C.c_double), ("b_norm", C.c_double), ("unknowns", C.c_int64),
-                ("rel_res_guess", C.c_double), ("rel_res_start", C.c_double)]
+                ("rel_res_guess", C.c_double), ("rel_res_start", C.c_double), ("fallback", C.c_int)]
 
 
 class c_batch_tuning(C.Structure):
@@ -239,12 +239,13 @@ class Stencils:
                                       _stream()))
         return b
 
-    def solve(self, rhs, bnd, p=None, tol=1e-8, mode=MIXED, max_iter=200000, inner_tol=0.1,
+    def solve(self, rhs, bnd, p=None, tol=1e-8, mode=MIXED, max_iter=200000, inner_tol=0.3,
               max_refine=60, check_every=64, update_restart=1, raise_on_error=True, net=None,
               dprev=None):
         """Solve the PPE; returns (p, info dict).  p is updated in place if given.
-        net (a Net) adds its warm-start correction to p first; dprev is the
-        last pressure increment it reads (or None)."""
+        net (a Net) adds its warm-start correction to p first; dprev (or
+        None) is the last pressure increment it reads, and is overwritten
+        with this solve's increment p(out) - p(in) when the solve converges."""
         if p is None:
             p = torch.zeros(self.N, dtype=torch.float64, device=rhs.device)
         sp = c_solve_params(tol=tol, max_iter=max_iter, mode=mode, inner_tol=inner_tol,
@@ -257,7 +258,8 @@ class Stencils:
                                       C.byref(sp), C.byref(info), _stream())
         d = dict(status=st, iters=info.iters, refinements=info.refinements, restarts=info.restarts,
                  rel_res=info.rel_res, b_norm=info.b_norm, unknowns=info.unknowns,
-                 rel_res_guess=info.rel_res_guess, rel_res_start=info.rel_res_start)
+                 rel_res_guess=info.rel_res_guess, rel_res_start=info.rel_res_start,
+                 fallback=info.fallback)
         if st != OK and raise_on_error:
             raise McdError(st, lib().mcd_last_error().decode())
         return p, d
@@ -336,7 +338,7 @@ class Batch:
         st = lib().mcd_batch_check(self.handle, C.byref(bad), _stream())
         return st, bad.value
 
-    def solve(self, rhs, bnd, p=None, tol=1e-8, mode=MIXED, max_iter=200000, inner_tol=0.1, graph=False,
+    def solve(self, rhs, bnd, p=None, tol=1e-8, mode=MIXED, max_iter=200000, inner_tol=0.3, graph=False,
               raise_on_error=True):
         """Solve every system; returns (p, dict of per-system arrays status,
         iters, updates, rel_res)."""
@@ -367,7 +369,7 @@ class Batch:
 
     def autotune(self, rhs, bnd, p, tol=1e-8, mode=MIXED, sweeps=40, cache_path=None):
         """Pick the fastest tiling; returns ms per sweep of the choice."""
-        sp = c_solve_params(tol=tol, max_iter=200000, mode=mode, inner_tol=0.1, max_refine=0, net=None,
+        sp = c_solve_params(tol=tol, max_iter=200000, mode=mode, inner_tol=0.3, max_refine=0, net=None,
                             check_every=0, update_restart=1, net_dprev=None)
         ms = C.c_double(0.0)
         f64 = torch.float64

@@ -246,11 +246,14 @@ def test_warm_start_parity_and_solve(mcd):
 
     # the same warm start inside the solve, then convergence to tol
     p_s = dev(p0)
-    p_s, info = st.solve(dev(rhs), dev(bnd), p=p_s, tol=1e-10, net=net, dprev=dev(dprev))
+    d_s = dev(dprev)
+    p_s, info = st.solve(dev(rhs), dev(bnd), p=p_s, tol=1e-10, net=net, dprev=d_s)
     assert info["rel_res_guess"] == pytest.approx(before, rel=1e-9)
     assert info["rel_res_start"] == pytest.approx(after, rel=1e-6)
     assert info["rel_res"] <= 1e-10
     assert rel(p_s.cpu().numpy(), p_true) <= 1e-8
+    # the solve leaves its own increment for the next warm start
+    assert np.array_equal(d_s.cpu().numpy(), p_s.cpu().numpy() - p0)
 
 
 def test_net_rejects_bad_shapes(mcd):
@@ -293,7 +296,7 @@ def cylinder_sequence(mcd, n, steps, net=None, train=None):
         dprev = p - p_m1
         p_prev = p.clone()
         if net is not None:
-            p, info = st.solve(rhs, neu, p=p, net=net, dprev=dprev)
+            p, info = st.solve(rhs, neu, p=p, net=net, dprev=dprev.clone())
             stats.append((info["rel_res_guess"], info["rel_res_start"], info["iters"]))
         else:
             p, info = st.solve(rhs, neu, p=p)
