@@ -229,3 +229,45 @@ def test_nonfinite_rhs_and_max_iter(mcd):
                         raise_on_error=False)
     assert info["status"] == mcd.ENOCONV
     assert info["iters"] <= 5 + 64
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_solve_manufactured_3d(mcd, mode):
+    """27-point 3D system with ragged 32x4x4 tiles against the direct solve."""
+    pb = inputs.manufactured_box((18, 14, 12), 3, seed=2)
+    W = mls.build_weights(pb.mesh, pb.pos, pb.mask)
+    A = solve.assemble(pb.mesh, W["row"])
+    b = solve.form_rhs(pb.mesh, W["kind"], W["QL"], pb.rhs, pb.bnd, W["rscale"])
+    x = solve.direct_solve(A, b)
+    st = gpu_stencils(mcd, pb, want_derivs=False)
+    tol = 1e-11 if mode == 0 else 1e-10
+    p, info = st.solve(dev(pb.rhs), dev(pb.bnd), tol=tol, mode=mode)
+    got = p.cpu().numpy()
+    assert info["rel_res"] <= tol
+    assert np.linalg.norm(got - x) / np.linalg.norm(x) <= (1e-8 if mode == 0 else 1e-6)
+    assert np.linalg.norm(b - A @ got) <= 1.01 * tol * np.linalg.norm(b)
+
+
+def test_solve_3d_full_size(mcd):
+    """The 128^3 Dirichlet sin^3 problem: rows of sampled DPs against the
+    oracle's per-DP fit, the FP64 residual of the mixed solve, and the
+    discretisation error against the closed form (second order in l0: the
+    quadratic MLS Laplacian is exact on quadratics)."""
+    n = 128
+    pb = inputs.manufactured_box(n, 3, seed=2)
+    N = pb.mesh.N
+    st = gpu_stencils(mcd, pb, want_derivs=False)
+    rows = st.array(mcd.ARR_ROW64).cpu().numpy().reshape(27, N)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(N, 40, replace=False):
+        f = mls.dp_fit(pb.mesh, pb.pos, pb.mask, None, pb.bc_kind, int(i))
+        scale = np.abs(f["row"]).max()
+        assert np.abs(rows[:, i] - f["row"]).max() <= WEIGHT_TOL * scale, i
+    p, info = st.solve(dev(pb.rhs), dev(pb.bnd), tol=1e-8, mode=1)
+    assert info["status"] == 0 and info["rel_res"] <= 1e-8
+    # residual of the returned field with the FP64 SpMV (a separate kernel)
+    b = st.assemble_rhs(dev(pb.rhs), dev(pb.bnd))
+    r = b - st.apply(p)
+    assert float(r.norm() / b.norm()) <= 1.01e-8
+    err = np.linalg.norm(p.cpu().numpy() - pb.exact) / np.linalg.norm(pb.exact)
+    assert err <= 20 * (1.0 / n) ** 2, err
