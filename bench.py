@@ -51,6 +51,13 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mcd", choices=["mcd", "reference"])
+    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "batched", "cnn"],
+                    help="cylinder: the 1024^2 moving-cylinder step (the metric's workload); "
+                         "batched: 256 independent Poisson systems of log-uniform size 32^2..512^2; "
+                         "cnn: the warm-start network's inference and training step on an n^2 grid")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="run one mixed solve of the cylinder system from p = 0 (for a profiler) "
+                         "and print its iteration count")
     ap.add_argument("--n", type=int, default=1024, help="background mesh cells per side")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -130,8 +137,10 @@ def measured_peaks():
 
 
 def committed_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel's
-    source is unchanged since the capture (sha256 of its translation unit)."""
+    """DRAM bytes per unit of work (per DP-iteration for the solve, per DP
+    for the build) from the committed ncu summary profiles/traffic.txt, if
+    the kernel's source is unchanged since the capture (sha256 of its
+    translation unit); None otherwise."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -413,8 +422,12 @@ def gpu_arm(args):
             algo = BUILD_BYTES_PER_DP * run.N * n_launch
             unit_note = f"{BUILD_BYTES_PER_DP} B per DP x {run.N} DPs x {n_launch} launches"
         achieved = algo / n_launch / (t_ms / n_launch / 1e3) / 1e9
+        per_unit = committed_traffic(name)
+        if per_unit is not None:
+            units = run.N * sum(i["iters"] for i in infos) if name == "bicg_persistent" else run.N * n_launch
+            per_unit = per_unit * units / n_launch
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": committed_traffic(name),
+                "frac": round(achieved / peak, 4), "traffic": per_unit,
                 "kernel": name, "launches": n_launch, "avg_launch_ms": round(t_ms / n_launch, 3),
                 "algorithmic_bytes_per_launch": algo / n_launch, "algorithmic_bytes": unit_note,
                 "peak_source": f"{peak_src} hbm_gbs",
@@ -538,10 +551,175 @@ def reference_arm(args):
 import numpy as np  # noqa: E402  (used by the oracle legs)
 
 
+def batched_arm(args):
+    """One line for the batched workload: 256 degree-4 polynomial Poisson
+    systems, sizes floor(exp U(ln 32, ln 512)) per side (seed 4), all solved
+    by one persistent launch replayed from a CUDA graph (mixed, autotuned
+    tiling), beside the same batch in FP64 and per-system plain FP64 solves
+    with the single-system solver.  A "step" solves every system from p = 0."""
+    import torch
+
+    from paper_2404_17542_gb300 import build, inputs, mcd
+    build.build()
+    mcd.lib()
+    dev = torch.device("cuda", 0)
+    probs = inputs.batched_poly4(4)
+    bt = mcd.Batch([pb.mesh for pb in probs], precision=mcd.MIXED)
+
+    def d(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    pos = d(bt.pack_positions([pb.pos for pb in probs]))
+    mask = d(np.concatenate([pb.mask for pb in probs]))
+    rhs = d(np.concatenate([pb.rhs for pb in probs]))
+    bnd = d(np.concatenate([pb.bnd for pb in probs]))
+    bt.build(pos, mask)
+    p = torch.zeros(bt.N, dtype=torch.float64, device=dev)
+    tune_ms = bt.autotune(rhs, bnd, p, tol=args.tol, sweeps=30)
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(mode, graph, steps):
+        tot, res = 0.0, None
+        for _ in range(args.warmup):
+            p.zero_()
+            bt.solve(rhs, bnd, p=p, tol=args.tol, mode=mode, graph=graph)
+        for _ in range(steps):
+            p.zero_()
+            flush_buf.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            _p, res = bt.solve(rhs, bnd, p=p, tol=args.tol, mode=mode, graph=graph)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / steps, res
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = mcd.launch_count()
+    ms, res = timed(mcd.MIXED, True, args.steps)
+    launches = (mcd.launch_count() - launches0) / max(1, args.steps + args.warmup)
+    clk = clocks.stop()
+    ms64, res64 = timed(mcd.FP64, True, max(1, args.steps // 2))
+    # per-system plain FP64 solves with the single-system solver
+    sts = [(mcd.Stencils(pb.mesh, d(pb.pos.ravel()), d(pb.mask), precision=mcd.FP64), d(pb.rhs), d(pb.bnd),
+            torch.zeros(pb.mesh.N, dtype=torch.float64, device=dev)) for pb in probs]
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    its = []
+    for st, r, b, pp in sts:
+        pp.zero_()
+        _x, info = st.solve(r, b, p=pp, tol=args.tol, mode=mcd.FP64)
+        its.append(info["iters"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_each = e0.elapsed_time(e1)
+    rows, cps = bt.tuning()
+    line = {"metric": METRIC, "value": bt.N / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 Krylov + f64 refinement", "data": "synthetic",
+            "config": {"workload": "256 independent 2D Poisson systems, sizes log-uniform 32^2..512^2 "
+                                   "(seed 4), degree-4 polynomial Dirichlet data",
+                       "dps": bt.N, "tol": args.tol, "mode": "mixed", "graph": True,
+                       "tiling": {"rows": rows, "ctas_per_sm": cps, "autotune_ms_per_sweep": tune_ms},
+                       "l2": "flushed between steps (256 MB write)"},
+            "iters_max": int(res["iters"].max()), "iters_mean": float(res["iters"].mean()),
+            "rel_res_max": float(res["rel_res"].max()),
+            "batched_fp64": {"value": bt.N / (ms64 / 1e3), "ms_per_step": ms64,
+                             "iters_max": int(res64["iters"].max())},
+            "per_system_fp64": {"value": bt.N / (ms_each / 1e3), "ms_per_step": ms_each,
+                                "iters_max": int(max(its))},
+            "speedup_vs_per_system_fp64": ms_each / ms,
+            "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+# FLOPs of one network inference per cell: 2 x 9 taps x (7 x 32 + 32 x 32 x 2 + 32 x 1)
+CNN_FLOP_PER_CELL = 2 * 9 * (7 * 32 + 32 * 32 * 2 + 32 * 1)
+
+
+def cnn_arm(args):
+    """One line for the network: inference (4 conv layers) and one training
+    step (forward, loss, input and weight gradients, Adam) on an n x n grid
+    of synthetic bf16 features, against the measured bf16 tensor peak."""
+    import torch
+
+    from paper_2404_17542_gb300 import build, inputs, mcd
+    build.build()
+    mcd.lib()
+    dev = torch.device("cuda", 0)
+    n = args.n
+    N = n * n
+    net = mcd.Net(inputs.cnn_flatten(*inputs.cnn_weights(0)))
+    g = torch.Generator(device=dev).manual_seed(0)
+    x = (torch.rand((N, 8), generator=g, device=dev) * 2 - 1).to(torch.bfloat16).view(torch.int16)
+    y = torch.empty(N, dtype=torch.float32, device=dev)
+    tg = torch.randn(N, generator=g, device=dev)
+    wt = torch.ones(N, dtype=torch.float32, device=dev)
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(f):
+        for _ in range(max(3, args.warmup)):
+            f()
+        tot = 0.0
+        for _ in range(args.steps):
+            flush_buf.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            f()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / args.steps
+    t_fwd = timed(lambda: net.forward(x, n, n, y))
+    t_train = timed(lambda: net.train_step(x, tg, wt, n, n, 1e-4))
+    flop = CNN_FLOP_PER_CELL * N
+    peak = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        peak = json.load(open(p)).get("bf16_tflops")
+    ach = flop / (t_fwd / 1e3) / 1e12
+    line = {"metric": "network inference cells/s", "value": N / (t_fwd / 1e3), "unit": "cells/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": t_fwd,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (f32 accumulate)",
+            "data": "synthetic", "config": {"workload": f"4-layer 3x3 conv network, 32 channels, {n}x{n} grid",
+                                            "l2": "flushed between steps (256 MB write)"},
+            "train_step_ms": t_train, "train_cells_per_s": N / (t_train / 1e3),
+            "roofline": {"bound": "tensor", "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
+                         "frac": round(ach / peak, 4) if peak else None,
+                         "algorithmic": f"{CNN_FLOP_PER_CELL} FLOP per cell x {N} cells per inference"}}
+    print(json.dumps(line), flush=True)
+
+
+def profile_solve(args):
+    """One mixed solve of the cylinder system at step 1 from p = 0."""
+    import torch
+
+    from paper_2404_17542_gb300 import build, inputs, mcd
+    build.build()
+    mcd.lib()
+    run = CylinderRun(args.n, torch.device("cuda", 0), mcd, inputs, args.tol)
+    info = run.step(mcd.MIXED)
+    print(json.dumps({"iters": info["iters"], "fallback": info["fallback"], "dps": run.N,
+                      "rel_res": info["rel_res"]}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.profile_solve:
+        profile_solve(args)
+    elif args.workload == "batched":
+        batched_arm(args)
+    elif args.workload == "cnn":
+        cnn_arm(args)
     else:
         gpu_arm(args)
 

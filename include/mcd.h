@@ -358,6 +358,7 @@ typedef struct {
     int iters;         /* Bi-CGSTAB iterations of this system */
     int updates;       /* true-residual updates after the first */
     double rel_res;    /* ||b - A p|| / ||b|| (FP64) at the last update */
+    int fallback;      /* MIXED: 1 if the FP32 recursion failed and FP64 finished */
 } mcd_batch_result;
 
 /* meshes: host [count], each 2D.  Returns MCD_ENOTSUP for a 3D mesh or a
@@ -384,7 +385,9 @@ mcd_status mcd_batch_check(const mcd_batch *bt, int64_t *first_bad_dp, mcd_strea
  * systems still running spread over all CTAs each sweep.  prm: tol (per
  * system, ||b_i - A_i p_i|| <= tol ||b_i||), max_iter (per system), mode
  * (MCD_MIXED: FP32 recursion with FP64 true-residual updates, inner_tol as
- * in mcd_solve_pressure; MCD_FP64), net must be NULL.  p_dev: initial guess
+ * in mcd_solve_pressure, and systems whose FP32 recursion fails finished by
+ * a second launch in FP64 from their last folded iterate; MCD_FP64), net
+ * must be NULL.  p_dev: initial guess
  * in, solutions out.  use_graph: capture the launches in a CUDA graph on the
  * first call and replay it while the arguments and tuning stay the same.
  * results: host [count] or NULL.  Synchronises the stream.  Returns MCD_OK

@@ -680,7 +680,9 @@ __global__ void prep_kernel(int64_t N, const int8_t *__restrict__ kind, const do
 
 // Scalars of every system reset to "true-residual update next", full work
 // list, zero accumulators (one block).
-__global__ void init_kernel(BArgs a, int max_iter) {
+// With `subset` (device int [nsys], may be NULL) only the systems with a
+// nonzero entry run; the others are marked converged.
+__global__ void init_kernel(BArgs a, int max_iter, const int *__restrict__ subset) {
     for (int i = threadIdx.x; i < a.nsys; i += blockDim.x) {
         BScal c;
         memset(&c, 0, sizeof(c));
@@ -689,27 +691,35 @@ __global__ void init_kernel(BArgs a, int max_iter) {
         c.restart = 1;
         c.mode = MODE_UPDATE;
         c.bb64 = -1.0;   // marks the first update
+        if (subset && !subset[i]) {
+            c.done = 1;
+            c.pending = 0;
+            c.mode = MODE_SKIP;
+        }
         a.sc[i] = c;
-        a.active[i] = i;
     }
     for (int i = threadIdx.x; i < 12 * a.nsys; i += blockDim.x) a.acc[i] = 0.0;
     __syncthreads();
-    // tile prefix of list 0 (all systems)
+    // list 0: the systems that run, with their tile prefix
     int base = 0;
     int64_t wbase = 0;
     for (int c0 = 0; c0 < a.nsys; c0 += 256) {
         const int j = c0 + threadIdx.x;
-        const int64_t tiles = (j < a.nsys) ? a.geo[j].ntiles : 0;
+        const int keep = (j < a.nsys && (!subset || subset[j])) ? 1 : 0;
+        const int64_t tiles = keep ? a.geo[j].ntiles : 0;
         int cpos, ctot;
         int64_t wpos, wtot;
-        scan2(j < a.nsys ? 1 : 0, tiles, cpos, wpos, ctot, wtot);
-        if (j < a.nsys) a.prefix[j] = wbase + wpos;
+        scan2(keep, tiles, cpos, wpos, ctot, wtot);
+        if (keep) {
+            a.active[base + cpos] = j;
+            a.prefix[base + cpos] = wbase + wpos;
+        }
         base += ctot;
         wbase += wtot;
     }
     if (threadIdx.x == 0) {
-        a.prefix[a.nsys] = wbase;
-        a.state->n_active = a.nsys;
+        a.prefix[base] = wbase;
+        a.state->n_active = base;
         a.state->phase_err = 0;
         a.state->list = 0;
         a.state->M = wbase;
@@ -750,6 +760,7 @@ struct mcd_batch {
     double *acc = nullptr;
     int *active = nullptr;
     int64_t *prefix = nullptr;
+    int *subset = nullptr;        // [nsys] systems of an FP64 finish
     BState *state = nullptr;
     BState *h_state = nullptr;
     GridBarrier *bar = nullptr;
@@ -823,6 +834,7 @@ mcd_status ensure_solver(mcd_batch *bt, int mode) {
         chk(cudaMalloc(&bt->acc, (size_t)12 * bt->nsys * sizeof(double)));
         chk(cudaMalloc(&bt->active, (size_t)2 * bt->nsys * sizeof(int)));
         chk(cudaMalloc(&bt->prefix, (size_t)2 * (bt->nsys + 1) * sizeof(int64_t)));
+        chk(cudaMalloc(&bt->subset, (size_t)bt->nsys * sizeof(int)));
         chk(cudaMalloc(&bt->state, sizeof(BState)));
         chk(cudaMallocHost(&bt->h_state, sizeof(BState)));
     }
@@ -904,17 +916,18 @@ mcd_status make_launch(mcd_batch *bt, double *p, const mcd_solve_params *prm, La
 // persistent kernel.  With `timed` the persistent launch is wrapped in a
 // KTimer (direct launches); inside a graph capture it is not.
 mcd_status enqueue_solve(mcd_batch *bt, const double *rhs, const double *bnd, double *p,
-                         const mcd_solve_params *prm, Launch &L, cudaStream_t s, bool capture) {
+                         const mcd_solve_params *prm, Launch &L, cudaStream_t s, bool capture,
+                         const int *subset = nullptr) {
     const int64_t N = bt->N;
     const unsigned eb = (unsigned)((N + 255) / 256);
     float *x32 = prm->mode == MCD_MIXED ? bt->f[0] : nullptr;
     const int max_iter = prm->max_iter > 0 ? prm->max_iter : (1 << 30);
     if (capture) {
         prep_kernel<<<eb, 256, 0, s>>>(N, bt->kind, rhs, bnd, bt->b, p, x32);
-        init_kernel<<<1, 256, 0, s>>>(L.args, max_iter);
+        init_kernel<<<1, 256, 0, s>>>(L.args, max_iter, subset);
     } else {
         MCD_KLAUNCH(MCD_K_OTHER, s, prep_kernel<<<eb, 256, 0, s>>>(N, bt->kind, rhs, bnd, bt->b, p, x32));
-        MCD_KLAUNCH(MCD_K_OTHER, s, init_kernel<<<1, 256, 0, s>>>(L.args, max_iter));
+        MCD_KLAUNCH(MCD_K_OTHER, s, init_kernel<<<1, 256, 0, s>>>(L.args, max_iter, subset));
     }
     MCD_LAUNCH_CHECK();
     MCD_CUDA_TRY(cudaMemsetAsync(bt->bar, 0, sizeof(GridBarrier) + (size_t)L.grid * sizeof(unsigned), s));
@@ -1035,6 +1048,7 @@ mcd_status finish_solve(mcd_batch *bt, Launch &L, mcd_batch_result *results, cud
             results[i].iters = c.iter;
             results[i].updates = c.updates;
             results[i].rel_res = c.bb64 > 0.0 ? sqrt(c.rr64 / c.bb64) : 0.0;
+            results[i].fallback = 0;
         }
         if (si != MCD_OK && worst == MCD_OK) worst = si;
     }
@@ -1132,6 +1146,7 @@ extern "C" void mcd_batch_destroy(mcd_batch *bt) {
     cudaFree(bt->bgeo_d); cudaFree(bt->b);
     for (int i = 0; i < 9; ++i) { cudaFree(bt->f[i]); cudaFree(bt->d[i]); }
     cudaFree(bt->sc); cudaFreeHost(bt->h_sc); cudaFree(bt->acc); cudaFree(bt->active); cudaFree(bt->prefix);
+    cudaFree(bt->subset);
     cudaFree(bt->state); cudaFreeHost(bt->h_state); cudaFree(bt->bar);
     delete bt;
 }
@@ -1190,7 +1205,51 @@ extern "C" mcd_status mcd_batch_solve(mcd_batch *bt, const double *rhs_dev, cons
     Launch L;
     s = run_solve(bt, rhs_dev, bnd_dev, p_dev, prm, use_graph != 0, stream, L);
     if (s != MCD_OK) return s;
-    return finish_solve(bt, L, results, stream);
+    std::vector<mcd_batch_result> res(bt->nsys);
+    s = finish_solve(bt, L, res.data(), stream);
+    if (s == MCD_ETIMEOUT || prm->mode != MCD_MIXED || s == MCD_OK) {
+        if (results) std::copy(res.begin(), res.end(), results);
+        return s;
+    }
+    // FP64 finish of the systems whose FP32 recursion failed, from their
+    // last folded iterate (the failed cycle never reached it)
+    std::vector<int> sub(bt->nsys, 0);
+    int nfail = 0;
+    for (int i = 0; i < bt->nsys; ++i)
+        if (res[i].status == MCD_EBREAKDOWN || res[i].status == MCD_ENONFINITE) {
+            sub[i] = 1;
+            ++nfail;
+        }
+    if (nfail == 0) {
+        if (results) std::copy(res.begin(), res.end(), results);
+        return s;
+    }
+    s = ensure_solver(bt, MCD_FP64);
+    if (s != MCD_OK) return s;
+    MCD_CUDA_TRY(cudaMemcpyAsync(bt->subset, sub.data(), bt->nsys * sizeof(int), cudaMemcpyHostToDevice, stream));
+    mcd_solve_params p64 = *prm;
+    p64.mode = MCD_FP64;
+    Launch L64;
+    s = make_launch(bt, p_dev, &p64, L64);
+    if (s != MCD_OK) return s;
+    s = enqueue_solve(bt, rhs_dev, bnd_dev, p_dev, &p64, L64, stream, false, bt->subset);
+    if (s != MCD_OK) return s;
+    std::vector<mcd_batch_result> r64(bt->nsys);
+    mcd_status s64 = finish_solve(bt, L64, r64.data(), stream);
+    if (s64 == MCD_ETIMEOUT) return s64;
+    mcd_status worst = MCD_OK;
+    for (int i = 0; i < bt->nsys; ++i) {
+        if (sub[i]) {
+            const int mixed_iters = res[i].iters;
+            res[i] = r64[i];
+            res[i].iters += mixed_iters;
+            res[i].fallback = 1;
+        }
+        if (res[i].status != MCD_OK && worst == MCD_OK) worst = (mcd_status)res[i].status;
+    }
+    if (results) std::copy(res.begin(), res.end(), results);
+    if (worst != MCD_OK) set_error("batch solve: some systems did not converge (see the per-system results)");
+    return worst;
 }
 
 extern "C" mcd_status mcd_batch_set_tuning(mcd_batch *bt, const mcd_batch_tuning *t) {

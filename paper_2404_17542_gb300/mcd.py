@@ -60,7 +60,8 @@ class c_batch_tuning(C.Structure):
 
 
 class c_batch_result(C.Structure):
-    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("updates", C.c_int), ("rel_res", C.c_double)]
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("updates", C.c_int), ("rel_res", C.c_double),
+                ("fallback", C.c_int)]
 
 
 class c_body(C.Structure):
@@ -352,7 +353,8 @@ class Batch:
         st = lib().mcd_batch_solve(self.handle, _ptr(rhs, f64, self.N), _ptr(bnd, f64, self.N),
                                    _ptr(p, f64, self.N), C.byref(sp), 1 if graph else 0,
                                    C.cast(res, C.c_void_p), _stream())
-        out = {k: np.array([getattr(r, k) for r in res]) for k in ("status", "iters", "updates", "rel_res")}
+        out = {k: np.array([getattr(r, k) for r in res])
+               for k in ("status", "iters", "updates", "rel_res", "fallback")}
         out["return"] = st
         if st != OK and raise_on_error:
             raise McdError(st, lib().mcd_last_error().decode())

@@ -136,8 +136,12 @@ def test_full_batched_workload(mcd):
     """256 systems of log-uniform size 32^2 .. 512^2 (seed 4)."""
     probs = inputs.batched_poly4(4)
     bt, rhs, bnd = make_batch(mcd, probs, mcd.MIXED)
-    p, res = bt.solve(rhs, bnd, tol=1e-8, graph=True)
-    assert np.all(res["status"] == 0)
+    for rows, cps in ((2, 2), (4, 2)):
+        bt.set_tuning(rows, cps)
+        p, res = bt.solve(rhs, bnd, tol=1e-8, graph=True)
+        print(f"tiling {rows}x{cps}: FP64 finishes {int(res['fallback'].sum())}, "
+              f"iterations max {res['iters'].max()}")
+        assert np.all(res["status"] == 0)
     assert np.all(res["rel_res"] <= 1e-8)
     got = p.cpu().numpy()
     order = np.argsort([pb.mesh.N for pb in probs])[:3]
