@@ -337,41 +337,27 @@ __device__ bool barrier(const BArgs &a, unsigned &epoch, F reduce) {
     ++epoch;
     if (tid == 0) s_err = 0;
     __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        *((volatile unsigned *)&a.bar->flag[blockIdx.x]) = epoch;
-    }
+    if (tid == 0) st_release(&a.bar->flag[blockIdx.x], epoch);
     if (blockIdx.x == 0) {
-        for (int b = tid; b < (int)gridDim.x; b += 256) {
-            long long polls = 0;
-            while (vload(&a.bar->flag[b]) != epoch) {
-                if (++polls > a.spin_limit) { s_err = 1; break; }
-                __nanosleep(32);
+        for (int b = tid; b < (int)gridDim.x; b += 256)
+            if (!wait_eq(&a.bar->flag[b], epoch, a.spin_limit)) {
+                s_err = 1;
+                break;
             }
-        }
         __syncthreads();
         if (s_err) {
             if (tid == 0) a.state->phase_err = 1;
             return false;
         }
-        __threadfence();
         reduce(tid);
         __syncthreads();
-        if (tid == 0) {
-            __threadfence();
-            *((volatile unsigned *)&a.bar->release) = epoch;
-        }
+        for (int b = 1 + tid; b < (int)gridDim.x; b += 256)
+            st_release(release_word(a.bar, gridDim.x, b), epoch);
     } else if (tid == 0) {
-        long long polls = 0;
-        while (vload(&a.bar->release) != epoch) {
-            if (++polls > a.spin_limit) {
-                s_err = 1;
-                a.state->phase_err = 1;
-                break;
-            }
-            __nanosleep(32);
+        if (!wait_eq(release_word(a.bar, gridDim.x, blockIdx.x), epoch, a.spin_limit)) {
+            s_err = 1;
+            a.state->phase_err = 1;
         }
-        __threadfence();
     }
     __syncthreads();
     return !s_err;
@@ -846,7 +832,7 @@ mcd_status ensure_solver(mcd_batch *bt, int mode) {
     if (bt->bar_cap < need) {
         cudaFree(bt->bar);
         bt->bar = nullptr;
-        chk(cudaMalloc(&bt->bar, sizeof(GridBarrier) + (size_t)need * sizeof(unsigned)));
+        chk(cudaMalloc(&bt->bar, barrier_bytes(need)));
         bt->bar_cap = need;
     }
     if (e != cudaSuccess) {
@@ -908,7 +894,7 @@ mcd_status make_launch(mcd_batch *bt, double *p, const mcd_solve_params *prm, La
     a.eps_breakdown = mixed ? 1e-12 : 1e-14;
     const long long mi = prm->max_iter > 0 ? prm->max_iter : (1 << 30);
     a.budget = (int)std::min<long long>(mi * 2 + 64, 1 << 30);
-    a.spin_limit = 1ll << 24;
+    a.spin_limit = 1ll << 21;
     return MCD_OK;
 }
 
@@ -930,7 +916,7 @@ mcd_status enqueue_solve(mcd_batch *bt, const double *rhs, const double *bnd, do
         MCD_KLAUNCH(MCD_K_OTHER, s, init_kernel<<<1, 256, 0, s>>>(L.args, max_iter, subset));
     }
     MCD_LAUNCH_CHECK();
-    MCD_CUDA_TRY(cudaMemsetAsync(bt->bar, 0, sizeof(GridBarrier) + (size_t)L.grid * sizeof(unsigned), s));
+    MCD_CUDA_TRY(cudaMemsetAsync(bt->bar, 0, barrier_bytes(L.grid), s));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(L.grid);
     cfg.blockDim = dim3(256);
@@ -953,7 +939,7 @@ mcd_status enqueue_solve(mcd_batch *bt, const double *rhs, const double *bnd, do
 
 // Continue a solve whose launch ran out of sweeps.
 mcd_status continue_solve(mcd_batch *bt, Launch &L, cudaStream_t s) {
-    MCD_CUDA_TRY(cudaMemsetAsync(bt->bar, 0, sizeof(GridBarrier) + (size_t)L.grid * sizeof(unsigned), s));
+    MCD_CUDA_TRY(cudaMemsetAsync(bt->bar, 0, barrier_bytes(L.grid), s));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(L.grid);
     cfg.blockDim = dim3(256);

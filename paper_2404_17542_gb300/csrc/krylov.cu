@@ -519,7 +519,7 @@ static mcd_status ensure_workspace(mcd_stencils *st, int mode) {
         chk(cudaMalloc(&w->partials, 4 * (size_t)w->pstride * sizeof(double)));
         chk(cudaMalloc(&w->counter, sizeof(unsigned int)));
         chk(cudaMalloc(&w->sc, sizeof(Scalars)));
-        chk(cudaMalloc(&w->bar, sizeof(GridBarrier) + (size_t)w->pstride * sizeof(unsigned int)));
+        chk(cudaMalloc(&w->bar, barrier_bytes(w->pstride)));
         chk(cudaMallocHost(&w->h_sc, sizeof(Scalars)));
         if (e == cudaSuccess) e = cudaMemset(w->counter, 0, sizeof(unsigned int));
         if (e != cudaSuccess) {
@@ -857,25 +857,19 @@ __device__ bool grid_reduce(const PArgs &a, unsigned &epoch, Acc (&d)[NV], Last 
     dot_partials<NV>(d, a.partials, a.pstride, blockIdx.x);
     if (tid == 0) s_err = 0;
     __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        *((volatile unsigned *)&a.bar->flag[blockIdx.x]) = epoch;
-    }
+    if (tid == 0) st_release(&a.bar->flag[blockIdx.x], epoch);
     if (blockIdx.x == 0) {
         // wait for every block's flag (each thread a strided subset)
-        for (int b = tid; b < (int)gridDim.x; b += 256) {
-            long long polls = 0;
-            while (vload(&a.bar->flag[b]) != epoch) {
-                if (++polls > a.spin_limit) { s_err = 1; break; }
-                __nanosleep(32);
+        for (int b = tid; b < (int)gridDim.x; b += 256)
+            if (!wait_eq(&a.bar->flag[b], epoch, a.spin_limit)) {
+                s_err = 1;
+                break;
             }
-        }
         __syncthreads();
         if (s_err) {
             if (tid == 0) a.sc->phase_err = 1;
             return false;
         }
-        __threadfence();
         double acc[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) acc[q] = 0.0;
@@ -905,20 +899,15 @@ __device__ bool grid_reduce(const PArgs &a, unsigned &epoch, Acc (&d)[NV], Last 
                 s_tot[q] = x;
             }
             last(s_tot);
-            __threadfence();
-            *((volatile unsigned *)&a.bar->release) = epoch;
         }
+        __syncthreads();
+        for (int b = 1 + tid; b < (int)gridDim.x; b += 256)
+            st_release(release_word(a.bar, gridDim.x, b), epoch);
     } else if (tid == 0) {
-        long long polls = 0;
-        while (vload(&a.bar->release) != epoch) {
-            if (++polls > a.spin_limit) {
-                s_err = 1;
-                a.sc->phase_err = 1;
-                break;
-            }
-            __nanosleep(32);
+        if (!wait_eq(release_word(a.bar, gridDim.x, blockIdx.x), epoch, a.spin_limit)) {
+            s_err = 1;
+            a.sc->phase_err = 1;
         }
-        __threadfence();
     }
     __syncthreads();
     return !s_err;
@@ -1402,9 +1391,9 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
     a.tol = prm->tol;
     a.eps_breakdown = mixed ? 1e-12 : 1e-14;
     a.iter_budget = 4096;
-    a.spin_limit = 1ll << 24;   // about 1 s of polls at 64 ns per poll
+    a.spin_limit = 1ll << 21;   // about 1.5 s of polls (L2 round trip + 64 ns sleep)
     a.trace = g_trace;
-    const size_t bar_bytes = sizeof(GridBarrier) + (size_t)grid * sizeof(unsigned int);
+    const size_t bar_bytes = barrier_bytes(grid);
     // start with a true-residual update of the initial guess
     int one = 1;
     MCD_CUDA_TRY(cudaMemcpyAsync(&w->sc->pending, &one, sizeof(int), cudaMemcpyHostToDevice, stream));

@@ -9,14 +9,28 @@
 
 namespace mcd {
 
-// Grid barrier state: `release` (its own 256-byte line) and one arrival
-// flag per block.  Both hold barrier epochs, 1, 2, ... within a launch (the
+// Grid barrier state: per block an arrival flag, and a release word on a
+// 128-byte line of its own (polling one shared word from every block queues
+// the polls on one L2 slice and delays the wake-up of the last blocks by
+// microseconds).  Both hold barrier epochs 1, 2, ... within a launch (the
 // host zeroes them before each launch), so nothing is reset in between.
 struct GridBarrier {
-    unsigned int release;
-    unsigned int pad[63];
-    unsigned int flag[1];     // [grid] arrival epochs (allocated past the struct)
+    unsigned int pad[64];
+    unsigned int flag[1];     // [grid] arrival epochs, then the release lines
 };
+
+__host__ __device__ __forceinline__ size_t barrier_release_offset(int grid) {
+    return ((size_t)grid * sizeof(unsigned int) + 127) / 128 * 128;
+}
+
+// Bytes of a barrier for `grid` blocks.
+__host__ __device__ __forceinline__ size_t barrier_bytes(int grid) {
+    return sizeof(GridBarrier) + barrier_release_offset(grid) + (size_t)grid * 128;
+}
+
+__device__ __forceinline__ unsigned *release_word(GridBarrier *bar, int grid, int block) {
+    return (unsigned *)((char *)bar->flag + barrier_release_offset(grid)) + (size_t)block * 32;
+}
 
 template <typename F>
 __device__ __forceinline__ F vload(const F *p) {
@@ -25,6 +39,31 @@ __device__ __forceinline__ F vload(const F *p) {
 
 // Tile of the Bi-CGSTAB stencil kernels: 256 threads own X x Y (x Z) DPs, R
 // per thread, strided along the last tiled axis (thread grid X x TY x TZ).
+// Grid-barrier flag accesses at GPU scope: a release store publishes every
+// write that precedes it (the block's writes, ordered by the __syncthreads in
+// front of it), an acquire load makes them visible to the polling thread,
+// and the __syncthreads after the poll hands them to the rest of its block.
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait until *p == v: back-to-back polls first, then polls spaced by
+// __nanosleep.  Returns false after `limit` polls.
+__device__ __forceinline__ bool wait_eq(const unsigned *p, unsigned v, long long limit) {
+    long long polls = 0;
+    while (ld_acquire(p) != v) {
+        if (++polls > limit) return false;
+        if (polls > 256) __nanosleep(64);
+    }
+    return true;
+}
+
 template <int DIM> struct Tile;
 template <> struct Tile<2> {
     static constexpr int X = 32, Y = 16, Z = 1, R = 2, TY = 8, TZ = 1;
