@@ -187,6 +187,9 @@ typedef struct mcd_net mcd_net;   /* learned warm start, declared below */
  * check_every  Krylov iterations between host convergence checks (0: auto).
  * update_restart (MIXED) 1: restart the FP32 recurrence (fresh shadow
  *              residual, p = r) at every reliable update; 0: keep p.
+ * barriers     grid barriers per Bi-CGSTAB iteration of the persistent solve:
+ *              2 (default; x, r update fused into the next p, v = A p phase,
+ *              beta from the recurrence r^.s - omega r^.t) or 3 (textbook).
  * net_dprev    with net: device float64 [N] or NULL, in and out: the
  *              increment the warm start reads (the pressure of the last
  *              step minus the one before); after a converged solve it
@@ -201,6 +204,7 @@ typedef struct {
     int check_every;
     int update_restart;
     double *net_dprev;
+    int barriers;
 } mcd_solve_params;
 
 typedef struct {
@@ -515,11 +519,13 @@ mcd_status mcd_timing_read(int kernel, int64_t *sampled, double *total_ms);
 
 /* Phase trace of the persistent solver: when enabled (on = 1), thread 0 of
  * block 0 records %globaltimer stamps (ns) for the first 64 iterations of
- * each launch: host_out[8*it + slot], slot 0 iteration start, 1 phase A
- * done, 2 A reduced, 3 B done, 4 B reduced, 5 C done, 6 C reduced; then,
- * for iteration 10, host_out[512 + b] = phase-A end of block b and
- * host_out[2560 + b] = its SM id (b < 2048).  mcd_trace_read synchronises
- * the device and copies the 4608 values. */
+ * each launch: host_out[8*it + slot].  Three-barrier schedule: slot 0
+ * iteration start, 1 phase A done, 2 A reduced, 3 B done, 4 B reduced, 5 C
+ * done, 6 C reduced; two-barrier schedule: 0 start, 1 phase CA done, 2 CA
+ * reduced, 3 B done, 4 B reduced.  For iteration 10 and block b < 2048:
+ * host_out[512 + b] = end of its first phase, host_out[2560 + b] = its SM
+ * id, host_out[4608 + b] = its start of the iteration.  mcd_trace_read
+ * synchronises the device and copies the 6656 values. */
 mcd_status mcd_trace_enable(int on);
 mcd_status mcd_trace_read(unsigned long long *host_out);
 

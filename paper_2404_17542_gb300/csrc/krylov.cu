@@ -516,7 +516,7 @@ static mcd_status ensure_workspace(mcd_stencils *st, int mode) {
         auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
         chk(cudaMalloc(&w->b, N * sizeof(double)));
         chk(cudaMalloc(&w->r64, N * sizeof(double)));
-        chk(cudaMalloc(&w->partials, 4 * (size_t)w->pstride * sizeof(double)));
+        chk(cudaMalloc(&w->partials, 5 * (size_t)w->pstride * sizeof(double)));
         chk(cudaMalloc(&w->counter, sizeof(unsigned int)));
         chk(cudaMalloc(&w->sc, sizeof(Scalars)));
         chk(cudaMalloc(&w->bar, barrier_bytes(w->pstride)));
@@ -832,7 +832,13 @@ __device__ __forceinline__ void stamp(const PArgs &a, int it, int slot) {
     if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && it < 64) a.trace[it * 8 + slot] = global_ns();
 }
 
-// Per-block stamp of iteration 10: phase A done time and the block's SM.
+// Per-block stamps of iteration 10: start (after the previous barrier),
+// end of the first phase, and the block's SM.
+__device__ __forceinline__ void stamp_block_start(const PArgs &a, int it) {
+    if (a.trace && threadIdx.x == 0 && it == 10 && blockIdx.x < 2048)
+        a.trace[512 + 4096 + blockIdx.x] = global_ns();
+}
+
 __device__ __forceinline__ void stamp_block(const PArgs &a, int it) {
     if (a.trace && threadIdx.x == 0 && it == 10 && blockIdx.x < 2048) {
         unsigned smid;
@@ -859,31 +865,24 @@ __device__ bool grid_reduce(const PArgs &a, unsigned &epoch, Acc (&d)[NV], Last 
     __syncthreads();
     if (tid == 0) st_release(&a.bar->flag[blockIdx.x], epoch);
     if (blockIdx.x == 0) {
-        // wait for every block's flag (each thread a strided subset)
-        for (int b = tid; b < (int)gridDim.x; b += 256)
+        // wait for every block's flag (each thread a strided subset) and add
+        // that block's partial sums as soon as its flag is seen; the fixed
+        // thread -> block assignment keeps the summation order deterministic
+        double acc[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+        for (int b = tid; b < (int)gridDim.x; b += 256) {
             if (!wait_eq(&a.bar->flag[b], epoch, a.spin_limit)) {
                 s_err = 1;
                 break;
             }
+#pragma unroll
+            for (int q = 0; q < NV; ++q) acc[q] += __ldcg(a.partials + q * a.pstride + b);
+        }
         __syncthreads();
         if (s_err) {
             if (tid == 0) a.sc->phase_err = 1;
             return false;
-        }
-        double acc[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) acc[q] = 0.0;
-        for (int b0 = tid; b0 < (int)gridDim.x; b0 += 4 * 256) {
-            double v[NV][4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int bb = b0 + u * 256;
-#pragma unroll
-                for (int q = 0; q < NV; ++q)
-                    v[q][u] = (bb < (int)gridDim.x) ? __ldcg(a.partials + q * a.pstride + bb) : 0.0;
-            }
-#pragma unroll
-            for (int q = 0; q < NV; ++q) acc[q] += (v[q][0] + v[q][1]) + (v[q][2] + v[q][3]);
         }
         __shared__ double red[NV][8];
 #pragma unroll
@@ -1237,6 +1236,7 @@ __global__ void __launch_bounds__(256) bicg_persistent(PArgs a) {
         const int it = iters;
         ++iters;
         stamp(a, it, 0);
+        stamp_block_start(a, it);
         const int par = vload(&sc->parity);
         T *p_old = (T *)(par ? a.p1 : a.p0), *p_new = (T *)(par ? a.p0 : a.p1);
         T *v_old = (T *)(par ? a.v1 : a.v0), *v_new = (T *)(par ? a.v0 : a.v1);
@@ -1334,11 +1334,352 @@ __global__ void __launch_bounds__(256) bicg_persistent(PArgs a) {
     }
 }
 
+// ===========================================================================
+// Two-barrier schedule.  The x / r update of iteration k is fused with the
+// p / v = A p phase of iteration k + 1 (phase CA), so an iteration has two
+// grid reductions instead of three:
+//   CA  r = s - omega t, x += alpha p + omega s (own DPs); on tile + halo
+//       p' = r + beta (p - omega v) (r from the halo's s and t), v' = A p';
+//       dots r^.v', r.r, r^.r             -> alpha = (r^.r) / (r^.v'), tests
+//   B   s = r - alpha v', t = A s; dots t.s, t.t, s.s, r^.s, r^.t
+//                                         -> omega, and beta from
+//       rho' = r^.s - omega r^.t (the recurrence of r^.r for the next r)
+// alpha uses the exact r^.r of phase CA; only beta uses the recurrence.
+// Modes of CA: restart (p = r, r^ = r; after a true-residual update or a
+// breakdown), normal, and ||s|| stop (x += alpha p, r = s, then an update).
+// ===========================================================================
+
+enum { CA_NORMAL = 0, CA_RESTART = 1, CA_SCONV = 2 };
+
+template <int DIM, typename T>
+__device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old, T *p_new, T *v_new,
+                         T alpha, T omega, T beta, int mode, DotAcc<T> (&dot)[3]) {
+    using HD = HaloDims<DIM>;
+    using TL = Tile<DIM>;
+    constexpr int S = HD::S;
+    constexpr bool PREF = (S == 9);
+    constexpr int HN = (HD::H + 255) / 256;
+    const Geo &g = a.ta.g;
+    const T *row = (const T *)a.row;
+    T *x = (T *)a.x;
+    T *r = (T *)a.r;
+    T *rhat = (T *)a.rh;
+    const T *s = (const T *)a.s;
+    const T *t = (const T *)a.t;
+    const int tid = threadIdx.x;
+    const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
+    for (int tl = tb; tl < te; ++tl) {
+        int x0, y0, z0;
+        tile_origin<DIM>(a.ta, tl, x0, y0, z0);
+        int64_t k[TL::R];
+        int lx[TL::R], ly[TL::R], lz[TL::R];
+        T w[TL::R][PREF ? S : 1];
+        T rh[TL::R], xo[TL::R], po[TL::R], so[TL::R], to[TL::R];
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            k[q] = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+            const bool in = k[q] >= 0;
+            if (PREF && mode != CA_SCONV) load_row<S, T>(row, g.N, k[q], w[q]);
+            rh[q] = (mode != CA_RESTART && in) ? __ldcg(rhat + k[q]) : (T)0;
+            xo[q] = (mode != CA_RESTART && in) ? __ldcg(x + k[q]) : (T)0;
+            po[q] = (mode != CA_RESTART && in) ? __ldcg(p_old + k[q]) : (T)0;
+            so[q] = (mode != CA_RESTART && in) ? __ldcg(s + k[q]) : (T)0;
+            to[q] = (mode == CA_NORMAL && in) ? __ldcg(t + k[q]) : (T)0;
+        }
+        if (mode == CA_SCONV) {
+            // x += alpha p, r = s; a true-residual update follows
+#pragma unroll
+            for (int q = 0; q < TL::R; ++q) {
+                if (k[q] < 0) continue;
+                x[k[q]] = xo[q] + alpha * po[q];
+                r[k[q]] = so[q];
+                dot[1].add(so[q], so[q]);
+                dot[2].add(rh[q], so[q]);
+            }
+            continue;
+        }
+        // p' on tile + halo (all halo loads issued before any is consumed)
+        T h1[HN], h2[HN], h3[HN], h4[HN];
+#pragma unroll
+        for (int u = 0; u < HN; ++u) {
+            const int h = tid + u * 256;
+            h1[u] = h2[u] = h3[u] = h4[u] = (T)0;
+            if (h < HD::H) {
+                const int64_t j = halo_index<DIM>(g, h, x0, y0, z0);
+                if (mode == CA_RESTART) {
+                    h1[u] = __ldcg(r + j);
+                } else {
+                    h1[u] = __ldcg(s + j);
+                    h2[u] = __ldcg(t + j);
+                    h3[u] = __ldcg(p_old + j);
+                    h4[u] = __ldcg(v_old + j);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < HN; ++u) {
+            const int h = tid + u * 256;
+            if (h < HD::H) {
+                if (mode == CA_RESTART) {
+                    tile[h] = h1[u];
+                } else {
+                    const T rj = h1[u] - omega * h2[u];
+                    tile[h] = rj + beta * (h3[u] - omega * h4[u]);
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            if (k[q] < 0) continue;
+            const T pk = tile[tile_centre<DIM>(lx[q], ly[q], lz[q])];
+            T rk, rq = rh[q];
+            if (mode == CA_RESTART) {
+                rk = pk;   // p = r on a restart
+                rq = pk;
+                rhat[k[q]] = pk;
+            } else {
+                rk = so[q] - omega * to[q];
+                x[k[q]] = xo[q] + alpha * po[q] + omega * so[q];
+                r[k[q]] = rk;
+            }
+            p_new[k[q]] = pk;
+            T vk;
+            if (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN) {
+                vk = pk;
+            } else if (PREF) {
+                vk = stencil_apply<DIM, T>(w[q], tile, lx[q], ly[q], lz[q]);
+            } else {
+                T wl[S];
+                load_row<S, T>(row, g.N, k[q], wl);
+                vk = stencil_apply<DIM, T>(wl, tile, lx[q], ly[q], lz[q]);
+            }
+            v_new[k[q]] = vk;
+            dot[0].add(rq, vk);
+            dot[1].add(rk, rk);
+            dot[2].add(rq, rk);
+        }
+        __syncthreads();
+    }
+}
+
+// Phase B of the two-barrier schedule: s = r - alpha v, t = A s; dots t.s,
+// t.t, s.s, r^.s, r^.t.
+template <int DIM, typename T>
+__device__ void phase_b2(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T> (&dot)[5]) {
+    using HD = HaloDims<DIM>;
+    using TL = Tile<DIM>;
+    constexpr int S = HD::S;
+    constexpr bool PREF = (S == 9);
+    constexpr int HN = (HD::H + 255) / 256;
+    const Geo &g = a.ta.g;
+    const T *row = (const T *)a.row;
+    const T *r = (const T *)a.r;
+    const T *rhat = (const T *)a.rh;
+    T *s_out = (T *)a.s;
+    T *t_out = (T *)a.t;
+    const int tid = threadIdx.x;
+    const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
+    for (int tl = tb; tl < te; ++tl) {
+        int x0, y0, z0;
+        tile_origin<DIM>(a.ta, tl, x0, y0, z0);
+        int64_t k[TL::R];
+        int lx[TL::R], ly[TL::R], lz[TL::R];
+        T w[TL::R][PREF ? S : 1];
+        T rh[TL::R];
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            k[q] = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+            if (PREF) load_row<S, T>(row, g.N, k[q], w[q]);
+            rh[q] = (k[q] >= 0) ? __ldcg(rhat + k[q]) : (T)0;
+        }
+        T hr[HN], hv[HN];
+#pragma unroll
+        for (int u = 0; u < HN; ++u) {
+            const int h = tid + u * 256;
+            hr[u] = hv[u] = (T)0;
+            if (h < HD::H) {
+                const int64_t j = halo_index<DIM>(g, h, x0, y0, z0);
+                hr[u] = __ldcg(r + j);
+                hv[u] = __ldcg(v + j);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < HN; ++u) {
+            const int h = tid + u * 256;
+            if (h < HD::H) tile[h] = hr[u] - alpha * hv[u];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            if (k[q] < 0) continue;
+            const T sk = tile[tile_centre<DIM>(lx[q], ly[q], lz[q])];
+            s_out[k[q]] = sk;
+            T tk;
+            if (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN) {
+                tk = sk;
+            } else if (PREF) {
+                tk = stencil_apply<DIM, T>(w[q], tile, lx[q], ly[q], lz[q]);
+            } else {
+                T wl[S];
+                load_row<S, T>(row, g.N, k[q], wl);
+                tk = stencil_apply<DIM, T>(wl, tile, lx[q], ly[q], lz[q]);
+            }
+            t_out[k[q]] = tk;
+            dot[0].add(tk, sk);
+            dot[1].add(tk, tk);
+            dot[2].add(sk, sk);
+            dot[3].add(rh[q], sk);
+            dot[4].add(rh[q], tk);
+        }
+        __syncthreads();
+    }
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) bicg_persistent2(PArgs a) {
+    using HD = HaloDims<DIM>;
+    __shared__ T tile[HD::H];
+    Scalars *sc = a.sc;
+    int iters = 0;
+    unsigned epoch = 0;
+    for (;;) {
+        if (vload(&sc->done) || vload(&sc->phase_err)) return;
+        if (vload(&sc->pending)) {
+            // ---- true residual (reliable) update: as in the three-barrier kernel
+            if (a.mixed) {
+                phase_fold<DIM, T>(a);
+                DotAcc<double> none[1];
+                if (!grid_reduce<1>(a, epoch, none, [&](double *) {})) return;
+            }
+            DotAcc<double> d64[2];
+            DotAcc<T> dt[2];
+            phase_true_residual<DIM, T>(a, d64, dt);
+            DotAcc<double> all[4];
+            all[0].v = d64[0].v;
+            all[1].v = d64[1].v;
+            if constexpr (sizeof(T) == 4) {
+                all[2].v = (double)dt[0].v.hi + (double)dt[0].v.lo;
+                all[3].v = (double)dt[1].v.hi + (double)dt[1].v.lo;
+            } else {
+                all[2].v = dt[0].v;
+                all[3].v = dt[1].v;
+            }
+            const double tol = a.tol;
+            if (!grid_reduce<4>(a, epoch, all, [&](double *tot) {
+                    sc->rr64 = tot[0];
+                    sc->bb64 = tot[1];
+                    sc->rr = tot[3];
+                    sc->tol2 = tol * tol * tot[1];
+                    sc->pending = 0;
+                    if (!isfinite(tot[0] + tot[1])) { sc->done = 4; return; }
+                    if (tot[0] <= sc->tol2) { sc->done = 1; return; }
+                    if (sc->max_hit) { sc->done = 2; return; }
+                    sc->rr_last = tot[3];
+                    sc->it_last = sc->iter;
+                    sc->restart = 1;
+                    sc->s_conv = 0;
+                    sc->alpha = sc->beta = sc->omega = 0.0;
+                    publish(sc);
+                }))
+                return;
+            continue;
+        }
+        if (iters >= a.iter_budget) return;
+        const int it = iters;
+        ++iters;
+        stamp(a, it, 0);
+        stamp_block_start(a, it);
+        const int par = vload(&sc->parity);
+        T *p_old = (T *)(par ? a.p1 : a.p0), *p_new = (T *)(par ? a.p0 : a.p1);
+        T *v_old = (T *)(par ? a.v1 : a.v0), *v_new = (T *)(par ? a.v0 : a.v1);
+        // ---- phase CA: x, r of the last iteration; p, v = A p; alpha ------
+        {
+            const int restart = vload(&sc->restart);
+            const int sconv = vload(&sc->s_conv);
+            const int mode = restart ? CA_RESTART : (sconv ? CA_SCONV : CA_NORMAL);
+            T alpha, omega, beta;
+            if constexpr (sizeof(T) == 4) {
+                alpha = vload(&sc->alpha_f); omega = vload(&sc->omega_f); beta = vload(&sc->beta_f);
+            } else {
+                alpha = (T)vload(&sc->alpha); omega = (T)vload(&sc->omega); beta = (T)vload(&sc->beta);
+            }
+            DotAcc<T> dot[3];
+            phase_ca<DIM, T>(a, tile, p_old, v_old, p_new, v_new, alpha, omega, beta, mode, dot);
+            stamp(a, it, 1);
+            stamp_block(a, it);
+            const double eps = a.eps_breakdown;
+            const double update2 = a.update2;
+            const int mixed = a.mixed;
+            const int stall = a.stall;
+            if (!grid_reduce<3>(a, epoch, dot, [&](double *tot) {
+                    const double rv = tot[0], rr = tot[1], rho = tot[2];
+                    sc->rv = rv;
+                    sc->rr = rr;
+                    if (mode != CA_RESTART) sc->iter += 1;   // iteration k finished (x, r)
+                    if (!isfinite(rv + rr + rho)) { sc->done = 4; return; }
+                    if (mode == CA_SCONV) { sc->s_conv = 0; sc->pending = 1; return; }
+                    if (mode == CA_RESTART) {
+                        sc->rhat2 = rr;
+                    } else {
+                        if (rr <= sc->tol2) { sc->pending = 1; return; }
+                        if (sc->iter >= sc->max_iter) { sc->max_hit = 1; sc->pending = 1; return; }
+                        if (mixed && rr <= update2 * sc->rr_last) { sc->pending = 1; return; }
+                        if (mixed && rr > 1e8 * sc->rr_last) { sc->diverged = 1; sc->done = 3; return; }
+                        if (mixed && sc->iter - sc->it_last >= stall) { sc->pending = 1; return; }
+                        if (fabs(rho) <= eps * sqrt(sc->rhat2 * rr)) {
+                            sc->restarts += 1;
+                            if (sc->restarts > 1000) { sc->done = 3; return; }
+                            sc->restart = 1;   // redo CA from this r with p = r
+                            return;
+                        }
+                    }
+                    sc->restart = 0;
+                    sc->parity ^= 1;
+                    sc->rho = rho;
+                    const double alpha_n = rho / rv;
+                    if (!isfinite(alpha_n) || alpha_n == 0.0) { sc->done = 3; return; }
+                    sc->alpha = alpha_n;
+                    publish(sc);
+                }))
+                return;
+            stamp(a, it, 2);
+        }
+        if (vload(&sc->done) || vload(&sc->pending) || vload(&sc->restart)) continue;
+        // ---- phase B: s, t = A s; omega, beta ------------------------------
+        {
+            T alpha;
+            if constexpr (sizeof(T) == 4) alpha = vload(&sc->alpha_f);
+            else alpha = (T)vload(&sc->alpha);
+            const int parb = vload(&sc->parity);
+            const T *v_cur = (const T *)(parb ? a.v1 : a.v0);
+            DotAcc<T> dot[5];
+            phase_b2<DIM, T>(a, tile, v_cur, alpha, dot);
+            stamp(a, it, 3);
+            if (!grid_reduce<5>(a, epoch, dot, [&](double *tot) {
+                    sc->ts = tot[0];
+                    sc->tt = tot[1];
+                    sc->ss = tot[2];
+                    if (!isfinite(tot[0] + tot[1] + tot[2] + tot[3] + tot[4])) { sc->done = 4; return; }
+                    if (tot[2] <= sc->tol2) { sc->s_conv = 1; return; }
+                    if (tot[1] == 0.0) { sc->done = 3; return; }
+                    const double omega = tot[0] / tot[1];
+                    const double rho_next = tot[3] - omega * tot[4];
+                    sc->omega = omega;
+                    sc->beta = (rho_next / sc->rho) * (sc->alpha / omega);
+                    publish(sc);
+                }))
+                return;
+            stamp(a, it, 4);
+        }
+    }
+}
+
 // Grid of the persistent launch: every resident slot (at most one block per
 // tile).
-template <int DIM, typename T>
+template <int DIM, typename T, int B>
 static int persistent_grid(int ntiles) {
-    static const int occ = occupancy(bicg_persistent<DIM, T>);
+    static const int occ = (B == 2) ? occupancy(bicg_persistent2<DIM, T>) : occupancy(bicg_persistent<DIM, T>);
     const int maxg = std::max(1, occ * sm_count());
     return std::min(ntiles, maxg);
 }
@@ -1362,7 +1703,8 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
     a.ta.bz = (DIM == 3) ? (g.n[2] + Tile<DIM>::Z - 1) / Tile<DIM>::Z : 1;
     a.ta.ntiles = a.ta.bx * a.ta.by * a.ta.bz;
     a.ta.kind = st->has_neumann ? st->kind : nullptr;
-    const int grid = persistent_grid<DIM, T>(a.ta.ntiles);
+    const bool two = prm->barriers != 3;   // default: the two-barrier schedule
+    const int grid = two ? persistent_grid<DIM, T, 2>(a.ta.ntiles) : persistent_grid<DIM, T, 3>(a.ta.ntiles);
     a.grid = grid;
     a.row64 = st->row64;
     a.b = w->b;
@@ -1404,8 +1746,8 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
         MCD_CUDA_TRY(cudaMemsetAsync(w->bar, 0, bar_bytes, stream));
         {
             KTimer kt(MCD_K_SOLVE, stream);
-            MCD_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)bicg_persistent<DIM, T>, dim3(grid),
-                                                     dim3(256), args, 0, stream));
+            const void *kern = two ? (const void *)bicg_persistent2<DIM, T> : (const void *)bicg_persistent<DIM, T>;
+            MCD_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(256), args, 0, stream));
         }
         mcd_status s = read_scalars(w, stream);
         if (s != MCD_OK) return s;
@@ -1556,8 +1898,8 @@ using namespace mcd;
 
 extern "C" mcd_status mcd_trace_enable(int on) {
     if (on && !g_trace) {
-        MCD_CUDA_TRY(cudaMalloc(&g_trace, (512 + 4096) * sizeof(unsigned long long)));
-        MCD_CUDA_TRY(cudaMemset(g_trace, 0, (512 + 4096) * sizeof(unsigned long long)));
+        MCD_CUDA_TRY(cudaMalloc(&g_trace, (512 + 6144) * sizeof(unsigned long long)));
+        MCD_CUDA_TRY(cudaMemset(g_trace, 0, (512 + 6144) * sizeof(unsigned long long)));
     } else if (!on && g_trace) {
         cudaFree(g_trace);
         g_trace = nullptr;
@@ -1568,7 +1910,7 @@ extern "C" mcd_status mcd_trace_enable(int on) {
 extern "C" mcd_status mcd_trace_read(unsigned long long *host_out) {
     MCD_CHECK_ARG(host_out, "NULL argument");
     MCD_CHECK_ARG(g_trace, "tracing is not enabled");
-    MCD_CUDA_TRY(cudaMemcpy(host_out, g_trace, (512 + 4096) * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    MCD_CUDA_TRY(cudaMemcpy(host_out, g_trace, (512 + 6144) * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     return MCD_OK;
 }
 

@@ -46,7 +46,8 @@ class c_mls_params(C.Structure):
 class c_solve_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("mode", C.c_int),
                 ("inner_tol", C.c_double), ("max_refine", C.c_int), ("net", C.c_void_p),
-                ("check_every", C.c_int), ("update_restart", C.c_int), ("net_dprev", C.c_void_p)]
+                ("check_every", C.c_int), ("update_restart", C.c_int), ("net_dprev", C.c_void_p),
+                ("barriers", C.c_int)]
 
 
 class c_solve_info(C.Structure):
@@ -242,7 +243,7 @@ class Stencils:
 
     def solve(self, rhs, bnd, p=None, tol=1e-8, mode=MIXED, max_iter=200000, inner_tol=0.3,
               max_refine=60, check_every=64, update_restart=1, raise_on_error=True, net=None,
-              dprev=None):
+              dprev=None, barriers=0):
         """Solve the PPE; returns (p, info dict).  p is updated in place if given.
         net (a Net) adds its warm-start correction to p first; dprev (or
         None) is the last pressure increment it reads, and is overwritten
@@ -252,7 +253,8 @@ class Stencils:
         sp = c_solve_params(tol=tol, max_iter=max_iter, mode=mode, inner_tol=inner_tol,
                             max_refine=max_refine, net=None if net is None else net.handle,
                             check_every=check_every, update_restart=int(update_restart),
-                            net_dprev=None if dprev is None else _ptr(dprev, torch.float64, self.N))
+                            net_dprev=None if dprev is None else _ptr(dprev, torch.float64, self.N),
+                            barriers=int(barriers))
         info = c_solve_info()
         st = lib().mcd_solve_pressure(self.handle, _ptr(rhs, torch.float64, self.N),
                                       _ptr(bnd, torch.float64, self.N), _ptr(p, torch.float64, self.N),
@@ -543,12 +545,13 @@ def trace_enable(on: bool):
 
 
 def trace_read():
-    """Phase timestamps (64, 8) of block 0, and per-block phase-A end times
-    and SM ids of iteration 10, from the last persistent launch."""
-    buf = (C.c_uint64 * (512 + 4096))()
+    """Phase timestamps (64, 8) of block 0, and for iteration 10 the per-block
+    end of the first phase, SM ids and iteration start times, from the last
+    persistent launch."""
+    buf = (C.c_uint64 * (512 + 6144))()
     _check(lib().mcd_trace_read(buf))
     a = np.array(buf, dtype=np.uint64)
-    return a[:512].reshape(64, 8), a[512:512 + 2048], a[512 + 2048:]
+    return a[:512].reshape(64, 8), a[512:512 + 2048], a[512 + 2048:512 + 4096], a[512 + 4096:]
 
 
 def launch_count() -> int:
