@@ -271,3 +271,23 @@ def test_solve_3d_full_size(mcd):
     assert float(r.norm() / b.norm()) <= 1.01e-8
     err = np.linalg.norm(p.cpu().numpy() - pb.exact) / np.linalg.norm(pb.exact)
     assert err <= 20 * (1.0 / n) ** 2, err
+
+
+def test_update_dps_boundary_fitted(mcd):
+    """The DP update with the boundary-fitted move of Sec. 4.7 (alpha > 0)."""
+    n = 96
+    pb = inputs.cylinder_box(n)
+    cyl = pb.meta["cylinder"]
+    c = cyl.centre(0.0)
+    pos_o, m_o, _ = omask.update_dps(pb.mesh, pb.pos, pb.mask, c, cyl.radius, band=0.0, n_relax=6,
+                                     alpha=0.03)
+    pos_g, m_g = dev(pb.pos.ravel()), dev(pb.mask)
+    prev_g = torch.empty_like(m_g)
+    mcd.update_dps(pb.mesh, c, cyl.radius, cyl.body_id, pos_g, m_g, prev_g, kappa=0.2, n_relax=6,
+                   band=0.0, alpha=0.03)
+    assert np.array_equal(m_g.cpu().numpy(), m_o)
+    pg = pos_g.cpu().numpy().reshape(2, -1)
+    assert np.abs(pg - pos_o).max() <= 1e-12 * pb.mesh.l0 * 1e2
+    # the move is visible: DPs near the body differ from the alpha = 0 arrangement
+    pos_0, _m, _ = omask.update_dps(pb.mesh, pb.pos, pb.mask, c, cyl.radius, band=0.0, n_relax=6)
+    assert np.abs(pos_0 - pos_o).max() > 1e-3 * pb.mesh.l0

@@ -157,3 +157,36 @@ def test_planted_mistake_natural_length(monkeypatch):
     monkeypatch.setattr(omask, "math", FakeMath())
     new = omask.relax_sweep(mesh, pos, m, movable, (5.0, 5.0), 0.1, 2, 0.2)
     assert np.abs(new - pos).max() > 1e-6
+
+
+def test_boundary_fitted_move_shape():
+    """Sec. 4.7 (Eqs. (45)-(46)) with the spring forces off (kappa = 0):
+    an inner DP within r_e of the body moves along the ray to the centre,
+    towards the body, by at most alpha psi; the relative pull is close to
+    alpha next to the surface, falls with the distance and is nearly 0 at
+    r_e; DPs at psi >= r_e stay put."""
+    from oracle import mask as om
+    n = 64
+    pb = inputs.jittered_box(n, 2, seed=11, jitter=0.0)
+    mesh = pb.mesh
+    c, R = (0.5, 0.5), 0.1
+    mask = om.remask(mesh, pb.mask, c, R, 2, 0.0)
+    movable = mask == -1
+    alpha, r_e = 0.03, 5.0 * mesh.l0
+    new = om.relax_sweep(mesh, pb.pos, mask, movable, c, R, 2, 0.0, alpha=alpha)
+    d0 = pb.pos - np.array(c)[:, None]
+    d1 = new - np.array(c)[:, None]
+    psi0 = np.hypot(*d0) - R
+    psi1 = np.hypot(*d1) - R
+    near = movable & (psi0 < r_e) & (psi0 > 0)
+    far = movable & (psi0 >= r_e)
+    assert near.sum() > 100 and far.sum() > 100
+    assert np.array_equal(new[:, far], pb.pos[:, far])
+    cross = d0[0] * d1[1] - d0[1] * d1[0]
+    assert np.abs(cross[near]).max() <= 1e-15                 # radial
+    assert np.all(psi1[near] <= psi0[near])                   # towards the body
+    assert np.all(psi0[near] - psi1[near] <= alpha * psi0[near] * (1 + 1e-12))
+    pull = (psi0[near] - psi1[near]) / (alpha * psi0[near])
+    order = np.argsort(psi0[near])
+    assert pull[order[0]] > 0.9 and pull[order[-1]] < 0.05   # ~alpha near the surface, 0 at r_e
+    assert np.all(np.diff(pull[order]) <= 1e-12)             # decreasing with distance
