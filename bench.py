@@ -639,6 +639,9 @@ def batched_arm(args):
 
 # FLOPs of one network inference per cell: 2 x 9 taps x (7 x 32 + 32 x 32 x 2 + 32 x 1)
 CNN_FLOP_PER_CELL = 2 * 9 * (7 * 32 + 32 * 32 * 2 + 32 * 1)
+# HBM bytes per cell of one layer-by-layer inference: features in (8 bf16),
+# three 32-channel bf16 activations each written and read once, f32 output
+CNN_LAYERED_BYTES_PER_CELL = 16 + 3 * (64 + 64) + 4
 
 
 def cnn_arm(args):
@@ -680,11 +683,13 @@ def cnn_arm(args):
     t_fwd = timed(lambda: net.forward(x, n, n, y))
     t_train = timed(lambda: net.train_step(x, tg, wt, n, n, 1e-4))
     flop = CNN_FLOP_PER_CELL * N
-    peak = None
+    peak = hbm = None
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
-        peak = json.load(open(p)).get("bf16_tflops")
+        peaks = json.load(open(p))
+        peak, hbm = peaks.get("bf16_tflops"), peaks.get("hbm_gbs")
     ach = flop / (t_fwd / 1e3) / 1e12
+    layered_gbs = CNN_LAYERED_BYTES_PER_CELL * N / (t_fwd / 1e3) / 1e9
     line = {"metric": "network inference cells/s", "value": N / (t_fwd / 1e3), "unit": "cells/s",
             "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": t_fwd,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (f32 accumulate)",
@@ -693,7 +698,12 @@ def cnn_arm(args):
             "train_step_ms": t_train, "train_cells_per_s": N / (t_train / 1e3),
             "roofline": {"bound": "tensor", "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
                          "frac": round(ach / peak, 4) if peak else None,
-                         "algorithmic": f"{CNN_FLOP_PER_CELL} FLOP per cell x {N} cells per inference"}}
+                         "algorithmic": f"{CNN_FLOP_PER_CELL} FLOP per cell x {N} cells per inference"},
+            # the layer-by-layer design moves every activation through HBM:
+            # this is the roof that bounds it (the compulsory traffic is 20 B per cell)
+            "layered_hbm": {"bytes_per_cell": CNN_LAYERED_BYTES_PER_CELL, "achieved": round(layered_gbs, 1),
+                            "peak": hbm, "unit": "GB/s",
+                            "frac": round(layered_gbs / hbm, 4) if hbm else None}}
     print(json.dumps(line), flush=True)
 
 

@@ -450,7 +450,9 @@ void mcd_net_destroy(mcd_net *net);
 
 /* Copy the FP32 parameters (MCD_NET_PARAMS), the gradients of the last
  * training step (MCD_NET_GRADS) or an Adam moment to host_out [count];
- * count must equal the parameter count.  Synchronises the device. */
+ * count must equal the parameter count.  Synchronises the device.  Returns
+ * MCD_ETIMEOUT if a tensor-core convolution of this network ever gave up
+ * waiting for its MMAs (bounded wait; its outputs were not written). */
 mcd_status mcd_net_read(const mcd_net *net, int which, float *host_out, int64_t count);
 
 /* mcd_net_features - features of the system of `st` at the guess p:

@@ -188,6 +188,223 @@ __global__ void __launch_bounds__(NTHR) conv_kernel(ConvArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Hidden 32 -> 32 convolution on the 5th-generation tensor cores
+// (tcgen05.mma, bf16 operands from shared memory, FP32 accumulators in
+// tensor memory).  One CTA (one warpgroup) computes a 16 x 16 cell tile as
+// two M = 128 (16 rows x 8 columns) by N = 32 accumulators.  The input tile
+// and its halo are staged as 8-cell x 16-byte core matrices
+// ([row][channel chunk][column][8 channels]), so the A operand of tap
+// (dj, di) is the same layout started dj rows and di cells further: every
+// MMA is a descriptor with a shifted start address.  The weights are read
+// from the packed [out][tap * 32 + c] copy, whose 8-channel runs are the
+// 16-byte rows of the B core matrices.  K = 9 taps x 32 channels in 18 MMAs
+// of K = 16 per accumulator.  The completion of the MMAs is signalled by
+// tcgen05.commit on an mbarrier whose wait is bounded; a wait that gives up
+// sets *err and skips the epilogue (the tensor memory is freed either way).
+// ---------------------------------------------------------------------------
+namespace tc {
+constexpr int HX = TW + 2, HY = TH + 2;         // 18 x 18 halo
+constexpr int RS = 4 * HX * 16;                  // bytes per halo row (4 chunks x 18 cells)
+constexpr int CQ = HX * 16;                      // bytes per chunk plane of a row
+constexpr int HALO = HY * RS;                    // 20736
+constexpr int WB = 9 * 4 * 32 * 16;              // 18432: [tap][chunk][out][8]
+constexpr size_t SMEM = (size_t)WB + 2 * HALO;
+constexpr int NCOL = 64;                         // two accumulators of 32 columns
+}  // namespace tc
+
+// Shared-memory matrix descriptor: start address, leading byte offset (the
+// stride between core matrices along K), stride byte offset (between core
+// matrices along M or N), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Epilogue of one accumulator stage: warp w reads tensor-memory lanes
+// 32 (w % 4) .. + 31 of accumulator h = w / 4 (tile columns 8 h .. 8 h + 7);
+// lane row m is tile cell (m / 8, 8 h + m % 8).
+template <int EPI>
+__device__ __forceinline__ void tc_epilogue(const ConvArgs &a, uint32_t tacc, int x0, int y0) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int h = warp >> 2, quad = warp & 3;
+    uint32_t r[32];
+    const uint32_t taddr = tacc + ((uint32_t)(quad * 32) << 16) + h * 32;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int m = quad * 32 + lane;
+    const int gy = y0 + (m >> 3), gx = x0 + 8 * h + (m & 7);
+    if (gy >= a.ny || gx >= a.nx) return;
+    const int64_t cell = (int64_t)gy * a.nx + gx;
+    float v[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+    if constexpr (EPI == EPI_RELU) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + a.bias[c], 0.0f);
+    } else {
+        const uint4 *gp = reinterpret_cast<const uint4 *>(a.gate + cell * 32);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint4 gv = gp[j];
+            const bf16 *ge = reinterpret_cast<const bf16 *>(&gv);
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (!(__bfloat162float(ge[e]) > 0.0f)) v[8 * j + e] = 0.0f;
+        }
+    }
+    uint4 *op = reinterpret_cast<uint4 *>(a.out + cell * 32);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint4 o;
+        o.x = pack2(__float2bfloat16_rn(v[8 * j + 0]), __float2bfloat16_rn(v[8 * j + 1]));
+        o.y = pack2(__float2bfloat16_rn(v[8 * j + 2]), __float2bfloat16_rn(v[8 * j + 3]));
+        o.z = pack2(__float2bfloat16_rn(v[8 * j + 4]), __float2bfloat16_rn(v[8 * j + 5]));
+        o.w = pack2(__float2bfloat16_rn(v[8 * j + 6]), __float2bfloat16_rn(v[8 * j + 7]));
+        op[j] = o;
+    }
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false if it gave up.
+__device__ __forceinline__ bool tc_wait(uint32_t mbar_a, uint32_t parity) {
+    for (long long polls = 0; polls < (1ll << 22); ++polls) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar_a), "r"(parity));
+        if (done) return true;
+    }
+    return false;
+}
+
+// Copy the input tile of (x0, y0) with its halo into `halo` in the
+// core-matrix layout, 16-byte asynchronous copies; chunks outside the grid
+// read 0 bytes and are zero-filled.
+__device__ __forceinline__ void tc_stage(const ConvArgs &a, unsigned char *halo, int x0, int y0) {
+    for (int i = threadIdx.x; i < tc::HY * tc::HX * 4; i += 256) {
+        const int cell = i >> 2, q = i & 3, hy = cell / tc::HX, hx = cell - hy * tc::HX;
+        const int gy = y0 + hy - 1, gx = x0 + hx - 1;
+        const bool in = gy >= 0 && gy < a.ny && gx >= 0 && gx < a.nx;
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.in) + (in ? ((int64_t)gy * a.nx + gx) * 4 + q : 0);
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(halo + (hy * 4 + q) * tc::CQ + hx * 16);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Persistent CTAs (256 threads): the weights are staged once; tiles are
+// taken in a grid-stride loop with two halo buffers and two accumulator
+// stages.  While the MMAs of tile i run on the tensor core, the halo of
+// tile i + 1 is copied asynchronously and the epilogue of tile i - 1 runs.
+template <int EPI>
+__global__ void __launch_bounds__(256) conv_tc_kernel(ConvArgs a, int *err) {
+    static_assert(EPI == EPI_RELU || EPI == EPI_DGRAD, "hidden-layer epilogues only");
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char *wsm = tc_smem;
+    unsigned char *hbuf = tc_smem + tc::WB;        // two halo buffers
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tiles_x = (a.nx + TW - 1) / TW;
+    const int ntiles = tiles_x * ((a.ny + TH - 1) / TH);
+    constexpr int KS = kstr(WIDTH);   // row stride (bf16) of the packed weights
+    for (int i = tid; i < 9 * 4 * 32; i += 256) {
+        const int t = i >> 7, rem = i & 127, q = rem >> 5, n = rem & 31;
+        *reinterpret_cast<uint4 *>(wsm + ((t * 4 + q) * 32 + n) * 16) =
+            *reinterpret_cast<const uint4 *>(a.w + (size_t)n * KS + t * WIDTH + q * 8);
+    }
+    const uint32_t mb0 = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
+    const uint32_t mb1 = (uint32_t)__cvta_generic_to_shared(&mbar[1]);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb1));
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&tmem_base)),
+                     "n"(2 * tc::NCOL));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    const uint32_t wbase = (uint32_t)__cvta_generic_to_shared(wsm);
+    const uint32_t hbase0 = (uint32_t)__cvta_generic_to_shared(hbuf);
+    // D f32, A and B bf16, both K-major, N = 32, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+    uint32_t phase0 = 0, phase1 = 0;
+    int prev_tile = -1, prev_s = 0;
+    bool ok = true;
+    if (blockIdx.x < ntiles)
+        tc_stage(a, hbuf, (blockIdx.x % tiles_x) * TW, (blockIdx.x / tiles_x) * TH);
+    for (int it = 0, tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++it) {
+        const int s = it & 1;
+        // the MMAs of tile i - 1 are done before its halo buffer is refilled
+        bool prev_done = true;
+        if (prev_tile >= 0) {
+            prev_done = tc_wait(prev_s ? mb1 : mb0, prev_s ? phase1 : phase0);
+            if (prev_s) phase1 ^= 1u; else phase0 ^= 1u;
+        }
+        ok = __syncthreads_and(prev_done);
+        if (!ok) break;
+        const int next = tile + gridDim.x;
+        if (next < ntiles) tc_stage(a, hbuf + (s ^ 1) * tc::HALO, (next % tiles_x) * TW, (next / tiles_x) * TH);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");   // this tile's halo has landed
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // staged tile -> tensor core
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t tmem = tmem_base;
+        if (tid == 0) {
+            const uint32_t hb = hbase0 + s * tc::HALO;
+            for (int h = 0; h < 2; ++h)
+                for (int t = 0; t < 9; ++t)
+                    for (int k2 = 0; k2 < 2; ++k2) {
+                        const uint32_t aaddr = hb + (t / 3) * tc::RS + 2 * k2 * tc::CQ + (8 * h + t % 3) * 16;
+                        const uint32_t baddr = wbase + (t * 4 + 2 * k2) * 512;
+                        const uint64_t ad = tc_desc(aaddr, tc::CQ, tc::RS), bd = tc_desc(baddr, 512, 128);
+                        const uint32_t accum = (t | k2) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
+                                tmem + s * tc::NCOL + h * 32),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                    }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                s ? mb1 : mb0));
+        }
+        if (prev_tile >= 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc_epilogue<EPI>(a, tmem + prev_s * tc::NCOL, (prev_tile % tiles_x) * TW, (prev_tile / tiles_x) * TH);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+        prev_tile = tile;
+        prev_s = s;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (ok && prev_tile >= 0) {
+        const bool done = tc_wait(prev_s ? mb1 : mb0, prev_s ? phase1 : phase0);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        ok = __syncthreads_and(done);
+        if (ok)
+            tc_epilogue<EPI>(a, tmem_base + prev_s * tc::NCOL, (prev_tile % tiles_x) * TW,
+                             (prev_tile / tiles_x) * TH);
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(2 * tc::NCOL));
+}
+
+// ---------------------------------------------------------------------------
 // Weight gradient: dW[tap][o][c] = sum_cells g[cell][o] x[cell + off(tap)][c]
 // (M = output channel, N = input channel, K = cells), per-CTA partial sums
 // over a grid-stride set of 16 x 16 tiles; db[o] = sum_cells g[cell][o].
@@ -620,6 +837,7 @@ struct mcd_net {
     double *part = nullptr;       // [RED_BLOCKS][NRED]
     double *sc = nullptr;         // [8]
     double *stat = nullptr;       // [4]
+    int *tc_err = nullptr;        // set by a tensor-core convolution whose MMA wait gave up
     float *wpart = nullptr;       // wgrad partials
     int wg_blocks = 0;
 };
@@ -688,6 +906,44 @@ mcd_status launch_conv(const ConvArgs &a, cudaStream_t s) {
     return MCD_OK;
 }
 
+// Hidden-layer convolution on the tcgen05 tensor cores (forward with bias and
+// ReLU, or the input-gradient pass gated by the forward activation).
+template <int EPI>
+mcd_status launch_conv_tc(const ConvArgs &a, int *err, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        MCD_CUDA_TRY(cudaFuncSetAttribute(conv_tc_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)tc::SMEM));
+        // prefer the whole unified L1 as shared memory, so that several
+        // CTAs fit on one SM
+        MCD_CUDA_TRY(cudaFuncSetAttribute(conv_tc_kernel<EPI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared));
+        attr = true;
+    }
+    static int slots = 0;
+    if (!slots) {
+        // resident CTAs per SM from the SM's shared memory, registers and
+        // tensor-memory columns (512, 2 x 64 per CTA)
+        int dev = 0, sms = 0, smem_sm = 0, smem_res = 0, regs_sm = 0;
+        cudaFuncAttributes fa;
+        MCD_CUDA_TRY(cudaGetDevice(&dev));
+        MCD_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        MCD_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        MCD_CUDA_TRY(cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+        MCD_CUDA_TRY(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+        MCD_CUDA_TRY(cudaFuncGetAttributes(&fa, conv_tc_kernel<EPI>));
+        const int by_smem = smem_sm / (int)(tc::SMEM + fa.sharedSizeBytes + smem_res);
+        const int by_regs = regs_sm / std::max(1, fa.numRegs * 256);
+        const int by_tmem = 512 / (2 * tc::NCOL);
+        slots = std::max(1, std::min(std::min(by_smem, by_regs), by_tmem)) * std::max(1, sms);
+    }
+    const int ntiles = ((a.nx + TW - 1) / TW) * ((a.ny + TH - 1) / TH);
+    const unsigned grid = (unsigned)std::min(ntiles, slots);
+    MCD_KLAUNCH(MCD_K_CNN, s, conv_tc_kernel<EPI><<<grid, 256, tc::SMEM, s>>>(a, err));
+    MCD_LAUNCH_CHECK();
+    return MCD_OK;
+}
+
 template <int CINP, int COUTP>
 mcd_status launch_wgrad(mcd_net *n, const bf16 *x, const bf16 *g, int nx, int ny, cudaStream_t s) {
     constexpr size_t sm = wgrad_smem(CINP, COUTP);
@@ -730,7 +986,7 @@ mcd_status forward(mcd_net *n, const bf16 *x, int nx, int ny, float *y, cudaStre
         mcd_status st;
         if (l + 1 < L) {
             a.out = n->act[l];
-            st = (l == 0) ? launch_conv<FEAT, WIDTH, EPI_RELU>(a, s) : launch_conv<WIDTH, WIDTH, EPI_RELU>(a, s);
+            st = (l == 0) ? launch_conv<FEAT, WIDTH, EPI_RELU>(a, s) : launch_conv_tc<EPI_RELU>(a, n->tc_err, s);
         } else {
             a.out32 = y;
             st = (l == 0) ? launch_conv<FEAT, FEAT, EPI_LAST>(a, s) : launch_conv<WIDTH, FEAT, EPI_LAST>(a, s);
@@ -892,6 +1148,8 @@ extern "C" mcd_status mcd_net_create(int c_in, int width, int layers, const floa
     chk(cudaMalloc(&n->part, (size_t)RED_BLOCKS * NRED * sizeof(double)));
     chk(cudaMalloc(&n->sc, 8 * sizeof(double)));
     chk(cudaMalloc(&n->stat, 4 * sizeof(double)));
+    chk(cudaMalloc(&n->tc_err, sizeof(int)));
+    if (e == cudaSuccess) chk(cudaMemset(n->tc_err, 0, sizeof(int)));
     if (e == cudaSuccess) chk(cudaMemcpy(n->master, params, want * sizeof(float), cudaMemcpyHostToDevice));
     if (e == cudaSuccess) chk(cudaMemset(n->grad, 0, want * sizeof(float)));
     if (e == cudaSuccess) chk(cudaMemset(n->m, 0, want * sizeof(float)));
@@ -928,6 +1186,7 @@ extern "C" void mcd_net_destroy(mcd_net *n) {
     cudaFree(n->part);
     cudaFree(n->sc);
     cudaFree(n->stat);
+    cudaFree(n->tc_err);
     delete n;
 }
 
@@ -942,6 +1201,12 @@ extern "C" mcd_status mcd_net_read(const mcd_net *n, int which, float *host_out,
     MCD_CHECK_ARG(src, "unknown array");
     MCD_CUDA_TRY(cudaDeviceSynchronize());
     MCD_CUDA_TRY(cudaMemcpy(host_out, src, count * sizeof(float), cudaMemcpyDeviceToHost));
+    int tc_err = 0;
+    MCD_CUDA_TRY(cudaMemcpy(&tc_err, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (tc_err) {
+        set_error("a tensor-core convolution gave up waiting for its MMAs; results since are invalid");
+        return MCD_ETIMEOUT;
+    }
     return MCD_OK;
 }
 
@@ -1015,7 +1280,8 @@ extern "C" mcd_status mcd_net_train_step(mcd_net *n, const uint16_t *x_dev, cons
             a.out = gout;
             a.nx = nx;
             a.ny = ny;
-            r = (l + 1 == L) ? launch_conv<FEAT, WIDTH, EPI_DGRAD>(a, s) : launch_conv<WIDTH, WIDTH, EPI_DGRAD>(a, s);
+            r = (l + 1 == L) ? launch_conv<FEAT, WIDTH, EPI_DGRAD>(a, s)
+                             : launch_conv_tc<EPI_DGRAD>(a, n->tc_err, s);
             if (r != MCD_OK) return r;
             g = gout;
         }
