@@ -15,6 +15,9 @@ Restates Sec. 2 of arXiv 2404.17542 for circular bodies in 2D:
     optional boundary-fitted inner move beta psi d^              (Sec. 4.7, Eqs. (45)-(46))
     (iv) clamp to the DP's own cell (nearest edge or vertex)      (Sec. 2.3, Fig. 2)
   * SDF of a circle psi = |x - c| - R, > 0 in the fluid          (Sec. 2.5)
+  * several bodies: at each point the SDF of smallest magnitude is taken
+    (Sec. 2.5, last paragraph), and boundary cells carry the id of their
+    body (Sec. 2.2)
   * only DPs whose cell lies within `band` of the boundary are re-masked
     and rearranged                                               (Sec. 2.4)
 
@@ -27,7 +30,17 @@ Readings (the paper leaves them open):
   * cells with a face on the domain wall keep the wall id and never move;
   * a fixed number n_relax of Jacobi sweeps (all DPs read iterate k);
   * a DP whose cell becomes void is reset to its centroid;
-  * relocation and the boundary-fitted move use the analytic circle SDF.
+  * relocation and the boundary-fitted move use the analytic circle SDF;
+  * with several bodies: a vertex is classified by the SDF of its nearest
+    body (smallest |psi|, the first body in list order on a tie, psi
+    evaluated as sqrt(dx*dx + dy*dy) - R with each operation rounded on its
+    own), then by the test above for that body; a cell's band test and its
+    boundary id use the body nearest its centroid; a boundary DP is
+    relocated onto the body whose id it carries, an inner DP's
+    boundary-fitted move follows the body nearest its spring-relaxed
+    position.  For disjoint circles the nearest-SDF rule classifies every
+    point as the union SDF min_b psi_b does: a point at depth d inside one
+    circle lies at least d + (gap) from every other circle.
 """
 from __future__ import annotations
 
@@ -38,21 +51,53 @@ import numpy as np
 INNER, VOID = -1, 0
 
 
-def vertex_fluid(mesh, centre, radius):
-    """Boolean (n_x+1, n_y+1): vertex (i, j) has psi >= 0 (Sec. 2.2)."""
+def as_bodies(centre, radius, body_id):
+    """The body list [(id, centre, radius)] of one circular body."""
+    return [(body_id, (float(centre[0]), float(centre[1])), float(radius))]
+
+
+def nearest_body(bodies, x, y):
+    """(index, psi): the body whose circle SDF has the smallest magnitude at
+    (x, y), the first in list order on a tie (Sec. 2.5)."""
+    best, best_psi = 0, None
+    for b, (_bid, c, R) in enumerate(bodies):
+        dx = x - c[0]
+        dy = y - c[1]
+        psi = math.sqrt(dx * dx + dy * dy) - R
+        if best_psi is None or abs(psi) < abs(best_psi):
+            best, best_psi = b, psi
+    return best, best_psi
+
+
+def body_index(bodies, body_id):
+    for b, (bid, _c, _R) in enumerate(bodies):
+        if bid == body_id:
+            return b
+    return None
+
+
+def vertex_fluid_bodies(mesh, bodies):
+    """Boolean (n_x+1, n_y+1): vertex (i, j) has psi >= 0 for its nearest
+    body (Sec. 2.2, Sec. 2.5)."""
     nx, ny = mesh.n[0], mesh.n[1]
     ox, oy = mesh.origin[0], mesh.origin[1]
     l0 = mesh.l0
     out = np.zeros((nx + 1, ny + 1), dtype=bool)
-    R2 = radius * radius
     for i in range(nx + 1):
         vx = ox + float(i) * l0
-        dx = vx - centre[0]
         for j in range(ny + 1):
             vy = oy + float(j) * l0
-            dy = vy - centre[1]
-            out[i, j] = (dx * dx + dy * dy) >= R2
+            b = nearest_body(bodies, vx, vy)[0] if len(bodies) > 1 else 0
+            _bid, c, R = bodies[b]
+            dx = vx - c[0]
+            dy = vy - c[1]
+            out[i, j] = (dx * dx + dy * dy) >= R * R
     return out
+
+
+def vertex_fluid(mesh, centre, radius):
+    """Boolean (n_x+1, n_y+1): vertex (i, j) has psi >= 0 (Sec. 2.2)."""
+    return vertex_fluid_bodies(mesh, as_bodies(centre, radius, 2))
 
 
 def cell_mask_from_count(count, body_id):
@@ -69,38 +114,54 @@ def centroid(mesh, i, j):
             mesh.origin[1] + (float(j) + 0.5) * mesh.l0)
 
 
-def in_band(mesh, i, j, centre, radius, band):
+def in_band_bodies(mesh, i, j, bodies, band):
     if band <= 0.0:
         return True
     cx, cy = centroid(mesh, i, j)
-    dx = cx - centre[0]
-    dy = cy - centre[1]
-    psi = math.sqrt(dx * dx + dy * dy) - radius
-    return abs(psi) < band
+    return abs(nearest_body(bodies, cx, cy)[1]) < band
+
+
+def in_band(mesh, i, j, centre, radius, band):
+    return in_band_bodies(mesh, i, j, as_bodies(centre, radius, 2), band)
 
 
 def is_wall_cell(mesh, i, j):
     return i == 0 or j == 0 or i == mesh.n[0] - 1 or j == mesh.n[1] - 1
 
 
-def remask(mesh, mask, centre, radius, body_id, band):
-    """Role reassignment of Sec. 2.4: new masks inside the band."""
+def remask_bodies(mesh, mask, bodies, band):
+    """Role reassignment of Sec. 2.4: new masks inside the band; a boundary
+    cell takes the id of the body nearest its centroid."""
     nx, ny = mesh.n[0], mesh.n[1]
-    fl = vertex_fluid(mesh, centre, radius)
+    fl = vertex_fluid_bodies(mesh, bodies)
     new = mask.copy()
     for j in range(ny):
         for i in range(nx):
             if is_wall_cell(mesh, i, j):
                 continue
-            if not in_band(mesh, i, j, centre, radius, band):
+            if not in_band_bodies(mesh, i, j, bodies, band):
                 continue
             cnt = int(fl[i, j]) + int(fl[i + 1, j]) + int(fl[i, j + 1]) + int(fl[i + 1, j + 1])
-            new[i + nx * j] = cell_mask_from_count(cnt, body_id)
+            cx, cy = centroid(mesh, i, j)
+            bid = bodies[nearest_body(bodies, cx, cy)[0]][0]
+            new[i + nx * j] = cell_mask_from_count(cnt, bid)
     return new
+
+
+def remask(mesh, mask, centre, radius, body_id, band):
+    """Role reassignment of Sec. 2.4 for one body."""
+    return remask_bodies(mesh, mask, as_bodies(centre, radius, body_id), band)
 
 
 def relax_sweep(mesh, pos, mask, movable, centre, radius, body_id, kappa,
                 alpha=0.0, r_e_fit=None):
+    """One Jacobi sweep of steps (ii)-(iv) of Sec. 2.3 for one body."""
+    return relax_sweep_bodies(mesh, pos, mask, movable, as_bodies(centre, radius, body_id),
+                              kappa, alpha, r_e_fit)
+
+
+def relax_sweep_bodies(mesh, pos, mask, movable, bodies, kappa, alpha=0.0,
+                       r_e_fit=None):
     """One Jacobi sweep of steps (ii)-(iv) of Sec. 2.3 on the movable DPs."""
     nx, ny = mesh.n[0], mesh.n[1]
     l0 = mesh.l0
@@ -128,15 +189,25 @@ def relax_sweep(mesh, pos, mask, movable, centre, radius, body_id, kappa,
                 G = 1.0 - r / lspg                         # Eq. (6)
                 F += G * (xij / r)                         # Eq. (5)
         xs = xi - kappa * l0 * F                           # Eq. (8), dimensional
-        dxc = xs[0] - centre[0]
-        dyc = xs[1] - centre[1]
-        dist = math.sqrt(dxc * dxc + dyc * dyc)
+        if mask[k] >= 1:
+            b = body_index(bodies, int(mask[k]))           # the DP's own body
+        elif mask[k] == INNER and alpha > 0.0:
+            b = nearest_body(bodies, xs[0], xs[1])[0] if len(bodies) > 1 else 0
+        else:
+            b = None
+        if b is not None:
+            _bid, centre, radius = bodies[b]
+            dxc = xs[0] - centre[0]
+            dyc = xs[1] - centre[1]
+            dist = math.sqrt(dxc * dxc + dyc * dyc)
+        else:
+            dist = 0.0
         if dist > 0.0:
             psi = dist - radius
             dhat = np.array([-dxc / dist, -dyc / dist])   # -grad psi / |grad psi|
-            if mask[k] == body_id:
+            if mask[k] >= 1:
                 xs = xs + psi * dhat                       # Eq. (9)
-            elif mask[k] == INNER and alpha > 0.0 and psi < r_e_fit:
+            elif psi < r_e_fit:
                 beta = 0.5 * alpha * (1.0 + math.cos(math.pi * psi / r_e_fit))  # Eq. (46)
                 xs = xs + beta * psi * dhat                # Eq. (45)
         lo = (mesh.origin[0] + i * l0, mesh.origin[1] + j * l0)
@@ -152,16 +223,27 @@ def update_dps(mesh, pos, mask, centre, radius, body_id=2, kappa=0.2,
 
     Returns (pos_new, mask_new, mask_prev).
     """
+    return update_dps_bodies(mesh, pos, mask, as_bodies(centre, radius, body_id),
+                             kappa, n_relax, band, alpha)
+
+
+def update_dps_bodies(mesh, pos, mask, bodies, kappa=0.2, n_relax=10,
+                      band=None, alpha=0.0):
+    """One moving-boundary DP update (Sec. 2.3-2.4) for the circular bodies
+    [(id, centre, radius)] (ids >= 2, disjoint circles).
+
+    Returns (pos_new, mask_new, mask_prev).
+    """
     nx, ny = mesh.n[0], mesh.n[1]
     band = 5.0 * mesh.l0 if band is None else band
     mask_prev = mask.copy()
-    mask_new = remask(mesh, mask, centre, radius, body_id, band)
+    mask_new = remask_bodies(mesh, mask, bodies, band)
     pos = pos.copy()
     movable = np.zeros(mesh.N, dtype=bool)
     for j in range(ny):
         for i in range(nx):
             k = i + nx * j
-            if is_wall_cell(mesh, i, j) or not in_band(mesh, i, j, centre, radius, band):
+            if is_wall_cell(mesh, i, j) or not in_band_bodies(mesh, i, j, bodies, band):
                 continue
             if mask_new[k] == VOID:
                 if mask_prev[k] != VOID:
@@ -170,8 +252,7 @@ def update_dps(mesh, pos, mask, centre, radius, body_id=2, kappa=0.2,
                 continue
             movable[k] = True
     for _ in range(n_relax):
-        pos = relax_sweep(mesh, pos, mask_new, movable, centre, radius,
-                          body_id, kappa, alpha)
+        pos = relax_sweep_bodies(mesh, pos, mask_new, movable, bodies, kappa, alpha)
     return pos, mask_new, mask_prev
 
 
@@ -181,4 +262,14 @@ def circle_normals(pos, mask, centre, body_id):
     sel = mask == body_id
     d = pos[:, sel] - np.array(centre)[:, None]
     n[:, sel] = d / np.sqrt((d * d).sum(axis=0))
+    return n
+
+
+def bodies_normals(pos, mask, bodies):
+    """circle_normals of every body, each on the DPs carrying its id."""
+    n = np.zeros_like(pos)
+    for bid, c, _R in bodies:
+        sel = mask == bid
+        d = pos[:, sel] - np.array(c)[:, None]
+        n[:, sel] = d / np.sqrt((d * d).sum(axis=0))
     return n

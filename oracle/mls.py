@@ -12,6 +12,9 @@ Restates Sec. 3.2 of arXiv 2404.17542:
     the Neumann term over Lambda^N_c, and the chi_c Lagrange constraint     (Eq. (15), (16))
   * weight w = cos^2(pi r / (2 r_e)) for r <= r_e, else 0                   (Eq. (17))
     plus the Gaussian w = exp(-(r / r_e)^2) used by the synthetic workloads
+    and the least-squares MPS weight w = (1 - r / r_e)^2 for r < r_e, else 0
+    (Tamai and Koshizuka, 2014), the scheme the paper pairs with its
+    expanded 9x9 stencil, r_e = 3.5 l0                                    (Sec. 4.1)
   * only chi_c = 1 with x_c = x_i and phi_c = phi_i is used (end of Sec. 3.2)
 
 With chi_c = 1 the constraint fixes phi_c = phi_i, and dJ/dPhi = 0 gives the
@@ -26,6 +29,11 @@ Neumann data) into each physical derivative.
 Readings where the paper is silent:
   * compact support D_c = the 3x3 (3x3x3) background cells around the DP's
     own cell (Sec. 2.3, Sec. 3.2); periodic axes wrap with the minimum image;
+  * the expanded stencil of Sec. 4.1 is the same fit over the (2R+1)^dim
+    cells around the DP's cell with R = 4 (9x9), `support` = R below; the
+    paper names its influence radius (3.5 l0) and the least-squares MPS
+    type-A scheme, whose weight is taken as (1 - r/r_e)^2; every other rule
+    (roles, Neumann terms, row scaling) is that of the 3x3 stencil;
   * a Neumann DP's own gradient comes from a linear chi=1 fit,
     p = (X, Y[, Z]), over all its non-void neighbours (no Neumann terms):
     a boundary DP can have as few as 4 non-void neighbours, too few for the
@@ -90,10 +98,15 @@ def laplacian_components(dim):
 
 
 def weight(r, kind, r_e):
-    """Eq. (17) (kind 1, cos^2 with cut-off r_e) or the Gaussian (kind 0)."""
+    """Eq. (17) (kind 1, cos^2 with cut-off r_e), the Gaussian (kind 0) or
+    the least-squares MPS weight (kind 2, (1 - r/r_e)^2 below r_e)."""
     if kind == 1:
         if r <= r_e:
             return math.cos(math.pi * r / (2.0 * r_e)) ** 2
+        return 0.0
+    if kind == 2:
+        if r < r_e:
+            return (1.0 - r / r_e) ** 2
         return 0.0
     return math.exp(-(r / r_e) ** 2)
 
@@ -107,19 +120,27 @@ def cell_coords(mesh, k):
     return (i, rest % mesh.n[1], rest // mesh.n[1])
 
 
-def stencil_slots(mesh, k):
+def support_of(mesh, S):
+    """Support radius R of a stencil with S = (2R+1)^dim slots."""
+    W = round(S ** (1.0 / mesh.dim))
+    assert W ** mesh.dim == S and W % 2 == 1, "slot count is not an odd power"
+    return W // 2
+
+
+def stencil_slots(mesh, k, support=1):
     """Neighbour cells of cell k in slot order (first offset fastest).
 
-    Returns a list of (slot, neighbour index or None, offset tuple).  Slot s
-    of a 2D stencil is (di+1) + 3 (dj+1); in 3D add 9 (dl+1).  Cells outside a
-    non-periodic domain give None; periodic axes wrap.
+    Returns a list of (slot, neighbour index or None, offset tuple).  With
+    W = 2 support + 1, slot s of a 2D stencil is (di+R) + W (dj+R); in 3D add
+    W^2 (dl+R).  Cells outside a non-periodic domain give None; periodic axes
+    wrap.
     """
     c = cell_coords(mesh, k)
     dim = mesh.dim
     out = []
-    rng3 = (-1, 0, 1)
-    offsets = ([(di, dj) for dj in rng3 for di in rng3] if dim == 2 else
-               [(di, dj, dl) for dl in rng3 for dj in rng3 for di in rng3])
+    rng = tuple(range(-support, support + 1))
+    offsets = ([(di, dj) for dj in rng for di in rng] if dim == 2 else
+               [(di, dj, dl) for dl in rng for dj in rng for di in rng])
     for s, off in enumerate(offsets):
         idx = []
         ok = True
@@ -151,8 +172,8 @@ def rel_offset(mesh, pos, i, j):
 
 
 def dp_fit(mesh, pos, mask, normal, bc_kind, i, weight_kind=0, r_e=None,
-           r_s=None):
-    """Weights of DP i.
+           r_s=None, support=1):
+    """Weights of DP i over the (2 support + 1)^dim cells around its cell.
 
     Returns a dict with
       kind  'void' | 'inner' | 'dirichlet' | 'neumann'
@@ -165,7 +186,7 @@ def dp_fit(mesh, pos, mask, normal, bc_kind, i, weight_kind=0, r_e=None,
       rscale  factor applied to the boundary datum in the right-hand side
     """
     dim = mesh.dim
-    S = 3 ** dim
+    S = (2 * support + 1) ** dim
     centre = S // 2
     nb = 5 if dim == 2 else 9
     r_e = mesh.l0 if r_e is None else r_e
@@ -191,7 +212,7 @@ def dp_fit(mesh, pos, mask, normal, bc_kind, i, weight_kind=0, r_e=None,
         return out
 
     value_js, neu_js = [], []
-    for s, j, _off in stencil_slots(mesh, i):
+    for s, j, _off in stencil_slots(mesh, i, support):
         if j is None or j == i:
             continue
         mj = int(mask[j])
@@ -258,8 +279,9 @@ KIND_CODE = {"void": 0, "inner": 1, "dirichlet": 2, "neumann": 3}
 
 
 def build_weights(mesh, pos, mask, normal=None, bc_kind=None, weight_kind=0,
-                  r_e=None, r_s=None, dps=None):
-    """Weights of every DP (or of the listed `dps`), slot-major SoA.
+                  r_e=None, r_s=None, dps=None, support=1):
+    """Weights of every DP (or of the listed `dps`), slot-major SoA, over the
+    (2 support + 1)^dim cells around each DP's cell.
 
     Returns dict(row (S,N), QL (S,N), D (nb,S,N), QD (nb,S,N), kind (N,) int,
     rscale (N,)).
@@ -267,7 +289,7 @@ def build_weights(mesh, pos, mask, normal=None, bc_kind=None, weight_kind=0,
     """
     N = mesh.N
     dim = mesh.dim
-    S = 3 ** dim
+    S = (2 * support + 1) ** dim
     nb = 5 if dim == 2 else 9
     if bc_kind is None:
         bc_kind = np.zeros(128, dtype=np.uint8)
@@ -278,7 +300,7 @@ def build_weights(mesh, pos, mask, normal=None, bc_kind=None, weight_kind=0,
                D=np.zeros((nb, S, N)), QD=np.zeros((nb, S, N)),
                kind=np.zeros(N, dtype=np.int64), rscale=np.ones(N))
     for i in idx:
-        f = dp_fit(mesh, pos, mask, normal, bc_kind, i, weight_kind, r_e, r_s)
+        f = dp_fit(mesh, pos, mask, normal, bc_kind, i, weight_kind, r_e, r_s, support)
         res["row"][:, i] = f["row"]
         res["QL"][:, i] = f["QL"]
         res["D"][:, :, i] = f["D"]

@@ -24,15 +24,17 @@ import numpy as np
 import scipy.sparse
 import scipy.sparse.linalg
 
-from .mls import stencil_slots
+from .mls import stencil_slots, support_of
 
 
 def assemble(mesh, row):
-    """CSR matrix with A[i, j_s] = row[s, i] over the stencil slots s of DP i."""
+    """CSR matrix with A[i, j_s] = row[s, i] over the stencil slots s of DP i
+    (3x3 or expanded support, from the slot count)."""
     S, N = row.shape
+    R = support_of(mesh, S)
     rows, cols, vals = [], [], []
     for i in range(N):
-        for s, j, _off in stencil_slots(mesh, i):
+        for s, j, _off in stencil_slots(mesh, i, R):
             if j is None:
                 continue
             v = row[s, i]
@@ -50,12 +52,13 @@ def form_rhs(mesh, kind, QL, rhs, bnd, rscale=None):
     equilibration factor of oracle.mls; 1 for Dirichlet rows).
     """
     N = mesh.N
+    R = support_of(mesh, QL.shape[0])
     b = np.zeros(N)
     for i in range(N):
         k = kind[i]
         if k == 1:        # inner: f_i minus the Neumann data moved to the RHS
             acc = rhs[i]
-            for s, j, _off in stencil_slots(mesh, i):
+            for s, j, _off in stencil_slots(mesh, i, R):
                 if j is not None and QL[s, i] != 0.0:
                     acc -= QL[s, i] * bnd[j]
             b[i] = acc

@@ -246,6 +246,45 @@ def cylinder_box(n: int, cyl: Cylinder | None = None) -> Problem:
     return pb
 
 
+def cylinder_array(n: int, gap: float, count: int = 5, side: float = 2.0):
+    """Stationary cylinder array of the multiple-cylinder flow (Sec. 4.1):
+    count x count equal circles on a square lattice of pitch side / count
+    filling the square [0, side]^2, diameter pitch - gap, on an n x n
+    background mesh (l0 = side / n; the paper's case is side 2 with l0 = 1/64,
+    n = 128).  `gap` is the surface-to-surface distance of neighbouring
+    cylinders.  Returns [(id, (cx, cy), radius)] with ids 2, 3, ... row by
+    row."""
+    pitch = side / count
+    radius = 0.5 * (pitch - gap)
+    if radius <= 0.0:
+        raise ValueError("gap must be smaller than the pitch")
+    out = []
+    for j in range(count):
+        for i in range(count):
+            out.append((BODY_ID + i + count * j, ((i + 0.5) * pitch, (j + 0.5) * pitch), radius))
+    return out
+
+
+def cylinder_array_box(n: int, gap_cells: float, count: int = 5, side: float = 2.0) -> Problem:
+    """Square box of side `side` (n x n cells) for the cylinder array of
+    Sec. 4.1 before any DP update: DPs at the cell centroids, Dirichlet wall
+    cells with their DPs on the wall, every other cell inner.  The gap is
+    gap_cells * (1/64), the paper's l0, whatever n is, so that finer meshes
+    resolve the same geometry.  Every cylinder id is a Neumann boundary; the
+    right-hand side is ppe_source at t = 0."""
+    l0 = side / n
+    mesh = Mesh(dim=2, n=(n, n, 1), l0=l0)
+    pos = snap_wall_dps(mesh, mesh.centroids())
+    mask = np.full(mesh.N, INNER, dtype=np.int8)
+    mask[wall_cells(mesh)] = WALL_ID
+    bodies = cylinder_array(n, gap_cells / 64.0, count, side)
+    pb = Problem(mesh=mesh, pos=pos, mask=mask,
+                 bc_kind=default_bc_kind(neumann_ids=[b[0] for b in bodies]))
+    pb.rhs = ppe_source(pos / side, 0.0)
+    pb.meta["bodies"] = bodies
+    return pb
+
+
 def ppe_source(pos: np.ndarray, t: float):
     """Smooth synthetic interior source for the pressure Poisson equation,
     standing in for div(u*)/dt of a flow step: O(1) amplitude, a few
