@@ -48,7 +48,7 @@ typedef enum {
 
 enum { MCD_FP64 = 0, MCD_MIXED = 1 };          /* arithmetic of a solve */
 enum { MCD_DT_F64 = 0, MCD_DT_F32 = 1 };       /* element type of a vector */
-enum { MCD_W_GAUSS = 0, MCD_W_COS2 = 1 };      /* MLS weight function */
+enum { MCD_W_GAUSS = 0, MCD_W_COS2 = 1, MCD_W_LSMPS = 2 };   /* MLS weight function */
 enum { MCD_BC_DIRICHLET = 0, MCD_BC_NEUMANN = 1 };
 
 /* Uniform Cartesian background mesh of width l0 (Sec. 2.1-2.2).  dim is 2 or
@@ -67,7 +67,10 @@ typedef struct {
 
 /* weight_kind  MCD_W_COS2: w = cos^2(pi r / (2 r_e)) for r <= r_e, else 0
  *              (Eq. (17); the paper uses r_e = 2.5 l0);
- *              MCD_W_GAUSS: w = exp(-(r / r_e)^2), no cut-off.
+ *              MCD_W_GAUSS: w = exp(-(r / r_e)^2), no cut-off;
+ *              MCD_W_LSMPS: w = (1 - r / r_e)^2 for r < r_e, else 0 (the
+ *              least-squares MPS weight the paper pairs with its expanded
+ *              9x9 stencil, r_e = 3.5 l0, Sec. 4.1).
  * r_s          scaling length of X = (x - x_c) / r_s (Eq. (12); paper: l0).
  * precision    MCD_FP64 keeps FP64 rows only; MCD_MIXED also keeps an FP32
  *              copy of the rows for the inner solve of a mixed solve.
@@ -81,6 +84,10 @@ typedef struct {
     int precision;
     int want_derivs;
     uint8_t bc_kind[128];
+    int support;   /* support radius R: the fit uses the (2R+1)^dim cells
+                      around the DP's cell; 0 or 1: 3x3 (3x3x3), the MCD
+                      stencil; 4 (2D only): the expanded 9x9 stencil of
+                      Sec. 4.1; other values: MCD_EINVAL */
 } mcd_mls_params;
 
 typedef struct mcd_stencils mcd_stencils;  /* opaque; owns its device arrays */
@@ -88,7 +95,10 @@ typedef struct mcd_stencils mcd_stencils;  /* opaque; owns its device arrays */
 /* mcd_build_stencils - chi=1 quadratic MLS weights of every DP and the rows
  * of the pressure-Poisson system (Sec. 3.2, Eqs. (12)-(17); Sec. 3.3, Eq. (21)).
  *
- * For DP i the fit uses the DPs of the 3x3 (3x3x3) cells around cell i.
+ * For DP i the fit uses the DPs of the 3x3 (3x3x3) cells around cell i, or
+ * of the 9x9 cells with prm->support = 4 (2D; every slot-major array below
+ * then has S = 81 slots, slot s = (di + 4) + 9 (dj + 4); periodic axes need
+ * n >= 9).
  *  inner DP:     Lambda_c = inner and Dirichlet neighbours (values),
  *                Lambda^N_c = Neumann neighbours (normal-derivative data),
  *                basis (X, Y, X^2/2, XY, Y^2/2) (3D: 9 terms);
@@ -122,7 +132,7 @@ mcd_status mcd_stencils_check(const mcd_stencils *st, int64_t *first_bad_dp,
 void mcd_stencils_destroy(mcd_stencils *st);
 
 /* Device arrays of a handle, for parity tests and drivers (read-only).
- *  MCD_ARR_ROW64   float64 [S][N] PPE rows (slot-major, S = 3^dim)
+ *  MCD_ARR_ROW64   float64 [S][N] PPE rows (slot-major, S = (2 support + 1)^dim)
  *  MCD_ARR_ROW32   float32 [S][N] (MCD_MIXED only), difference form: slots
  *                  other than the centre C = S/2 hold the rounded FP64
  *                  weights, slot C the row sum (0 for MLS rows, whose sum
@@ -272,6 +282,7 @@ mcd_status mcd_flow_project(const mcd_stencils *pst, const double *P_dev,
  * the domain wall), centre c, radius, translational velocity and
  * acceleration (the paper's V_trans and dV_trans/dt, Eqs. (24)-(29); a
  * circle needs no rotation). */
+#define MCD_MAX_BODIES 64   /* bodies per call of the functions below */
 typedef struct {
     int id;
     double c[3];
@@ -281,21 +292,27 @@ typedef struct {
 } mcd_body;
 
 /* mcd_update_dps - one DP update for the body positions of the new step.
+ *  bodies[0 .. nbodies-1], 1 <= nbodies <= MCD_MAX_BODIES, distinct ids in
+ *  2..127, disjoint circles.  At every point the SDF psi is that of the body
+ *  with the smallest |psi| (Sec. 2.5; the first in the list on a tie),
+ *  psi = sqrt(dx*dx + dy*dy) - R with every operation rounded separately.
  *  1. mask_prev <- mask.
  *  2. Role reassignment (Sec. 2.4) of every non-wall cell whose centroid is
  *     within `band` of the boundary (|psi(centroid)| < band; band <= 0: every
- *     cell): count the cell vertices with psi >= 0, evaluated as
- *     dx*dx + dy*dy >= R*R with every operation rounded separately, and map
- *     0/1 -> void, 2/3 -> body id, 4 -> inner (Eq. (1)).  Cells with a face
- *     on the domain wall keep their mask.
+ *     cell): count the cell vertices with psi >= 0, evaluated for the
+ *     vertex's nearest body as dx*dx + dy*dy >= R*R with every operation
+ *     rounded separately, and map 0/1 -> void, 2/3 -> the id of the body
+ *     nearest the centroid, 4 -> inner (Eq. (1)).  Cells with a face on the
+ *     domain wall keep their mask.
  *  3. DPs of band cells that became void go to their cell centroid.
  *  4. n_relax Jacobi sweeps over the non-void band DPs: spring relaxation
  *     x* = x - kappa l0 sum_j (1 - r_ij/l0^SPG) x~_ij (Eqs. (5)-(8)), body DPs
- *     relocated onto the circle (Eq. (9)), inner DPs moved by beta psi d^ when
- *     alpha > 0 (Sec. 4.7, Eqs. (45)-(46), r_e = 5 l0), clamp into the cell.
+ *     relocated onto the circle whose id they carry (Eq. (9)), inner DPs
+ *     moved by beta psi d^ of the body nearest x* when alpha > 0 (Sec. 4.7,
+ *     Eqs. (45)-(46), r_e = 5 l0), clamp into the cell.
  * pos_dev (float64 [2][N]) and mask_dev (int8 [N]) are updated in place;
- * mask_prev_dev (int8 [N]) receives the old mask.  2D, nbodies = 1 only
- * (MCD_ENOTSUP otherwise).  Asynchronous. */
+ * mask_prev_dev (int8 [N]) receives the old mask.  2D only (MCD_ENOTSUP
+ * otherwise); a bad body list gives MCD_EINVAL.  Asynchronous. */
 mcd_status mcd_update_dps(const mcd_mesh *mesh, const mcd_body *bodies,
                           int nbodies, double *pos_dev, int8_t *mask_dev,
                           int8_t *mask_prev_dev, double kappa, int n_relax,
@@ -327,12 +344,21 @@ mcd_status mcd_update_dps_static(const mcd_mesh *mesh, const mcd_body *bodies,
                                  int8_t *mask_prev_dev, double kappa, int n_relax,
                                  double band, double alpha, mcd_stream_t stream);
 
-/* mcd_body_boundary - boundary data of the body's DPs (mask == id):
- *  normal_dev  float64 [2][N]: unit normal n = (x - c)/|x - c| (the analytic
- *              gradient of the circle SDF, Sec. 2.5); 0 at other DPs;
+/* mcd_bodies_boundary - boundary data of the DPs of every body (mask == id
+ * of bodies[b], 1 <= nbodies <= MCD_MAX_BODIES, distinct ids in 2..127):
+ *  normal_dev  float64 [2][N]: unit normal n = (x - c)/|x - c| of the DP's
+ *              body (the analytic gradient of the circle SDF, Sec. 2.5); 0
+ *              at every other DP;
  *  neumann_dev float64 [N] or NULL: the pressure Neumann datum of Eq. (23),
- *              dP/dn = -(dV/dt) . n with dV/dt = acc; 0 at other DPs.
- * Asynchronous. */
+ *              dP/dn = -(dV/dt) . n with dV/dt = that body's acc; 0 at every
+ *              other DP.
+ * 2D only.  Asynchronous. */
+mcd_status mcd_bodies_boundary(const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
+                               const double *pos_dev, const int8_t *mask_dev,
+                               double *normal_dev, double *neumann_dev,
+                               mcd_stream_t stream);
+
+/* mcd_body_boundary - mcd_bodies_boundary for the single body *body. */
 mcd_status mcd_body_boundary(const mcd_mesh *mesh, const mcd_body *body,
                              const double *pos_dev, const int8_t *mask_dev,
                              double *normal_dev, double *neumann_dev,

@@ -1060,7 +1060,13 @@ extern "C" mcd_status mcd_batch_create(const mcd_mesh *meshes, int count, const 
                                        mcd_batch **out) {
     MCD_CHECK_ARG(meshes && prm && out && count > 0, "NULL argument or empty batch");
     MCD_CHECK_ARG(prm->r_e > 0.0 && prm->r_s > 0.0, "r_e and r_s must be positive");
-    MCD_CHECK_ARG(prm->weight_kind == MCD_W_GAUSS || prm->weight_kind == MCD_W_COS2, "unknown weight_kind");
+    MCD_CHECK_ARG(prm->weight_kind == MCD_W_GAUSS || prm->weight_kind == MCD_W_COS2 ||
+                      prm->weight_kind == MCD_W_LSMPS,
+                  "unknown weight_kind");
+    if (prm->support != 0 && prm->support != 1) {
+        set_error("batched systems use the 3x3 stencil (support 1)");
+        return MCD_ENOTSUP;
+    }
     MCD_CHECK_ARG(prm->precision == MCD_FP64 || prm->precision == MCD_MIXED, "unknown precision");
     for (int b = 1; b < 128; ++b)
         if (prm->bc_kind[b] == MCD_BC_NEUMANN) {

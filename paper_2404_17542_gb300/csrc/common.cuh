@@ -55,6 +55,37 @@ struct Geo {
     int64_t N;
 };
 
+// Stencil shape of a solve: the (2R+1)^dim background cells around a DP's
+// own cell.  G = 2: 2D 3x3, G = 3: 3D 3x3x3 (the MCD stencils of Sec. 3.2),
+// G = 9: 2D 9x9 (the expanded stencil of Sec. 4.1).  Slot s holds the cell
+// at offset (s % W - R, (s / W) % W - R, s / W^2 - R), W = 2R + 1.
+template <int D, int RR> struct ShapeOf {
+    static constexpr int dim = D;
+    static constexpr int R = RR;
+    static constexpr int W = 2 * RR + 1;
+    static constexpr int S = (D == 2) ? W * W : W * W * W;
+    static constexpr int C = S / 2;
+};
+template <int G> struct Shape;
+template <> struct Shape<2> : ShapeOf<2, 1> {};
+template <> struct Shape<3> : ShapeOf<3, 1> {};
+template <> struct Shape<9> : ShapeOf<2, 4> {};
+
+template <int G>
+__host__ __device__ __forceinline__ void slot_offset(int s, int *o) {
+    using SH = Shape<G>;
+    o[0] = s % SH::W - SH::R;
+    o[1] = (s / SH::W) % SH::W - SH::R;
+    o[2] = (SH::dim == 3) ? s / (SH::W * SH::W) - SH::R : 0;
+}
+
+// Shape code of a (dim, support radius) pair; 0 if unsupported.
+inline int shape_code(int dim, int support) {
+    if (support == 1) return dim;
+    if (support == 4 && dim == 2) return 9;
+    return 0;
+}
+
 inline Geo make_geo(const mcd_mesh &m) {
     Geo g;
     g.dim = m.dim;
@@ -113,7 +144,9 @@ struct mcd_stencils {
     mcd_mesh mesh;
     mcd_mls_params prm;
     mcd::Geo geo;
-    int S;               // 9 or 27
+    int S;               // (2 support + 1)^dim: 9, 27 or 81
+    int support;         // support radius R: 1 (3x3, 3x3x3) or 4 (2D 9x9)
+    int shape;           // Shape<G> code G: 2, 3 or 9
     int nb;              // 5 or 9 derivative components
     int has_neumann;     // any bc_kind entry is Neumann
     double *row64;       // [S][N]

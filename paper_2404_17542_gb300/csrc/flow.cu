@@ -122,8 +122,8 @@ using namespace mcd;
 
 static mcd_status flow_check(const mcd_stencils *st) {
     MCD_CHECK_ARG(st, "NULL handle");
-    if (st->mesh.dim != 2) {
-        set_error("flow driver: 2D only");
+    if (st->mesh.dim != 2 || st->support != 1) {
+        set_error("flow driver: 2D 3x3 stencils only");
         return MCD_ENOTSUP;
     }
     MCD_CHECK_ARG(st->d64, "flow driver needs a stencil handle built with want_derivs = 1");

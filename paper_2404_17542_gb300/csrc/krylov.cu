@@ -117,14 +117,14 @@ void free_workspace(mcd_stencils *st) {
 // choice; a random shadow vector converged more slowly on these systems), and
 // r^.r and r^.r^ are reduced too so that rho = r^.r.  Neumann rows (ta.kind)
 // act as identity rows.
-template <int DIM, typename T, typename A>
+template <int G, typename T, typename A>
 __global__ void __launch_bounds__(256) bicg_ka(TileArgs ta, const T *__restrict__ row, const T *__restrict__ r,
                                                T *__restrict__ rhat, const T *__restrict__ p_old,
                                                const T *__restrict__ v_old, T *__restrict__ p_new,
                                                T *__restrict__ v_new, Scalars *sc, double *partials,
                                                int pstride, unsigned int *counter) {
-    using HD = HaloDims<DIM>;
-    using TL = Tile<DIM>;
+    using HD = HaloDims<G>;
+    using TL = Tile<G>;
     constexpr int S = HD::S;
     constexpr bool PREF = (S == 9);
     __shared__ T tile[HD::H];
@@ -134,19 +134,19 @@ __global__ void __launch_bounds__(256) bicg_ka(TileArgs ta, const T *__restrict_
     const Geo &g = ta.g;
     const int tid = threadIdx.x;
     int x0, y0, z0;
-    tile_origin<DIM>(ta, blockIdx.x, x0, y0, z0);
+    tile_origin<G>(ta, blockIdx.x, x0, y0, z0);
     int64_t k[TL::R];
     int lx[TL::R], ly[TL::R], lz[TL::R];
     T w[TL::R][PREF ? S : 1];
     T rh[TL::R];
 #pragma unroll
     for (int q = 0; q < TL::R; ++q) {
-        k[q] = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+        k[q] = tile_dp<G>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
         if (PREF) load_row<S, T>(row, g.N, k[q], w[q]);
         rh[q] = (!restart && k[q] >= 0) ? rhat[k[q]] : (T)0;
     }
     for (int h = tid; h < HD::H; h += 256) {
-        const int64_t j = halo_index<DIM>(g, h, x0, y0, z0);
+        const int64_t j = halo_index<G>(g, h, x0, y0, z0);
         const T rj = r[j];
         tile[h] = restart ? rj : rj + beta * (p_old[j] - omega * v_old[j]);
     }
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256) bicg_ka(TileArgs ta, const T *__restrict_
 #pragma unroll
     for (int q = 0; q < TL::R; ++q) {
         if (k[q] < 0) continue;
-        const T pk = tile[tile_centre<DIM>(lx[q], ly[q], lz[q])];
+        const T pk = tile[tile_centre<G>(lx[q], ly[q], lz[q])];
         p_new[k[q]] = pk;
         T rq = rh[q];
         if (restart) {
@@ -168,11 +168,15 @@ __global__ void __launch_bounds__(256) bicg_ka(TileArgs ta, const T *__restrict_
         if (ta.kind && ta.kind[k[q]] == KIND_NEUMANN) {
             vk = pk;
         } else if (PREF) {
-            vk = stencil_apply<DIM, T>(w[q], tile, lx[q], ly[q], lz[q]);
+            vk = stencil_apply<G, T>(w[q], tile, lx[q], ly[q], lz[q]);
         } else {
-            T wl[S];
-            load_row<S, T>(row, g.N, k[q], wl);
-            vk = stencil_apply<DIM, T>(wl, tile, lx[q], ly[q], lz[q]);
+            if constexpr (S > 27) {
+                vk = stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
+            } else {
+                T wl[S];
+                load_row<S, T>(row, g.N, k[q], wl);
+                vk = stencil_apply<G, T>(wl, tile, lx[q], ly[q], lz[q]);
+            }
         }
         v_new[k[q]] = vk;
         dot[0].add(rq, vk);
@@ -194,13 +198,13 @@ __global__ void __launch_bounds__(256) bicg_ka(TileArgs ta, const T *__restrict_
 }
 
 // ---- KB: s = r - alpha v; t = A s; partials t.s, t.t, s.s ------------------
-template <int DIM, typename T, typename A>
+template <int G, typename T, typename A>
 __global__ void __launch_bounds__(256) bicg_kb(TileArgs ta, const T *__restrict__ row, const T *__restrict__ r,
                                                const T *__restrict__ v, T *__restrict__ s_out,
                                                T *__restrict__ t_out, Scalars *sc, double *partials,
                                                int pstride, unsigned int *counter) {
-    using HD = HaloDims<DIM>;
-    using TL = Tile<DIM>;
+    using HD = HaloDims<G>;
+    using TL = Tile<G>;
     constexpr int S = HD::S;
     constexpr bool PREF = (S == 9);
     __shared__ T tile[HD::H];
@@ -209,17 +213,17 @@ __global__ void __launch_bounds__(256) bicg_kb(TileArgs ta, const T *__restrict_
     const Geo &g = ta.g;
     const int tid = threadIdx.x;
     int x0, y0, z0;
-    tile_origin<DIM>(ta, blockIdx.x, x0, y0, z0);
+    tile_origin<G>(ta, blockIdx.x, x0, y0, z0);
     int64_t k[TL::R];
     int lx[TL::R], ly[TL::R], lz[TL::R];
     T w[TL::R][PREF ? S : 1];
 #pragma unroll
     for (int q = 0; q < TL::R; ++q) {
-        k[q] = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+        k[q] = tile_dp<G>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
         if (PREF) load_row<S, T>(row, g.N, k[q], w[q]);
     }
     for (int h = tid; h < HD::H; h += 256) {
-        const int64_t j = halo_index<DIM>(g, h, x0, y0, z0);
+        const int64_t j = halo_index<G>(g, h, x0, y0, z0);
         tile[h] = r[j] - alpha * v[j];
     }
     __syncthreads();
@@ -227,17 +231,21 @@ __global__ void __launch_bounds__(256) bicg_kb(TileArgs ta, const T *__restrict_
 #pragma unroll
     for (int q = 0; q < TL::R; ++q) {
         if (k[q] < 0) continue;
-        const T sk = tile[tile_centre<DIM>(lx[q], ly[q], lz[q])];
+        const T sk = tile[tile_centre<G>(lx[q], ly[q], lz[q])];
         s_out[k[q]] = sk;
         T tk;
         if (ta.kind && ta.kind[k[q]] == KIND_NEUMANN) {
             tk = sk;
         } else if (PREF) {
-            tk = stencil_apply<DIM, T>(w[q], tile, lx[q], ly[q], lz[q]);
+            tk = stencil_apply<G, T>(w[q], tile, lx[q], ly[q], lz[q]);
         } else {
-            T wl[S];
-            load_row<S, T>(row, g.N, k[q], wl);
-            tk = stencil_apply<DIM, T>(wl, tile, lx[q], ly[q], lz[q]);
+            if constexpr (S > 27) {
+                tk = stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
+            } else {
+                T wl[S];
+                load_row<S, T>(row, g.N, k[q], wl);
+                tk = stencil_apply<G, T>(wl, tile, lx[q], ly[q], lz[q]);
+            }
         }
         t_out[k[q]] = tk;
         dot[0].add(tk, sk);
@@ -332,13 +340,13 @@ __global__ void __launch_bounds__(256) bicg_kc(int64_t N, T *__restrict__ x, T *
 // ---- FP64 residual r = b - A x (1D; neighbours through L1) ---------------
 // Its last block records ||r||^2, ||b||^2 and primes the Krylov scalars for a
 // (re)start from this residual with tolerance tol2 = (tol ||b||)^2.
-template <int DIM>
+template <int G>
 __global__ void __launch_bounds__(256) residual64(Geo g, const double *__restrict__ row, const double *__restrict__ b,
                                                   const double *__restrict__ x, double *__restrict__ r,
                                                   Scalars *sc, double *partials, int pstride,
                                                   unsigned int *counter, double tol,
                                                   const int8_t *__restrict__ excl) {
-    constexpr int S = (DIM == 2) ? 9 : 27;
+    constexpr int S = Shape<G>::S;
     const int64_t N = g.N;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double dot[2] = {0.0, 0.0};
@@ -346,15 +354,17 @@ __global__ void __launch_bounds__(256) residual64(Geo g, const double *__restric
         int c[3] = {0, 0, 0};
         c[0] = (int)(k % g.n[0]);
         const int64_t rest = k / g.n[0];
-        if (DIM == 2) c[1] = (int)rest; else { c[1] = (int)(rest % g.n[1]); c[2] = (int)(rest / g.n[1]); }
+        if (Shape<G>::dim == 2) c[1] = (int)rest; else { c[1] = (int)(rest % g.n[1]); c[2] = (int)(rest / g.n[1]); }
         double acc = 0.0;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            const int ox = s % 3 - 1, oy = (s / 3) % 3 - 1, oz = s / 9 - 1;
+            int o[3];
+            slot_offset<G>(s, o);
+            const int ox = o[0], oy = o[1], oz = o[2];
             const int gx = wrap_clamp(c[0] + ox, g.n[0], g.per[0]);
             const int gy = wrap_clamp(c[1] + oy, g.n[1], g.per[1]);
             int64_t j = (int64_t)gx + (int64_t)g.n[0] * gy;
-            if (DIM == 3) {
+            if (Shape<G>::dim == 3) {
                 const int gz = wrap_clamp(c[2] + oz, g.n[2], g.per[2]);
                 j = (int64_t)gx + (int64_t)g.n[0] * ((int64_t)gy + (int64_t)g.n[1] * gz);
             }
@@ -392,7 +402,7 @@ __global__ void __launch_bounds__(256) residual64(Geo g, const double *__restric
 // direction p is kept; rho = r^.r32 and beta are recomputed from the new
 // residual.  `prime` (or a preceding ||s|| stop) restarts the recurrence
 // instead (r^ = r, p = r).  Stops (done = 1) when ||r64|| <= tol ||b||.
-template <int DIM>
+template <int G>
 __global__ void __launch_bounds__(256) reliable_residual(Geo g, const double *__restrict__ row,
                                                          const double *__restrict__ b,
                                                          const double *__restrict__ x,
@@ -401,7 +411,7 @@ __global__ void __launch_bounds__(256) reliable_residual(Geo g, const double *__
                                                          double *partials, int pstride,
                                                          unsigned int *counter, double tol, int prime,
                                                          const int8_t *__restrict__ excl) {
-    constexpr int S = (DIM == 2) ? 9 : 27;
+    constexpr int S = Shape<G>::S;
     const int64_t N = g.N;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double dot[4] = {0.0, 0.0, 0.0, 0.0};
@@ -409,15 +419,17 @@ __global__ void __launch_bounds__(256) reliable_residual(Geo g, const double *__
         int c[3] = {0, 0, 0};
         c[0] = (int)(k % g.n[0]);
         const int64_t rest = k / g.n[0];
-        if (DIM == 2) c[1] = (int)rest; else { c[1] = (int)(rest % g.n[1]); c[2] = (int)(rest / g.n[1]); }
+        if (Shape<G>::dim == 2) c[1] = (int)rest; else { c[1] = (int)(rest % g.n[1]); c[2] = (int)(rest / g.n[1]); }
         double acc = 0.0;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            const int ox = s % 3 - 1, oy = (s / 3) % 3 - 1, oz = s / 9 - 1;
+            int o[3];
+            slot_offset<G>(s, o);
+            const int ox = o[0], oy = o[1], oz = o[2];
             const int gx = wrap_clamp(c[0] + ox, g.n[0], g.per[0]);
             const int gy = wrap_clamp(c[1] + oy, g.n[1], g.per[1]);
             int64_t j = (int64_t)gx + (int64_t)g.n[0] * gy;
-            if (DIM == 3) {
+            if (Shape<G>::dim == 3) {
                 const int gz = wrap_clamp(c[2] + oz, g.n[2], g.per[2]);
                 j = (int64_t)gx + (int64_t)g.n[0] * ((int64_t)gy + (int64_t)g.n[1] * gz);
             }
@@ -583,16 +595,16 @@ static int occupancy(K kernel) {
 
 // Launch `count` Bi-CGSTAB iterations (3 kernels each); parity selects the
 // p / v ping-pong buffers and is advanced.
-template <int DIM, typename T, typename A>
+template <int G, typename T, typename A>
 static mcd_status launch_iters(const mcd_stencils *st, const T *row, Vecs<T> &vv, int &parity,
                                int count, double eps_breakdown, cudaStream_t stream) {
     Workspace *w = st->ws;
     const Geo &g = st->geo;
     TileArgs ta;
     ta.g = g;
-    ta.bx = (g.n[0] + Tile<DIM>::X - 1) / Tile<DIM>::X;
-    ta.by = (g.n[1] + Tile<DIM>::Y - 1) / Tile<DIM>::Y;
-    ta.bz = (DIM == 3) ? (g.n[2] + Tile<DIM>::Z - 1) / Tile<DIM>::Z : 1;
+    ta.bx = (g.n[0] + Tile<G>::X - 1) / Tile<G>::X;
+    ta.by = (g.n[1] + Tile<G>::Y - 1) / Tile<G>::Y;
+    ta.bz = (Shape<G>::dim == 3) ? (g.n[2] + Tile<G>::Z - 1) / Tile<G>::Z : 1;
     ta.ntiles = ta.bx * ta.by * ta.bz;
     ta.kind = st->has_neumann ? st->kind : nullptr;
     // one block per tile for KA / KB; KC threads take KC_VEC elements each
@@ -601,9 +613,9 @@ static mcd_status launch_iters(const mcd_stencils *st, const T *row, Vecs<T> &vv
     const int grid_c = (int)std::max<int64_t>(1, (g.N + 256 * KC_VEC - 1) / (256 * KC_VEC));
     for (int it = 0; it < count; ++it) {
         const int a = parity, b = parity ^ 1;
-        MCD_KLAUNCH(MCD_K_BICG_A, stream, bicg_ka<DIM, T, A><<<grid_a, 256, 0, stream>>>(ta, row, vv.r, vv.rh, vv.p[a], vv.v[a], vv.p[b],
+        MCD_KLAUNCH(MCD_K_BICG_A, stream, bicg_ka<G, T, A><<<grid_a, 256, 0, stream>>>(ta, row, vv.r, vv.rh, vv.p[a], vv.v[a], vv.p[b],
                                                         vv.v[b], w->sc, w->partials, w->pstride, w->counter));
-        MCD_KLAUNCH(MCD_K_BICG_B, stream, bicg_kb<DIM, T, A><<<grid_b, 256, 0, stream>>>(ta, row, vv.r, vv.v[b], vv.s, vv.t, w->sc,
+        MCD_KLAUNCH(MCD_K_BICG_B, stream, bicg_kb<G, T, A><<<grid_b, 256, 0, stream>>>(ta, row, vv.r, vv.v[b], vv.s, vv.t, w->sc,
                                                         w->partials, w->pstride, w->counter));
         MCD_KLAUNCH(MCD_K_BICG_C, stream, bicg_kc<T, A><<<grid_c, 256, 0, stream>>>(g.N, vv.x, vv.r, vv.rh, vv.p[b], vv.s, vv.t, w->sc,
                                                     w->partials, w->pstride, w->counter, eps_breakdown));
@@ -621,7 +633,7 @@ static mcd_status read_scalars(Workspace *w, cudaStream_t stream) {
 
 // Run Bi-CGSTAB until the device flags `done`.  The chunk of iterations
 // between host checks grows geometrically up to check_every.
-template <int DIM, typename T, typename A>
+template <int G, typename T, typename A>
 static mcd_status run_krylov(const mcd_stencils *st, const T *row, Vecs<T> &vv, int check_every,
                              double eps_breakdown, int max_launch, cudaStream_t stream) {
     Workspace *w = st->ws;
@@ -629,7 +641,7 @@ static mcd_status run_krylov(const mcd_stencils *st, const T *row, Vecs<T> &vv, 
     int chunk = 4;
     int launched = 0;
     for (;;) {
-        mcd_status s = launch_iters<DIM, T, A>(st, row, vv, parity, chunk, eps_breakdown, stream);
+        mcd_status s = launch_iters<G, T, A>(st, row, vv, parity, chunk, eps_breakdown, stream);
         if (s != MCD_OK) return s;
         launched += chunk;
         s = read_scalars(w, stream);
@@ -646,12 +658,12 @@ static mcd_status run_krylov(const mcd_stencils *st, const T *row, Vecs<T> &vv, 
 
 // FP64 residual b - A x; with `interior` set the Neumann rows are left out
 // (their residual reads 0), which is the residual of the interior block.
-template <int DIM>
+template <int G>
 static mcd_status residual(const mcd_stencils *st, const double *x, double tol, int interior,
                            cudaStream_t stream) {
     Workspace *w = st->ws;
     const int8_t *excl = (interior && st->has_neumann) ? st->kind : nullptr;
-    MCD_KLAUNCH(MCD_K_RESIDUAL, stream, residual64<DIM><<<w->nblk1, 256, 0, stream>>>(st->geo, st->row64, w->b, x, w->r64, w->sc, w->partials,
+    MCD_KLAUNCH(MCD_K_RESIDUAL, stream, residual64<G><<<w->nblk1, 256, 0, stream>>>(st->geo, st->row64, w->b, x, w->r64, w->sc, w->partials,
                                                   w->pstride, w->counter, tol, excl));
     MCD_LAUNCH_CHECK();
     return MCD_OK;
@@ -662,25 +674,27 @@ static mcd_status residual(const mcd_stencils *st, const double *x, double tol, 
 // diagonally dominant (its rows are scaled to diagonal -1/r_s^2 and couple to
 // other Neumann DPs only through nearly tangential neighbours), so a few
 // sweeps solve it to rounding once the interior values are final.
-template <int DIM>
+template <int G>
 __global__ void neumann_delta(Geo g, const double *__restrict__ row, const int8_t *__restrict__ kind,
                               const double *__restrict__ b, const double *__restrict__ x,
                               double *__restrict__ delta) {
-    constexpr int S = (DIM == 2) ? 9 : 27;
+    constexpr int S = Shape<G>::S;
     const int64_t N = g.N;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N || kind[k] != KIND_NEUMANN) return;
     int c[3] = {0, 0, 0};
     c[0] = (int)(k % g.n[0]);
     const int64_t rest = k / g.n[0];
-    if (DIM == 2) c[1] = (int)rest; else { c[1] = (int)(rest % g.n[1]); c[2] = (int)(rest / g.n[1]); }
+    if (Shape<G>::dim == 2) c[1] = (int)rest; else { c[1] = (int)(rest % g.n[1]); c[2] = (int)(rest / g.n[1]); }
     double acc = 0.0;
     for (int s = 0; s < S; ++s) {
-        const int gx = wrap_clamp(c[0] + s % 3 - 1, g.n[0], g.per[0]);
-        const int gy = wrap_clamp(c[1] + (s / 3) % 3 - 1, g.n[1], g.per[1]);
+        int o[3];
+        slot_offset<G>(s, o);
+        const int gx = wrap_clamp(c[0] + o[0], g.n[0], g.per[0]);
+        const int gy = wrap_clamp(c[1] + o[1], g.n[1], g.per[1]);
         int64_t j = (int64_t)gx + (int64_t)g.n[0] * gy;
-        if (DIM == 3) {
-            const int gz = wrap_clamp(c[2] + s / 9 - 1, g.n[2], g.per[2]);
+        if (Shape<G>::dim == 3) {
+            const int gz = wrap_clamp(c[2] + o[2], g.n[2], g.per[2]);
             j = (int64_t)gx + (int64_t)g.n[0] * ((int64_t)gy + (int64_t)g.n[1] * gz);
         }
         acc += row[(int64_t)s * N + k] * x[j];
@@ -694,12 +708,12 @@ __global__ void neumann_apply(int64_t N, const int8_t *__restrict__ kind, const 
     if (k < N && kind[k] == KIND_NEUMANN) x[k] += delta[k];
 }
 
-template <int DIM>
+template <int G>
 static mcd_status neumann_sweeps(const mcd_stencils *st, double *x, int sweeps, cudaStream_t stream) {
     Workspace *w = st->ws;
     const int64_t N = st->geo.N;
     for (int i = 0; i < sweeps; ++i) {
-        MCD_KLAUNCH(MCD_K_OTHER, stream, neumann_delta<DIM><<<w->nblk1, 256, 0, stream>>>(st->geo, st->row64, st->kind,
+        MCD_KLAUNCH(MCD_K_OTHER, stream, neumann_delta<G><<<w->nblk1, 256, 0, stream>>>(st->geo, st->row64, st->kind,
                                                                                          w->b, x, w->r64));
         MCD_KLAUNCH(MCD_K_OTHER, stream, neumann_apply<<<w->nblk1, 256, 0, stream>>>(N, st->kind, w->r64, x));
     }
@@ -707,14 +721,14 @@ static mcd_status neumann_sweeps(const mcd_stencils *st, double *x, int sweeps, 
     return MCD_OK;
 }
 
-template <int DIM>
+template <int G>
 static mcd_status reliable_update(const mcd_stencils *st, double *x, double tol, int prime,
                                   cudaStream_t stream) {
     Workspace *w = st->ws;
     const int64_t N = st->geo.N;
     MCD_KLAUNCH(MCD_K_OTHER, stream, fold_correction<<<w->nblk1, 256, 0, stream>>>(N, x, w->fd));
     MCD_KLAUNCH(MCD_K_RESIDUAL, stream,
-                reliable_residual<DIM><<<w->nblk1, 256, 0, stream>>>(st->geo, st->row64, w->b, x, w->frh, w->fr,
+                reliable_residual<G><<<w->nblk1, 256, 0, stream>>>(st->geo, st->row64, w->b, x, w->frh, w->fr,
                                                                      w->sc, w->partials, w->pstride, w->counter,
                                                                      tol, prime,
                                                                      st->has_neumann ? st->kind : nullptr));
@@ -729,7 +743,7 @@ static mcd_status reliable_update(const mcd_stencils *st, double *x, double tol,
 // x += d32 and the FP64 residual b - A64 x replaces the FP32 one.  The solve
 // ends when that FP64 residual meets tol.  `updates` counts the reliable
 // updates after the first.
-template <int DIM>
+template <int G>
 static mcd_status run_mixed(const mcd_stencils *st, double *x, const mcd_solve_params *prm,
                             int check_every, int max_launch, int &updates, mcd_status &result,
                             cudaStream_t stream) {
@@ -737,7 +751,7 @@ static mcd_status run_mixed(const mcd_stencils *st, double *x, const mcd_solve_p
     const int64_t N = st->geo.N;
     const double update = prm->inner_tol;
     MCD_CUDA_TRY(cudaMemsetAsync(w->fd, 0, N * sizeof(float), stream));
-    mcd_status s = reliable_update<DIM>(st, x, prm->tol, 1, stream);
+    mcd_status s = reliable_update<G>(st, x, prm->tol, 1, stream);
     if (s != MCD_OK) return s;
     updates = 0;
     if (w->h_sc->done == 4) { result = MCD_ENONFINITE; return MCD_OK; }
@@ -747,7 +761,7 @@ static mcd_status run_mixed(const mcd_stencils *st, double *x, const mcd_solve_p
     int parity = 0, chunk = 4, launched = 0;
     for (;;) {
         // compensated dots keep rho meaningful far below FP32 epsilon
-        s = launch_iters<DIM, float, float>(st, st->row32, vv, parity, chunk, 1e-12, stream);
+        s = launch_iters<G, float, float>(st, st->row32, vv, parity, chunk, 1e-12, stream);
         if (s != MCD_OK) return s;
         launched += chunk;
         s = read_scalars(w, stream);
@@ -758,7 +772,7 @@ static mcd_status run_mixed(const mcd_stencils *st, double *x, const mcd_solve_p
         const bool want = h.done == 1 || h.done == 2 || h.s_conv || h.rr <= update * update * rr_last;
         if (want) {
             const int was_max = (h.done == 2);
-            s = reliable_update<DIM>(st, x, prm->tol,
+            s = reliable_update<G>(st, x, prm->tol,
                                      prm->update_restart == 1 ? 1 : (prm->update_restart == 2 ? 2 : 0), stream);
             if (s != MCD_OK) return s;
             ++updates;
@@ -915,11 +929,11 @@ __device__ bool grid_reduce(const PArgs &a, unsigned &epoch, Acc (&d)[NV], Last 
 // Phase A over the block's tiles: p = r + beta (p_old - omega v_old) (or
 // p = r on a restart, with r^ = r) on tile + halo, v = A p.
 // Dots: r^.v, and on a restart r^.r and r^.r^.
-template <int DIM, typename T>
+template <int G, typename T>
 __device__ void phase_a(const PArgs &a, T *tile, const T *p_old, const T *v_old, T *p_new, T *v_new,
                         T beta, T omega, int restart, DotAcc<T> (&dot)[3]) {
-    using HD = HaloDims<DIM>;
-    using TL = Tile<DIM>;
+    using HD = HaloDims<G>;
+    using TL = Tile<G>;
     constexpr int S = HD::S;
     constexpr bool PREF = (S == 9);
     constexpr int HN = (HD::H + 255) / 256;
@@ -931,14 +945,14 @@ __device__ void phase_a(const PArgs &a, T *tile, const T *p_old, const T *v_old,
     const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
     for (int tl = tb; tl < te; ++tl) {
         int x0, y0, z0;
-        tile_origin<DIM>(a.ta, tl, x0, y0, z0);
+        tile_origin<G>(a.ta, tl, x0, y0, z0);
         int64_t k[TL::R];
         int lx[TL::R], ly[TL::R], lz[TL::R];
         T w[TL::R][PREF ? S : 1];
         T rh[TL::R];
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
-            k[q] = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+            k[q] = tile_dp<G>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
             if (PREF) load_row<S, T>(row, g.N, k[q], w[q]);
             rh[q] = (!restart && k[q] >= 0) ? __ldcg(rhat + k[q]) : (T)0;
         }
@@ -949,7 +963,7 @@ __device__ void phase_a(const PArgs &a, T *tile, const T *p_old, const T *v_old,
             const int h = tid + u * 256;
             hr[u] = hp[u] = hv[u] = (T)0;
             if (h < HD::H) {
-                const int64_t j = halo_index<DIM>(g, h, x0, y0, z0);
+                const int64_t j = halo_index<G>(g, h, x0, y0, z0);
                 hr[u] = __ldcg(r + j);
                 if (!restart) {
                     hp[u] = __ldcg(p_old + j);
@@ -966,7 +980,7 @@ __device__ void phase_a(const PArgs &a, T *tile, const T *p_old, const T *v_old,
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
             if (k[q] < 0) continue;
-            const T pk = tile[tile_centre<DIM>(lx[q], ly[q], lz[q])];
+            const T pk = tile[tile_centre<G>(lx[q], ly[q], lz[q])];
             p_new[k[q]] = pk;
             T rq = rh[q];
             if (restart) {
@@ -979,11 +993,15 @@ __device__ void phase_a(const PArgs &a, T *tile, const T *p_old, const T *v_old,
             if (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN) {
                 vk = pk;
             } else if (PREF) {
-                vk = stencil_apply<DIM, T>(w[q], tile, lx[q], ly[q], lz[q]);
+                vk = stencil_apply<G, T>(w[q], tile, lx[q], ly[q], lz[q]);
             } else {
-                T wl[S];
-                load_row<S, T>(row, g.N, k[q], wl);
-                vk = stencil_apply<DIM, T>(wl, tile, lx[q], ly[q], lz[q]);
+                if constexpr (S > 27) {
+                    vk = stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
+                } else {
+                    T wl[S];
+                    load_row<S, T>(row, g.N, k[q], wl);
+                    vk = stencil_apply<G, T>(wl, tile, lx[q], ly[q], lz[q]);
+                }
             }
             v_new[k[q]] = vk;
             dot[0].add(rq, vk);
@@ -993,10 +1011,10 @@ __device__ void phase_a(const PArgs &a, T *tile, const T *p_old, const T *v_old,
 }
 
 // Phase B: s = r - alpha v (tile + halo), t = A s; dots t.s, t.t, s.s.
-template <int DIM, typename T>
+template <int G, typename T>
 __device__ void phase_b(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T> (&dot)[3]) {
-    using HD = HaloDims<DIM>;
-    using TL = Tile<DIM>;
+    using HD = HaloDims<G>;
+    using TL = Tile<G>;
     constexpr int S = HD::S;
     constexpr bool PREF = (S == 9);
     constexpr int HN = (HD::H + 255) / 256;
@@ -1009,13 +1027,13 @@ __device__ void phase_b(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T> 
     const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
     for (int tl = tb; tl < te; ++tl) {
         int x0, y0, z0;
-        tile_origin<DIM>(a.ta, tl, x0, y0, z0);
+        tile_origin<G>(a.ta, tl, x0, y0, z0);
         int64_t k[TL::R];
         int lx[TL::R], ly[TL::R], lz[TL::R];
         T w[TL::R][PREF ? S : 1];
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
-            k[q] = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+            k[q] = tile_dp<G>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
             if (PREF) load_row<S, T>(row, g.N, k[q], w[q]);
         }
         T hr[HN], hv[HN];
@@ -1024,7 +1042,7 @@ __device__ void phase_b(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T> 
             const int h = tid + u * 256;
             hr[u] = hv[u] = (T)0;
             if (h < HD::H) {
-                const int64_t j = halo_index<DIM>(g, h, x0, y0, z0);
+                const int64_t j = halo_index<G>(g, h, x0, y0, z0);
                 hr[u] = __ldcg(r + j);
                 hv[u] = __ldcg(v + j);
             }
@@ -1038,17 +1056,21 @@ __device__ void phase_b(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T> 
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
             if (k[q] < 0) continue;
-            const T sk = tile[tile_centre<DIM>(lx[q], ly[q], lz[q])];
+            const T sk = tile[tile_centre<G>(lx[q], ly[q], lz[q])];
             s_out[k[q]] = sk;
             T tk;
             if (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN) {
                 tk = sk;
             } else if (PREF) {
-                tk = stencil_apply<DIM, T>(w[q], tile, lx[q], ly[q], lz[q]);
+                tk = stencil_apply<G, T>(w[q], tile, lx[q], ly[q], lz[q]);
             } else {
-                T wl[S];
-                load_row<S, T>(row, g.N, k[q], wl);
-                tk = stencil_apply<DIM, T>(wl, tile, lx[q], ly[q], lz[q]);
+                if constexpr (S > 27) {
+                    tk = stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
+                } else {
+                    T wl[S];
+                    load_row<S, T>(row, g.N, k[q], wl);
+                    tk = stencil_apply<G, T>(wl, tile, lx[q], ly[q], lz[q]);
+                }
             }
             t_out[k[q]] = tk;
             dot[0].add(tk, sk);
@@ -1061,9 +1083,9 @@ __device__ void phase_b(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T> 
 
 // Phase C (the block's own DPs): x += alpha p + omega s, r = s - omega t (or
 // x += alpha p, r = s after an ||s|| stop); dots r^.r, r.r.
-template <int DIM, typename T>
+template <int G, typename T>
 __device__ void phase_c(const PArgs &a, const T *p, T alpha, T omega, int sconv, DotAcc<T> (&dot)[2]) {
-    using TL = Tile<DIM>;
+    using TL = Tile<G>;
     const Geo &g = a.ta.g;
     T *x = (T *)a.x;
     T *r = (T *)a.r;
@@ -1074,13 +1096,13 @@ __device__ void phase_c(const PArgs &a, const T *p, T alpha, T omega, int sconv,
     const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
     for (int tl = tb; tl < te; ++tl) {
         int x0, y0, z0;
-        tile_origin<DIM>(a.ta, tl, x0, y0, z0);
+        tile_origin<G>(a.ta, tl, x0, y0, z0);
         int64_t k[TL::R];
         T xv[TL::R], pv[TL::R], sv[TL::R], tv[TL::R], hv[TL::R];
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
             int lx, ly, lz;
-            k[q] = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx, ly, lz);
+            k[q] = tile_dp<G>(g, tid, q, x0, y0, z0, lx, ly, lz);
             const bool in = k[q] >= 0;
             xv[q] = in ? __ldcg(x + k[q]) : (T)0;
             pv[q] = in ? __ldcg(p + k[q]) : (T)0;
@@ -1107,20 +1129,20 @@ __device__ void phase_c(const PArgs &a, const T *p, T alpha, T omega, int sconv,
 }
 
 // Fold (MIXED): x64 += x; x = 0 over the block's own DPs.
-template <int DIM, typename T>
+template <int G, typename T>
 __device__ void phase_fold(const PArgs &a) {
-    using TL = Tile<DIM>;
+    using TL = Tile<G>;
     const Geo &g = a.ta.g;
     T *x = (T *)a.x;
     const int tid = threadIdx.x;
     const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
     for (int tl = tb; tl < te; ++tl) {
         int x0, y0, z0;
-        tile_origin<DIM>(a.ta, tl, x0, y0, z0);
+        tile_origin<G>(a.ta, tl, x0, y0, z0);
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
             int lx, ly, lz;
-            const int64_t k = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx, ly, lz);
+            const int64_t k = tile_dp<G>(g, tid, q, x0, y0, z0, lx, ly, lz);
             if (k < 0) continue;
             a.x64[k] += (double)__ldcg(x + k);
             x[k] = (T)0;
@@ -1131,10 +1153,10 @@ __device__ void phase_fold(const PArgs &a) {
 // True residual r64 = b - A64 x64 (FP64 matrix form) of the block's DPs,
 // stored in the recursion's precision; Neumann rows read 0 (interior block).
 // Dots ||r64||^2, ||b||^2, r^.r, r.r.
-template <int DIM, typename T>
+template <int G, typename T>
 __device__ void phase_true_residual(const PArgs &a, DotAcc<double> (&d64)[2], DotAcc<T> (&dt)[2]) {
-    using TL = Tile<DIM>;
-    constexpr int S = (DIM == 2) ? 9 : 27;
+    using TL = Tile<G>;
+    constexpr int S = Shape<G>::S;
     const Geo &g = a.ta.g;
     T *r = (T *)a.r;
     const T *rhat = (const T *)a.rh;
@@ -1142,21 +1164,23 @@ __device__ void phase_true_residual(const PArgs &a, DotAcc<double> (&d64)[2], Do
     const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
     for (int tl = tb; tl < te; ++tl) {
         int x0, y0, z0;
-        tile_origin<DIM>(a.ta, tl, x0, y0, z0);
+        tile_origin<G>(a.ta, tl, x0, y0, z0);
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
             int lx, ly, lz;
-            const int64_t k = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx, ly, lz);
+            const int64_t k = tile_dp<G>(g, tid, q, x0, y0, z0, lx, ly, lz);
             if (k < 0) continue;
             const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
             double acc = 0.0;
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                const int jx = wrap_clamp(gx + s % 3 - 1, g.n[0], g.per[0]);
-                const int jy = wrap_clamp(gy + (s / 3) % 3 - 1, g.n[1], g.per[1]);
+                int o[3];
+                slot_offset<G>(s, o);
+                const int jx = wrap_clamp(gx + o[0], g.n[0], g.per[0]);
+                const int jy = wrap_clamp(gy + o[1], g.n[1], g.per[1]);
                 int64_t j = (int64_t)jx + (int64_t)g.n[0] * jy;
-                if (DIM == 3) {
-                    const int jz = wrap_clamp(gz + s / 9 - 1, g.n[2], g.per[2]);
+                if (Shape<G>::dim == 3) {
+                    const int jz = wrap_clamp(gz + o[2], g.n[2], g.per[2]);
                     j = (int64_t)jx + (int64_t)g.n[0] * ((int64_t)jy + (int64_t)g.n[1] * jz);
                 }
                 acc += __ldg(a.row64 + (int64_t)s * g.N + k) * __ldcg(a.x64 + j);
@@ -1180,9 +1204,9 @@ __device__ void phase_true_residual(const PArgs &a, DotAcc<double> (&d64)[2], Do
 // sqrt(update2) since the last update.  update_mode 1 restarts the recursion
 // after each update; update_mode 2 replaces r only and keeps rho and beta
 // (the reliable update of Sleijpen and van der Vorst, 1996).
-template <int DIM, typename T>
+template <int G, typename T>
 __global__ void __launch_bounds__(256) bicg_persistent(PArgs a) {
-    using HD = HaloDims<DIM>;
+    using HD = HaloDims<G>;
     __shared__ T tile[HD::H];
     Scalars *sc = a.sc;
     int iters = 0;
@@ -1192,13 +1216,13 @@ __global__ void __launch_bounds__(256) bicg_persistent(PArgs a) {
         if (vload(&sc->pending)) {
             // ---- true residual (reliable) update ----------------------------
             if (a.mixed) {
-                phase_fold<DIM, T>(a);
+                phase_fold<G, T>(a);
                 DotAcc<double> none[1];
                 if (!grid_reduce<1>(a, epoch, none, [&](double *) {})) return;
             }
             DotAcc<double> d64[2];
             DotAcc<T> dt[2];
-            phase_true_residual<DIM, T>(a, d64, dt);
+            phase_true_residual<G, T>(a, d64, dt);
             DotAcc<double> all[4];
             all[0].v = d64[0].v;
             all[1].v = d64[1].v;
@@ -1247,7 +1271,7 @@ __global__ void __launch_bounds__(256) bicg_persistent(PArgs a) {
             if constexpr (sizeof(T) == 4) { beta = vload(&sc->beta_f); omega = vload(&sc->omega_f); }
             else { beta = (T)vload(&sc->beta); omega = (T)vload(&sc->omega); }
             DotAcc<T> dot[3];
-            phase_a<DIM, T>(a, tile, p_old, v_old, p_new, v_new, beta, omega, restart, dot);
+            phase_a<G, T>(a, tile, p_old, v_old, p_new, v_new, beta, omega, restart, dot);
             stamp(a, it, 1);
             stamp_block(a, it);
             if (!grid_reduce<3>(a, epoch, dot, [&](double *tot) {
@@ -1272,7 +1296,7 @@ __global__ void __launch_bounds__(256) bicg_persistent(PArgs a) {
             if constexpr (sizeof(T) == 4) alpha = vload(&sc->alpha_f);
             else alpha = (T)vload(&sc->alpha);
             DotAcc<T> dot[3];
-            phase_b<DIM, T>(a, tile, v_new, alpha, dot);
+            phase_b<G, T>(a, tile, v_new, alpha, dot);
             stamp(a, it, 3);
             if (!grid_reduce<3>(a, epoch, dot, [&](double *tot) {
                     sc->ts = tot[0];
@@ -1295,7 +1319,7 @@ __global__ void __launch_bounds__(256) bicg_persistent(PArgs a) {
             else { alpha = (T)vload(&sc->alpha); omega = (T)vload(&sc->omega); }
             const int sconv = vload(&sc->s_conv);
             DotAcc<T> dot[2];
-            phase_c<DIM, T>(a, p_new, alpha, omega, sconv, dot);
+            phase_c<G, T>(a, p_new, alpha, omega, sconv, dot);
             stamp(a, it, 5);
             const double eps = a.eps_breakdown;
             const double update2 = a.update2;
@@ -1351,11 +1375,11 @@ __global__ void __launch_bounds__(256) bicg_persistent(PArgs a) {
 
 enum { CA_NORMAL = 0, CA_RESTART = 1, CA_SCONV = 2 };
 
-template <int DIM, typename T>
+template <int G, typename T>
 __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old, T *p_new, T *v_new,
                          T alpha, T omega, T beta, int mode, DotAcc<T> (&dot)[3]) {
-    using HD = HaloDims<DIM>;
-    using TL = Tile<DIM>;
+    using HD = HaloDims<G>;
+    using TL = Tile<G>;
     constexpr int S = HD::S;
     constexpr bool PREF = (S == 9);
     constexpr int HN = (HD::H + 255) / 256;
@@ -1370,14 +1394,14 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
     const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
     for (int tl = tb; tl < te; ++tl) {
         int x0, y0, z0;
-        tile_origin<DIM>(a.ta, tl, x0, y0, z0);
+        tile_origin<G>(a.ta, tl, x0, y0, z0);
         int64_t k[TL::R];
         int lx[TL::R], ly[TL::R], lz[TL::R];
         T w[TL::R][PREF ? S : 1];
         T rh[TL::R], xo[TL::R], po[TL::R], so[TL::R], to[TL::R];
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
-            k[q] = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+            k[q] = tile_dp<G>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
             const bool in = k[q] >= 0;
             if (PREF && mode != CA_SCONV) load_row<S, T>(row, g.N, k[q], w[q]);
             rh[q] = (mode != CA_RESTART && in) ? __ldcg(rhat + k[q]) : (T)0;
@@ -1405,7 +1429,7 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
             const int h = tid + u * 256;
             h1[u] = h2[u] = h3[u] = h4[u] = (T)0;
             if (h < HD::H) {
-                const int64_t j = halo_index<DIM>(g, h, x0, y0, z0);
+                const int64_t j = halo_index<G>(g, h, x0, y0, z0);
                 if (mode == CA_RESTART) {
                     h1[u] = __ldcg(r + j);
                 } else {
@@ -1432,7 +1456,7 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
             if (k[q] < 0) continue;
-            const T pk = tile[tile_centre<DIM>(lx[q], ly[q], lz[q])];
+            const T pk = tile[tile_centre<G>(lx[q], ly[q], lz[q])];
             T rk, rq = rh[q];
             if (mode == CA_RESTART) {
                 rk = pk;   // p = r on a restart
@@ -1448,11 +1472,15 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
             if (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN) {
                 vk = pk;
             } else if (PREF) {
-                vk = stencil_apply<DIM, T>(w[q], tile, lx[q], ly[q], lz[q]);
+                vk = stencil_apply<G, T>(w[q], tile, lx[q], ly[q], lz[q]);
             } else {
-                T wl[S];
-                load_row<S, T>(row, g.N, k[q], wl);
-                vk = stencil_apply<DIM, T>(wl, tile, lx[q], ly[q], lz[q]);
+                if constexpr (S > 27) {
+                    vk = stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
+                } else {
+                    T wl[S];
+                    load_row<S, T>(row, g.N, k[q], wl);
+                    vk = stencil_apply<G, T>(wl, tile, lx[q], ly[q], lz[q]);
+                }
             }
             v_new[k[q]] = vk;
             dot[0].add(rq, vk);
@@ -1465,10 +1493,10 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
 
 // Phase B of the two-barrier schedule: s = r - alpha v, t = A s; dots t.s,
 // t.t, s.s, r^.s, r^.t.
-template <int DIM, typename T>
+template <int G, typename T>
 __device__ void phase_b2(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T> (&dot)[5]) {
-    using HD = HaloDims<DIM>;
-    using TL = Tile<DIM>;
+    using HD = HaloDims<G>;
+    using TL = Tile<G>;
     constexpr int S = HD::S;
     constexpr bool PREF = (S == 9);
     constexpr int HN = (HD::H + 255) / 256;
@@ -1482,14 +1510,14 @@ __device__ void phase_b2(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T>
     const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
     for (int tl = tb; tl < te; ++tl) {
         int x0, y0, z0;
-        tile_origin<DIM>(a.ta, tl, x0, y0, z0);
+        tile_origin<G>(a.ta, tl, x0, y0, z0);
         int64_t k[TL::R];
         int lx[TL::R], ly[TL::R], lz[TL::R];
         T w[TL::R][PREF ? S : 1];
         T rh[TL::R];
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
-            k[q] = tile_dp<DIM>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+            k[q] = tile_dp<G>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
             if (PREF) load_row<S, T>(row, g.N, k[q], w[q]);
             rh[q] = (k[q] >= 0) ? __ldcg(rhat + k[q]) : (T)0;
         }
@@ -1499,7 +1527,7 @@ __device__ void phase_b2(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T>
             const int h = tid + u * 256;
             hr[u] = hv[u] = (T)0;
             if (h < HD::H) {
-                const int64_t j = halo_index<DIM>(g, h, x0, y0, z0);
+                const int64_t j = halo_index<G>(g, h, x0, y0, z0);
                 hr[u] = __ldcg(r + j);
                 hv[u] = __ldcg(v + j);
             }
@@ -1513,17 +1541,21 @@ __device__ void phase_b2(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T>
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
             if (k[q] < 0) continue;
-            const T sk = tile[tile_centre<DIM>(lx[q], ly[q], lz[q])];
+            const T sk = tile[tile_centre<G>(lx[q], ly[q], lz[q])];
             s_out[k[q]] = sk;
             T tk;
             if (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN) {
                 tk = sk;
             } else if (PREF) {
-                tk = stencil_apply<DIM, T>(w[q], tile, lx[q], ly[q], lz[q]);
+                tk = stencil_apply<G, T>(w[q], tile, lx[q], ly[q], lz[q]);
             } else {
-                T wl[S];
-                load_row<S, T>(row, g.N, k[q], wl);
-                tk = stencil_apply<DIM, T>(wl, tile, lx[q], ly[q], lz[q]);
+                if constexpr (S > 27) {
+                    tk = stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
+                } else {
+                    T wl[S];
+                    load_row<S, T>(row, g.N, k[q], wl);
+                    tk = stencil_apply<G, T>(wl, tile, lx[q], ly[q], lz[q]);
+                }
             }
             t_out[k[q]] = tk;
             dot[0].add(tk, sk);
@@ -1536,9 +1568,9 @@ __device__ void phase_b2(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T>
     }
 }
 
-template <int DIM, typename T>
+template <int G, typename T>
 __global__ void __launch_bounds__(256) bicg_persistent2(PArgs a) {
-    using HD = HaloDims<DIM>;
+    using HD = HaloDims<G>;
     __shared__ T tile[HD::H];
     Scalars *sc = a.sc;
     int iters = 0;
@@ -1548,13 +1580,13 @@ __global__ void __launch_bounds__(256) bicg_persistent2(PArgs a) {
         if (vload(&sc->pending)) {
             // ---- true residual (reliable) update: as in the three-barrier kernel
             if (a.mixed) {
-                phase_fold<DIM, T>(a);
+                phase_fold<G, T>(a);
                 DotAcc<double> none[1];
                 if (!grid_reduce<1>(a, epoch, none, [&](double *) {})) return;
             }
             DotAcc<double> d64[2];
             DotAcc<T> dt[2];
-            phase_true_residual<DIM, T>(a, d64, dt);
+            phase_true_residual<G, T>(a, d64, dt);
             DotAcc<double> all[4];
             all[0].v = d64[0].v;
             all[1].v = d64[1].v;
@@ -1605,7 +1637,7 @@ __global__ void __launch_bounds__(256) bicg_persistent2(PArgs a) {
                 alpha = (T)vload(&sc->alpha); omega = (T)vload(&sc->omega); beta = (T)vload(&sc->beta);
             }
             DotAcc<T> dot[3];
-            phase_ca<DIM, T>(a, tile, p_old, v_old, p_new, v_new, alpha, omega, beta, mode, dot);
+            phase_ca<G, T>(a, tile, p_old, v_old, p_new, v_new, alpha, omega, beta, mode, dot);
             stamp(a, it, 1);
             stamp_block(a, it);
             const double eps = a.eps_breakdown;
@@ -1654,7 +1686,7 @@ __global__ void __launch_bounds__(256) bicg_persistent2(PArgs a) {
             const int parb = vload(&sc->parity);
             const T *v_cur = (const T *)(parb ? a.v1 : a.v0);
             DotAcc<T> dot[5];
-            phase_b2<DIM, T>(a, tile, v_cur, alpha, dot);
+            phase_b2<G, T>(a, tile, v_cur, alpha, dot);
             stamp(a, it, 3);
             if (!grid_reduce<5>(a, epoch, dot, [&](double *tot) {
                     sc->ts = tot[0];
@@ -1677,9 +1709,9 @@ __global__ void __launch_bounds__(256) bicg_persistent2(PArgs a) {
 
 // Grid of the persistent launch: every resident slot (at most one block per
 // tile).
-template <int DIM, typename T, int B>
+template <int G, typename T, int B>
 static int persistent_grid(int ntiles) {
-    static const int occ = (B == 2) ? occupancy(bicg_persistent2<DIM, T>) : occupancy(bicg_persistent<DIM, T>);
+    static const int occ = (B == 2) ? occupancy(bicg_persistent2<G, T>) : occupancy(bicg_persistent<G, T>);
     const int maxg = std::max(1, occ * sm_count());
     return std::min(ntiles, maxg);
 }
@@ -1690,7 +1722,7 @@ static int persistent_grid(int ntiles) {
 // Phase trace buffer (instrumentation; NULL unless mcd_trace_enable(1)).
 static unsigned long long *g_trace = nullptr;
 
-template <int DIM, typename T>
+template <int G, typename T>
 static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_solve_params *prm,
                                  mcd_status &result, cudaStream_t stream) {
     Workspace *w = st->ws;
@@ -1698,13 +1730,13 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
     const bool mixed = sizeof(T) == 4;
     PArgs a;
     a.ta.g = g;
-    a.ta.bx = (g.n[0] + Tile<DIM>::X - 1) / Tile<DIM>::X;
-    a.ta.by = (g.n[1] + Tile<DIM>::Y - 1) / Tile<DIM>::Y;
-    a.ta.bz = (DIM == 3) ? (g.n[2] + Tile<DIM>::Z - 1) / Tile<DIM>::Z : 1;
+    a.ta.bx = (g.n[0] + Tile<G>::X - 1) / Tile<G>::X;
+    a.ta.by = (g.n[1] + Tile<G>::Y - 1) / Tile<G>::Y;
+    a.ta.bz = (Shape<G>::dim == 3) ? (g.n[2] + Tile<G>::Z - 1) / Tile<G>::Z : 1;
     a.ta.ntiles = a.ta.bx * a.ta.by * a.ta.bz;
     a.ta.kind = st->has_neumann ? st->kind : nullptr;
     const bool two = prm->barriers != 3;   // default: the two-barrier schedule
-    const int grid = two ? persistent_grid<DIM, T, 2>(a.ta.ntiles) : persistent_grid<DIM, T, 3>(a.ta.ntiles);
+    const int grid = two ? persistent_grid<G, T, 2>(a.ta.ntiles) : persistent_grid<G, T, 3>(a.ta.ntiles);
     a.grid = grid;
     a.row64 = st->row64;
     a.b = w->b;
@@ -1746,7 +1778,7 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
         MCD_CUDA_TRY(cudaMemsetAsync(w->bar, 0, bar_bytes, stream));
         {
             KTimer kt(MCD_K_SOLVE, stream);
-            const void *kern = two ? (const void *)bicg_persistent2<DIM, T> : (const void *)bicg_persistent<DIM, T>;
+            const void *kern = two ? (const void *)bicg_persistent2<G, T> : (const void *)bicg_persistent<G, T>;
             MCD_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(256), args, 0, stream));
         }
         mcd_status s = read_scalars(w, stream);
@@ -1765,7 +1797,7 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
     }
 }
 
-template <int DIM>
+template <int G>
 static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const double *bnd, double *p,
                              const mcd_solve_params *prm, mcd_solve_info *info, cudaStream_t stream) {
     Workspace *w = st->ws;
@@ -1796,8 +1828,8 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
     int mixed_iters = 0, fallback = 0;
     if (prm->check_every >= 0) {
         // persistent cooperative solve (the default)
-        s = (prm->mode == MCD_FP64) ? run_persistent<DIM, double>(st, p, prm, result, stream)
-                                    : run_persistent<DIM, float>(st, p, prm, result, stream);
+        s = (prm->mode == MCD_FP64) ? run_persistent<G, double>(st, p, prm, result, stream)
+                                    : run_persistent<G, float>(st, p, prm, result, stream);
         if (s != MCD_OK) return s;
         if (prm->mode == MCD_MIXED && result != MCD_OK && result != MCD_ETIMEOUT) {
             // the FP32 recursion failed (diverged or broke down): finish in
@@ -1813,13 +1845,13 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
             MCD_CUDA_TRY(cudaMemcpyAsync(w->sc, &re, sizeof(re), cudaMemcpyHostToDevice, stream));
             s = ensure_workspace(const_cast<mcd_stencils *>(st), MCD_FP64);
             if (s != MCD_OK) return s;
-            s = run_persistent<DIM, double>(st, p, prm, result, stream);
+            s = run_persistent<G, double>(st, p, prm, result, stream);
             if (s != MCD_OK) return s;
         }
     } else if (prm->mode == MCD_FP64) {
         for (;; ++outer) {
             // FP64 residual of the current iterate (primes the Krylov scalars)
-            s = residual<DIM>(st, p, prm->tol, 1, stream);
+            s = residual<G>(st, p, prm->tol, 1, stream);
             if (s != MCD_OK) return s;
             s = read_scalars(w, stream);
             if (s != MCD_OK) return s;
@@ -1829,7 +1861,7 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
             if (h.iter >= init.max_iter) { result = MCD_ENOCONV; break; }
             if (outer >= max_outer) { result = MCD_ENOCONV; break; }
             Vecs<double> vv{p, w->r64, w->drh, {w->dp[0], w->dp[1]}, {w->dv[0], w->dv[1]}, w->ds, w->dt};
-            s = run_krylov<DIM, double, double>(st, st->row64, vv, check_every, 1e-14, max_launch, stream);
+            s = run_krylov<G, double, double>(st, st->row64, vv, check_every, 1e-14, max_launch, stream);
             if (s != MCD_OK) return s;
             const int done = w->h_sc->done;
             if (done == 4) { result = MCD_ENONFINITE; break; }
@@ -1838,7 +1870,7 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
             // FP64 residual decides, and restarts the recurrence if needed
         }
     } else {
-        s = run_mixed<DIM>(st, p, prm, check_every, max_launch, outer, result, stream);
+        s = run_mixed<G>(st, p, prm, check_every, max_launch, outer, result, stream);
         if (s != MCD_OK) return s;
     }
     // Block lower-triangular system: no inner row references a Neumann DP
@@ -1848,9 +1880,9 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
     if (result == MCD_OK && st->has_neumann) {
         result = MCD_ENOCONV;
         for (int round = 0; round < 6; ++round) {
-            s = neumann_sweeps<DIM>(st, p, 8, stream);
+            s = neumann_sweeps<G>(st, p, 8, stream);
             if (s != MCD_OK) return s;
-            s = residual<DIM>(st, p, prm->tol, 0, stream);
+            s = residual<G>(st, p, prm->tol, 0, stream);
             if (s != MCD_OK) return s;
             s = read_scalars(w, stream);
             if (s != MCD_OK) return s;
@@ -1928,6 +1960,7 @@ extern "C" mcd_status mcd_solve_pressure(const mcd_stencils *st, const double *r
     if (s != MCD_OK) return s;
     s = ensure_workspace(const_cast<mcd_stencils *>(st), prm->mode);
     if (s != MCD_OK) return s;
-    if (st->mesh.dim == 2) return solve_impl<2>(st, rhs_dev, bnd_dev, p_dev, prm, info, stream);
-    return solve_impl<3>(st, rhs_dev, bnd_dev, p_dev, prm, info, stream);
+    if (st->shape == 2) return solve_impl<2>(st, rhs_dev, bnd_dev, p_dev, prm, info, stream);
+    if (st->shape == 3) return solve_impl<3>(st, rhs_dev, bnd_dev, p_dev, prm, info, stream);
+    return solve_impl<9>(st, rhs_dev, bnd_dev, p_dev, prm, info, stream);
 }

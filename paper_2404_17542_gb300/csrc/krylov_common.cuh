@@ -64,20 +64,25 @@ __device__ __forceinline__ bool wait_eq(const unsigned *p, unsigned v, long long
     return true;
 }
 
-template <int DIM> struct Tile;
+// Tile of DPs one block works on (X x Y x Z cells; each thread owns R rows,
+// TY / TZ apart), for the stencil shape G of common.cuh.
+template <int G> struct Tile;
 template <> struct Tile<2> {
     static constexpr int X = 32, Y = 16, Z = 1, R = 2, TY = 8, TZ = 1;
 };
 template <> struct Tile<3> {
     static constexpr int X = 32, Y = 4, Z = 4, R = 2, TY = 4, TZ = 2;
 };
+template <> struct Tile<9> : Tile<2> {};
 
-template <int DIM> struct HaloDims {
-    static constexpr int HX = Tile<DIM>::X + 2;
-    static constexpr int HY = Tile<DIM>::Y + 2;
-    static constexpr int HZ = (DIM == 3) ? Tile<DIM>::Z + 2 : 1;
+// The tile plus its halo of Shape<G>::R cells on every side.
+template <int G> struct HaloDims {
+    static constexpr int RH = Shape<G>::R;
+    static constexpr int HX = Tile<G>::X + 2 * RH;
+    static constexpr int HY = Tile<G>::Y + 2 * RH;
+    static constexpr int HZ = (Shape<G>::dim == 3) ? Tile<G>::Z + 2 * RH : 1;
     static constexpr int H = HX * HY * HZ;
-    static constexpr int S = (DIM == 2) ? 9 : 27;
+    static constexpr int S = Shape<G>::S;
 };
 
 __device__ __forceinline__ int wrap_clamp(int v, int n, int per) {
@@ -261,37 +266,38 @@ struct TileArgs {
     const int8_t *kind;  // non-NULL: Neumann rows act as identity rows
 };
 
-template <int DIM>
+template <int G>
 __device__ __forceinline__ void tile_origin(const TileArgs &ta, int tile, int &x0, int &y0, int &z0) {
     const int tx = tile % ta.bx;
     const int rest = tile / ta.bx;
     const int ty = rest % ta.by;
     const int tz = rest / ta.by;
-    x0 = tx * Tile<DIM>::X;
-    y0 = ty * Tile<DIM>::Y;
-    z0 = tz * Tile<DIM>::Z;
+    x0 = tx * Tile<G>::X;
+    y0 = ty * Tile<G>::Y;
+    z0 = tz * Tile<G>::Z;
 }
 
 // Global index of halo element h of the tile at (x0, y0, z0).
-template <int DIM>
+template <int G>
 __device__ __forceinline__ int64_t halo_index(const Geo &g, int h, int x0, int y0, int z0) {
-    using HD = HaloDims<DIM>;
+    using HD = HaloDims<G>;
     const int hx = h % HD::HX;
     const int hy = (h / HD::HX) % HD::HY;
     const int hz = h / (HD::HX * HD::HY);
-    const int gx = wrap_clamp(x0 + hx - 1, g.n[0], g.per[0]);
-    const int gy = wrap_clamp(y0 + hy - 1, g.n[1], g.per[1]);
-    if (DIM == 2) return (int64_t)gx + (int64_t)g.n[0] * gy;
-    const int gz = wrap_clamp(z0 + hz - 1, g.n[2], g.per[2]);
+    const int gx = wrap_clamp(x0 + hx - HD::RH, g.n[0], g.per[0]);
+    const int gy = wrap_clamp(y0 + hy - HD::RH, g.n[1], g.per[1]);
+    if (Shape<G>::dim == 2) return (int64_t)gx + (int64_t)g.n[0] * gy;
+    const int gz = wrap_clamp(z0 + hz - HD::RH, g.n[2], g.per[2]);
     return (int64_t)gx + (int64_t)g.n[0] * ((int64_t)gy + (int64_t)g.n[1] * gz);
 }
 
 // DP r of thread tid in the tile at (x0, y0, z0): global index, or -1
 // outside the mesh; (lx, ly, lz) are its coordinates inside the tile.
-template <int DIM>
+template <int G>
 __device__ __forceinline__ int64_t tile_dp(const Geo &g, int tid, int r, int x0, int y0, int z0, int &lx,
                                            int &ly, int &lz) {
-    using TL = Tile<DIM>;
+    using TL = Tile<G>;
+    constexpr int DIM = Shape<G>::dim;
     lx = tid % TL::X;
     if (DIM == 2) {
         ly = (tid / TL::X) + r * TL::TY;
@@ -306,10 +312,10 @@ __device__ __forceinline__ int64_t tile_dp(const Geo &g, int tid, int r, int x0,
                       : (int64_t)gx + (int64_t)g.n[0] * ((int64_t)gy + (int64_t)g.n[1] * gz);
 }
 
-template <int DIM>
+template <int G>
 __device__ __forceinline__ int tile_centre(int lx, int ly, int lz) {
-    using HD = HaloDims<DIM>;
-    return (lx + 1) + HD::HX * ((ly + 1) + HD::HY * (lz + (DIM == 3 ? 1 : 0)));
+    using HD = HaloDims<G>;
+    return (lx + HD::RH) + HD::HX * ((ly + HD::RH) + HD::HY * (lz + (Shape<G>::dim == 3 ? HD::RH : 0)));
 }
 
 // (A x)_k from the shared-memory tile of x and the row weights w[] (already
@@ -331,17 +337,17 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-template <int DIM, typename T>
+template <int G, typename T>
 __device__ __forceinline__ T stencil_apply(const T *w, const T *tile, int lx, int ly, int lz) {
-    using HD = HaloDims<DIM>;
-    constexpr int C = HD::S / 2;
-    const T xk = tile[tile_centre<DIM>(lx, ly, lz)];
+    using HD = HaloDims<G>;
+    constexpr int C = HD::S / 2, W = Shape<G>::W;
+    const T xk = tile[tile_centre<G>(lx, ly, lz)];
     if (sizeof(T) == 4) {
         float hi = (float)w[C] * (float)xk, lo = 0.0f;   // centre weight is 0 or 1: exact
 #pragma unroll
         for (int s = 0; s < HD::S; ++s) {
             if (s == C) continue;
-            const int ox = s % 3, oy = (s / 3) % 3, oz = s / 9;
+            const int ox = s % W, oy = (s / W) % W, oz = s / (W * W);
             const int h = (lx + ox) + HD::HX * ((ly + oy) + HD::HY * (lz + oz));
             const float d = __fsub_rn((float)tile[h], (float)xk);
             const float p = __fmul_rn((float)w[s], d);
@@ -355,9 +361,45 @@ __device__ __forceinline__ T stencil_apply(const T *w, const T *tile, int lx, in
     T acc = (T)0;
 #pragma unroll
     for (int s = 0; s < HD::S; ++s) {
-        const int ox = s % 3, oy = (s / 3) % 3, oz = s / 9;
+        const int ox = s % W, oy = (s / W) % W, oz = s / (W * W);
         const int h = (lx + ox) + HD::HX * ((ly + oy) + HD::HY * (lz + oz));
         acc += w[s] * tile[h];
+    }
+    return acc;
+}
+
+// stencil_apply for wide stencils (81 weights per row): each weight is read
+// from the slot-major rows just before it is used, instead of staging the
+// whole row in registers.  Same arithmetic and summation order.
+template <int G, typename T>
+__device__ __forceinline__ T stencil_apply_rows(const T *__restrict__ row, int64_t N, int64_t k, const T *tile,
+                                                int lx, int ly, int lz) {
+    using HD = HaloDims<G>;
+    constexpr int C = HD::S / 2, W = Shape<G>::W;
+    const T xk = tile[tile_centre<G>(lx, ly, lz)];
+    if (sizeof(T) == 4) {
+        float hi = (float)__ldg(row + (int64_t)C * N + k) * (float)xk, lo = 0.0f;
+#pragma unroll 9
+        for (int s = 0; s < HD::S; ++s) {
+            if (s == C) continue;
+            const int ox = s % W, oy = (s / W) % W, oz = s / (W * W);
+            const int h = (lx + ox) + HD::HX * ((ly + oy) + HD::HY * (lz + oz));
+            const float ws = (float)__ldg(row + (int64_t)s * N + k);
+            const float d = __fsub_rn((float)tile[h], (float)xk);
+            const float p = __fmul_rn(ws, d);
+            const float pe = __fmaf_rn(ws, d, -p);
+            float e;
+            two_sum(hi, p, hi, e);
+            lo = __fadd_rn(lo, __fadd_rn(e, pe));
+        }
+        return (T)__fadd_rn(hi, lo);
+    }
+    T acc = (T)0;
+#pragma unroll 9
+    for (int s = 0; s < HD::S; ++s) {
+        const int ox = s % W, oy = (s / W) % W, oz = s / (W * W);
+        const int h = (lx + ox) + HD::HX * ((ly + oy) + HD::HY * (lz + oz));
+        acc += __ldg(row + (int64_t)s * N + k) * tile[h];
     }
     return acc;
 }

@@ -1,7 +1,8 @@
 // MLS stencil weights and the pressure-Poisson rows (arXiv 2404.17542,
 // Sec. 3.2, Eqs. (12)-(17); Sec. 3.3, Eq. (21), (23)).
 //
-// One thread per DP.  Pass 1 gathers the DP's 3x3 (3x3x3) cells, forms the
+// One thread per DP.  Pass 1 gathers the DP's 3x3 (3x3x3, or expanded 9x9)
+// cells, forms the
 // moment matrix M = sum w p p^T (+ Neumann terms w p^N p^N^T) and the vector
 // sum w p, and factors M by Cholesky in registers.  Pass 2 revisits the
 // neighbours and writes, slot by slot, z = M^{-1} (w p) -- the weight that
@@ -83,6 +84,11 @@ __device__ __forceinline__ double mls_weight(double r, int kind, double r_e) {
         double c = cos(M_PI * r / (2.0 * r_e));
         return c * c;
     }
+    if (kind == MCD_W_LSMPS) {
+        if (!(r < r_e)) return 0.0;
+        const double q = 1.0 - r / r_e;
+        return q * q;
+    }
     double q = r / r_e;
     return exp(-q * q);
 }
@@ -151,11 +157,12 @@ __device__ __forceinline__ void decode(const Geo &g, int64_t k, int *c) {
     }
 }
 
-template <int DIM>
+template <int G, int DIM = Shape<G>::dim>
 __device__ __forceinline__ Nbr<DIM> neighbour(const Geo &g, const int *c, int s) {
     Nbr<DIM> r;
     r.valid = true;
-    int o[3] = {s % 3 - 1, (s / 3) % 3 - 1, s / 9 - 1};
+    int o[3];
+    slot_offset<G>(s, o);
     int v[3];
     for (int d = 0; d < DIM; ++d) {
         double sh;
@@ -170,13 +177,14 @@ __device__ __forceinline__ Nbr<DIM> neighbour(const Geo &g, const int *c, int s)
 // Weights of DP k of the system with geometry g whose arrays start at DP
 // offset `off` in the arrays of `a` (a batch of systems stored back to back,
 // each in its own [slot][N] layout; off = 0 for a single system).
-template <int DIM>
+template <int G>
 __device__ __forceinline__ void build_dp(const BuildArgs &a, const Geo &g, int64_t off, int64_t k,
                                          double r_e, double r_s) {
+    constexpr int DIM = Shape<G>::dim;
     using B = Basis<DIM>;
     constexpr int NB = B::NB;
-    constexpr int S = B::S;
-    constexpr int C = S / 2;
+    constexpr int S = Shape<G>::S;
+    constexpr int C = Shape<G>::C;
     const int64_t N = g.N;
     const double *pos = a.pos + DIM * off;
     const int8_t *mask = a.mask + off;
@@ -230,7 +238,7 @@ __device__ __forceinline__ void build_dp(const BuildArgs &a, const Geo &g, int64
 
     for (int s = 0; s < S; ++s) {
         if (s == C) continue;
-        Nbr<DIM> nb = neighbour<DIM>(g, c, s);
+        Nbr<DIM> nb = neighbour<G>(g, c, s);
         if (!nb.valid) continue;
         const int8_t mj = mask[nb.j];
         if (mj == 0) continue;
@@ -299,7 +307,7 @@ __device__ __forceinline__ void build_dp(const BuildArgs &a, const Geo &g, int64
         if (s == C) {
             for (int q = 0; q < NB; ++q) z[q] = cen[q];
         } else {
-            Nbr<DIM> nb = neighbour<DIM>(g, c, s);
+            Nbr<DIM> nb = neighbour<G>(g, c, s);
             int8_t mj = nb.valid ? mask[nb.j] : (int8_t)0;
             if (mj != 0) {
                 const bool neu = (kind == KIND_INNER) && mj > 0 && a.bc[(uint8_t)mj] == MCD_BC_NEUMANN;
@@ -348,16 +356,16 @@ __device__ __forceinline__ void build_dp(const BuildArgs &a, const Geo &g, int64
 }
 
 
-template <int DIM>
+template <int G>
 __global__ void __launch_bounds__(128) build_kernel(const __grid_constant__ BuildArgs a) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= a.g.N) return;
-    build_dp<DIM>(a, a.g, 0, k, a.r_e, a.r_s);
+    build_dp<G>(a, a.g, 0, k, a.r_e, a.r_s);
 }
 
 // Batched build: the blocks of system i start at blk_start[i]; geo[i] and
 // off[i] give its geometry and DP offset; r_e and r_s are multiples of its l0.
-template <int DIM>
+template <int G>
 __global__ void __launch_bounds__(128) build_batch_kernel(const __grid_constant__ BuildArgs a,
                                                           const Geo *__restrict__ geo,
                                                           const int64_t *__restrict__ off,
@@ -371,7 +379,7 @@ __global__ void __launch_bounds__(128) build_batch_kernel(const __grid_constant_
     const Geo g = geo[lo];
     const int64_t k = (int64_t)(blk - blk_start[lo]) * blockDim.x + threadIdx.x;
     if (k >= g.N) return;
-    build_dp<DIM>(a, g, off[lo], k, a.r_e * g.l0, a.r_s * g.l0);
+    build_dp<G>(a, g, off[lo], k, a.r_e * g.l0, a.r_s * g.l0);
 }
 
 cudaError_t launch_build_batch(const BatchBuildDesc &d, cudaStream_t stream) {
@@ -403,11 +411,12 @@ cudaError_t launch_build_batch(const BatchBuildDesc &d, cudaStream_t stream) {
 // the O(1/l0^2) weights from consuming the FP32 mantissa; the products are
 // split exactly with fma and summed with TwoSum (double-float accumulation).
 // ---------------------------------------------------------------------------
-template <typename T, int DIM>
+template <typename T, int G>
 __global__ void __launch_bounds__(256) spmv_kernel(Geo g, const T *__restrict__ row,
                                                    const T *__restrict__ x, T *__restrict__ y) {
-    constexpr int S = (DIM == 2) ? 9 : 27;
-    constexpr int C = S / 2;
+    constexpr int DIM = Shape<G>::dim;
+    constexpr int S = Shape<G>::S;
+    constexpr int C = Shape<G>::C;
     constexpr bool diff_form = sizeof(T) == 4;
     const int64_t N = g.N;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -421,7 +430,7 @@ __global__ void __launch_bounds__(256) spmv_kernel(Geo g, const T *__restrict__ 
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             if (s == C) continue;
-            Nbr<DIM> nb = neighbour<DIM>(g, c, s);
+            Nbr<DIM> nb = neighbour<G>(g, c, s);
             const float w = (float)row[(int64_t)s * N + k];
             // _rn intrinsics: never contracted into fused multiply-adds
             const float d = __fsub_rn((float)x[nb.j], (float)xi);
@@ -438,18 +447,19 @@ __global__ void __launch_bounds__(256) spmv_kernel(Geo g, const T *__restrict__ 
     T acc = (T)0;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        Nbr<DIM> nb = neighbour<DIM>(g, c, s);
+        Nbr<DIM> nb = neighbour<G>(g, c, s);
         acc += row[(int64_t)s * N + k] * x[nb.j];
     }
     y[k] = acc;
 }
 
 // b: inner DP f - sum QL * bnd (Neumann neighbours); boundary DP rscale * bnd.
-template <int DIM>
+template <int G>
 __global__ void rhs_kernel(Geo g, const int8_t *__restrict__ kind, const double *__restrict__ ql,
                            const double *__restrict__ rscale, const double *__restrict__ rhs,
                            const double *__restrict__ bnd, double *__restrict__ b) {
-    constexpr int S = (DIM == 2) ? 9 : 27;
+    constexpr int DIM = Shape<G>::dim;
+    constexpr int S = Shape<G>::S;
     const int64_t N = g.N;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
@@ -463,7 +473,7 @@ __global__ void rhs_kernel(Geo g, const int8_t *__restrict__ kind, const double 
             for (int s = 0; s < S; ++s) {
                 const double q = ql[(int64_t)s * N + k];
                 if (q != 0.0) {
-                    Nbr<DIM> nb = neighbour<DIM>(g, c, s);
+                    Nbr<DIM> nb = neighbour<G>(g, c, s);
                     out -= q * bnd[nb.j];
                 }
             }
@@ -500,7 +510,7 @@ static bool same_layout(const mcd_stencils *st, const mcd_mesh &m, const mcd_mls
     int has_neu = 0;
     for (int b = 1; b < 128; ++b) has_neu |= (p.bc_kind[b] == MCD_BC_NEUMANN);
     return st->prm.precision == p.precision && st->prm.want_derivs == p.want_derivs &&
-           st->has_neumann == has_neu;
+           st->has_neumann == has_neu && st->support == (p.support == 0 ? 1 : p.support);
 }
 
 }  // namespace mcd
@@ -524,8 +534,15 @@ extern "C" mcd_status mcd_build_stencils(const mcd_mesh *mesh, const double *pos
     if (v != MCD_OK) return v;
     MCD_CHECK_ARG(pos_dev && mask_dev && prm && st, "NULL argument");
     MCD_CHECK_ARG(prm->r_e > 0.0 && prm->r_s > 0.0, "r_e and r_s must be positive");
-    MCD_CHECK_ARG(prm->weight_kind == MCD_W_GAUSS || prm->weight_kind == MCD_W_COS2,
+    MCD_CHECK_ARG(prm->weight_kind == MCD_W_GAUSS || prm->weight_kind == MCD_W_COS2 ||
+                      prm->weight_kind == MCD_W_LSMPS,
                   "unknown weight_kind");
+    const int support = prm->support == 0 ? 1 : prm->support;
+    const int shape = shape_code(mesh->dim, support);
+    MCD_CHECK_ARG(shape != 0, "support must be 1 (3x3, 3x3x3) or 4 (2D 9x9)");
+    for (int d = 0; d < mesh->dim; ++d)
+        MCD_CHECK_ARG(!mesh->periodic[d] || mesh->n[d] >= 2 * support + 1,
+                      "a periodic axis needs at least 2 support + 1 cells");
     MCD_CHECK_ARG(prm->precision == MCD_FP64 || prm->precision == MCD_MIXED, "unknown precision");
     int has_neu = 0;
     for (int b = 1; b < 128; ++b) has_neu |= (prm->bc_kind[b] == MCD_BC_NEUMANN);
@@ -537,7 +554,8 @@ extern "C" mcd_status mcd_build_stencils(const mcd_mesh *mesh, const double *pos
         return MCD_EINVAL;
     }
     const Geo g = make_geo(*mesh);
-    const int S = (mesh->dim == 2) ? 9 : 27;
+    const int S = (mesh->dim == 2) ? (2 * support + 1) * (2 * support + 1)
+                                   : (2 * support + 1) * (2 * support + 1) * (2 * support + 1);
     const int nb = (mesh->dim == 2) ? 5 : 9;
     const int64_t N = g.N;
     if (!h) {
@@ -546,6 +564,8 @@ extern "C" mcd_status mcd_build_stencils(const mcd_mesh *mesh, const double *pos
         h->prm = *prm;
         h->geo = g;
         h->S = S;
+        h->support = support;
+        h->shape = shape;
         h->nb = nb;
         h->has_neumann = has_neu;
         cudaError_t e = cudaSuccess;
@@ -594,10 +614,12 @@ extern "C" mcd_status mcd_build_stencils(const mcd_mesh *mesh, const double *pos
     a.bad = h->bad_dp;
     const int threads = 128;
     const unsigned blocks = (unsigned)((N + threads - 1) / threads);
-    if (mesh->dim == 2)
+    if (shape == 2)
         MCD_KLAUNCH(MCD_K_BUILD, stream, build_kernel<2><<<blocks, threads, 0, stream>>>(a));
-    else
+    else if (shape == 3)
         MCD_KLAUNCH(MCD_K_BUILD, stream, build_kernel<3><<<blocks, threads, 0, stream>>>(a));
+    else
+        MCD_KLAUNCH(MCD_K_BUILD, stream, build_kernel<9><<<blocks, threads, 0, stream>>>(a));
     MCD_LAUNCH_CHECK();
     MCD_CUDA_TRY(cnn_store_offsets(h, pos_dev, mask_dev, stream));
     return MCD_OK;
@@ -669,16 +691,26 @@ extern "C" mcd_status mcd_apply_laplacian(const mcd_stencils *st, const void *x_
     const int threads = 256;
     const unsigned blocks = (unsigned)((N + threads - 1) / threads);
     if (dtype == MCD_DT_F64) {
-        if (st->mesh.dim == 2)
-            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<double, 2><<<blocks, threads, 0, stream>>>(st->geo, st->row64, (const double *)x_dev, (double *)y_dev));
+        const double *row = st->row64;
+        const double *x = (const double *)x_dev;
+        double *y = (double *)y_dev;
+        if (st->shape == 2)
+            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<double, 2><<<blocks, threads, 0, stream>>>(st->geo, row, x, y));
+        else if (st->shape == 3)
+            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<double, 3><<<blocks, threads, 0, stream>>>(st->geo, row, x, y));
         else
-            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<double, 3><<<blocks, threads, 0, stream>>>(st->geo, st->row64, (const double *)x_dev, (double *)y_dev));
+            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<double, 9><<<blocks, threads, 0, stream>>>(st->geo, row, x, y));
     } else if (dtype == MCD_DT_F32) {
         MCD_CHECK_ARG(st->row32, "FP32 rows need an MCD_MIXED stencil handle");
-        if (st->mesh.dim == 2)
-            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<float, 2><<<blocks, threads, 0, stream>>>(st->geo, st->row32, (const float *)x_dev, (float *)y_dev));
+        const float *row = st->row32;
+        const float *x = (const float *)x_dev;
+        float *y = (float *)y_dev;
+        if (st->shape == 2)
+            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<float, 2><<<blocks, threads, 0, stream>>>(st->geo, row, x, y));
+        else if (st->shape == 3)
+            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<float, 3><<<blocks, threads, 0, stream>>>(st->geo, row, x, y));
         else
-            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<float, 3><<<blocks, threads, 0, stream>>>(st->geo, st->row32, (const float *)x_dev, (float *)y_dev));
+            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<float, 9><<<blocks, threads, 0, stream>>>(st->geo, row, x, y));
     } else {
         set_error("unknown dtype");
         return MCD_EINVAL;
@@ -694,10 +726,12 @@ extern "C" mcd_status mcd_assemble_rhs(const mcd_stencils *st, const double *rhs
     const int threads = 256;
     const unsigned blocks = (unsigned)((N + threads - 1) / threads);
     const double *ql = st->has_neumann ? st->ql64 : nullptr;
-    if (st->mesh.dim == 2)
+    if (st->shape == 2)
         MCD_KLAUNCH(MCD_K_OTHER, stream, rhs_kernel<2><<<blocks, threads, 0, stream>>>(st->geo, st->kind, ql, st->rscale, rhs_dev, bnd_dev, b_dev));
-    else
+    else if (st->shape == 3)
         MCD_KLAUNCH(MCD_K_OTHER, stream, rhs_kernel<3><<<blocks, threads, 0, stream>>>(st->geo, st->kind, ql, st->rscale, rhs_dev, bnd_dev, b_dev));
+    else
+        MCD_KLAUNCH(MCD_K_OTHER, stream, rhs_kernel<9><<<blocks, threads, 0, stream>>>(st->geo, st->kind, ql, st->rscale, rhs_dev, bnd_dev, b_dev));
     MCD_LAUNCH_CHECK();
     return MCD_OK;
 }

@@ -6,6 +6,9 @@
 //                operations (__dmul_rn / __dadd_rn / __dsqrt_rn), so no
 //                multiply-add is fused and the decision is bit-identical to
 //                a plain IEEE evaluation of the same expression.
+//                With several bodies each point takes the SDF of smallest
+//                magnitude (Sec. 2.5; the first body on a tie), and a
+//                boundary cell the id of the body nearest its centroid.
 // relax_kernel   one thread per cell: one Jacobi sweep of spring relaxation
 //                (Eqs. (5)-(8)), relocation onto the body (Eq. (9)),
 //                optional boundary-fitted inner move (Eqs. (45)-(46)) and the
@@ -23,27 +26,63 @@ struct Circle {
     double cx, cy, R;
 };
 
-__device__ __forceinline__ bool vertex_fluid(double ox, double oy, double l0, int i, int j, const Circle &b) {
+// The bodies of one update, passed by value as a kernel parameter.
+struct Bodies {
+    int n;
+    Circle c[MCD_MAX_BODIES];
+};
+
+// Circle SDF psi = |x - c| - R with every operation rounded on its own.
+__device__ __forceinline__ double circle_psi(double x, double y, const Circle &b) {
+    const double dx = __dsub_rn(x, b.cx);
+    const double dy = __dsub_rn(y, b.cy);
+    return __dsub_rn(__dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy))), b.R);
+}
+
+// Index of the body whose SDF has the smallest magnitude at (x, y), the
+// first on a tie (Sec. 2.5); its SDF value in *psi.
+__device__ __forceinline__ int nearest_body(const Bodies &B, double x, double y, double *psi) {
+    int best = 0;
+    double bp = circle_psi(x, y, B.c[0]);
+    for (int b = 1; b < B.n; ++b) {
+        const double p = circle_psi(x, y, B.c[b]);
+        if (fabs(p) < fabs(bp)) { best = b; bp = p; }
+    }
+    *psi = bp;
+    return best;
+}
+
+__device__ __forceinline__ int body_with_id(const Bodies &B, int id) {
+    for (int b = 0; b < B.n; ++b)
+        if (B.c[b].id == id) return b;
+    return -1;
+}
+
+// Vertex (i, j) has psi >= 0 for its nearest body (tested as d^2 >= R^2).
+__device__ __forceinline__ bool vertex_fluid(double ox, double oy, double l0, int i, int j, const Bodies &B) {
     const double vx = __dadd_rn(ox, __dmul_rn((double)i, l0));
     const double vy = __dadd_rn(oy, __dmul_rn((double)j, l0));
+    double psi;
+    const Circle &b = B.c[B.n > 1 ? nearest_body(B, vx, vy, &psi) : 0];
     const double dx = __dsub_rn(vx, b.cx);
     const double dy = __dsub_rn(vy, b.cy);
     const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
     return d2 >= __dmul_rn(b.R, b.R);
 }
 
+// Band test of cell (i, j) and (out) the index of the body nearest its
+// centroid.
 __device__ __forceinline__ bool cell_in_band(double ox, double oy, double l0, int i, int j,
-                                             const Circle &b, double band) {
-    if (band <= 0.0) return true;
+                                             const Bodies &B, double band, int *nearest) {
     const double cx = __dadd_rn(ox, __dmul_rn((double)i + 0.5, l0));
     const double cy = __dadd_rn(oy, __dmul_rn((double)j + 0.5, l0));
-    const double dx = __dsub_rn(cx, b.cx);
-    const double dy = __dsub_rn(cy, b.cy);
-    const double psi = __dsub_rn(__dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy))), b.R);
+    double psi;
+    *nearest = nearest_body(B, cx, cy, &psi);
+    if (band <= 0.0) return true;
     return fabs(psi) < band;
 }
 
-__global__ void remask_kernel(Geo g, Circle body, double band, double *__restrict__ pos,
+__global__ void remask_kernel(Geo g, Bodies bodies, double band, double *__restrict__ pos,
                               int8_t *__restrict__ mask, int8_t *__restrict__ mask_prev) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.N) return;
@@ -52,12 +91,13 @@ __global__ void remask_kernel(Geo g, Circle body, double band, double *__restric
     const int8_t old = mask[k];
     mask_prev[k] = old;
     if (i == 0 || j == 0 || i == nx - 1 || j == ny - 1) return;   // wall cell
-    if (!cell_in_band(g.org[0], g.org[1], g.l0, i, j, body, band)) return;
-    const int cnt = (int)vertex_fluid(g.org[0], g.org[1], g.l0, i, j, body) +
-                    (int)vertex_fluid(g.org[0], g.org[1], g.l0, i + 1, j, body) +
-                    (int)vertex_fluid(g.org[0], g.org[1], g.l0, i, j + 1, body) +
-                    (int)vertex_fluid(g.org[0], g.org[1], g.l0, i + 1, j + 1, body);
-    const int8_t nm = (cnt <= 1) ? (int8_t)0 : (cnt <= 3 ? (int8_t)body.id : (int8_t)-1);
+    int near = 0;
+    if (!cell_in_band(g.org[0], g.org[1], g.l0, i, j, bodies, band, &near)) return;
+    const int cnt = (int)vertex_fluid(g.org[0], g.org[1], g.l0, i, j, bodies) +
+                    (int)vertex_fluid(g.org[0], g.org[1], g.l0, i + 1, j, bodies) +
+                    (int)vertex_fluid(g.org[0], g.org[1], g.l0, i, j + 1, bodies) +
+                    (int)vertex_fluid(g.org[0], g.org[1], g.l0, i + 1, j + 1, bodies);
+    const int8_t nm = (cnt <= 1) ? (int8_t)0 : (cnt <= 3 ? (int8_t)bodies.c[near].id : (int8_t)-1);
     mask[k] = nm;
     if (nm == 0 && old != 0) {
         pos[k] = g.org[0] + ((double)i + 0.5) * g.l0;
@@ -65,7 +105,7 @@ __global__ void remask_kernel(Geo g, Circle body, double band, double *__restric
     }
 }
 
-__global__ void relax_kernel(Geo g, Circle body, double band, double kappa, double alpha,
+__global__ void relax_kernel(Geo g, Bodies bodies, double band, double kappa, double alpha,
                              const int8_t *__restrict__ mask, const double *__restrict__ pin,
                              double *__restrict__ pout) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -75,8 +115,9 @@ __global__ void relax_kernel(Geo g, Circle body, double band, double kappa, doub
     const int i = (int)(k % nx), j = (int)(k / nx);
     const double xi = pin[k], yi = pin[N + k];
     const int8_t mk = mask[k];
+    int near = 0;
     const bool movable = !(i == 0 || j == 0 || i == nx - 1 || j == ny - 1) && mk != 0 &&
-                         cell_in_band(g.org[0], g.org[1], g.l0, i, j, body, band);
+                         cell_in_band(g.org[0], g.org[1], g.l0, i, j, bodies, band, &near);
     if (!movable) {
         pout[k] = xi;
         pout[N + k] = yi;
@@ -103,15 +144,24 @@ __global__ void relax_kernel(Geo g, Circle body, double band, double kappa, doub
     }
     double sx = xi - kappa * l0 * fx;                                   // Eq. (8)
     double sy = yi - kappa * l0 * fy;
+    // a boundary DP follows its own body, an inner DP the nearest one
+    int b = -1;
+    if (mk >= 1) {
+        b = body_with_id(bodies, mk);
+    } else if (mk == -1 && alpha > 0.0) {
+        double psi_near;
+        b = bodies.n > 1 ? nearest_body(bodies, sx, sy, &psi_near) : 0;
+    }
+    const Circle body = bodies.c[b < 0 ? 0 : b];
     const double dxc = sx - body.cx, dyc = sy - body.cy;
-    const double dist = sqrt(dxc * dxc + dyc * dyc);
+    const double dist = (b < 0) ? 0.0 : sqrt(dxc * dxc + dyc * dyc);
     if (dist > 0.0) {
         const double psi = dist - body.R;
         const double hx = -dxc / dist, hy = -dyc / dist;                // -grad psi / |grad psi|
-        if (mk == body.id) {
+        if (mk >= 1) {
             sx += psi * hx;                                             // Eq. (9)
             sy += psi * hy;
-        } else if (mk == -1 && alpha > 0.0) {
+        } else {
             const double re = 5.0 * l0;
             if (psi < re) {
                 const double beta = 0.5 * alpha * (1.0 + cos(M_PI * psi / re));   // Eq. (46)
@@ -126,21 +176,61 @@ __global__ void relax_kernel(Geo g, Circle body, double band, double kappa, doub
     pout[N + k] = fmin(fmax(sy, loy), hiy);
 }
 
-__global__ void body_bc_kernel(Geo g, Circle body, double ax, double ay, const double *__restrict__ pos,
+// Body accelerations for the Neumann datum, in body order.
+struct BodyAcc {
+    double a[MCD_MAX_BODIES][2];
+};
+
+__global__ void body_bc_kernel(Geo g, Bodies bodies, BodyAcc acc, const double *__restrict__ pos,
                                const int8_t *__restrict__ mask, double *__restrict__ nrm,
                                double *__restrict__ neu) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t N = g.N;
     if (k >= N) return;
-    double nx = 0.0, ny = 0.0;
-    if (mask[k] == body.id) {
+    double nx = 0.0, ny = 0.0, ax = 0.0, ay = 0.0;
+    const int b = mask[k] >= 1 ? body_with_id(bodies, mask[k]) : -1;
+    if (b >= 0) {
+        const Circle &body = bodies.c[b];
         const double dx = pos[k] - body.cx, dy = pos[N + k] - body.cy;
         const double d = sqrt(dx * dx + dy * dy);
         if (d > 0.0) { nx = dx / d; ny = dy / d; }
+        ax = acc.a[b][0];
+        ay = acc.a[b][1];
     }
     nrm[k] = nx;
     nrm[N + k] = ny;
     if (neu) neu[k] = -(ax * nx + ay * ny);                            // Eq. (23)
+}
+
+// Checks the body list of an update and packs it for the kernels.
+static mcd_status pack_bodies(const char *who, const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
+                              Bodies *out) {
+    if (mesh->dim != 2) {
+        set_error(std::string(who) + ": 2D only");
+        return MCD_ENOTSUP;
+    }
+    if (nbodies < 1 || nbodies > MCD_MAX_BODIES) {
+        set_error(std::string(who) + ": nbodies must be in 1..MCD_MAX_BODIES");
+        return MCD_EINVAL;
+    }
+    out->n = nbodies;
+    for (int b = 0; b < nbodies; ++b) {
+        if (bodies[b].id < 2 || bodies[b].id > 127) {
+            set_error(std::string(who) + ": body id must be in 2..127");
+            return MCD_EINVAL;
+        }
+        if (!(bodies[b].radius > 0.0)) {
+            set_error(std::string(who) + ": body radius must be positive");
+            return MCD_EINVAL;
+        }
+        for (int a = 0; a < b; ++a)
+            if (bodies[a].id == bodies[b].id) {
+                set_error(std::string(who) + ": body ids must be distinct");
+                return MCD_EINVAL;
+            }
+        out->c[b] = Circle{bodies[b].id, bodies[b].c[0], bodies[b].c[1], bodies[b].radius};
+    }
+    return MCD_OK;
 }
 
 // Position scratch for the Jacobi ping-pong, grown on demand and kept for
@@ -176,19 +266,15 @@ extern "C" mcd_status mcd_update_dps(const mcd_mesh *mesh, const mcd_body *bodie
                                      double kappa, int n_relax, double band, double alpha,
                                      mcd_stream_t stream) {
     MCD_CHECK_ARG(mesh && bodies && pos_dev && mask_dev && mask_prev_dev, "NULL argument");
-    if (mesh->dim != 2 || nbodies != 1) {
-        set_error("mcd_update_dps: 2D with one body only");
-        return MCD_ENOTSUP;
-    }
+    Bodies bl;
+    mcd_status st = pack_bodies("mcd_update_dps", mesh, bodies, nbodies, &bl);
+    if (st != MCD_OK) return st;
     MCD_CHECK_ARG(mesh->n[0] >= 3 && mesh->n[1] >= 3 && mesh->l0 > 0.0, "bad mesh");
-    MCD_CHECK_ARG(bodies[0].id >= 2 && bodies[0].id <= 127, "body id must be in 2..127");
-    MCD_CHECK_ARG(bodies[0].radius > 0.0, "body radius must be positive");
     MCD_CHECK_ARG(n_relax >= 0 && kappa >= 0.0, "bad relaxation parameters");
     const Geo g = make_geo(*mesh);
-    Circle c{bodies[0].id, bodies[0].c[0], bodies[0].c[1], bodies[0].radius};
     const int threads = 256;
     const unsigned blocks = (unsigned)((g.N + threads - 1) / threads);
-    MCD_KLAUNCH(MCD_K_UPDATE, stream, remask_kernel<<<blocks, threads, 0, stream>>>(g, c, band, pos_dev, mask_dev, mask_prev_dev));
+    MCD_KLAUNCH(MCD_K_UPDATE, stream, remask_kernel<<<blocks, threads, 0, stream>>>(g, bl, band, pos_dev, mask_dev, mask_prev_dev));
     MCD_LAUNCH_CHECK();
     if (n_relax == 0) return MCD_OK;
     double *tmp = scratch_positions(2 * (size_t)g.N);
@@ -198,7 +284,7 @@ extern "C" mcd_status mcd_update_dps(const mcd_mesh *mesh, const mcd_body *bodie
     }
     double *a = pos_dev, *b = tmp;
     for (int it = 0; it < n_relax; ++it) {
-        MCD_KLAUNCH(MCD_K_UPDATE, stream, relax_kernel<<<blocks, threads, 0, stream>>>(g, c, band, kappa, alpha, mask_dev, a, b));
+        MCD_KLAUNCH(MCD_K_UPDATE, stream, relax_kernel<<<blocks, threads, 0, stream>>>(g, bl, band, kappa, alpha, mask_dev, a, b));
         double *t = a; a = b; b = t;
     }
     MCD_LAUNCH_CHECK();
@@ -208,22 +294,31 @@ extern "C" mcd_status mcd_update_dps(const mcd_mesh *mesh, const mcd_body *bodie
     return MCD_OK;
 }
 
+extern "C" mcd_status mcd_bodies_boundary(const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
+                                          const double *pos_dev, const int8_t *mask_dev, double *normal_dev,
+                                          double *neumann_dev, mcd_stream_t stream) {
+    MCD_CHECK_ARG(mesh && bodies && pos_dev && mask_dev && normal_dev, "NULL argument");
+    Bodies bl;
+    mcd_status st = pack_bodies("mcd_bodies_boundary", mesh, bodies, nbodies, &bl);
+    if (st != MCD_OK) return st;
+    BodyAcc acc;
+    for (int b = 0; b < nbodies; ++b) {
+        acc.a[b][0] = bodies[b].acc[0];
+        acc.a[b][1] = bodies[b].acc[1];
+    }
+    const Geo g = make_geo(*mesh);
+    const unsigned blocks = (unsigned)((g.N + 255) / 256);
+    MCD_KLAUNCH(MCD_K_OTHER, stream, body_bc_kernel<<<blocks, 256, 0, stream>>>(g, bl, acc, pos_dev, mask_dev,
+                                                                              normal_dev, neumann_dev));
+    MCD_LAUNCH_CHECK();
+    return MCD_OK;
+}
+
 extern "C" mcd_status mcd_body_boundary(const mcd_mesh *mesh, const mcd_body *body, const double *pos_dev,
                                         const int8_t *mask_dev, double *normal_dev, double *neumann_dev,
                                         mcd_stream_t stream) {
-    MCD_CHECK_ARG(mesh && body && pos_dev && mask_dev && normal_dev, "NULL argument");
-    if (mesh->dim != 2) {
-        set_error("mcd_body_boundary: 2D only");
-        return MCD_ENOTSUP;
-    }
-    const Geo g = make_geo(*mesh);
-    Circle c{body->id, body->c[0], body->c[1], body->radius};
-    const unsigned blocks = (unsigned)((g.N + 255) / 256);
-    MCD_KLAUNCH(MCD_K_OTHER, stream, body_bc_kernel<<<blocks, 256, 0, stream>>>(g, c, body->acc[0], body->acc[1],
-                                                                              pos_dev, mask_dev, normal_dev,
-                                                                              neumann_dev));
-    MCD_LAUNCH_CHECK();
-    return MCD_OK;
+    MCD_CHECK_ARG(body, "NULL argument");
+    return mcd_bodies_boundary(mesh, body, 1, pos_dev, mask_dev, normal_dev, neumann_dev, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -276,13 +371,10 @@ extern "C" mcd_status mcd_update_dps_static(const mcd_mesh *mesh, const mcd_body
                                             double kappa, int n_relax, double band, double alpha,
                                             mcd_stream_t stream) {
     MCD_CHECK_ARG(mesh && bodies && pos_dev && mask_dev && mask_prev_dev, "NULL argument");
-    if (mesh->dim != 2 || nbodies != 1) {
-        set_error("mcd_update_dps_static: 2D with one body only");
-        return MCD_ENOTSUP;
-    }
+    Bodies bl;
+    mcd_status st = pack_bodies("mcd_update_dps_static", mesh, bodies, nbodies, &bl);
+    if (st != MCD_OK) return st;
     MCD_CHECK_ARG(mesh->n[0] >= 3 && mesh->n[1] >= 3 && mesh->l0 > 0.0, "bad mesh");
-    MCD_CHECK_ARG(bodies[0].id >= 2 && bodies[0].id <= 127, "body id must be in 2..127");
-    MCD_CHECK_ARG(bodies[0].radius > 0.0, "body radius must be positive");
     MCD_CHECK_ARG(n_relax >= 0 && kappa >= 0.0, "bad relaxation parameters");
     const Geo g = make_geo(*mesh);
     if (g.N > (int64_t)MCD_NOALLOC_MAX_DPS) {
@@ -292,19 +384,18 @@ extern "C" mcd_status mcd_update_dps_static(const mcd_mesh *mesh, const mcd_body
         return MCD_EINVAL;
     }
     double *tmp = nullptr;
-    mcd_status st = noalloc_scratch(&tmp);
+    st = noalloc_scratch(&tmp);
     if (st != MCD_OK) return st;
-    Circle c{bodies[0].id, bodies[0].c[0], bodies[0].c[1], bodies[0].radius};
     const int threads = 256;
     const unsigned blocks = (unsigned)((g.N + threads - 1) / threads);
-    MCD_KLAUNCH(MCD_K_UPDATE, stream, remask_kernel<<<blocks, threads, 0, stream>>>(g, c, band, pos_dev, mask_dev,
+    MCD_KLAUNCH(MCD_K_UPDATE, stream, remask_kernel<<<blocks, threads, 0, stream>>>(g, bl, band, pos_dev, mask_dev,
                                                                                   mask_prev_dev));
     MCD_LAUNCH_CHECK();
     // Each sweep writes every one of the 2N scratch positions before any is
     // read, so contents left by an earlier call never leak into this one.
     double *a = pos_dev, *b = tmp;
     for (int it = 0; it < n_relax; ++it) {
-        MCD_KLAUNCH(MCD_K_UPDATE, stream, relax_kernel<<<blocks, threads, 0, stream>>>(g, c, band, kappa, alpha,
+        MCD_KLAUNCH(MCD_K_UPDATE, stream, relax_kernel<<<blocks, threads, 0, stream>>>(g, bl, band, kappa, alpha,
                                                                                      mask_dev, a, b));
         double *t = a; a = b; b = t;
     }

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "MCD_OK", 1: "MCD_EINVAL", 2: "MCD_ENOMEM", 3: "MCD_ECUDA", 4
                 9: "MCD_ENOTSUP"}
 FP64, MIXED = 0, 1
 DT_F64, DT_F32 = 0, 1
-W_GAUSS, W_COS2 = 0, 1
+W_GAUSS, W_COS2, W_LSMPS = 0, 1, 2
 ARR_ROW64, ARR_ROW32, ARR_QL64, ARR_D64, ARR_QD64, ARR_RSCALE, ARR_KIND = range(7)
 
 
@@ -40,7 +40,8 @@ class c_mesh(C.Structure):
 
 class c_mls_params(C.Structure):
     _fields_ = [("weight_kind", C.c_int), ("r_e", C.c_double), ("r_s", C.c_double),
-                ("precision", C.c_int), ("want_derivs", C.c_int), ("bc_kind", C.c_uint8 * 128)]
+                ("precision", C.c_int), ("want_derivs", C.c_int), ("bc_kind", C.c_uint8 * 128),
+                ("support", C.c_int)]
 
 
 class c_solve_params(C.Structure):
@@ -91,6 +92,8 @@ _SIGS = {
                                         C.c_double, C.c_void_p]),
     "mcd_body_boundary": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mcd_bodies_boundary": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_int, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mcd_flow_predict": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_double, C.c_double]
                          + [C.c_void_p] * 3 + [C.c_void_p]),
     "mcd_flow_project": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.c_double]
@@ -183,12 +186,13 @@ class Stencils:
     """Owner of an mcd_stencils handle (MLS weights + PPE rows)."""
 
     def __init__(self, mesh, pos, mask, normal=None, bc_kind=None, weight_kind=W_GAUSS,
-                 r_e=None, r_s=None, precision=MIXED, want_derivs=False):
+                 r_e=None, r_s=None, precision=MIXED, want_derivs=False, support=1):
         self.mesh = mesh
         self.cmesh = make_mesh(mesh)
         self.N = int(np.prod([mesh.n[d] for d in range(mesh.dim)]))
         self.dim = mesh.dim
-        self.S = 3 ** mesh.dim
+        self.support = int(support)
+        self.S = (2 * self.support + 1) ** mesh.dim
         self.nb = 5 if mesh.dim == 2 else 9
         p = c_mls_params()
         p.weight_kind = int(weight_kind)
@@ -199,6 +203,7 @@ class Stencils:
         bc = np.zeros(128, dtype=np.uint8) if bc_kind is None else np.asarray(bc_kind, dtype=np.uint8)
         for i in range(128):
             p.bc_kind[i] = int(bc[i])
+        p.support = self.support
         self.prm = p
         self.handle = C.c_void_p(None)
         self.rebuild(pos, mask, normal)
@@ -483,6 +488,40 @@ def make_body(centre, radius, body_id, vel=(0.0, 0.0), acc=(0.0, 0.0)) -> c_body
     b.vel[0], b.vel[1], b.vel[2] = float(vel[0]), float(vel[1]), 0.0
     b.acc[0], b.acc[1], b.acc[2] = float(acc[0]), float(acc[1]), 0.0
     return b
+
+
+def make_bodies(bodies, accs=None):
+    """C array of bodies from [(id, centre, radius)] (and per-body accelerations)."""
+    arr = (c_body * len(bodies))()
+    for b, (bid, c, R) in enumerate(bodies):
+        arr[b] = make_body(c, R, bid, acc=(0.0, 0.0) if accs is None else accs[b])
+    return arr
+
+
+def update_dps_bodies(mesh, bodies, pos, mask, mask_prev, kappa=0.2, n_relax=10, band=None,
+                      alpha=0.0):
+    """One DP update (Sec. 2.2-2.4, nearest SDF of Sec. 2.5) for the bodies
+    [(id, centre, radius)], in place on pos/mask."""
+    cm = make_mesh(mesh)
+    arr = make_bodies(bodies)
+    N = mesh.n[0] * mesh.n[1]
+    band = 5.0 * mesh.l0 if band is None else band
+    _check(lib().mcd_update_dps(C.byref(cm), arr, len(bodies), _ptr(pos, torch.float64, 2 * N),
+                                _ptr(mask, torch.int8, N), _ptr(mask_prev, torch.int8, N),
+                                float(kappa), int(n_relax), float(band), float(alpha), _stream()))
+
+
+def bodies_boundary(mesh, bodies, pos, mask, accs=None, normal=None, neumann=None):
+    """Normals of every body's DPs and the Neumann data -acc . n (Eq. (23))."""
+    cm = make_mesh(mesh)
+    arr = make_bodies(bodies, accs)
+    N = mesh.n[0] * mesh.n[1]
+    n = torch.empty(2 * N, dtype=torch.float64, device=pos.device) if normal is None else normal
+    f = torch.empty(N, dtype=torch.float64, device=pos.device) if neumann is None else neumann
+    _check(lib().mcd_bodies_boundary(C.byref(cm), arr, len(bodies), _ptr(pos, torch.float64, 2 * N),
+                                     _ptr(mask, torch.int8, N), _ptr(n, torch.float64, 2 * N),
+                                     _ptr(f, torch.float64, N), _stream()))
+    return n, f
 
 
 def update_dps(mesh, centre, radius, body_id, pos, mask, mask_prev, kappa=0.2, n_relax=10,
