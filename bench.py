@@ -51,10 +51,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mcd", choices=["mcd", "reference"])
-    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "batched", "cnn"],
+    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "batched", "cnn", "array"],
                     help="cylinder: the 1024^2 moving-cylinder step (the metric's workload); "
                          "batched: 256 independent Poisson systems of log-uniform size 32^2..512^2; "
-                         "cnn: the warm-start network's inference and training step on an n^2 grid")
+                         "cnn: the warm-start network's inference and training step on an n^2 grid; "
+                         "array: the 25-cylinder array (multiple stationary cylinders), 3x3 against "
+                         "the expanded 9x9 stencil, on an n^2 grid (n = 128 is the paper's l0)")
     ap.add_argument("--profile-solve", action="store_true",
                     help="run one mixed solve of the cylinder system from p = 0 (for a profiler) "
                          "and print its iteration count")
@@ -707,6 +709,136 @@ def cnn_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# Algorithmic bytes per DP-iteration of the persistent solve: two SpMVs read
+# the S-slot rows, plus 68 (FP32) / 136 (FP64) bytes of vectors.
+def solve_bytes_per_dp_iter(S, fp64):
+    return 2 * S * (8 if fp64 else 4) + (136 if fp64 else 68)
+
+
+def array_arm(args):
+    """The multiple-stationary-cylinder experiment of Sec. 4.1 (the cost
+    contrast of its Table 1): a 5 x 5 cylinder array in the square of side 2
+    on an n x n mesh, gaps 12 and 2 (units of the paper's l0 = 1/64),
+    Neumann cylinders, Dirichlet walls, the smooth synthetic source.  DPs
+    from the multi-body DP update (10 relaxation sweeps).  For the 3x3
+    stencil (cos^2 weight, r_e = 2.5 l0) and the expanded 9x9 stencil
+    (least-squares MPS weight, r_e = 3.5 l0): the stencil build and PPE solves
+    from p = 0 at the paper's tolerance 1e-2 and at --tol, mixed and FP64,
+    each timed with CUDA events after warm-up, L2 flushed before each."""
+    import torch
+
+    from paper_2404_17542_gb300 import build, inputs, mcd
+    build.build()
+    mcd.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    n = args.n
+    hbm = None
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        hbm = json.load(open(pk)).get("hbm_gbs")
+
+    def d(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    def timed(f, steps):
+        for _ in range(max(1, args.warmup)):
+            f()
+        tot, out = 0.0, None
+        for _ in range(steps):
+            flush_buf.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            out = f()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / steps, out
+
+    stencils = {"3x3": dict(weight_kind=mcd.W_COS2, r_e=2.5, support=1),
+                "9x9": dict(weight_kind=mcd.W_LSMPS, r_e=3.5, support=4)}
+    results = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = mcd.launch_count()
+    for gap in (12, 2):
+        pb = inputs.cylinder_array_box(n, gap)
+        bodies = pb.meta["bodies"]
+        l0 = pb.mesh.l0
+        pos, mask = d(pb.pos.ravel()), d(pb.mask)
+        prev = torch.empty_like(mask)
+        mcd.update_dps_bodies(pb.mesh, bodies, pos, mask, prev, n_relax=10, band=0.0)
+        normal, _f = mcd.bodies_boundary(pb.mesh, bodies, pos, mask)
+        m = mask.cpu().numpy()
+        unknowns = int((m != 0).sum())
+        rhs = d(np.where(m == -1, pb.rhs, 0.0))
+        bnd = torch.zeros(pb.mesh.N, dtype=torch.float64, device=dev)
+        porosity = 1.0 - math.pi * (2 * bodies[0][2]) ** 2 * len(bodies) / 16.0   # Sec. 4.1, L = 1
+        for name, sp in stencils.items():
+            st = mcd.Stencils(pb.mesh, pos, mask, normal, bc_kind=pb.bc_kind, weight_kind=sp["weight_kind"],
+                              r_e=sp["r_e"] * l0, precision=mcd.MIXED, want_derivs=False,
+                              support=sp["support"])
+            if st.check()[0] != 0:
+                raise RuntimeError(f"singular stencil in the {name} array system")
+            ms_build, _ = timed(lambda: st.rebuild(pos, mask, normal), max(1, args.steps))
+            p = torch.zeros(pb.mesh.N, dtype=torch.float64, device=dev)
+            for tol in (1e-2, args.tol):
+                for mode, mname in ((mcd.MIXED, "mixed"), (mcd.FP64, "fp64")):
+                    def one():
+                        p.zero_()
+                        return st.solve(rhs, bnd, p=p, tol=tol, mode=mode)[1]
+                    ms, info = timed(one, max(1, args.steps))
+                    S = st.S
+                    gbs = solve_bytes_per_dp_iter(S, mode == mcd.FP64) * pb.mesh.N * info["iters"] / (ms / 1e3) / 1e9
+                    results.append({"gap_l0": gap, "stencil": name, "tol": tol, "mode": mname,
+                                    "iters": int(info["iters"]), "rel_res": float(info["rel_res"]),
+                                    "fallback": int(info.get("fallback", 0)),
+                                    "solve_ms": round(ms, 3), "build_ms": round(ms_build, 3),
+                                    "dp_unknowns_per_s": unknowns / (ms / 1e3),
+                                    "solve_gbs": round(gbs, 1),
+                                    "solve_hbm_frac": round(gbs / hbm, 4) if hbm else None})
+            del st
+        results_gap = [r for r in results if r["gap_l0"] == gap]
+        for r in results_gap:
+            r["unknowns"] = unknowns
+            r["porosity"] = round(porosity, 4)
+    clk = clocks.stop()
+    launches = mcd.launch_count() - launches0
+
+    def pick(gap, stencil, tol, mode):
+        return next(r for r in results if r["gap_l0"] == gap and r["stencil"] == stencil and r["tol"] == tol
+                    and r["mode"] == mode)
+    contrast = []
+    for gap in (12, 2):
+        for tol in (1e-2, args.tol):
+            a, b = pick(gap, "3x3", tol, "mixed"), pick(gap, "9x9", tol, "mixed")
+            contrast.append({"gap_l0": gap, "tol": tol, "iters_3x3": a["iters"], "iters_9x9": b["iters"],
+                             "iters_ratio": round(b["iters"] / max(1, a["iters"]), 3),
+                             "time_ratio_solve": round(b["solve_ms"] / a["solve_ms"], 3),
+                             "time_ratio_build_plus_solve": round((b["solve_ms"] + b["build_ms"]) /
+                                                                  (a["solve_ms"] + a["build_ms"]), 3)})
+    main = pick(12, "3x3", args.tol, "mixed")
+    main_S = 9
+    ach = solve_bytes_per_dp_iter(main_S, False) * n * n * main["iters"] / (main["solve_ms"] / 1e3) / 1e9
+    line = {"metric": "PPE DP-unknowns solved/s, 25-cylinder array (Sec. 4.1)", "value": main["dp_unknowns_per_s"],
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup),
+            "ms_per_step": main["solve_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 Krylov + f64 refinement", "data": "synthetic",
+            "config": {"workload": f"5x5 stationary cylinder array, side 2, {n}x{n} mesh (l0 = {2.0 / n:g}), "
+                                   "gaps 12 and 2 x (1/64), Neumann cylinders, Dirichlet walls; "
+                                   "value: 3x3 cos^2 stencil, gap 12, mixed, tol " + f"{args.tol:g}",
+                       "l2": "flushed before every timed build and solve (256 MB write)"},
+            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(ach / hbm, 4) if hbm else None,
+                         "algorithmic": f"{solve_bytes_per_dp_iter(main_S, False)} B per DP-iteration "
+                                        f"x {n * n} DPs x iterations"},
+            "table1_contrast": contrast, "results": results, "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def profile_solve(args):
     """One mixed solve of the cylinder system at step 1 from p = 0."""
     import torch
@@ -730,6 +862,8 @@ def main():
         batched_arm(args)
     elif args.workload == "cnn":
         cnn_arm(args)
+    elif args.workload == "array":
+        array_arm(args)
     else:
         gpu_arm(args)
 

@@ -369,39 +369,53 @@ __device__ __forceinline__ T stencil_apply(const T *w, const T *tile, int lx, in
 }
 
 // stencil_apply for wide stencils (81 weights per row): each weight is read
-// from the slot-major rows just before it is used, instead of staging the
-// whole row in registers.  Same arithmetic and summation order.
+// from the slot-major rows where it is used, instead of staging the whole
+// row in registers.  The FP32 difference form keeps the compensated
+// (double-float) sum, but over NA independent (hi, lo) accumulators (slot s
+// goes to accumulator s % NA), merged with TwoSum at the end: one chain of 80
+// dependent TwoSums left the SM waiting on latency.
 template <int G, typename T>
 __device__ __forceinline__ T stencil_apply_rows(const T *__restrict__ row, int64_t N, int64_t k, const T *tile,
                                                 int lx, int ly, int lz) {
     using HD = HaloDims<G>;
     constexpr int C = HD::S / 2, W = Shape<G>::W;
     const T xk = tile[tile_centre<G>(lx, ly, lz)];
+    const T *rk = row + k;
     if (sizeof(T) == 4) {
-        float hi = (float)__ldg(row + (int64_t)C * N + k) * (float)xk, lo = 0.0f;
-#pragma unroll 9
+        constexpr int NA = 4;
+        float hi[NA], lo[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) { hi[a] = 0.0f; lo[a] = 0.0f; }
+        hi[C % NA] = (float)__ldg(rk + (int64_t)C * N) * (float)xk;   // centre weight is 0 or 1: exact
+#pragma unroll
         for (int s = 0; s < HD::S; ++s) {
             if (s == C) continue;
             const int ox = s % W, oy = (s / W) % W, oz = s / (W * W);
             const int h = (lx + ox) + HD::HX * ((ly + oy) + HD::HY * (lz + oz));
-            const float ws = (float)__ldg(row + (int64_t)s * N + k);
+            const float ws = (float)__ldg(rk + (int64_t)s * N);
             const float d = __fsub_rn((float)tile[h], (float)xk);
             const float p = __fmul_rn(ws, d);
             const float pe = __fmaf_rn(ws, d, -p);
             float e;
-            two_sum(hi, p, hi, e);
-            lo = __fadd_rn(lo, __fadd_rn(e, pe));
+            two_sum(hi[s % NA], p, hi[s % NA], e);
+            lo[s % NA] = __fadd_rn(lo[s % NA], __fadd_rn(e, pe));
         }
-        return (T)__fadd_rn(hi, lo);
+        float h01, e01, h23, e23, hs, es;
+        two_sum(hi[0], hi[1], h01, e01);
+        two_sum(hi[2], hi[3], h23, e23);
+        two_sum(h01, h23, hs, es);
+        const float lsum = __fadd_rn(__fadd_rn(__fadd_rn(lo[0], lo[1]), __fadd_rn(lo[2], lo[3])),
+                                     __fadd_rn(__fadd_rn(e01, e23), es));
+        return (T)__fadd_rn(hs, lsum);
     }
-    T acc = (T)0;
-#pragma unroll 9
+    T acc[3] = {(T)0, (T)0, (T)0};
+#pragma unroll
     for (int s = 0; s < HD::S; ++s) {
         const int ox = s % W, oy = (s / W) % W, oz = s / (W * W);
         const int h = (lx + ox) + HD::HX * ((ly + oy) + HD::HY * (lz + oz));
-        acc += __ldg(row + (int64_t)s * N + k) * tile[h];
+        acc[s % 3] += __ldg(rk + (int64_t)s * N) * tile[h];
     }
-    return acc;
+    return (acc[0] + acc[1]) + acc[2];
 }
 
 // Row weights of DP k into registers (zeros for k < 0).
