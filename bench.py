@@ -61,6 +61,8 @@ def parse_args():
                     help="run one mixed solve of the cylinder system from p = 0 (for a profiler) "
                          "and print its iteration count")
     ap.add_argument("--n", type=int, default=1024, help="background mesh cells per side")
+    ap.add_argument("--support", type=int, default=1, choices=[1, 4],
+                    help="with --profile-solve --workload array: 1 = 3x3 stencil, 4 = 9x9 stencil")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -840,12 +842,33 @@ def array_arm(args):
 
 
 def profile_solve(args):
-    """One mixed solve of the cylinder system at step 1 from p = 0."""
+    """One mixed solve of the cylinder system at step 1 from p = 0 (or, with
+    --workload array, of the 25-cylinder array system, gap 12, on the stencil
+    --support selects)."""
     import torch
 
     from paper_2404_17542_gb300 import build, inputs, mcd
     build.build()
     mcd.lib()
+    if args.workload == "array":
+        dev = torch.device("cuda", 0)
+        pb = inputs.cylinder_array_box(args.n, 12)
+        bodies = pb.meta["bodies"]
+        pos = torch.from_numpy(pb.pos.ravel().copy()).to(dev)
+        mask = torch.from_numpy(pb.mask.copy()).to(dev)
+        mcd.update_dps_bodies(pb.mesh, bodies, pos, mask, torch.empty_like(mask), n_relax=10, band=0.0)
+        normal, _f = mcd.bodies_boundary(pb.mesh, bodies, pos, mask)
+        wide = args.support == 4
+        st = mcd.Stencils(pb.mesh, pos, mask, normal, bc_kind=pb.bc_kind,
+                          weight_kind=mcd.W_LSMPS if wide else mcd.W_COS2,
+                          r_e=(3.5 if wide else 2.5) * pb.mesh.l0, want_derivs=False, support=args.support)
+        m = mask.cpu().numpy()
+        rhs = torch.from_numpy(np.where(m == -1, pb.rhs, 0.0)).to(dev)
+        bnd = torch.zeros_like(rhs)
+        _p, info = st.solve(rhs, bnd, tol=args.tol, mode=mcd.MIXED)
+        print(json.dumps({"iters": info["iters"], "fallback": info["fallback"], "dps": pb.mesh.N,
+                          "rel_res": info["rel_res"], "support": args.support}), flush=True)
+        return
     run = CylinderRun(args.n, torch.device("cuda", 0), mcd, inputs, args.tol)
     info = run.step(mcd.MIXED)
     print(json.dumps({"iters": info["iters"], "fallback": info["fallback"], "dps": run.N,
