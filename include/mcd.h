@@ -365,6 +365,49 @@ mcd_status mcd_body_boundary(const mcd_mesh *mesh, const mcd_body *body,
                              mcd_stream_t stream);
 
 /* -------------------------------------------------------------------------
+ * ALE step and fluid force (Sec. 3.3, Eq. (19), Appendix A; Sec. 3.4)
+ * ---------------------------------------------------------------------- */
+
+/* mcd_ale_interpolate - the step-k velocity (u_dev, v_dev, float64 [N]) at
+ * the step-(k+1) DP positions (Eq. (19) with p = 2):
+ *   u~ = u + dx u_x + dy u_y + (dx^2 u_xx + 2 dx dy u_xy + dy^2 u_yy) / 2
+ * with the derivatives of the step-k chi=1 quadratic MLS fit (vel_k: a 2D
+ * 3x3 handle built with want_derivs = 1 on pos_k_dev / mask_k_dev, every
+ * boundary a Dirichlet boundary), (dx, dy) = x^{k+1} - x_src^k:
+ *  - DP inner at k and k+1: src = the DP itself (Eq. (A.1));
+ *  - DP inner at k+1 only (role changed): src = the DP at the centre of its
+ *    support shifted by (sign n_x, sign n_y) cells, n the outward normal of
+ *    the body of bodies_k nearest its step-k position (Eq. (A.2)); if src is
+ *    not inner at step k the DP keeps its step-k value and *fallbacks_dev
+ *    (int32 device counter, may be NULL) is incremented;
+ *  - DPs not inner at k+1 keep their step-k values.
+ * pos_* float64 [2][N]; mask_* int8 [N]; the outputs must not alias the
+ * inputs.  MCD_ENOTSUP for other stencil shapes.  Asynchronous. */
+mcd_status mcd_ale_interpolate(const mcd_stencils *vel_k, const mcd_body *bodies_k, int nbodies,
+                               const double *pos_k_dev, const double *pos_k1_dev,
+                               const int8_t *mask_k_dev, const int8_t *mask_k1_dev,
+                               const double *u_dev, const double *v_dev,
+                               double *u_out_dev, double *v_out_dev, int *fallbacks_dev,
+                               mcd_stream_t stream);
+
+/* mcd_fluid_force - force of the fluid on the DPs with mask == body_id
+ * (Eq. (30)): F = sum_i t_i dGamma_i, t = (-P I + mu (grad u + grad u^T)) . n
+ * with n = normal_dev (float64 [2][N], outward from the body).  P and
+ * grad u at a boundary DP come from the chi=1 quadratic fit of the DP at
+ * the centre of its support shifted by (sign n_x, sign n_y) cells (Sec.
+ * 3.4); the pressure fit includes the Neumann data bnd_dev (the boundary
+ * data given to the solve; required when pres has Neumann ids).  dGamma_i
+ * (Eq. (31)) is half the sum of the distances to the nearest DP of the same
+ * id on each side of the tangent (-n_y, n_x) within the 5x5 cells around
+ * it.  pres / vel: 2D 3x3 handles with want_derivs = 1 on the same cloud.
+ * out_host[4] = {F_x, F_y, sum dGamma, DPs skipped because their shifted
+ * centre is not an inner DP}.  Synchronises the stream. */
+mcd_status mcd_fluid_force(const mcd_stencils *pres, const mcd_stencils *vel, int body_id,
+                           const double *pos_dev, const int8_t *mask_dev, const double *normal_dev,
+                           const double *P_dev, const double *bnd_dev, const double *u_dev,
+                           const double *v_dev, double mu, double *out_host, mcd_stream_t stream);
+
+/* -------------------------------------------------------------------------
  * Batched systems (an addition: the paper solves one system at a time)
  *
  * `count` independent 2D systems (Sec. 2.2 meshes, Dirichlet boundary ids

@@ -116,6 +116,49 @@ __device__ __forceinline__ int nb_coord(int c, int o, int n, int per, double len
     return v;
 }
 
+// Circular bodies of a DP update (Sec. 2.5), passed to kernels by value.
+struct Circle {
+    int id;
+    double cx, cy, R;
+};
+
+// The bodies of one update, passed by value as a kernel parameter.
+struct Bodies {
+    int n;
+    Circle c[MCD_MAX_BODIES];
+};
+
+// Circle SDF psi = |x - c| - R with every operation rounded on its own.
+__device__ __forceinline__ double circle_psi(double x, double y, const Circle &b) {
+    const double dx = __dsub_rn(x, b.cx);
+    const double dy = __dsub_rn(y, b.cy);
+    return __dsub_rn(__dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy))), b.R);
+}
+
+// Index of the body whose SDF has the smallest magnitude at (x, y), the
+// first on a tie (Sec. 2.5); its SDF value in *psi.
+__device__ __forceinline__ int nearest_body(const Bodies &B, double x, double y, double *psi) {
+    int best = 0;
+    double bp = circle_psi(x, y, B.c[0]);
+    for (int b = 1; b < B.n; ++b) {
+        const double p = circle_psi(x, y, B.c[b]);
+        if (fabs(p) < fabs(bp)) { best = b; bp = p; }
+    }
+    *psi = bp;
+    return best;
+}
+
+__device__ __forceinline__ int body_with_id(const Bodies &B, int id) {
+    for (int b = 0; b < B.n; ++b)
+        if (B.c[b].id == id) return b;
+    return -1;
+}
+
+// Checks a body list (2D mesh, 1..MCD_MAX_BODIES bodies, distinct ids in
+// 2..127, positive radii) and packs it for the kernels (update.cu).
+mcd_status pack_bodies(const char *who, const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
+                       Bodies *out);
+
 // Add n to the launch counter (launches made by a CUDA graph replay).
 void count_launches(long long n);
 

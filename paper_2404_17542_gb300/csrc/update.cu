@@ -21,43 +21,6 @@
 
 namespace mcd {
 
-struct Circle {
-    int id;
-    double cx, cy, R;
-};
-
-// The bodies of one update, passed by value as a kernel parameter.
-struct Bodies {
-    int n;
-    Circle c[MCD_MAX_BODIES];
-};
-
-// Circle SDF psi = |x - c| - R with every operation rounded on its own.
-__device__ __forceinline__ double circle_psi(double x, double y, const Circle &b) {
-    const double dx = __dsub_rn(x, b.cx);
-    const double dy = __dsub_rn(y, b.cy);
-    return __dsub_rn(__dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy))), b.R);
-}
-
-// Index of the body whose SDF has the smallest magnitude at (x, y), the
-// first on a tie (Sec. 2.5); its SDF value in *psi.
-__device__ __forceinline__ int nearest_body(const Bodies &B, double x, double y, double *psi) {
-    int best = 0;
-    double bp = circle_psi(x, y, B.c[0]);
-    for (int b = 1; b < B.n; ++b) {
-        const double p = circle_psi(x, y, B.c[b]);
-        if (fabs(p) < fabs(bp)) { best = b; bp = p; }
-    }
-    *psi = bp;
-    return best;
-}
-
-__device__ __forceinline__ int body_with_id(const Bodies &B, int id) {
-    for (int b = 0; b < B.n; ++b)
-        if (B.c[b].id == id) return b;
-    return -1;
-}
-
 // Vertex (i, j) has psi >= 0 for its nearest body (tested as d^2 >= R^2).
 __device__ __forceinline__ bool vertex_fluid(double ox, double oy, double l0, int i, int j, const Bodies &B) {
     const double vx = __dadd_rn(ox, __dmul_rn((double)i, l0));
@@ -203,7 +166,7 @@ __global__ void body_bc_kernel(Geo g, Bodies bodies, BodyAcc acc, const double *
 }
 
 // Checks the body list of an update and packs it for the kernels.
-static mcd_status pack_bodies(const char *who, const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
+mcd_status pack_bodies(const char *who, const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
                               Bodies *out) {
     if (mesh->dim != 2) {
         set_error(std::string(who) + ": 2D only");

@@ -94,6 +94,9 @@ _SIGS = {
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
     "mcd_bodies_boundary": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mcd_ale_interpolate": (C.c_int, [C.c_void_p, C.POINTER(c_body), C.c_int] + [C.c_void_p] * 10),
+    "mcd_fluid_force": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int] + [C.c_void_p] * 7
+                        + [C.c_double, C.POINTER(C.c_double), C.c_void_p]),
     "mcd_flow_predict": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_double, C.c_double]
                          + [C.c_void_p] * 3 + [C.c_void_p]),
     "mcd_flow_project": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.c_double]
@@ -522,6 +525,36 @@ def bodies_boundary(mesh, bodies, pos, mask, accs=None, normal=None, neumann=Non
                                      _ptr(mask, torch.int8, N), _ptr(n, torch.float64, 2 * N),
                                      _ptr(f, torch.float64, N), _stream()))
     return n, f
+
+
+def ale_interpolate(vel_k, bodies_k, pos_k, pos_k1, mask_k, mask_k1, u, v):
+    """Step-k velocity at the step-(k+1) positions (Eq. (19), Appendix A).
+    Returns (u~, v~, number of fallbacks)."""
+    N = vel_k.N
+    uo = torch.empty_like(u)
+    vo = torch.empty_like(v)
+    fb = torch.zeros(1, dtype=torch.int32, device=u.device)
+    arr = make_bodies(bodies_k)
+    _check(lib().mcd_ale_interpolate(vel_k.handle, arr, len(bodies_k), _ptr(pos_k, torch.float64, 2 * N),
+                                     _ptr(pos_k1, torch.float64, 2 * N), _ptr(mask_k, torch.int8, N),
+                                     _ptr(mask_k1, torch.int8, N), _ptr(u, torch.float64, N),
+                                     _ptr(v, torch.float64, N), _ptr(uo, torch.float64, N),
+                                     _ptr(vo, torch.float64, N), _ptr(fb, torch.int32, 1), _stream()))
+    return uo, vo, int(fb.item())
+
+
+def fluid_force(pres, vel, body_id, pos, mask, normal, P, bnd, u, v, mu):
+    """Force of the fluid on body `body_id` (Eqs. (30)-(31)).
+    Returns ((F_x, F_y), sum dGamma, skipped DPs)."""
+    N = pres.N
+    out = (C.c_double * 4)()
+    _check(lib().mcd_fluid_force(pres.handle, vel.handle, int(body_id), _ptr(pos, torch.float64, 2 * N),
+                                 _ptr(mask, torch.int8, N), _ptr(normal, torch.float64, 2 * N),
+                                 _ptr(P, torch.float64, N),
+                                 _ptr(bnd, torch.float64, N) if bnd is not None else C.c_void_p(None),
+                                 _ptr(u, torch.float64, N), _ptr(v, torch.float64, N), float(mu), out,
+                                 _stream()))
+    return (out[0], out[1]), out[2], int(out[3])
 
 
 def update_dps(mesh, centre, radius, body_id, pos, mask, mask_prev, kappa=0.2, n_relax=10,
