@@ -358,6 +358,15 @@ mcd_status mcd_bodies_boundary(const mcd_mesh *mesh, const mcd_body *bodies, int
                                double *normal_dev, double *neumann_dev,
                                mcd_stream_t stream);
 
+/* mcd_bodies_velocity - the boundary velocity of every DP (the velocity
+ * boundary data of mcd_flow_predict / mcd_flow_project): a DP with the id of
+ * bodies[b] takes bodies[b].vel (a translating rigid body, Eqs. (24)-(25)
+ * without rotation), every other DP (domain walls included) 0.
+ * ubc_dev, vbc_dev float64 [N].  2D only.  Asynchronous. */
+mcd_status mcd_bodies_velocity(const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
+                               const int8_t *mask_dev, double *ubc_dev, double *vbc_dev,
+                               mcd_stream_t stream);
+
 /* mcd_body_boundary - mcd_bodies_boundary for the single body *body. */
 mcd_status mcd_body_boundary(const mcd_mesh *mesh, const mcd_body *body,
                              const double *pos_dev, const int8_t *mask_dev,

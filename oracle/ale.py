@@ -165,3 +165,62 @@ def fluid_force(mesh, pos, mask, body_id, normal, P, bnd_p, u, v, mu, Wp, Wv, nb
         F[0] += tx * dG                                        # Eq. (30)
         F[1] += ty * dG
     return F, perim, skipped
+
+
+def boundary_velocity(mask, bodies_vel):
+    """(ubc, vbc): the velocity (vx, vy) of the body whose id a DP carries,
+    0 at every other DP; bodies_vel = [(id, (vx, vy))]."""
+    ubc = np.zeros(mask.shape[0])
+    vbc = np.zeros(mask.shape[0])
+    for bid, V in bodies_vel:
+        sel = mask == bid
+        ubc[sel] = V[0]
+        vbc[sel] = V[1]
+    return ubc, vbc
+
+
+def moving_step(mesh, pos_k, mask_k, u_k, v_k, Wv_k, bodies_k, bodies_k1, V_k, V_k1, dt, nu,
+                weight_kind=0, r_e=None, kappa=0.2, n_relax=10, band=None):
+    """One moving-boundary fractional step in the order of Sec. 3.3.
+
+    bodies_k, bodies_k1: [(id, centre, radius)] at t_k and t_{k+1}; V_k, V_k1:
+    their translational velocities [(vx, vy)]; Wv_k: the step-k velocity
+    weights.
+      1. DP update to the bodies at t_{k+1} (Sec. 2.3-2.4);
+      2. u~ = u^k(x^{k+1}) (Eq. (19), Appendix A);
+      3. MLS weights of the step-(k+1) cloud: velocity (every boundary a
+         Dirichlet boundary) and pressure (bodies Neumann, walls Dirichlet);
+      4. u* and the PPE source (Eqs. (20)-(21)) with the bodies' velocities
+         on their DPs and 0 on the walls;
+      5. the PPE (direct solve) with dP/dn = -dV/dt . n on the bodies,
+         dV/dt = (V^{k+1} - V^k) / dt (Eqs. (23), (29)), P = 0 on the walls;
+      6. u^{k+1} = u* - dt grad P (Eq. (22));
+      7. the force on each body (Eqs. (30)-(31)), mu = nu (unit density).
+    Returns a dict with pos, mask, u, v, P, F {id: (F, perimeter, skipped)},
+    Wv (the step-(k+1) velocity weights), normal, fallbacks.
+    """
+    from . import flow, mls, solve
+    from . import mask as omask
+    pos1, mask1, _prev = omask.update_dps_bodies(mesh, pos_k, mask_k, bodies_k1, kappa, n_relax, band)
+    ut, fb = ale_interpolate(mesh, pos_k, pos1, mask_k, mask1, u_k, Wv_k, bodies_k)
+    vt, _ = ale_interpolate(mesh, pos_k, pos1, mask_k, mask1, v_k, Wv_k, bodies_k)
+    normal = omask.bodies_normals(pos1, mask1, bodies_k1)
+    bc_p = np.zeros(128, dtype=np.uint8)
+    for bid, _c, _R in bodies_k1:
+        bc_p[bid] = 1
+    Wv = mls.build_weights(mesh, pos1, mask1, weight_kind=weight_kind, r_e=r_e)
+    Wp = mls.build_weights(mesh, pos1, mask1, normal, bc_p, weight_kind, r_e)
+    ubc, vbc = boundary_velocity(mask1, [(b[0], V) for b, V in zip(bodies_k1, V_k1)])
+    us, vs, src = flow.predict(mesh, Wv, ut, vt, ubc, vbc, nu, dt, mask1)
+    bnd = np.zeros(mesh.N)
+    for (bid, _c, _R), V0, V1 in zip(bodies_k1, V_k, V_k1):
+        sel = mask1 == bid
+        ax, ay = (V1[0] - V0[0]) / dt, (V1[1] - V0[1]) / dt
+        bnd[sel] = -(ax * normal[0, sel] + ay * normal[1, sel])
+    A = solve.assemble(mesh, Wp["row"])
+    b = solve.form_rhs(mesh, Wp["kind"], Wp["QL"], src, bnd, Wp["rscale"])
+    P = solve.direct_solve(A, b)
+    u1, v1 = flow.project(mesh, Wp, P, bnd, us, vs, ubc, vbc, dt, mask1)
+    F = {bid: fluid_force(mesh, pos1, mask1, bid, normal, P, bnd, u1, v1, nu, Wp, Wv)
+         for bid, _c, _R in bodies_k1}
+    return dict(pos=pos1, mask=mask1, u=u1, v=v1, P=P, F=F, Wv=Wv, normal=normal, fallbacks=fb)

@@ -139,7 +139,7 @@ __global__ void relax_kernel(Geo g, Bodies bodies, double band, double kappa, do
     pout[N + k] = fmin(fmax(sy, loy), hiy);
 }
 
-// Body accelerations for the Neumann datum, in body order.
+// One 2D vector per body (accelerations or velocities), in body order.
 struct BodyAcc {
     double a[MCD_MAX_BODIES][2];
 };
@@ -163,6 +163,17 @@ __global__ void body_bc_kernel(Geo g, Bodies bodies, BodyAcc acc, const double *
     nrm[k] = nx;
     nrm[N + k] = ny;
     if (neu) neu[k] = -(ax * nx + ay * ny);                            // Eq. (23)
+}
+
+// Boundary velocity of every DP: that of the body whose id it carries (a
+// translating rigid body, Eqs. (24)-(25) without rotation), 0 elsewhere.
+__global__ void body_vel_kernel(int64_t N, Bodies bodies, BodyAcc vel, const int8_t *__restrict__ mask,
+                                double *__restrict__ ubc, double *__restrict__ vbc) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int b = mask[k] >= 1 ? body_with_id(bodies, mask[k]) : -1;
+    ubc[k] = b >= 0 ? vel.a[b][0] : 0.0;
+    vbc[k] = b >= 0 ? vel.a[b][1] : 0.0;
 }
 
 // Checks the body list of an update and packs it for the kernels.
@@ -273,6 +284,26 @@ extern "C" mcd_status mcd_bodies_boundary(const mcd_mesh *mesh, const mcd_body *
     const unsigned blocks = (unsigned)((g.N + 255) / 256);
     MCD_KLAUNCH(MCD_K_OTHER, stream, body_bc_kernel<<<blocks, 256, 0, stream>>>(g, bl, acc, pos_dev, mask_dev,
                                                                               normal_dev, neumann_dev));
+    MCD_LAUNCH_CHECK();
+    return MCD_OK;
+}
+
+extern "C" mcd_status mcd_bodies_velocity(const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
+                                          const int8_t *mask_dev, double *ubc_dev, double *vbc_dev,
+                                          mcd_stream_t stream) {
+    MCD_CHECK_ARG(mesh && bodies && mask_dev && ubc_dev && vbc_dev, "NULL argument");
+    Bodies bl;
+    mcd_status st = pack_bodies("mcd_bodies_velocity", mesh, bodies, nbodies, &bl);
+    if (st != MCD_OK) return st;
+    BodyAcc vel;
+    for (int b = 0; b < nbodies; ++b) {
+        vel.a[b][0] = bodies[b].vel[0];
+        vel.a[b][1] = bodies[b].vel[1];
+    }
+    const Geo g = make_geo(*mesh);
+    const unsigned blocks = (unsigned)((g.N + 255) / 256);
+    MCD_KLAUNCH(MCD_K_OTHER, stream, body_vel_kernel<<<blocks, 256, 0, stream>>>(g.N, bl, vel, mask_dev, ubc_dev,
+                                                                               vbc_dev));
     MCD_LAUNCH_CHECK();
     return MCD_OK;
 }

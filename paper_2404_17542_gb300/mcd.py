@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "MCD_OK", 1: "MCD_EINVAL", 2: "MCD_ENOMEM", 3: "MCD_ECUDA", 4
 FP64, MIXED = 0, 1
 DT_F64, DT_F32 = 0, 1
 W_GAUSS, W_COS2, W_LSMPS = 0, 1, 2
+BC_DIRICHLET, BC_NEUMANN = 0, 1
 ARR_ROW64, ARR_ROW32, ARR_QL64, ARR_D64, ARR_QD64, ARR_RSCALE, ARR_KIND = range(7)
 
 
@@ -94,6 +95,8 @@ _SIGS = {
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
     "mcd_bodies_boundary": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mcd_bodies_velocity": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_int, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p]),
     "mcd_ale_interpolate": (C.c_int, [C.c_void_p, C.POINTER(c_body), C.c_int] + [C.c_void_p] * 10),
     "mcd_fluid_force": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int] + [C.c_void_p] * 7
                         + [C.c_double, C.POINTER(C.c_double), C.c_void_p]),
@@ -493,12 +496,26 @@ def make_body(centre, radius, body_id, vel=(0.0, 0.0), acc=(0.0, 0.0)) -> c_body
     return b
 
 
-def make_bodies(bodies, accs=None):
-    """C array of bodies from [(id, centre, radius)] (and per-body accelerations)."""
+def make_bodies(bodies, accs=None, vels=None):
+    """C array of bodies from [(id, centre, radius)] (and per-body
+    accelerations and velocities)."""
     arr = (c_body * len(bodies))()
     for b, (bid, c, R) in enumerate(bodies):
-        arr[b] = make_body(c, R, bid, acc=(0.0, 0.0) if accs is None else accs[b])
+        arr[b] = make_body(c, R, bid, vel=(0.0, 0.0) if vels is None else vels[b],
+                           acc=(0.0, 0.0) if accs is None else accs[b])
     return arr
+
+
+def bodies_velocity(mesh, bodies, vels, mask, ubc=None, vbc=None):
+    """Boundary velocity of every DP: its body's velocity, 0 elsewhere."""
+    cm = make_mesh(mesh)
+    arr = make_bodies(bodies, vels=vels)
+    N = mesh.n[0] * mesh.n[1]
+    ubc = torch.empty(N, dtype=torch.float64, device=mask.device) if ubc is None else ubc
+    vbc = torch.empty(N, dtype=torch.float64, device=mask.device) if vbc is None else vbc
+    _check(lib().mcd_bodies_velocity(C.byref(cm), arr, len(bodies), _ptr(mask, torch.int8, N),
+                                     _ptr(ubc, torch.float64, N), _ptr(vbc, torch.float64, N), _stream()))
+    return ubc, vbc
 
 
 def update_dps_bodies(mesh, bodies, pos, mask, mask_prev, kappa=0.2, n_relax=10, band=None,
@@ -632,3 +649,72 @@ def launch_count() -> int:
 
 def version():
     return lib().mcd_version().decode()
+
+
+class AleFlow:
+    """Moving-boundary fractional steps on the device, in the order of
+    Sec. 3.3; every stage is one call of the C ABI.
+
+    bodies_at(t) -> ([(id, centre, radius)], [(vx, vy)]): the circular
+    bodies and their translational velocities at time t.  The state (DP
+    positions and masks, u, v, P) lives in device tensors; the velocity
+    stencils of the current step are kept for the next step's ALE
+    interpolation.  Per step:
+      1. DP update to the bodies at t + dt (band 5 l0);
+      2. u~ = u(x^{k+1}) (Eq. (19), Appendix A);
+      3. velocity and pressure stencils of the new cloud;
+      4. boundary velocities, u* and the PPE source (Eqs. (20)-(21));
+      5. the PPE with dP/dn = -(V^{k+1} - V^k)/dt . n on the bodies
+         (Eqs. (23), (29)), warm-started from the previous P;
+      6. u^{k+1} = u* - dt grad P (Eq. (22));
+      7. the force on every body (Eqs. (30)-(31)), mu = nu.
+    """
+
+    def __init__(self, mesh, pos, mask, bodies_at, nu, dt, t0=0.0, weight_kind=W_GAUSS, r_e=None,
+                 precision=MIXED, mode=MIXED, tol=1e-8, kappa=0.2, n_relax=10, band=None):
+        self.mesh, self.bodies_at, self.nu, self.dt, self.t = mesh, bodies_at, nu, dt, t0
+        self.kappa, self.n_relax = kappa, n_relax
+        self.band = 5.0 * mesh.l0 if band is None else band
+        self.mode, self.tol = mode, tol
+        self.kw = dict(weight_kind=weight_kind, r_e=r_e)
+        self.precision = precision
+        self.N = mesh.n[0] * mesh.n[1]
+        dev = pos.device
+        self.pos, self.mask = pos, mask
+        self.prev = torch.empty_like(mask)
+        geo, _vel = bodies_at(t0)
+        update_dps_bodies(mesh, geo, self.pos, self.mask, self.prev, kappa, n_relax, band=0.0)
+        self.vel = Stencils(mesh, self.pos, self.mask, want_derivs=True, precision=FP64, **self.kw)
+        self.pres = None
+        z = lambda: torch.zeros(self.N, dtype=torch.float64, device=dev)  # noqa: E731
+        self.u, self.v, self.P = z(), z(), z()
+        self.info = {}
+
+    def step(self):
+        mesh, dt = self.mesh, self.dt
+        geo_k, V_k = self.bodies_at(self.t)
+        geo_1, V_1 = self.bodies_at(self.t + dt)
+        pos_k, mask_k = self.pos.clone(), self.mask.clone()
+        update_dps_bodies(mesh, geo_1, self.pos, self.mask, self.prev, self.kappa, self.n_relax, self.band)
+        ut, vt, fallbacks = ale_interpolate(self.vel, geo_k, pos_k, self.pos, mask_k, self.mask, self.u, self.v)
+        self.vel.rebuild(self.pos, self.mask)
+        accs = [((b[0] - a[0]) / dt, (b[1] - a[1]) / dt) for a, b in zip(V_k, V_1)]
+        normal, bnd = bodies_boundary(mesh, geo_1, self.pos, self.mask, accs=accs)
+        if self.pres is None:
+            bc = np.zeros(128, dtype=np.uint8)
+            for bid, _c, _R in geo_1:
+                bc[bid] = BC_NEUMANN
+            self.pres = Stencils(mesh, self.pos, self.mask, normal, bc_kind=bc, want_derivs=True,
+                                 precision=self.precision, **self.kw)
+        else:
+            self.pres.rebuild(self.pos, self.mask, normal)
+        ubc, vbc = bodies_velocity(mesh, geo_1, V_1, self.mask)
+        us, vs, src = self.vel.flow_predict(ut, vt, ubc, vbc, self.nu, dt)
+        _p, info = self.pres.solve(src, bnd, p=self.P, tol=self.tol, mode=self.mode)
+        self.u, self.v = self.pres.flow_project(self.P, bnd, us, vs, ubc, vbc, dt)
+        forces = {bid: fluid_force(self.pres, self.vel, bid, self.pos, self.mask, normal, self.P, bnd,
+                                   self.u, self.v, self.nu) for bid, _c, _R in geo_1}
+        self.t += dt
+        self.normal, self.bnd = normal, bnd
+        self.info = dict(solve=info, fallbacks=fallbacks, forces=forces)
+        return self.info
