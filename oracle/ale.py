@@ -43,7 +43,7 @@ import math
 import numpy as np
 
 from .flow import derivatives, neighbour_table, neumann_terms
-from .mask import nearest_body
+from .mask import nearest_body, psi_grad
 
 INNER = -1
 
@@ -70,12 +70,10 @@ def shifted_centre(mesh, k, nx_, ny_):
 
 
 def body_normal(bodies, x, y):
-    """Outward unit normal of the body nearest (x, y) (its circle SDF gradient)."""
+    """Outward unit normal grad psi / |grad psi| of the body nearest (x, y)."""
     b = nearest_body(bodies, x, y)[0]
-    _bid, c, _R = bodies[b]
-    dx, dy = x - c[0], y - c[1]
-    d = math.sqrt(dx * dx + dy * dy)
-    return (dx / d, dy / d) if d > 0.0 else (0.0, 0.0)
+    _psi, unit = psi_grad(bodies[b], x, y)
+    return unit if unit is not None else (0.0, 0.0)
 
 
 def ale_interpolate(mesh, pos_k, pos_k1, mask_k, mask_k1, u_k, Wv_k, bodies_k, nbr=None):

@@ -30,7 +30,10 @@ Readings (the paper leaves them open):
   * cells with a face on the domain wall keep the wall id and never move;
   * a fixed number n_relax of Jacobi sweeps (all DPs read iterate k);
   * a DP whose cell becomes void is reset to its centroid;
-  * relocation and the boundary-fitted move use the analytic circle SDF;
+  * relocation and the boundary-fitted move use the analytic circle SDF, or
+    for a body given by a discrete SDF (oracle.sdf.SdfBody, Sec. 2.5) its
+    interpolated psi and grad psi: d^ = -grad psi / |grad psi|; its vertex
+    test is psi >= 0 of the interpolated psi;
   * with several bodies: a vertex is classified by the SDF of its nearest
     body (smallest |psi|, the first body in list order on a tie, psi
     evaluated as sqrt(dx*dx + dy*dy) - R with each operation rounded on its
@@ -51,6 +54,14 @@ import numpy as np
 INNER, VOID = -1, 0
 
 
+def is_sdf(b):
+    return hasattr(b, "eval")
+
+
+def body_id_of(b):
+    return b.id if is_sdf(b) else b[0]
+
+
 def as_bodies(centre, radius, body_id):
     """The body list [(id, centre, radius)] of one circular body."""
     return [(body_id, (float(centre[0]), float(centre[1])), float(radius))]
@@ -60,18 +71,34 @@ def nearest_body(bodies, x, y):
     """(index, psi): the body whose circle SDF has the smallest magnitude at
     (x, y), the first in list order on a tie (Sec. 2.5)."""
     best, best_psi = 0, None
-    for b, (_bid, c, R) in enumerate(bodies):
-        dx = x - c[0]
-        dy = y - c[1]
-        psi = math.sqrt(dx * dx + dy * dy) - R
+    for b, body in enumerate(bodies):
+        if is_sdf(body):
+            psi = body.eval(x, y)[0]
+        else:
+            _bid, c, R = body
+            dx = x - c[0]
+            dy = y - c[1]
+            psi = math.sqrt(dx * dx + dy * dy) - R
         if best_psi is None or abs(psi) < abs(best_psi):
             best, best_psi = b, psi
     return best, best_psi
 
 
+def psi_grad(body, x, y):
+    """(psi, unit direction of grad psi or None) of one body at (x, y)."""
+    if is_sdf(body):
+        psi, g = body.eval(x, y)
+        n = math.sqrt(g[0] * g[0] + g[1] * g[1])
+        return psi, ((g[0] / n, g[1] / n) if n > 0.0 and math.isfinite(psi) else None)
+    _bid, c, R = body
+    dx, dy = x - c[0], y - c[1]
+    d = math.sqrt(dx * dx + dy * dy)
+    return d - R, ((dx / d, dy / d) if d > 0.0 else None)
+
+
 def body_index(bodies, body_id):
-    for b, (bid, _c, _R) in enumerate(bodies):
-        if bid == body_id:
+    for b, body in enumerate(bodies):
+        if body_id_of(body) == body_id:
             return b
     return None
 
@@ -88,6 +115,9 @@ def vertex_fluid_bodies(mesh, bodies):
         for j in range(ny + 1):
             vy = oy + float(j) * l0
             b = nearest_body(bodies, vx, vy)[0] if len(bodies) > 1 else 0
+            if is_sdf(bodies[b]):
+                out[i, j] = bodies[b].eval(vx, vy)[0] >= 0.0
+                continue
             _bid, c, R = bodies[b]
             dx = vx - c[0]
             dy = vy - c[1]
@@ -143,7 +173,7 @@ def remask_bodies(mesh, mask, bodies, band):
                 continue
             cnt = int(fl[i, j]) + int(fl[i + 1, j]) + int(fl[i, j + 1]) + int(fl[i + 1, j + 1])
             cx, cy = centroid(mesh, i, j)
-            bid = bodies[nearest_body(bodies, cx, cy)[0]][0]
+            bid = body_id_of(bodies[nearest_body(bodies, cx, cy)[0]])
             new[i + nx * j] = cell_mask_from_count(cnt, bid)
     return new
 
@@ -195,16 +225,9 @@ def relax_sweep_bodies(mesh, pos, mask, movable, bodies, kappa, alpha=0.0,
             b = nearest_body(bodies, xs[0], xs[1])[0] if len(bodies) > 1 else 0
         else:
             b = None
-        if b is not None:
-            _bid, centre, radius = bodies[b]
-            dxc = xs[0] - centre[0]
-            dyc = xs[1] - centre[1]
-            dist = math.sqrt(dxc * dxc + dyc * dyc)
-        else:
-            dist = 0.0
-        if dist > 0.0:
-            psi = dist - radius
-            dhat = np.array([-dxc / dist, -dyc / dist])   # -grad psi / |grad psi|
+        psi, unit = psi_grad(bodies[b], xs[0], xs[1]) if b is not None else (0.0, None)
+        if unit is not None:
+            dhat = np.array([-unit[0], -unit[1]])          # -grad psi / |grad psi|
             if mask[k] >= 1:
                 xs = xs + psi * dhat                       # Eq. (9)
             elif psi < r_e_fit:
@@ -266,9 +289,17 @@ def circle_normals(pos, mask, centre, body_id):
 
 
 def bodies_normals(pos, mask, bodies):
-    """circle_normals of every body, each on the DPs carrying its id."""
+    """Unit normal grad psi / |grad psi| of every body on the DPs carrying its
+    id (for a circle (x - c)/|x - c|); zero elsewhere."""
     n = np.zeros_like(pos)
-    for bid, c, _R in bodies:
+    for body in bodies:
+        if is_sdf(body):
+            for k in np.nonzero(mask == body.id)[0]:
+                _psi, unit = psi_grad(body, pos[0, k], pos[1, k])
+                if unit is not None:
+                    n[:, k] = unit
+            continue
+        bid, c, _R = body
         sel = mask == bid
         d = pos[:, sel] - np.array(c)[:, None]
         n[:, sel] = d / np.sqrt((d * d).sum(axis=0))

@@ -285,6 +285,34 @@ def cylinder_array_box(n: int, gap_cells: float, count: int = 5, side: float = 2
     return pb
 
 
+def sample_sdf_grid(psi_local, origin, h: float, n):
+    """SDF samples of a body in its own frame: grid[j, i] = psi_local(x, y)
+    at (x, y) = origin + (i, j) h, n = (n_x, n_y) points (data for a body
+    described by a discrete SDF, psi > 0 in the fluid)."""
+    nx, ny = n
+    xs = origin[0] + h * np.arange(nx)
+    ys = origin[1] + h * np.arange(ny)
+    X, Y = np.meshgrid(xs, ys)
+    return np.ascontiguousarray(psi_local(X, Y), dtype=np.float64)
+
+
+def circle_sdf(radius: float):
+    """psi(x, y) = |x| - R of a circle centred at the local origin."""
+    return lambda x, y: np.sqrt(x * x + y * y) - radius
+
+
+def ellipse_sdf(a: float, b: float):
+    """A signed distance-like function of the ellipse (x/a)^2 + (y/b)^2 = 1
+    (local frame): the level-set function scaled to unit gradient on the
+    ellipse, (r - 1) / |grad r| with r = sqrt((x/a)^2 + (y/b)^2); exact on
+    the boundary, a smooth approximation off it."""
+    def psi(x, y):
+        r = np.sqrt((x / a) ** 2 + (y / b) ** 2)
+        g = np.sqrt((x / (a * a)) ** 2 + (y / (b * b)) ** 2) / np.maximum(r, 1e-300)
+        return (r - 1.0) / np.maximum(g, 1e-300)
+    return psi
+
+
 def ppe_source(pos: np.ndarray, t: float):
     """Smooth synthetic interior source for the pressure Poisson equation,
     standing in for div(u*)/dt of a flow step: O(1) amplitude, a few
