@@ -278,10 +278,21 @@ mcd_status mcd_flow_project(const mcd_stencils *pst, const double *P_dev,
  * Moving-boundary DP update (Sec. 2.2-2.4)
  * ---------------------------------------------------------------------- */
 
-/* A rigid circular body (2D) at the new time: boundary id (>= 2; id 1 is
- * the domain wall), centre c, radius, translational velocity and
- * acceleration (the paper's V_trans and dV_trans/dt, Eqs. (24)-(29); a
- * circle needs no rotation). */
+/* A rigid body (2D) at the new time: boundary id (>= 2; id 1 is the domain
+ * wall), centre c, translational velocity and acceleration (the paper's
+ * V_trans and dV_trans/dt, Eqs. (24)-(29)), posture angle theta, angular
+ * velocity omega and acceleration omega_dot.
+ *  sdf_dev == NULL: a circle of `radius` about c (analytic SDF).
+ *  sdf_dev != NULL: a body given by SDF samples (Sec. 2.5), device float64
+ *    [sdf_n[1]][sdf_n[0]], psi > 0 in the fluid, at
+ *    sdf_origin + (i, j) sdf_h in the body's local frame; a world point x
+ *    has local coordinates R(-theta) (x - c).  psi and grad psi at a point
+ *    come from the chi = 1 quadratic MLS fit centred at the nearest grid
+ *    point over its 3x3 grid support (cos^2 weight, r_e = 2.5 sdf_h,
+ *    r_s = sdf_h), evaluated at the point; outside the box of grid points
+ *    1 .. n - 2 psi is +inf, so the grid has to cover the DP band around
+ *    the body.  The array must stay valid until the call's kernels finish.
+ * Fields left zero give a circle without rotation. */
 #define MCD_MAX_BODIES 64   /* bodies per call of the functions below */
 typedef struct {
     int id;
@@ -289,6 +300,13 @@ typedef struct {
     double radius;
     double vel[3];
     double acc[3];
+    double theta;
+    double omega;
+    double omega_dot;
+    const double *sdf_dev;
+    int sdf_n[2];
+    double sdf_origin[2];
+    double sdf_h;
 } mcd_body;
 
 /* mcd_update_dps - one DP update for the body positions of the new step.
@@ -346,12 +364,13 @@ mcd_status mcd_update_dps_static(const mcd_mesh *mesh, const mcd_body *bodies,
 
 /* mcd_bodies_boundary - boundary data of the DPs of every body (mask == id
  * of bodies[b], 1 <= nbodies <= MCD_MAX_BODIES, distinct ids in 2..127):
- *  normal_dev  float64 [2][N]: unit normal n = (x - c)/|x - c| of the DP's
- *              body (the analytic gradient of the circle SDF, Sec. 2.5); 0
- *              at every other DP;
+ *  normal_dev  float64 [2][N]: unit normal grad psi / |grad psi| of the
+ *              DP's body (Sec. 2.5; (x - c)/|x - c| for a circle); 0 at
+ *              every other DP;
  *  neumann_dev float64 [N] or NULL: the pressure Neumann datum of Eq. (23),
- *              dP/dn = -(dV/dt) . n with dV/dt = that body's acc; 0 at every
- *              other DP.
+ *              dP/dn = -(dV/dt) . n with the rigid-body
+ *              dV/dt = acc + omega_dot x r + omega x (omega x r), r = x - c
+ *              (Eqs. (26)-(29)); 0 at every other DP.
  * 2D only.  Asynchronous. */
 mcd_status mcd_bodies_boundary(const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
                                const double *pos_dev, const int8_t *mask_dev,
@@ -359,13 +378,13 @@ mcd_status mcd_bodies_boundary(const mcd_mesh *mesh, const mcd_body *bodies, int
                                mcd_stream_t stream);
 
 /* mcd_bodies_velocity - the boundary velocity of every DP (the velocity
- * boundary data of mcd_flow_predict / mcd_flow_project): a DP with the id of
- * bodies[b] takes bodies[b].vel (a translating rigid body, Eqs. (24)-(25)
- * without rotation), every other DP (domain walls included) 0.
- * ubc_dev, vbc_dev float64 [N].  2D only.  Asynchronous. */
+ * boundary data of mcd_flow_predict / mcd_flow_project): a DP at x with the
+ * id of bodies[b] takes V = vel + omega x (x - c) (Eqs. (24)-(25)), every
+ * other DP (domain walls included) 0.  pos_dev float64 [2][N]; ubc_dev,
+ * vbc_dev float64 [N].  2D only.  Asynchronous. */
 mcd_status mcd_bodies_velocity(const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
-                               const int8_t *mask_dev, double *ubc_dev, double *vbc_dev,
-                               mcd_stream_t stream);
+                               const double *pos_dev, const int8_t *mask_dev, double *ubc_dev,
+                               double *vbc_dev, mcd_stream_t stream);
 
 /* mcd_body_boundary - mcd_bodies_boundary for the single body *body. */
 mcd_status mcd_body_boundary(const mcd_mesh *mesh, const mcd_body *body,

@@ -92,9 +92,10 @@ __global__ void __launch_bounds__(256) ale_kernel(const __grid_constant__ AleArg
     if (a.mask_k[k] != -1) {
         // moved into the fluid: the support shifted along the body normal
         const double x = a.pos_k[k], y = a.pos_k[N + k];
-        double psi;
-        const Circle &b = a.bodies.c[nearest_body(a.bodies, x, y, &psi)];
-        src = shifted_centre(a.g, k, sgn(x - b.cx), sgn(y - b.cy));    // Eq. (A.2)
+        double psi, ux = 0.0, uy = 0.0;
+        const BodyDev &b = a.bodies.c[nearest_body(a.bodies, x, y, &psi)];
+        if (!body_psi_dir(a.bodies, b, x, y, &psi, &ux, &uy)) { ux = 0.0; uy = 0.0; }
+        src = shifted_centre(a.g, k, sgn(ux), sgn(uy));               // Eq. (A.2)
         if (a.mask_k[src] != -1) {
             if (a.fallbacks) atomicAdd(a.fallbacks, 1);
             return;

@@ -117,31 +117,112 @@ __device__ __forceinline__ int nb_coord(int c, int o, int n, int per, double len
 }
 
 // Circular bodies of a DP update (Sec. 2.5), passed to kernels by value.
-struct Circle {
+// A body of a DP update (Sec. 2.5): a circle of radius R about (cx, cy), or
+// (sdf != NULL) SDF samples sdf[j * nx + i] at (ox, oy) + (i, j) h in the
+// body's local frame, placed at (cx, cy) with posture angle theta
+// (ct = cos theta, st = sin theta).  omega / omega_dot: angular velocity and
+// acceleration (boundary velocity and Neumann datum).
+struct BodyDev {
     int id;
+    int nx, ny;
     double cx, cy, R;
+    double ct, st;
+    const double *sdf;
+    double ox, oy, h;
+    double omega, omega_dot;
 };
 
-// The bodies of one update, passed by value as a kernel parameter.
+// The bodies of one update, passed by value as a kernel parameter, with the
+// weights Z (5 x 9) of the chi = 1 quadratic fit over a 3x3 lattice in units
+// of its spacing (cos^2 weight, r_e = 2.5 spacings), shared by every SDF grid.
 struct Bodies {
     int n;
-    Circle c[MCD_MAX_BODIES];
+    double Z[45];
+    BodyDev c[MCD_MAX_BODIES];
 };
 
 // Circle SDF psi = |x - c| - R with every operation rounded on its own.
-__device__ __forceinline__ double circle_psi(double x, double y, const Circle &b) {
+__device__ __forceinline__ double circle_psi(double x, double y, const BodyDev &b) {
     const double dx = __dsub_rn(x, b.cx);
     const double dy = __dsub_rn(y, b.cy);
     return __dsub_rn(__dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy))), b.R);
+}
+
+// psi and the world-frame grad psi of an SDF-grid body: the chi = 1
+// quadratic fit centred at the grid point nearest the point (clamped so that
+// its 3x3 support lies in the grid), evaluated at the point.  psi = +inf and
+// grad = 0 outside the box of grid points 1 .. n - 2.
+__device__ inline double sdf_eval(const BodyDev &b, const double *Z, double x, double y, double *gx, double *gy) {
+    const double dx = __dsub_rn(x, b.cx), dy = __dsub_rn(y, b.cy);
+    const double xl = __dadd_rn(__dmul_rn(b.ct, dx), __dmul_rn(b.st, dy));
+    const double yl = __dadd_rn(__dmul_rn(-b.st, dx), __dmul_rn(b.ct, dy));
+    const double fx = __ddiv_rn(__dsub_rn(xl, b.ox), b.h);
+    const double fy = __ddiv_rn(__dsub_rn(yl, b.oy), b.h);
+    *gx = 0.0;
+    *gy = 0.0;
+    if (!(fx >= 1.0 && fx <= (double)(b.nx - 2) && fy >= 1.0 && fy <= (double)(b.ny - 2))) return INFINITY;
+    int i = (int)floor(fx + 0.5), j = (int)floor(fy + 0.5);
+    i = i < 1 ? 1 : (i > b.nx - 2 ? b.nx - 2 : i);
+    j = j < 1 ? 1 : (j > b.ny - 2 ? b.ny - 2 : j);
+    const double ps = b.sdf[(int64_t)j * b.nx + i];
+    double d[9];
+#pragma unroll
+    for (int s = 0; s < 9; ++s)
+        d[s] = __dsub_rn(b.sdf[(int64_t)(j + s / 3 - 1) * b.nx + (i + s % 3 - 1)], ps);
+    double Phi[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        double acc = 0.0;
+#pragma unroll
+        for (int s = 0; s < 9; ++s) acc = __dadd_rn(acc, __dmul_rn(Z[q * 9 + s], d[s]));
+        Phi[q] = acc;
+    }
+    const double X = __dsub_rn(fx, (double)i), Y = __dsub_rn(fy, (double)j);
+    const double psi = ps + Phi[0] * X + Phi[1] * Y + 0.5 * Phi[2] * X * X + Phi[3] * X * Y + 0.5 * Phi[4] * Y * Y;
+    const double gxl = (Phi[0] + Phi[2] * X + Phi[3] * Y) / b.h;
+    const double gyl = (Phi[1] + Phi[3] * X + Phi[4] * Y) / b.h;
+    *gx = b.ct * gxl - b.st * gyl;
+    *gy = b.st * gxl + b.ct * gyl;
+    return psi;
+}
+
+// SDF value of body b at (x, y).
+__device__ __forceinline__ double body_psi(const Bodies &B, const BodyDev &b, double x, double y) {
+    if (!b.sdf) return circle_psi(x, y, b);
+    double gx, gy;
+    return sdf_eval(b, B.Z, x, y, &gx, &gy);
+}
+
+// psi of body b at (x, y) and the unit vector along grad psi (false if it
+// is undefined: the point at a circle's centre, outside an SDF grid, or a
+// vanishing gradient).  Circles: the analytic (x - c) / |x - c|.
+__device__ inline bool body_psi_dir(const Bodies &B, const BodyDev &b, double x, double y, double *psi,
+                                    double *ux, double *uy) {
+    if (!b.sdf) {
+        const double dx = x - b.cx, dy = y - b.cy;
+        const double d = sqrt(dx * dx + dy * dy);
+        *psi = d - b.R;
+        if (!(d > 0.0)) return false;
+        *ux = dx / d;
+        *uy = dy / d;
+        return true;
+    }
+    double gx, gy;
+    *psi = sdf_eval(b, B.Z, x, y, &gx, &gy);
+    const double g = sqrt(gx * gx + gy * gy);
+    if (!(g > 0.0) || !isfinite(*psi)) return false;
+    *ux = gx / g;
+    *uy = gy / g;
+    return true;
 }
 
 // Index of the body whose SDF has the smallest magnitude at (x, y), the
 // first on a tie (Sec. 2.5); its SDF value in *psi.
 __device__ __forceinline__ int nearest_body(const Bodies &B, double x, double y, double *psi) {
     int best = 0;
-    double bp = circle_psi(x, y, B.c[0]);
+    double bp = body_psi(B, B.c[0], x, y);
     for (int b = 1; b < B.n; ++b) {
-        const double p = circle_psi(x, y, B.c[b]);
+        const double p = body_psi(B, B.c[b], x, y);
         if (fabs(p) < fabs(bp)) { best = b; bp = p; }
     }
     *psi = bp;
@@ -155,7 +236,8 @@ __device__ __forceinline__ int body_with_id(const Bodies &B, int id) {
 }
 
 // Checks a body list (2D mesh, 1..MCD_MAX_BODIES bodies, distinct ids in
-// 2..127, positive radii) and packs it for the kernels (update.cu).
+// 2..127, positive radii of circles, SDF grids of at least 3 x 3 points
+// with a positive spacing) and packs it for the kernels (update.cu).
 mcd_status pack_bodies(const char *who, const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
                        Bodies *out);
 

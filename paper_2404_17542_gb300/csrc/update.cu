@@ -15,6 +15,8 @@
 //                clamp into the cell; positions ping-pong between two buffers.
 #include <math.h>
 
+#include <cmath>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -26,7 +28,8 @@ __device__ __forceinline__ bool vertex_fluid(double ox, double oy, double l0, in
     const double vx = __dadd_rn(ox, __dmul_rn((double)i, l0));
     const double vy = __dadd_rn(oy, __dmul_rn((double)j, l0));
     double psi;
-    const Circle &b = B.c[B.n > 1 ? nearest_body(B, vx, vy, &psi) : 0];
+    const BodyDev &b = B.c[B.n > 1 ? nearest_body(B, vx, vy, &psi) : 0];
+    if (b.sdf) return body_psi(B, b, vx, vy) >= 0.0;
     const double dx = __dsub_rn(vx, b.cx);
     const double dy = __dsub_rn(vy, b.cy);
     const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
@@ -115,12 +118,9 @@ __global__ void relax_kernel(Geo g, Bodies bodies, double band, double kappa, do
         double psi_near;
         b = bodies.n > 1 ? nearest_body(bodies, sx, sy, &psi_near) : 0;
     }
-    const Circle body = bodies.c[b < 0 ? 0 : b];
-    const double dxc = sx - body.cx, dyc = sy - body.cy;
-    const double dist = (b < 0) ? 0.0 : sqrt(dxc * dxc + dyc * dyc);
-    if (dist > 0.0) {
-        const double psi = dist - body.R;
-        const double hx = -dxc / dist, hy = -dyc / dist;                // -grad psi / |grad psi|
+    double psi = 0.0, ux = 0.0, uy = 0.0;
+    if (b >= 0 && body_psi_dir(bodies, bodies.c[b], sx, sy, &psi, &ux, &uy)) {
+        const double hx = -ux, hy = -uy;                                // -grad psi / |grad psi|
         if (mk >= 1) {
             sx += psi * hx;                                             // Eq. (9)
             sy += psi * hy;
@@ -153,30 +153,67 @@ __global__ void body_bc_kernel(Geo g, Bodies bodies, BodyAcc acc, const double *
     double nx = 0.0, ny = 0.0, ax = 0.0, ay = 0.0;
     const int b = mask[k] >= 1 ? body_with_id(bodies, mask[k]) : -1;
     if (b >= 0) {
-        const Circle &body = bodies.c[b];
-        const double dx = pos[k] - body.cx, dy = pos[N + k] - body.cy;
-        const double d = sqrt(dx * dx + dy * dy);
-        if (d > 0.0) { nx = dx / d; ny = dy / d; }
-        ax = acc.a[b][0];
-        ay = acc.a[b][1];
+        const BodyDev &body = bodies.c[b];
+        double psi, ux, uy;
+        if (body_psi_dir(bodies, body, pos[k], pos[N + k], &psi, &ux, &uy)) { nx = ux; ny = uy; }
+        // dV/dt of a rigid body at x (Eqs. (26)-(29)): dV_trans/dt
+        // + domega/dt x r + omega x (omega x r), r = x - x_c
+        const double rx = pos[k] - body.cx, ry = pos[N + k] - body.cy;
+        const double w2 = body.omega * body.omega;
+        ax = acc.a[b][0] - body.omega_dot * ry - w2 * rx;
+        ay = acc.a[b][1] + body.omega_dot * rx - w2 * ry;
     }
     nrm[k] = nx;
     nrm[N + k] = ny;
     if (neu) neu[k] = -(ax * nx + ay * ny);                            // Eq. (23)
 }
 
-// Boundary velocity of every DP: that of the body whose id it carries (a
-// translating rigid body, Eqs. (24)-(25) without rotation), 0 elsewhere.
-__global__ void body_vel_kernel(int64_t N, Bodies bodies, BodyAcc vel, const int8_t *__restrict__ mask,
-                                double *__restrict__ ubc, double *__restrict__ vbc) {
+// Boundary velocity of every DP: that of the rigid body whose id it carries
+// at the DP's position, 0 elsewhere.
+__global__ void body_vel_kernel(int64_t N, Bodies bodies, BodyAcc vel, const double *__restrict__ pos,
+                                const int8_t *__restrict__ mask, double *__restrict__ ubc,
+                                double *__restrict__ vbc) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     const int b = mask[k] >= 1 ? body_with_id(bodies, mask[k]) : -1;
-    ubc[k] = b >= 0 ? vel.a[b][0] : 0.0;
-    vbc[k] = b >= 0 ? vel.a[b][1] : 0.0;
+    if (b < 0) {
+        ubc[k] = 0.0;
+        vbc[k] = 0.0;
+        return;
+    }
+    // V = V_trans + omega x r (Eqs. (24)-(25)), r = x - x_c
+    const BodyDev &body = bodies.c[b];
+    ubc[k] = vel.a[b][0] - body.omega * (pos[N + k] - body.cy);
+    vbc[k] = vel.a[b][1] + body.omega * (pos[k] - body.cx);
 }
 
 // Checks the body list of an update and packs it for the kernels.
+// Weights Z (5 x 9, slot s = (di+1) + 3 (dj+1)) of the chi = 1 quadratic fit
+// over a 3x3 lattice in units of its spacing, cos^2 weight with r_e = 2.5
+// (Eqs. (12)-(17)).  On the symmetric lattice the normal equations
+// decouple: psi_X = sum w X dpsi / sum w X^2 (likewise psi_Y), psi_XY =
+// sum w X Y dpsi / sum w X^2 Y^2, and a 2 x 2 system [[a, b], [b, a]] for
+// psi_XX, psi_YY with a = sum w X^4 / 4, b = sum w X^2 Y^2 / 4.
+static void sdf_fit_weights(double *Z) {
+    const double re = 2.5;
+    const double ca = std::cos(M_PI * 1.0 / (2.0 * re)), cd = std::cos(M_PI * std::sqrt(2.0) / (2.0 * re));
+    const double wa = ca * ca, wd = cd * cd;
+    const double a = (2.0 * wa + 4.0 * wd) / 4.0, bb = wd;
+    for (int q = 0; q < 45; ++q) Z[q] = 0.0;
+    for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di) {
+            if (di == 0 && dj == 0) continue;
+            const int s = (di + 1) + 3 * (dj + 1);
+            const double w = (di == 0 || dj == 0) ? wa : wd;
+            Z[0 * 9 + s] = w * di / (2.0 * wa + 4.0 * wd);
+            Z[1 * 9 + s] = w * dj / (2.0 * wa + 4.0 * wd);
+            Z[3 * 9 + s] = w * di * dj / (4.0 * wd);
+            const double r1 = w * di * di / 2.0, r3 = w * dj * dj / 2.0;
+            Z[2 * 9 + s] = (a * r1 - bb * r3) / (a * a - bb * bb);
+            Z[4 * 9 + s] = (a * r3 - bb * r1) / (a * a - bb * bb);
+        }
+}
+
 mcd_status pack_bodies(const char *who, const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
                               Bodies *out) {
     if (mesh->dim != 2) {
@@ -193,8 +230,13 @@ mcd_status pack_bodies(const char *who, const mcd_mesh *mesh, const mcd_body *bo
             set_error(std::string(who) + ": body id must be in 2..127");
             return MCD_EINVAL;
         }
-        if (!(bodies[b].radius > 0.0)) {
-            set_error(std::string(who) + ": body radius must be positive");
+        const mcd_body &bd = bodies[b];
+        if (!bd.sdf_dev && !(bd.radius > 0.0)) {
+            set_error(std::string(who) + ": a circle's radius must be positive");
+            return MCD_EINVAL;
+        }
+        if (bd.sdf_dev && (bd.sdf_n[0] < 3 || bd.sdf_n[1] < 3 || !(bd.sdf_h > 0.0))) {
+            set_error(std::string(who) + ": an SDF grid needs at least 3 x 3 points and a positive spacing");
             return MCD_EINVAL;
         }
         for (int a = 0; a < b; ++a)
@@ -202,8 +244,23 @@ mcd_status pack_bodies(const char *who, const mcd_mesh *mesh, const mcd_body *bo
                 set_error(std::string(who) + ": body ids must be distinct");
                 return MCD_EINVAL;
             }
-        out->c[b] = Circle{bodies[b].id, bodies[b].c[0], bodies[b].c[1], bodies[b].radius};
+        BodyDev &o = out->c[b];
+        o.id = bd.id;
+        o.nx = bd.sdf_n[0];
+        o.ny = bd.sdf_n[1];
+        o.cx = bd.c[0];
+        o.cy = bd.c[1];
+        o.R = bd.radius;
+        o.ct = std::cos(bd.theta);
+        o.st = std::sin(bd.theta);
+        o.sdf = bd.sdf_dev;
+        o.ox = bd.sdf_origin[0];
+        o.oy = bd.sdf_origin[1];
+        o.h = bd.sdf_h;
+        o.omega = bd.omega;
+        o.omega_dot = bd.omega_dot;
     }
+    sdf_fit_weights(out->Z);
     return MCD_OK;
 }
 
@@ -289,9 +346,9 @@ extern "C" mcd_status mcd_bodies_boundary(const mcd_mesh *mesh, const mcd_body *
 }
 
 extern "C" mcd_status mcd_bodies_velocity(const mcd_mesh *mesh, const mcd_body *bodies, int nbodies,
-                                          const int8_t *mask_dev, double *ubc_dev, double *vbc_dev,
-                                          mcd_stream_t stream) {
-    MCD_CHECK_ARG(mesh && bodies && mask_dev && ubc_dev && vbc_dev, "NULL argument");
+                                          const double *pos_dev, const int8_t *mask_dev, double *ubc_dev,
+                                          double *vbc_dev, mcd_stream_t stream) {
+    MCD_CHECK_ARG(mesh && bodies && pos_dev && mask_dev && ubc_dev && vbc_dev, "NULL argument");
     Bodies bl;
     mcd_status st = pack_bodies("mcd_bodies_velocity", mesh, bodies, nbodies, &bl);
     if (st != MCD_OK) return st;
@@ -302,7 +359,7 @@ extern "C" mcd_status mcd_bodies_velocity(const mcd_mesh *mesh, const mcd_body *
     }
     const Geo g = make_geo(*mesh);
     const unsigned blocks = (unsigned)((g.N + 255) / 256);
-    MCD_KLAUNCH(MCD_K_OTHER, stream, body_vel_kernel<<<blocks, 256, 0, stream>>>(g.N, bl, vel, mask_dev, ubc_dev,
+    MCD_KLAUNCH(MCD_K_OTHER, stream, body_vel_kernel<<<blocks, 256, 0, stream>>>(g.N, bl, vel, pos_dev, mask_dev, ubc_dev,
                                                                                vbc_dev));
     MCD_LAUNCH_CHECK();
     return MCD_OK;

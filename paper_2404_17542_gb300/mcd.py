@@ -69,7 +69,9 @@ class c_batch_result(C.Structure):
 
 class c_body(C.Structure):
     _fields_ = [("id", C.c_int), ("c", C.c_double * 3), ("radius", C.c_double),
-                ("vel", C.c_double * 3), ("acc", C.c_double * 3)]
+                ("vel", C.c_double * 3), ("acc", C.c_double * 3), ("theta", C.c_double),
+                ("omega", C.c_double), ("omega_dot", C.c_double), ("sdf_dev", C.c_void_p),
+                ("sdf_n", C.c_int * 2), ("sdf_origin", C.c_double * 2), ("sdf_h", C.c_double)]
 
 
 _lib = None
@@ -96,7 +98,7 @@ _SIGS = {
     "mcd_bodies_boundary": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mcd_bodies_velocity": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_body), C.c_int, C.c_void_p,
-                                      C.c_void_p, C.c_void_p, C.c_void_p]),
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mcd_ale_interpolate": (C.c_int, [C.c_void_p, C.POINTER(c_body), C.c_int] + [C.c_void_p] * 10),
     "mcd_fluid_force": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int] + [C.c_void_p] * 7
                         + [C.c_double, C.POINTER(C.c_double), C.c_void_p]),
@@ -496,25 +498,61 @@ def make_body(centre, radius, body_id, vel=(0.0, 0.0), acc=(0.0, 0.0)) -> c_body
     return b
 
 
+class SdfBody:
+    """A body given by SDF samples on a grid in its local frame (Sec. 2.5):
+    grid is a contiguous device float64 tensor [n_y][n_x] of psi (> 0 in the
+    fluid) at origin + (i, j) h; the body sits at `centre` with posture angle
+    `theta` and turns at `omega` (angular acceleration `omega_dot`)."""
+
+    def __init__(self, body_id, centre, theta, grid, origin, h, omega=0.0, omega_dot=0.0):
+        self.id = int(body_id)
+        self.centre = (float(centre[0]), float(centre[1]))
+        self.theta = float(theta)
+        if not (grid.is_cuda and grid.dtype == torch.float64 and grid.is_contiguous() and grid.dim() == 2):
+            raise ValueError("grid must be a contiguous 2D float64 CUDA tensor")
+        self.grid = grid
+        self.origin = (float(origin[0]), float(origin[1]))
+        self.h = float(h)
+        self.omega = float(omega)
+        self.omega_dot = float(omega_dot)
+
+
 def make_bodies(bodies, accs=None, vels=None):
-    """C array of bodies from [(id, centre, radius)] (and per-body
-    accelerations and velocities)."""
+    """C array of bodies from circles (id, centre, radius) and SdfBody
+    objects (and per-body accelerations and velocities)."""
     arr = (c_body * len(bodies))()
-    for b, (bid, c, R) in enumerate(bodies):
-        arr[b] = make_body(c, R, bid, vel=(0.0, 0.0) if vels is None else vels[b],
-                           acc=(0.0, 0.0) if accs is None else accs[b])
+    for b, body in enumerate(bodies):
+        vel = (0.0, 0.0) if vels is None else vels[b]
+        acc = (0.0, 0.0) if accs is None else accs[b]
+        if isinstance(body, SdfBody):
+            cb = make_body(body.centre, 0.0, body.id, vel=vel, acc=acc)
+            cb.theta, cb.omega, cb.omega_dot = body.theta, body.omega, body.omega_dot
+            cb.sdf_dev = body.grid.data_ptr()
+            cb.sdf_n[0], cb.sdf_n[1] = body.grid.shape[1], body.grid.shape[0]
+            cb.sdf_origin[0], cb.sdf_origin[1] = body.origin
+            cb.sdf_h = body.h
+            arr[b] = cb
+        else:
+            bid, c, R = body
+            arr[b] = make_body(c, R, bid, vel=vel, acc=acc)
     return arr
 
 
-def bodies_velocity(mesh, bodies, vels, mask, ubc=None, vbc=None):
-    """Boundary velocity of every DP: its body's velocity, 0 elsewhere."""
+def body_id(body):
+    return body.id if isinstance(body, SdfBody) else body[0]
+
+
+def bodies_velocity(mesh, bodies, vels, pos, mask, ubc=None, vbc=None):
+    """Boundary velocity of every DP: its rigid body's velocity at the DP,
+    0 elsewhere."""
     cm = make_mesh(mesh)
     arr = make_bodies(bodies, vels=vels)
     N = mesh.n[0] * mesh.n[1]
     ubc = torch.empty(N, dtype=torch.float64, device=mask.device) if ubc is None else ubc
     vbc = torch.empty(N, dtype=torch.float64, device=mask.device) if vbc is None else vbc
-    _check(lib().mcd_bodies_velocity(C.byref(cm), arr, len(bodies), _ptr(mask, torch.int8, N),
-                                     _ptr(ubc, torch.float64, N), _ptr(vbc, torch.float64, N), _stream()))
+    _check(lib().mcd_bodies_velocity(C.byref(cm), arr, len(bodies), _ptr(pos, torch.float64, 2 * N),
+                                     _ptr(mask, torch.int8, N), _ptr(ubc, torch.float64, N),
+                                     _ptr(vbc, torch.float64, N), _stream()))
     return ubc, vbc
 
 
@@ -702,18 +740,18 @@ class AleFlow:
         normal, bnd = bodies_boundary(mesh, geo_1, self.pos, self.mask, accs=accs)
         if self.pres is None:
             bc = np.zeros(128, dtype=np.uint8)
-            for bid, _c, _R in geo_1:
-                bc[bid] = BC_NEUMANN
+            for body in geo_1:
+                bc[body_id(body)] = BC_NEUMANN
             self.pres = Stencils(mesh, self.pos, self.mask, normal, bc_kind=bc, want_derivs=True,
                                  precision=self.precision, **self.kw)
         else:
             self.pres.rebuild(self.pos, self.mask, normal)
-        ubc, vbc = bodies_velocity(mesh, geo_1, V_1, self.mask)
+        ubc, vbc = bodies_velocity(mesh, geo_1, V_1, self.pos, self.mask)
         us, vs, src = self.vel.flow_predict(ut, vt, ubc, vbc, self.nu, dt)
         _p, info = self.pres.solve(src, bnd, p=self.P, tol=self.tol, mode=self.mode)
         self.u, self.v = self.pres.flow_project(self.P, bnd, us, vs, ubc, vbc, dt)
-        forces = {bid: fluid_force(self.pres, self.vel, bid, self.pos, self.mask, normal, self.P, bnd,
-                                   self.u, self.v, self.nu) for bid, _c, _R in geo_1}
+        forces = {body_id(b): fluid_force(self.pres, self.vel, body_id(b), self.pos, self.mask, normal, self.P,
+                                          bnd, self.u, self.v, self.nu) for b in geo_1}
         self.t += dt
         self.normal, self.bnd = normal, bnd
         self.info = dict(solve=info, fallbacks=fallbacks, forces=forces)
