@@ -63,6 +63,12 @@ def parse_args():
                     help="run one mixed solve of the cylinder system from p = 0 (for a profiler) "
                          "and print its iteration count")
     ap.add_argument("--n", type=int, default=1024, help="background mesh cells per side")
+    ap.add_argument("--bodies", default="cylinder", choices=["cylinder", "passing", "passing-sdf"],
+                    help="with --workload flow: the oscillating cylinder, or the two cylinders passing "
+                         "each other (analytic circles, or circles given as discrete SDF grids)")
+    ap.add_argument("--t0", type=float, default=None,
+                    help="with --workload flow: start time (the flow starts at rest); default 0 for the "
+                         "cylinder, 3T - 0.5 (just before the passing cylinders meet) for passing")
     ap.add_argument("--support", type=int, default=1, choices=[1, 4],
                     help="with --profile-solve --workload array: 1 = 3x3 stencil, 4 = 9x9 stencil")
     ap.add_argument("--tol", type=float, default=1e-8)
@@ -860,17 +866,46 @@ def flow_arm(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
     n = args.n
-    cyl = inputs.Cylinder()
-    pb = inputs.cylinder_box(n, cyl)
-    D, U = 2 * cyl.radius, 1.0
-    nu = U * D / 100.0
-    dt = 0.2 * pb.mesh.l0
+    if args.bodies == "cylinder":
+        cyl = inputs.Cylinder()
+        pb = inputs.cylinder_box(n, cyl)
+        D, U = 2 * cyl.radius, 1.0
+        nu = U * D / 100.0
+        dt = 0.2 * pb.mesh.l0
+        t0 = 0.0 if args.t0 is None else args.t0
+        ids = [cyl.body_id]
+        workload = f"oscillating cylinder (D = 0.1, KC = 5, Re = 100) {n}x{n}, full ALE steps from rest"
 
-    def bodies_at(t):
-        return [(cyl.body_id, cyl.centre(t), cyl.radius)], [cyl.velocity(t)]
+        def bodies_at(t):
+            return [(cyl.body_id, cyl.centre(t), cyl.radius)], [cyl.velocity(t)]
+    else:
+        cfg = inputs.PassingCylinders()
+        pb = inputs.passing_cylinders_box(cfg=cfg)
+        D, U = cfg.D, cfg.U
+        nu = U * D / 40.0
+        dt = 5e-3
+        t0 = 3 * cfg.T - 0.5 if args.t0 is None else args.t0
+        ids = [2, 3]
+        nx, ny = pb.mesh.n[0], pb.mesh.n[1]
+        workload = (f"two cylinders passing each other (D = 1, 32D x 16D closed box, Re = 40, l0 = "
+                    f"{pb.mesh.l0:.4g}, dt = 5e-3) {nx}x{ny}, full ALE steps from rest at t0 = {t0:g}")
+        if args.bodies == "passing-sdf":
+            h = 0.5 * pb.mesh.l0
+            R = 0.5 * cfg.D
+            m = int(round(5 * R / h)) + 1
+            org = (-2.5 * R, -2.5 * R)
+            grid = torch.from_numpy(inputs.sample_sdf_grid(inputs.circle_sdf(R), org, h, (m, m))).to(dev)
+            workload += f"; cylinders given as {m}x{m} SDF grids (h = l0/2)"
+
+            def bodies_at(t):
+                geo, vel = cfg.bodies(t)
+                return [mcd.SdfBody(bid, c, 0.0, grid, org, h) for bid, c, _R in geo], vel
+        else:
+            def bodies_at(t):
+                return cfg.bodies(t)
 
     flow = mcd.AleFlow(pb.mesh, torch.from_numpy(pb.pos.ravel().copy()).to(dev),
-                       torch.from_numpy(pb.mask.copy()).to(dev), bodies_at, nu, dt, tol=args.tol)
+                       torch.from_numpy(pb.mask.copy()).to(dev), bodies_at, nu, dt, t0=t0, tol=args.tol)
     for _ in range(max(1, args.warmup)):
         flow.step()
     mcd.timing_enable(1)
@@ -889,11 +924,15 @@ def flow_arm(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         tot += ms
-        F = info["forces"][cyl.body_id][0]
-        rows.append({"t": round(flow.t, 6), "ms": round(ms, 3), "iters": info["solve"]["iters"],
-                     "unknowns": info["solve"]["unknowns"], "fallback": info["solve"]["fallback"],
-                     "ale_fallbacks": info["fallbacks"],
-                     "cd": 2 * F[0] / (D * U * U), "cl": 2 * F[1] / (D * U * U)})
+        row = {"t": round(flow.t, 6), "ms": round(ms, 3), "iters": info["solve"]["iters"],
+               "unknowns": info["solve"]["unknowns"], "fallback": info["solve"]["fallback"],
+               "ale_fallbacks": info["fallbacks"]}
+        for bid in ids:
+            F = info["forces"][bid][0]
+            sfx = "" if len(ids) == 1 else f"_{bid}"
+            row["cd" + sfx] = 2 * F[0] / (D * U * U)     # Eqs. (35)-(36)
+            row["cl" + sfx] = 2 * F[1] / (D * U * U)
+        rows.append(row)
     clk = clocks.stop()
     launches = (mcd.launch_count() - launches0) / max(1, args.steps)
     solve_ms = mcd.timing_read(mcd.K_SOLVE)[1]
@@ -910,8 +949,7 @@ def flow_arm(args):
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64 stencils / ALE / driver, f32 Krylov + f64 refinement", "data": "synthetic",
-            "config": {"workload": f"oscillating cylinder (D = 0.1, KC = 5, Re = 100) {n}x{n}, full ALE steps "
-                                   "from rest", "dt": dt, "tol": args.tol,
+            "config": {"workload": workload, "dt": dt, "tol": args.tol,
                        "l2": "not flushed (per-step working set above L2)"},
             "solve_share": round(solve_ms / tot, 4) if tot else None,
             "roofline": {"bound": "hbm", "achieved": round(ach, 1) if ach else None, "peak": hbm, "unit": "GB/s",

@@ -313,6 +313,68 @@ def ellipse_sdf(a: float, b: float):
     return psi
 
 
+@dataclass
+class PassingCylinders:
+    """Two cylinders passing each other (the configuration of Sec. 4.4):
+    D = 1 in a closed box of H = 16 D by L = 32 D, lower cylinder at
+    (L_c, 0), upper at (L - L_c, H_s) at t = 0 (L_c = 8 D, H_s = 1.5 D);
+    both oscillate along x with amplitude A = 1 / (2 pi f), f = 1 / T,
+    T = 8, for two periods, then move at U = 2 pi f A = 1, the lower one
+    towards +x and the upper one towards -x.  Ids 2 (lower) and 3 (upper).
+    The box spans y in [-7.25, 8.75] (centred between the cylinders)."""
+
+    D: float = 1.0
+    L: float = 32.0
+    H: float = 16.0
+    Lc: float = 8.0
+    Hs: float = 1.5
+    T: float = 8.0
+
+    @property
+    def f(self):
+        return 1.0 / self.T
+
+    @property
+    def A(self):
+        return 1.0 / (2 * math.pi * self.f)
+
+    @property
+    def U(self):
+        return 2 * math.pi * self.f * self.A
+
+    def x_offset(self, t):
+        """Displacement and velocity of the lower cylinder (the upper one
+        moves by the opposite)."""
+        if t <= 2 * self.T:
+            w = 2 * math.pi * self.f
+            return self.A * math.sin(w * t), self.A * w * math.cos(w * t)
+        return self.U * (t - 2 * self.T), self.U
+
+    def bodies(self, t):
+        """[(id, centre, radius)] and [(vx, vy)] at time t."""
+        dx, v = self.x_offset(t)
+        R = 0.5 * self.D
+        return ([(2, (self.Lc + dx, 0.0), R), (3, (self.L - self.Lc - dx, self.Hs), R)],
+                [(v, 0.0), (-v, 0.0)])
+
+
+def passing_cylinders_box(l0: float = 2.55e-2, cfg: PassingCylinders | None = None) -> Problem:
+    """The closed box of the two passing cylinders on cells of width l0 (the
+    paper's 2.55e-2 gives 1255 x 627 cells): DPs at the centroids, Dirichlet
+    wall cells with their DPs on the walls, every other cell inner."""
+    cfg = cfg or PassingCylinders()
+    nx = int(round(cfg.L / l0))
+    ny = int(round(cfg.H / l0))
+    y0 = 0.5 * cfg.Hs - 0.5 * cfg.H
+    mesh = Mesh(dim=2, n=(nx, ny, 1), l0=cfg.L / nx, origin=(0.0, y0, 0.0))
+    pos = snap_wall_dps(mesh, mesh.centroids())
+    mask = np.full(mesh.N, INNER, dtype=np.int8)
+    mask[wall_cells(mesh)] = WALL_ID
+    pb = Problem(mesh=mesh, pos=pos, mask=mask, bc_kind=default_bc_kind(neumann_ids=(2, 3)))
+    pb.meta["passing"] = cfg
+    return pb
+
+
 def ppe_source(pos: np.ndarray, t: float):
     """Smooth synthetic interior source for the pressure Poisson equation,
     standing in for div(u*)/dt of a flow step: O(1) amplitude, a few
