@@ -148,6 +148,18 @@ def measured_peaks():
     return HBM_FALLBACK_GBS, "fallback"
 
 
+def traffic_source_sha(kernel):
+    """sha256[:16] of the kernel's translation unit: its .cu file and the
+    csrc headers it includes."""
+    csrc = os.path.join(ROOT, "paper_2404_17542_gb300", "csrc")
+    files = (["krylov.cu", "krylov_common.cuh", "common.cuh"] if kernel.startswith("bicg")
+             else ["stencils.cu", "common.cuh"])
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def committed_traffic(kernel):
     """DRAM bytes per unit of work (per DP-iteration for the solve, per DP
     for the build) from the committed ncu summary profiles/traffic.txt, if
@@ -156,9 +168,7 @@ def committed_traffic(kernel):
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    src = os.path.join(ROOT, "paper_2404_17542_gb300", "csrc",
-                       "krylov.cu" if kernel.startswith("bicg") else "stencils.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = traffic_source_sha(kernel)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 4 and parts[0] == kernel and parts[1] == sha:
