@@ -16,6 +16,7 @@
 // which sums the per-block partials in block order: deterministic results.
 // Scalars live on the device; the host polls them every few iterations, and
 // kernels launched after convergence return at once.
+#include <cuda.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -827,6 +828,8 @@ struct PArgs {
     int iter_budget;         // iterations this launch may run
     long long spin_limit;
     unsigned long long *trace;   // non-NULL: block 0 stamps phase times here
+    int tma_rows;                // wide stencils: rows streamed by TMA (tmap_rows)
+    CUtensorMap tmap_rows;       // rows as a [S][n_y][n_x] tensor, box one tile x 9 slots
 };
 
 __device__ __forceinline__ int tile_first(const PArgs &a, int block) {
@@ -1373,11 +1376,159 @@ __global__ void __launch_bounds__(256) bicg_persistent(PArgs a) {
 // breakdown), normal, and ||s|| stop (x += alpha p, r = s, then an update).
 // ===========================================================================
 
+// ---- TMA stream of wide-stencil rows -----------------------------------
+// The 81 weights of a 9x9 row come from HBM (340 MB of FP32 rows at 1024^2
+// do not stay in L2).  Instead of 81 dependent-latency loads per DP, the
+// tile's rows are streamed into shared memory by TMA in chunks of 9 slots
+// (one row of the 9x9 window) for the whole tile, NB chunks in
+// flight.  Within a phase the chunks of the block's consecutive tiles form
+// one sequence i = 9 (tile - tb) + c; buffer i % NB; the rows do not change
+// during a solve, so a chunk may be fetched any time ahead of its use.  A
+// phase consumes every chunk it issues, so nothing is in flight at a grid
+// barrier.
+template <typename T> struct RowPipe {
+    static constexpr int NB = (sizeof(T) == 4) ? 3 : 2;
+    static constexpr int SL = 9;                        // slots per chunk
+    static constexpr int TILE = 512;                    // DPs of a wide-stencil tile (64 x 8)
+    static constexpr int CHUNK = SL * TILE;             // elements per chunk
+    static constexpr unsigned BYTES = CHUNK * sizeof(T);
+    T *buf;              // NB * CHUNK elements of dynamic shared memory, [slot][y][x]
+    uint64_t *mbar;      // NB transaction barriers
+    unsigned parity;     // bit b: parity of buffer b's next completion
+    bool failed;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Thread 0: fetch chunk i of the phase (tile tb + i / 9, slots 9 (i % 9) ..)
+// into buffer i % NB.  x0 is a multiple of the tile width (64): the
+// innermost coordinate times the element size is a multiple of 16 bytes.
+template <int G, typename T>
+__device__ __forceinline__ void pipe_issue(const PArgs &a, const RowPipe<T> &pp, int tb, int i) {
+    using RP = RowPipe<T>;
+    static_assert(Shape<G>::S <= 27 || Tile<G>::X * Tile<G>::Y == RP::TILE, "a chunk holds 9 slots of one tile");
+    int x0, y0, z0;
+    tile_origin<G>(a.ta, tb + i / RP::SL, x0, y0, z0);
+    const int b = i % RP::NB;
+    const uint32_t mb = smem_addr(pp.mbar + b);
+    const uint32_t dst = smem_addr(pp.buf + (size_t)b * RP::CHUNK);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of the buffer
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(RP::BYTES) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(dst), "l"(reinterpret_cast<uint64_t>(&a.tmap_rows)), "r"(x0), "r"(y0), "r"((i % RP::SL) * RP::SL),
+        "r"(mb)
+        : "memory");
+}
+
+// Wait (bounded) for buffer b's next completion.
+template <typename T>
+__device__ __forceinline__ bool pipe_wait(RowPipe<T> &pp, int b, long long limit) {
+    const uint32_t mb = smem_addr(pp.mbar + b);
+    const uint32_t ph = (pp.parity >> b) & 1u;
+    uint32_t done = 0;
+    long long polls = 0;
+    while (!done) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mb), "r"(ph)
+            : "memory");
+        if (!done && ++polls > limit) return false;
+    }
+    pp.parity ^= 1u << b;
+    return true;
+}
+
+// Thread 0: start the phase's chunk sequence (total chunks).
+template <int G, typename T>
+__device__ __forceinline__ void pipe_start(const PArgs &a, const RowPipe<T> &pp, int tb, int total) {
+    if (threadIdx.x != 0 || pp.failed) return;
+    for (int i = 0; i < RowPipe<T>::NB && i < total; ++i) pipe_issue<G, T>(a, pp, tb, i);
+}
+
+// (A x)_k for the thread's TL::R DPs of the tile whose first chunk is i0,
+// from the shared tile of x and the streamed rows; the same arithmetic as
+// stencil_apply_rows (compensated FP32 over four accumulators, or FP64),
+// slots in chunk order.  Every thread of the block calls it.
+template <int G, typename T>
+__device__ void pipe_stencil(const PArgs &a, RowPipe<T> &pp, int tb, int i0, int total, const T *tile,
+                             const int *lx, const int *ly, T *vk) {
+    using HD = HaloDims<G>;
+    using TL = Tile<G>;
+    using RP = RowPipe<T>;
+    constexpr int C = HD::S / 2, NA = 4;
+    float hi[TL::R][NA], lo[TL::R][NA];
+    T acc[TL::R][3];
+    T xk[TL::R];
+#pragma unroll
+    for (int q = 0; q < TL::R; ++q) {
+        xk[q] = tile[tile_centre<G>(lx[q], ly[q], 0)];
+#pragma unroll
+        for (int u = 0; u < NA; ++u) { hi[q][u] = 0.0f; lo[q][u] = 0.0f; }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) acc[q][u] = (T)0;
+    }
+    for (int c = 0; c < RP::SL; ++c) {
+        const int i = i0 + c, b = i % RP::NB;
+        if (!pp.failed && !pipe_wait(pp, b, a.spin_limit)) {
+            pp.failed = true;
+            atomicExch(&a.sc->phase_err, 5);
+        }
+        const T *w = pp.buf + (size_t)b * RP::CHUNK;
+        // slot s = 9 c + sl sits at offset (sl, c) of the 9x9 window; it
+        // goes to accumulator sl % NA (a compile-time index)
+#pragma unroll
+        for (int sl = 0; sl < RP::SL; ++sl) {
+#pragma unroll
+            for (int q = 0; q < TL::R; ++q) {
+                const T ws = w[(sl * TL::Y + ly[q]) * TL::X + lx[q]];
+                const int h = (lx[q] + sl) + HD::HX * (ly[q] + c);
+                if constexpr (sizeof(T) == 4) {
+                    float p, pe;
+                    if (sl == C % RP::SL && c == C / RP::SL) {
+                        p = (float)ws * (float)xk[q];   // centre weight is 0 or 1: exact
+                        pe = 0.0f;
+                    } else {
+                        const float d = __fsub_rn((float)tile[h], (float)xk[q]);
+                        p = __fmul_rn((float)ws, d);
+                        pe = __fmaf_rn((float)ws, d, -p);
+                    }
+                    float e;
+                    two_sum(hi[q][sl % NA], p, hi[q][sl % NA], e);
+                    lo[q][sl % NA] = __fadd_rn(lo[q][sl % NA], __fadd_rn(e, pe));
+                } else {
+                    acc[q][sl % 3] += ws * tile[h];
+                }
+            }
+        }
+        __syncthreads();   // every thread is done with buffer b
+        if (threadIdx.x == 0 && !pp.failed && i + RP::NB < total) pipe_issue<G, T>(a, pp, tb, i + RP::NB);
+    }
+#pragma unroll
+    for (int q = 0; q < TL::R; ++q) {
+        if constexpr (sizeof(T) == 4) {
+            float h01, e01, h23, e23, hs, es;
+            two_sum(hi[q][0], hi[q][1], h01, e01);
+            two_sum(hi[q][2], hi[q][3], h23, e23);
+            two_sum(h01, h23, hs, es);
+            const float lsum = __fadd_rn(__fadd_rn(__fadd_rn(lo[q][0], lo[q][1]), __fadd_rn(lo[q][2], lo[q][3])),
+                                         __fadd_rn(__fadd_rn(e01, e23), es));
+            vk[q] = (T)__fadd_rn(hs, lsum);
+        } else {
+            vk[q] = (acc[q][0] + acc[q][1]) + acc[q][2];
+        }
+    }
+}
+
 enum { CA_NORMAL = 0, CA_RESTART = 1, CA_SCONV = 2 };
 
 template <int G, typename T>
 __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old, T *p_new, T *v_new,
-                         T alpha, T omega, T beta, int mode, DotAcc<T> (&dot)[3]) {
+                         T alpha, T omega, T beta, int mode, DotAcc<T> (&dot)[3], RowPipe<T> &pp) {
     using HD = HaloDims<G>;
     using TL = Tile<G>;
     constexpr int S = HD::S;
@@ -1392,6 +1543,9 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
     const T *t = (const T *)a.t;
     const int tid = threadIdx.x;
     const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
+    const bool tma = (S > 27) && a.tma_rows && mode != CA_SCONV;
+    const int total = RowPipe<T>::SL * (te - tb);
+    if (tma) pipe_start<G, T>(a, pp, tb, total);
     for (int tl = tb; tl < te; ++tl) {
         int x0, y0, z0;
         tile_origin<G>(a.ta, tl, x0, y0, z0);
@@ -1453,6 +1607,8 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
             }
         }
         __syncthreads();
+        T vks[TL::R];
+        if (tma) pipe_stencil<G, T>(a, pp, tb, RowPipe<T>::SL * (tl - tb), total, tile, lx, ly, vks);
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
             if (k[q] < 0) continue;
@@ -1475,7 +1631,7 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
                 vk = stencil_apply<G, T>(w[q], tile, lx[q], ly[q], lz[q]);
             } else {
                 if constexpr (S > 27) {
-                    vk = stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
+                    vk = tma ? vks[q] : stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
                 } else {
                     T wl[S];
                     load_row<S, T>(row, g.N, k[q], wl);
@@ -1494,7 +1650,7 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
 // Phase B of the two-barrier schedule: s = r - alpha v, t = A s; dots t.s,
 // t.t, s.s, r^.s, r^.t.
 template <int G, typename T>
-__device__ void phase_b2(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T> (&dot)[5]) {
+__device__ void phase_b2(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T> (&dot)[5], RowPipe<T> &pp) {
     using HD = HaloDims<G>;
     using TL = Tile<G>;
     constexpr int S = HD::S;
@@ -1508,6 +1664,9 @@ __device__ void phase_b2(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T>
     T *t_out = (T *)a.t;
     const int tid = threadIdx.x;
     const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
+    const bool tma = (S > 27) && a.tma_rows;
+    const int total = RowPipe<T>::SL * (te - tb);
+    if (tma) pipe_start<G, T>(a, pp, tb, total);
     for (int tl = tb; tl < te; ++tl) {
         int x0, y0, z0;
         tile_origin<G>(a.ta, tl, x0, y0, z0);
@@ -1538,6 +1697,8 @@ __device__ void phase_b2(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T>
             if (h < HD::H) tile[h] = hr[u] - alpha * hv[u];
         }
         __syncthreads();
+        T vks[TL::R];
+        if (tma) pipe_stencil<G, T>(a, pp, tb, RowPipe<T>::SL * (tl - tb), total, tile, lx, ly, vks);
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
             if (k[q] < 0) continue;
@@ -1550,7 +1711,7 @@ __device__ void phase_b2(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T>
                 tk = stencil_apply<G, T>(w[q], tile, lx[q], ly[q], lz[q]);
             } else {
                 if constexpr (S > 27) {
-                    tk = stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
+                    tk = tma ? vks[q] : stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
                 } else {
                     T wl[S];
                     load_row<S, T>(row, g.N, k[q], wl);
@@ -1568,10 +1729,28 @@ __device__ void phase_b2(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T>
     }
 }
 
+// Wide stencils ask for two blocks per SM explicitly (their accumulators
+// otherwise lead the register allocator to spill); a minimum of 0 leaves the
+// compact stencils as the compiler places them.
 template <int G, typename T>
-__global__ void __launch_bounds__(256) bicg_persistent2(PArgs a) {
+__global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent2(const __grid_constant__ PArgs a) {
     using HD = HaloDims<G>;
     __shared__ T tile[HD::H];
+    extern __shared__ __align__(128) unsigned char pipe_smem[];
+    __shared__ __align__(8) uint64_t pipe_mbar[Shape<G>::S > 27 ? RowPipe<T>::NB : 1];
+    RowPipe<T> pp;
+    pp.buf = reinterpret_cast<T *>(pipe_smem);
+    pp.mbar = pipe_mbar;
+    pp.parity = 0;
+    pp.failed = false;
+    if constexpr (Shape<G>::S > 27) {
+        if (a.tma_rows && threadIdx.x == 0) {
+            for (int b = 0; b < RowPipe<T>::NB; ++b)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(pipe_mbar + b)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
     Scalars *sc = a.sc;
     int iters = 0;
     unsigned epoch = 0;
@@ -1637,7 +1816,7 @@ __global__ void __launch_bounds__(256) bicg_persistent2(PArgs a) {
                 alpha = (T)vload(&sc->alpha); omega = (T)vload(&sc->omega); beta = (T)vload(&sc->beta);
             }
             DotAcc<T> dot[3];
-            phase_ca<G, T>(a, tile, p_old, v_old, p_new, v_new, alpha, omega, beta, mode, dot);
+            phase_ca<G, T>(a, tile, p_old, v_old, p_new, v_new, alpha, omega, beta, mode, dot, pp);
             stamp(a, it, 1);
             stamp_block(a, it);
             const double eps = a.eps_breakdown;
@@ -1686,7 +1865,7 @@ __global__ void __launch_bounds__(256) bicg_persistent2(PArgs a) {
             const int parb = vload(&sc->parity);
             const T *v_cur = (const T *)(parb ? a.v1 : a.v0);
             DotAcc<T> dot[5];
-            phase_b2<G, T>(a, tile, v_cur, alpha, dot);
+            phase_b2<G, T>(a, tile, v_cur, alpha, dot, pp);
             stamp(a, it, 3);
             if (!grid_reduce<5>(a, epoch, dot, [&](double *tot) {
                     sc->ts = tot[0];
@@ -1709,11 +1888,70 @@ __global__ void __launch_bounds__(256) bicg_persistent2(PArgs a) {
 
 // Grid of the persistent launch: every resident slot (at most one block per
 // tile).
+// Dynamic shared memory of the two-barrier kernel: the TMA row buffers of a
+// wide stencil, none otherwise.
+template <int G, typename T>
+static size_t pipe_smem_bytes(bool tma) {
+    return (Shape<G>::S > 27 && tma) ? (size_t)RowPipe<T>::NB * RowPipe<T>::BYTES : 0;
+}
+
 template <int G, typename T, int B>
-static int persistent_grid(int ntiles) {
-    static const int occ = (B == 2) ? occupancy(bicg_persistent2<G, T>) : occupancy(bicg_persistent<G, T>);
+static int persistent_grid(int ntiles, bool tma) {
+    static const int occ3 = occupancy(bicg_persistent<G, T>);
+    static int occ2[2] = {0, 0};
+    int occ = occ3;
+    if (B == 2) {
+        int &o = occ2[tma ? 1 : 0];
+        if (!o) {
+            const size_t dyn = pipe_smem_bytes<G, T>(tma);
+            if (dyn) cudaFuncSetAttribute(bicg_persistent2<G, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+            int blocks = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, bicg_persistent2<G, T>, 256, dyn) != cudaSuccess ||
+                blocks < 1)
+                blocks = 1;
+            o = blocks;
+        }
+        occ = o;
+    }
     const int maxg = std::max(1, occ * sm_count());
     return std::min(ntiles, maxg);
+}
+
+// Tensor map of the rows as a [S][n_y][n_x] tensor with a box of one tile
+// by 9 slots, for the TMA row stream of wide stencils.  False when
+// TMA cannot be used: a row stride or the slot stride is not a multiple of
+// 16 bytes, or the driver does not provide the encoder.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+template <int G, typename T>
+static bool encode_row_map(const Geo &g, const void *row, CUtensorMap *map) {
+    if (Shape<G>::S <= 27) return false;
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    if (!fn) return false;
+    const uint64_t esz = sizeof(T);
+    const uint64_t nx = (uint64_t)g.n[0], ny = (uint64_t)g.n[1];
+    if ((nx * esz) % 16 != 0 || (nx * ny * esz) % 16 != 0 || ((uintptr_t)row % 16) != 0) return false;
+    const cuuint64_t dims[3] = {nx, ny, (cuuint64_t)Shape<G>::S};
+    const cuuint64_t strides[2] = {nx * esz, nx * ny * esz};
+    const cuuint32_t box[3] = {(cuuint32_t)Tile<G>::X, (cuuint32_t)Tile<G>::Y, (cuuint32_t)RowPipe<T>::SL};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                          const_cast<void *>(row), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 // Run the whole solve in persistent launches (each bounded by an iteration
@@ -1736,7 +1974,14 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
     a.ta.ntiles = a.ta.bx * a.ta.by * a.ta.bz;
     a.ta.kind = st->has_neumann ? st->kind : nullptr;
     const bool two = prm->barriers != 3;   // default: the two-barrier schedule
-    const int grid = two ? persistent_grid<G, T, 2>(a.ta.ntiles) : persistent_grid<G, T, 3>(a.ta.ntiles);
+    memset(&a.tmap_rows, 0, sizeof(a.tmap_rows));
+    a.tma_rows = (two && encode_row_map<G, T>(g, mixed ? (const void *)st->row32 : (const void *)st->row64,
+                                               &a.tmap_rows))
+                     ? 1
+                     : 0;
+    const size_t dyn_smem = two ? pipe_smem_bytes<G, T>(a.tma_rows != 0) : 0;
+    const int grid = two ? persistent_grid<G, T, 2>(a.ta.ntiles, a.tma_rows != 0)
+                         : persistent_grid<G, T, 3>(a.ta.ntiles, false);
     a.grid = grid;
     a.row64 = st->row64;
     a.b = w->b;
@@ -1779,7 +2024,7 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
         {
             KTimer kt(MCD_K_SOLVE, stream);
             const void *kern = two ? (const void *)bicg_persistent2<G, T> : (const void *)bicg_persistent<G, T>;
-            MCD_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(256), args, 0, stream));
+            MCD_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(256), args, dyn_smem, stream));
         }
         mcd_status s = read_scalars(w, stream);
         if (s != MCD_OK) return s;

@@ -73,7 +73,11 @@ template <> struct Tile<2> {
 template <> struct Tile<3> {
     static constexpr int X = 32, Y = 4, Z = 4, R = 2, TY = 4, TZ = 2;
 };
-template <> struct Tile<9> : Tile<2> {};
+// 9x9: 64 x 8 tiles, so that each row of a tile's weights is a 256-byte
+// segment of the slot-major rows (the rows come from HBM).
+template <> struct Tile<9> {
+    static constexpr int X = 64, Y = 8, Z = 1, R = 2, TY = 4, TZ = 1;
+};
 
 // The tile plus its halo of Shape<G>::R cells on every side.
 template <int G> struct HaloDims {
