@@ -76,7 +76,7 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="time the mixed solve without the network")
-    ap.add_argument("--train-steps", type=int, default=48, help="steps whose solves train the network")
+    ap.add_argument("--train-steps", type=int, default=160, help="steps whose solves train the network")
     ap.add_argument("--train-epochs", type=int, default=10)
     return ap.parse_args()
 
