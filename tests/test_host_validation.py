@@ -2,9 +2,9 @@
 
 Every call here is rejected by the library's host code before any device
 work: bad body lists and SDF grids, stencil options (support radius, weight
-kind, periodic axes too short for the 9x9 window), the flow driver and the
-batch on wide stencils, and NULL arguments of the ALE and force entry
-points.  Pointers are placeholders that the rejected calls never touch.
+kind, periodic axes too short for the 9x9 window, the batch on wide
+stencils), and NULL arguments of the ALE and force entry points (the flow
+driver's refusal of wide stencils needs a built handle: a GPU test).  Pointers are placeholders that the rejected calls never touch.
 """
 import ctypes as C
 
