@@ -63,9 +63,10 @@ def parse_args():
                     help="run one mixed solve of the cylinder system from p = 0 (for a profiler) "
                          "and print its iteration count")
     ap.add_argument("--n", type=int, default=1024, help="background mesh cells per side")
-    ap.add_argument("--bodies", default="cylinder", choices=["cylinder", "passing", "passing-sdf"],
-                    help="with --workload flow: the oscillating cylinder, or the two cylinders passing "
-                         "each other (analytic circles, or circles given as discrete SDF grids)")
+    ap.add_argument("--bodies", default="cylinder", choices=["cylinder", "passing", "passing-sdf", "wing"],
+                    help="with --workload flow: the oscillating cylinder, the two cylinders passing "
+                         "each other (analytic circles, or circles given as discrete SDF grids), or the "
+                         "flapping elliptic wing (a rotating SDF body)")
     ap.add_argument("--t0", type=float, default=None,
                     help="with --workload flow: start time (the flow starts at rest); default 0 for the "
                          "cylinder, 3T - 0.5 (just before the passing cylinders meet) for passing")
@@ -888,6 +889,26 @@ def flow_arm(args):
 
         def bodies_at(t):
             return [(cyl.body_id, cyl.centre(t), cyl.radius)], [cyl.velocity(t)]
+    elif args.bodies == "wing":
+        wing = inputs.FlappingWing()
+        pb = inputs.flapping_wing_box(cfg=wing)
+        D, U = wing.c, 1.0
+        nu = U * D / 75.0
+        dt = math.pi / 600.0
+        t0 = 0.0 if args.t0 is None else args.t0
+        ids = [wing.body_id]
+        h = 0.5 * pb.mesh.l0
+        grid_h, org = wing.sdf_grid(h)
+        grid = torch.from_numpy(grid_h).to(dev)
+        nx, ny = pb.mesh.n[0], pb.mesh.n[1]
+        workload = (f"flapping elliptic wing (c = 1, e = 4, 16c x 16c closed box, stroke plane pi/3, "
+                    f"a0 = 2.5, theta0 = pi/4, Re = 75, l0 = {pb.mesh.l0:.4g}, dt = pi/600) {nx}x{ny}, "
+                    f"the wing as a {grid_h.shape[1]}x{grid_h.shape[0]} SDF grid, full ALE steps from rest "
+                    f"at t0 = {t0:g}")
+
+        def bodies_at(t):
+            return ([mcd.SdfBody(wing.body_id, wing.centre(t), wing.posture(t), grid, org, h,
+                                 omega=wing.omega(t))], [wing.velocity(t)])
     else:
         cfg = inputs.PassingCylinders()
         pb = inputs.passing_cylinders_box(cfg=cfg)

@@ -165,15 +165,28 @@ def fluid_force(mesh, pos, mask, body_id, normal, P, bnd_p, u, v, mu, Wp, Wv, nb
     return F, perim, skipped
 
 
-def boundary_velocity(mask, bodies_vel):
-    """(ubc, vbc): the velocity (vx, vy) of the body whose id a DP carries,
-    0 at every other DP; bodies_vel = [(id, (vx, vy))]."""
+def body_frame(body):
+    """(id, centre, angular velocity) of a circle tuple or an SDF body."""
+    if hasattr(body, "eval"):
+        return body.id, body.centre, body.omega
+    return body[0], body[1], 0.0
+
+
+def boundary_velocity(mask, bodies_vel, pos=None):
+    """(ubc, vbc): the rigid-body velocity V + omega x (x - c) (Eqs.
+    (24)-(25)) of the body whose id a DP carries, 0 at every other DP;
+    bodies_vel = [(id, (vx, vy))] or [(id, (vx, vy), omega, centre)]."""
     ubc = np.zeros(mask.shape[0])
     vbc = np.zeros(mask.shape[0])
-    for bid, V in bodies_vel:
+    for entry in bodies_vel:
+        bid, V = entry[0], entry[1]
         sel = mask == bid
         ubc[sel] = V[0]
         vbc[sel] = V[1]
+        if len(entry) > 2 and entry[2] != 0.0:
+            om, c = entry[2], entry[3]
+            ubc[sel] -= om * (pos[1, sel] - c[1])
+            vbc[sel] += om * (pos[0, sel] - c[0])
     return ubc, vbc
 
 
@@ -181,9 +194,10 @@ def moving_step(mesh, pos_k, mask_k, u_k, v_k, Wv_k, bodies_k, bodies_k1, V_k, V
                 weight_kind=0, r_e=None, kappa=0.2, n_relax=10, band=None):
     """One moving-boundary fractional step in the order of Sec. 3.3.
 
-    bodies_k, bodies_k1: [(id, centre, radius)] at t_k and t_{k+1}; V_k, V_k1:
-    their translational velocities [(vx, vy)]; Wv_k: the step-k velocity
-    weights.
+    bodies_k, bodies_k1: the bodies at t_k and t_{k+1}, circles
+    (id, centre, radius) or SDF bodies (oracle.sdf.SdfBody, with their
+    angular velocity omega); V_k, V_k1: their translational velocities
+    [(vx, vy)]; Wv_k: the step-k velocity weights.
       1. DP update to the bodies at t_{k+1} (Sec. 2.3-2.4);
       2. u~ = u^k(x^{k+1}) (Eq. (19), Appendix A);
       3. MLS weights of the step-(k+1) cloud: velocity (every boundary a
@@ -203,22 +217,29 @@ def moving_step(mesh, pos_k, mask_k, u_k, v_k, Wv_k, bodies_k, bodies_k1, V_k, V
     ut, fb = ale_interpolate(mesh, pos_k, pos1, mask_k, mask1, u_k, Wv_k, bodies_k)
     vt, _ = ale_interpolate(mesh, pos_k, pos1, mask_k, mask1, v_k, Wv_k, bodies_k)
     normal = omask.bodies_normals(pos1, mask1, bodies_k1)
+    frames_k = [body_frame(b) for b in bodies_k]
+    frames_1 = [body_frame(b) for b in bodies_k1]
     bc_p = np.zeros(128, dtype=np.uint8)
-    for bid, _c, _R in bodies_k1:
+    for bid, _c, _om in frames_1:
         bc_p[bid] = 1
     Wv = mls.build_weights(mesh, pos1, mask1, weight_kind=weight_kind, r_e=r_e)
     Wp = mls.build_weights(mesh, pos1, mask1, normal, bc_p, weight_kind, r_e)
-    ubc, vbc = boundary_velocity(mask1, [(b[0], V) for b, V in zip(bodies_k1, V_k1)])
+    ubc, vbc = boundary_velocity(mask1, [(f[0], V, f[2], f[1]) for f, V in zip(frames_1, V_k1)], pos1)
     us, vs, src = flow.predict(mesh, Wv, ut, vt, ubc, vbc, nu, dt, mask1)
     bnd = np.zeros(mesh.N)
-    for (bid, _c, _R), V0, V1 in zip(bodies_k1, V_k, V_k1):
+    for (bid, c, om1), (_b0, _c0, om0), V0, V1 in zip(frames_1, frames_k, V_k, V_k1):
         sel = mask1 == bid
-        ax, ay = (V1[0] - V0[0]) / dt, (V1[1] - V0[1]) / dt
+        # dV/dt of a rigid body (Eqs. (26)-(29)): the finite differences of
+        # V_trans and omega, plus omega x (omega x r) = -omega^2 r
+        rx, ry = pos1[0, sel] - c[0], pos1[1, sel] - c[1]
+        omd = (om1 - om0) / dt
+        ax = (V1[0] - V0[0]) / dt - omd * ry - om1 * om1 * rx
+        ay = (V1[1] - V0[1]) / dt + omd * rx - om1 * om1 * ry
         bnd[sel] = -(ax * normal[0, sel] + ay * normal[1, sel])
     A = solve.assemble(mesh, Wp["row"])
     b = solve.form_rhs(mesh, Wp["kind"], Wp["QL"], src, bnd, Wp["rscale"])
     P = solve.direct_solve(A, b)
     u1, v1 = flow.project(mesh, Wp, P, bnd, us, vs, ubc, vbc, dt, mask1)
     F = {bid: fluid_force(mesh, pos1, mask1, bid, normal, P, bnd, u1, v1, nu, Wp, Wv)
-         for bid, _c, _R in bodies_k1}
+         for bid, _c, _om in frames_1}
     return dict(pos=pos1, mask=mask1, u=u1, v=v1, P=P, F=F, Wv=Wv, normal=normal, fallbacks=fb)

@@ -375,6 +375,80 @@ def passing_cylinders_box(l0: float = 2.55e-2, cfg: PassingCylinders | None = No
     return pb
 
 
+@dataclass
+class FlappingWing:
+    """The hovering elliptic wing (the configuration of Sec. 4.6): chord
+    c = 1, aspect ratio e = 4, in a closed 16 c x 16 c box whose upper and
+    right walls are H0 = L0 = 6 c from the origin; stroke plane at
+    beta = pi / 3; a(t) = a0 / 2 (1 + cos(2 t / a0)) along it and attack
+    angle theta(t) = theta0 (1 - sin(2 t / a0 + phi)), a0 = 5 / 2,
+    theta0 = pi / 4, phi = 0; period T = pi a0.  Reading: the wing's
+    centre is a(t) (cos beta, sin beta) and its chord makes the angle
+    beta - theta(t) with the x axis.  Body id 2."""
+
+    c: float = 1.0
+    e: float = 4.0
+    L: float = 16.0
+    H0: float = 6.0
+    beta: float = math.pi / 3
+    a0: float = 2.5
+    theta0: float = math.pi / 4
+    phi: float = 0.0
+    body_id: int = BODY_ID
+
+    @property
+    def T(self):
+        return math.pi * self.a0
+
+    def a(self, t):
+        return 0.5 * self.a0 * (1.0 + math.cos(2.0 * t / self.a0))
+
+    def a_dot(self, t):
+        return -math.sin(2.0 * t / self.a0)
+
+    def theta(self, t):
+        return self.theta0 * (1.0 - math.sin(2.0 * t / self.a0 + self.phi))
+
+    def posture(self, t):
+        return self.beta - self.theta(t)
+
+    def omega(self, t):
+        """d posture / dt = -d theta / dt."""
+        return self.theta0 * (2.0 / self.a0) * math.cos(2.0 * t / self.a0 + self.phi)
+
+    def centre(self, t):
+        return (self.a(t) * math.cos(self.beta), self.a(t) * math.sin(self.beta))
+
+    def velocity(self, t):
+        return (self.a_dot(t) * math.cos(self.beta), self.a_dot(t) * math.sin(self.beta))
+
+    def sdf_grid(self, h):
+        """The wing's SDF (ellipse_sdf) sampled in its own frame, with a
+        margin of 0.3 c around it; returns (grid, origin)."""
+        ax, by = 0.5 * self.c, 0.5 * self.c / self.e
+        m = 0.3 * self.c
+        org = (-(ax + m), -(by + m))
+        n = (int(math.ceil(2 * (ax + m) / h)) + 1, int(math.ceil(2 * (by + m) / h)) + 1)
+        return sample_sdf_grid(ellipse_sdf(ax, by), org, h, n), org
+
+
+def flapping_wing_box(l0: float = 51.0 / 1600.0, cfg: FlappingWing | None = None) -> Problem:
+    """The closed box of the flapping wing on cells of width about l0 (the
+    paper's 51/1600 gives 502 x 502 cells): DPs at the centroids,
+    Dirichlet wall cells with their DPs on the walls, every other cell
+    inner."""
+    cfg = cfg or FlappingWing()
+    n = int(round(cfg.L / l0))
+    lo = cfg.H0 - cfg.L
+    mesh = Mesh(dim=2, n=(n, n, 1), l0=cfg.L / n, origin=(lo, lo, 0.0))
+    pos = snap_wall_dps(mesh, mesh.centroids())
+    mask = np.full(mesh.N, INNER, dtype=np.int8)
+    mask[wall_cells(mesh)] = WALL_ID
+    pb = Problem(mesh=mesh, pos=pos, mask=mask, bc_kind=default_bc_kind(neumann_ids=(cfg.body_id,)))
+    pb.meta["wing"] = cfg
+    return pb
+
+
 def ppe_source(pos: np.ndarray, t: float):
     """Smooth synthetic interior source for the pressure Poisson equation,
     standing in for div(u*)/dt of a flow step: O(1) amplitude, a few

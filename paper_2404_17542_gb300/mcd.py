@@ -693,8 +693,10 @@ class AleFlow:
     """Moving-boundary fractional steps on the device, in the order of
     Sec. 3.3; every stage is one call of the C ABI.
 
-    bodies_at(t) -> ([(id, centre, radius)], [(vx, vy)]): the circular
-    bodies and their translational velocities at time t.  The state (DP
+    bodies_at(t) -> ([bodies], [(vx, vy)]): the bodies at time t (circles
+    (id, centre, radius) or SdfBody objects with their posture angle and
+    angular velocity) and their translational velocities.  dV/dt and
+    d omega/dt of the Neumann datum are the finite differences of Eq. (29).  The state (DP
     positions and masks, u, v, P) lives in device tensors; the velocity
     stencils of the current step are kept for the next step's ALE
     interpolation.  Per step:
@@ -732,6 +734,9 @@ class AleFlow:
         mesh, dt = self.mesh, self.dt
         geo_k, V_k = self.bodies_at(self.t)
         geo_1, V_1 = self.bodies_at(self.t + dt)
+        for bk, b1 in zip(geo_k, geo_1):
+            if isinstance(b1, SdfBody):   # d omega / dt of Eq. (29)
+                b1.omega_dot = (b1.omega - bk.omega) / dt
         pos_k, mask_k = self.pos.clone(), self.mask.clone()
         update_dps_bodies(mesh, geo_1, self.pos, self.mask, self.prev, self.kappa, self.n_relax, self.band)
         ut, vt, fallbacks = ale_interpolate(self.vel, geo_k, pos_k, self.pos, mask_k, self.mask, self.u, self.v)
