@@ -62,6 +62,9 @@ def parse_args():
     ap.add_argument("--profile-solve", action="store_true",
                     help="run one mixed solve of the cylinder system from p = 0 (for a profiler) "
                          "and print its iteration count")
+    ap.add_argument("--trace-solve", action="store_true",
+                    help="one traced mixed cylinder solve at --n: per-phase and grid-barrier stage "
+                         "times from the device timestamps (medians, us)")
     ap.add_argument("--n", type=int, default=1024, help="background mesh cells per side")
     ap.add_argument("--bodies", default="cylinder", choices=["cylinder", "passing", "passing-sdf", "wing"],
                     help="with --workload flow: the oscillating cylinder, the two cylinders passing "
@@ -1025,12 +1028,61 @@ def profile_solve(args):
                       "rel_res": info["rel_res"]}), flush=True)
 
 
+def trace_solve(args):
+    """Where one Bi-CGSTAB iteration's time goes: a cylinder step at --n
+    (after one untimed step) with the persistent solver's %globaltimer
+    stamps on.  Prints medians over the solve's first iterations: block 0's
+    phase work and barrier waits, the stages of the grid barriers (block 0's
+    reduction and scalar update, the latest arrival and wake-up of any
+    block), and the spread of the blocks' start times in iteration 10."""
+    import torch
+
+    from paper_2404_17542_gb300 import build, inputs, mcd
+    build.build()
+    mcd.lib()
+    run = CylinderRun(args.n, torch.device("cuda", 0), mcd, inputs, args.tol)
+    run.step(mcd.MIXED)
+    mcd.trace_enable(True)
+    try:
+        info = run.step(mcd.MIXED)
+        ph, _end, _sm, start, bar = mcd.trace_read()
+    finally:
+        mcd.trace_enable(False)
+    ph = ph.astype(np.int64)
+    bar = bar.astype(np.int64)
+    rows = [r for r in range(4, 63) if (ph[r, :5] > 0).all() and ph[r + 1, 0] > 0]
+    epochs = [e for e in range(10, 256) if (bar[e] > 0).all()]
+
+    def med(vals):
+        return round(float(np.median(vals)) / 1000.0, 3) if len(vals) else None
+
+    s = start[:2048].astype(np.int64)
+    s = s[s > 0]
+    print(json.dumps({
+        "n": args.n, "iters": info["iters"], "fallback": info["fallback"],
+        "iteration_us": med([ph[r + 1, 0] - ph[r, 0] for r in rows]),
+        "block0_us": {"ca_work": med([ph[r, 1] - ph[r, 0] for r in rows]),
+                      "ca_barrier": med([ph[r, 2] - ph[r, 1] for r in rows]),
+                      "b_work": med([ph[r, 3] - ph[r, 2] for r in rows]),
+                      "b_barrier": med([ph[r, 4] - ph[r, 3] for r in rows])},
+        "barrier_us": {"last_arrival_to_all_partials": med([bar[e, 2] - bar[e, 6] for e in epochs]),
+                       "block0_reduction": med([bar[e, 3] - bar[e, 2] for e in epochs]),
+                       "scalar_update": med([bar[e, 4] - bar[e, 3] for e in epochs]),
+                       "release_stores": med([bar[e, 5] - bar[e, 4] for e in epochs]),
+                       "release_to_last_wake": med([bar[e, 7] - bar[e, 5] for e in epochs]),
+                       "last_arrival_to_last_wake": med([bar[e, 7] - bar[e, 6] for e in epochs])},
+        "start_spread_us_iteration_10": round(float(s.max() - s.min()) / 1000.0, 3) if s.size else None,
+    }), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         reference_arm(args)
     elif args.profile_solve:
         profile_solve(args)
+    elif args.trace_solve:
+        trace_solve(args)
     elif args.workload == "batched":
         batched_arm(args)
     elif args.workload == "cnn":

@@ -623,8 +623,14 @@ mcd_status mcd_timing_read(int kernel, int64_t *sampled, double *total_ms);
  * done, 6 C reduced; two-barrier schedule: 0 start, 1 phase CA done, 2 CA
  * reduced, 3 B done, 4 B reduced.  For iteration 10 and block b < 2048:
  * host_out[512 + b] = end of its first phase, host_out[2560 + b] = its SM
- * id, host_out[4608 + b] = its start of the iteration.  mcd_trace_read
- * synchronises the device and copies the 6656 values. */
+ * id, host_out[4608 + b] = its start of the iteration.  Stages of the grid
+ * barriers with epoch e < 256 of a launch (the barriers of its first ~120
+ * iterations), host_out[6656 + 8*e + k]: block 0 entering (k = 0), its
+ * partial sums published (1), every block's partials seen and added (2, 3),
+ * the scalars updated (4), the other blocks released (5); the latest
+ * arrival of any block (6) and the latest wake-up of a released block (7),
+ * both maxima over the launches since tracing was enabled.  mcd_trace_read
+ * synchronises the device and copies the 8704 values. */
 mcd_status mcd_trace_enable(int on);
 mcd_status mcd_trace_read(unsigned long long *host_out);
 

@@ -19,6 +19,7 @@
 #include <cuda.h>
 #include <math.h>
 #include <stdio.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <algorithm>
@@ -865,6 +866,75 @@ __device__ __forceinline__ void stamp_block(const PArgs &a, int it) {
     }
 }
 
+// Block 0 releases the others: one fence per storing thread (ordering the
+// scalars its thread 0 wrote before the preceding __syncthreads), then plain
+// strong stores of the epoch, which the waiting blocks read with acquire
+// loads.
+__device__ __forceinline__ void release_all(const PArgs &a, unsigned epoch) {
+    const int grid = (int)gridDim.x;
+    if (1 + (int)threadIdx.x >= grid) return;
+    __threadfence();
+    for (int b = 1 + threadIdx.x; b < grid; b += 256) st_relaxed_u32(release_word(a.bar, grid, b), epoch);
+}
+
+// Scalars of one step of the two-barrier kernel, as its block sees them.
+template <typename T> struct ScalarSnap {
+    int done, perr, pend, par, restart, sconv;
+    T alpha, omega, beta;
+};
+
+template <typename T>
+__device__ __forceinline__ void take_scalars(const Scalars *sc, ScalarSnap<T> &sn) {
+    if (threadIdx.x == 0) {
+        sn.done = vload(&sc->done);
+        sn.perr = vload(&sc->phase_err);
+        sn.pend = vload(&sc->pending);
+        sn.par = vload(&sc->parity);
+        sn.restart = vload(&sc->restart);
+        sn.sconv = vload(&sc->s_conv);
+        if constexpr (sizeof(T) == 4) {
+            sn.alpha = vload(&sc->alpha_f);
+            sn.omega = vload(&sc->omega_f);
+            sn.beta = vload(&sc->beta_f);
+        } else {
+            sn.alpha = vload(&sc->alpha);
+            sn.omega = vload(&sc->omega);
+            sn.beta = vload(&sc->beta);
+        }
+    }
+    __syncthreads();
+}
+
+// Block 0's copy of the scalars to global memory, all but the timeout word
+// (any block may set that one).
+__device__ __forceinline__ void store_scalars(Scalars *dst, const Scalars &src) {
+    const unsigned *sw = reinterpret_cast<const unsigned *>(&src);
+    unsigned *dw = reinterpret_cast<unsigned *>(dst);
+    constexpr int skip = (int)(offsetof(Scalars, phase_err) / sizeof(unsigned));
+    for (int i = 0; i < (int)(sizeof(Scalars) / sizeof(unsigned)); ++i)
+        if (i != skip) dw[i] = sw[i];
+}
+
+// The fields take_scalars reads, from block 0's copy (the rest goes out at
+// the FP64 barriers and when the launch ends).
+template <typename T>
+__device__ __forceinline__ void store_step_scalars(Scalars *g, const Scalars &l) {
+    g->done = l.done;
+    g->pending = l.pending;
+    g->parity = l.parity;
+    g->restart = l.restart;
+    g->s_conv = l.s_conv;
+    if constexpr (sizeof(T) == 4) {
+        g->alpha_f = l.alpha_f;
+        g->omega_f = l.omega_f;
+        g->beta_f = l.beta_f;
+    } else {
+        g->alpha = l.alpha;
+        g->omega = l.omega;
+        g->beta = l.beta;
+    }
+}
+
 // Grid barrier that finishes the NV-value reduction: returns false if a wait
 // gave up.  Every block writes its partial sums and then its arrival flag
 // (a plain release store: no atomics on a shared word).  Block 0 polls all
@@ -877,10 +947,17 @@ __device__ bool grid_reduce(const PArgs &a, unsigned &epoch, Acc (&d)[NV], Last 
     __shared__ double s_tot[NV];
     const int tid = threadIdx.x;
     ++epoch;
+    unsigned long long *tb = (a.trace && epoch < 256) ? a.trace + 6656 + epoch * 8 : nullptr;
+    if (tb && blockIdx.x == 0 && tid == 0) tb[0] = global_ns();
     dot_partials<NV>(d, a.partials, a.pstride, blockIdx.x);
     if (tid == 0) s_err = 0;
     __syncthreads();
-    if (tid == 0) st_release(&a.bar->flag[blockIdx.x], epoch);
+    if (tb && blockIdx.x == 0 && tid == 0) tb[1] = global_ns();
+    if (tid == 0) {
+        const unsigned long long tarr = tb ? global_ns() : 0ull;
+        st_release(&a.bar->flag[blockIdx.x], epoch);
+        if (tb) atomicMax(tb + 6, tarr);
+    }
     if (blockIdx.x == 0) {
         // wait for every block's flag (each thread a strided subset) and add
         // that block's partial sums as soon as its flag is seen; the fixed
@@ -888,15 +965,16 @@ __device__ bool grid_reduce(const PArgs &a, unsigned &epoch, Acc (&d)[NV], Last 
         double acc[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) acc[q] = 0.0;
-        for (int b = tid; b < (int)gridDim.x; b += 256) {
-            if (!wait_eq(&a.bar->flag[b], epoch, a.spin_limit)) {
-                s_err = 1;
-                break;
-            }
+        bool ok = true;
+        for (int b = tid; b < (int)gridDim.x && ok; b += 256) ok = wait_eq(&a.bar->flag[b], epoch, a.spin_limit);
+        if (!ok) s_err = 1;
+        else
+            for (int b = tid; b < (int)gridDim.x; b += 256) {
 #pragma unroll
-            for (int q = 0; q < NV; ++q) acc[q] += __ldcg(a.partials + q * a.pstride + b);
-        }
+                for (int q = 0; q < NV; ++q) acc[q] += __ldcg(a.partials + q * a.pstride + b);
+            }
         __syncthreads();
+        if (tb && tid == 0) tb[2] = global_ns();
         if (s_err) {
             if (tid == 0) a.sc->phase_err = 1;
             return false;
@@ -908,6 +986,7 @@ __device__ bool grid_reduce(const PArgs &a, unsigned &epoch, Acc (&d)[NV], Last 
             if ((tid & 31) == 0) red[q][tid >> 5] = acc[q];
         }
         __syncthreads();
+        if (tb && tid == 0) tb[3] = global_ns();
         if (tid == 0) {
             for (int q = 0; q < NV; ++q) {
                 double x = 0.0;
@@ -915,15 +994,115 @@ __device__ bool grid_reduce(const PArgs &a, unsigned &epoch, Acc (&d)[NV], Last 
                 s_tot[q] = x;
             }
             last(s_tot);
+            if (tb) tb[4] = global_ns();
         }
         __syncthreads();
-        for (int b = 1 + tid; b < (int)gridDim.x; b += 256)
-            st_release(release_word(a.bar, gridDim.x, b), epoch);
+        release_all(a, epoch);
+        if (tb && tid == 0) tb[5] = global_ns();
     } else if (tid == 0) {
         if (!wait_eq(release_word(a.bar, gridDim.x, blockIdx.x), epoch, a.spin_limit)) {
             s_err = 1;
             a.sc->phase_err = 1;
         }
+        if (tb) atomicMax(tb + 7, global_ns());
+    }
+    __syncthreads();
+    return !s_err;
+}
+
+// The barrier of the two-barrier FP32 kernel: grid_reduce with every sum
+// kept as a double-float pair (the block sums, block 0's sum over the blocks
+// in block order, its shuffle tree), handed to `last` as pairs.  No FP64
+// instruction is on the barrier's path up to `last`: the FP64 pipe of this
+// GPU runs at 1/64 of the FP32 rate, and grid_reduce's FP64 sums over the
+// blocks cost about 3 us per barrier.  (Tried and slower: records that
+// carry the barrier epoch next to each value, read without a separate flag,
+// and a release that carries the next phase's scalars; the fences their
+// relaxed accesses need cost more than the round trips they save.)
+template <int NV, typename Last>
+__device__ bool grid_reduce_df(const PArgs &a, unsigned &epoch, DotAcc<float> (&d)[NV], Last last) {
+    __shared__ int s_err;
+    __shared__ DF s_tot[NV];
+    __shared__ DF s_blk[NV][8];
+    __shared__ DF s_red[NV][8];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int grid = (int)gridDim.x;
+    float2 *pf = reinterpret_cast<float2 *>(a.partials);
+    ++epoch;
+    unsigned long long *tb = (a.trace && epoch < 256) ? a.trace + 6656 + epoch * 8 : nullptr;
+    if (tb && blockIdx.x == 0 && tid == 0) tb[0] = global_ns();
+    DF v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        v[q] = d[q].v;
+        for (int o = 16; o > 0; o >>= 1) v[q] = df_add(v[q], df_shfl_down(v[q], o));
+        if (lane == 0) s_blk[q][wid] = v[q];
+    }
+    if (tid == 0) s_err = 0;
+    __syncthreads();
+    if (tid < 32) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            DF x = (tid < 8) ? s_blk[q][tid] : DF{0.0f, 0.0f};
+            for (int o = 4; o > 0; o >>= 1) x = df_add(x, df_shfl_down(x, o));
+            if (tid == 0) pf[q * a.pstride + blockIdx.x] = make_float2(x.hi, x.lo);
+        }
+        if (tid == 0) {
+            if (tb && blockIdx.x == 0) tb[1] = global_ns();
+            const unsigned long long tarr = tb ? global_ns() : 0ull;
+            st_release(&a.bar->flag[blockIdx.x], epoch);   // after this thread's partials
+            if (tb) atomicMax(tb + 6, tarr);
+        }
+    }
+    if (blockIdx.x == 0) {
+        DF acc[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] = DF{0.0f, 0.0f};
+        // every flag of this thread first, then all its partial sums in one
+        // round of independent loads
+        bool ok = true;
+        for (int b = tid; b < grid && ok; b += 256) ok = wait_eq(&a.bar->flag[b], epoch, a.spin_limit);
+        if (!ok) s_err = 1;
+        else
+            for (int b = tid; b < grid; b += 256) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    const float2 pv = __ldcg(pf + q * a.pstride + b);
+                    acc[q] = df_add(acc[q], DF{pv.x, pv.y});
+                }
+            }
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            for (int o = 16; o > 0; o >>= 1) acc[q] = df_add(acc[q], df_shfl_down(acc[q], o));
+            if (lane == 0) s_red[q][wid] = acc[q];
+        }
+        __syncthreads();
+        if (tb && tid == 0) tb[2] = tb[3] = global_ns();
+        if (s_err) {
+            if (tid == 0) a.sc->phase_err = 1;
+            return false;
+        }
+        if (tid < 32) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                DF x = (tid < 8) ? s_red[q][tid] : DF{0.0f, 0.0f};
+                for (int o = 4; o > 0; o >>= 1) x = df_add(x, df_shfl_down(x, o));
+                if (tid == 0) s_tot[q] = x;
+            }
+            if (tid == 0) {
+                last(s_tot);
+                if (tb) tb[4] = global_ns();
+            }
+        }
+        __syncthreads();
+        release_all(a, epoch);
+        if (tb && tid == 0) tb[5] = global_ns();
+    } else if (tid == 0) {
+        if (!wait_eq(release_word(a.bar, grid, blockIdx.x), epoch, a.spin_limit)) {
+            s_err = 1;
+            a.sc->phase_err = 1;
+        }
+        if (tb) atomicMax(tb + 7, global_ns());
     }
     __syncthreads();
     return !s_err;
@@ -1751,17 +1930,32 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
         }
         __syncthreads();
     }
-    Scalars *sc = a.sc;
+    // Block 0 alone updates the scalars (in the barriers' `last` step), on a
+    // copy in its shared memory (the tests and updates then read no global
+    // memory), and writes the copy out before it releases the other blocks.
+    __shared__ Scalars ls;
+    if (threadIdx.x == 0) ls = *a.sc;
+    Scalars *sc = &ls;
     int iters = 0;
     unsigned epoch = 0;
+    // After each barrier thread 0 alone reads the scalars (it is the thread
+    // that acquired the release) and hands them to its block through shared
+    // memory.  When all 256 threads of every block read them, the
+    // requests of about 2400 warps for the same two lines queue at one L2
+    // slice, and the last blocks start their phase microseconds late.
+    __shared__ ScalarSnap<T> snap;
+    take_scalars(a.sc, snap);
     for (;;) {
-        if (vload(&sc->done) || vload(&sc->phase_err)) return;
-        if (vload(&sc->pending)) {
+        const int done0 = snap.done, perr0 = snap.perr, pend0 = snap.pend;
+        const int par = snap.par, restart0 = snap.restart, sconv0 = snap.sconv;
+        const T alpha0 = snap.alpha, omega0 = snap.omega, beta0 = snap.beta;
+        if (done0 || perr0) goto finish;
+        if (pend0) {
             // ---- true residual (reliable) update: as in the three-barrier kernel
             if (a.mixed) {
                 phase_fold<G, T>(a);
                 DotAcc<double> none[1];
-                if (!grid_reduce<1>(a, epoch, none, [&](double *) {})) return;
+                if (!grid_reduce<1>(a, epoch, none, [&](double *) {})) goto finish;
             }
             DotAcc<double> d64[2];
             DotAcc<T> dt[2];
@@ -1777,7 +1971,7 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
                 all[3].v = dt[1].v;
             }
             const double tol = a.tol;
-            if (!grid_reduce<4>(a, epoch, all, [&](double *tot) {
+            auto tr_last = [&](double *tot) {
                     sc->rr64 = tot[0];
                     sc->bb64 = tot[1];
                     sc->rr = tot[3];
@@ -1792,98 +1986,116 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
                     sc->s_conv = 0;
                     sc->alpha = sc->beta = sc->omega = 0.0;
                     publish(sc);
-                }))
-                return;
+                };
+            if (!grid_reduce<4>(a, epoch, all, [&](double *tot) { tr_last(tot); store_scalars(a.sc, ls); }))
+                goto finish;
+            take_scalars(a.sc, snap);
             continue;
         }
-        if (iters >= a.iter_budget) return;
+        if (iters >= a.iter_budget) goto finish;
         const int it = iters;
         ++iters;
         stamp(a, it, 0);
         stamp_block_start(a, it);
-        const int par = vload(&sc->parity);
         T *p_old = (T *)(par ? a.p1 : a.p0), *p_new = (T *)(par ? a.p0 : a.p1);
         T *v_old = (T *)(par ? a.v1 : a.v0), *v_new = (T *)(par ? a.v0 : a.v1);
         // ---- phase CA: x, r of the last iteration; p, v = A p; alpha ------
         {
-            const int restart = vload(&sc->restart);
-            const int sconv = vload(&sc->s_conv);
-            const int mode = restart ? CA_RESTART : (sconv ? CA_SCONV : CA_NORMAL);
-            T alpha, omega, beta;
-            if constexpr (sizeof(T) == 4) {
-                alpha = vload(&sc->alpha_f); omega = vload(&sc->omega_f); beta = vload(&sc->beta_f);
-            } else {
-                alpha = (T)vload(&sc->alpha); omega = (T)vload(&sc->omega); beta = (T)vload(&sc->beta);
-            }
+            const int mode = restart0 ? CA_RESTART : (sconv0 ? CA_SCONV : CA_NORMAL);
             DotAcc<T> dot[3];
-            phase_ca<G, T>(a, tile, p_old, v_old, p_new, v_new, alpha, omega, beta, mode, dot, pp);
+            phase_ca<G, T>(a, tile, p_old, v_old, p_new, v_new, alpha0, omega0, beta0, mode, dot, pp);
             stamp(a, it, 1);
             stamp_block(a, it);
+            const int stall = a.stall;
             const double eps = a.eps_breakdown;
             const double update2 = a.update2;
             const int mixed = a.mixed;
-            const int stall = a.stall;
-            if (!grid_reduce<3>(a, epoch, dot, [&](double *tot) {
-                    const double rv = tot[0], rr = tot[1], rho = tot[2];
-                    sc->rv = rv;
-                    sc->rr = rr;
-                    if (mode != CA_RESTART) sc->iter += 1;   // iteration k finished (x, r)
-                    if (!isfinite(rv + rr + rho)) { sc->done = 4; return; }
-                    if (mode == CA_SCONV) { sc->s_conv = 0; sc->pending = 1; return; }
-                    if (mode == CA_RESTART) {
-                        sc->rhat2 = rr;
-                    } else {
-                        if (rr <= sc->tol2) { sc->pending = 1; return; }
-                        if (sc->iter >= sc->max_iter) { sc->max_hit = 1; sc->pending = 1; return; }
-                        if (mixed && rr <= update2 * sc->rr_last) { sc->pending = 1; return; }
-                        if (mixed && rr > 1e8 * sc->rr_last) { sc->diverged = 1; sc->done = 3; return; }
-                        if (mixed && sc->iter - sc->it_last >= stall) { sc->pending = 1; return; }
-                        if (fabs(rho) <= eps * sqrt(sc->rhat2 * rr)) {
-                            sc->restarts += 1;
-                            if (sc->restarts > 1000) { sc->done = 3; return; }
-                            sc->restart = 1;   // redo CA from this r with p = r
-                            return;
-                        }
+            auto ca_last = [&](const double *tot) {
+                const double rv = tot[0], rr = tot[1], rho = tot[2];
+                sc->rv = rv;
+                sc->rr = rr;
+                if (mode != CA_RESTART) sc->iter += 1;   // iteration k finished (x, r)
+                if (!isfinite(rv + rr + rho)) { sc->done = 4; return; }
+                if (mode == CA_SCONV) { sc->s_conv = 0; sc->pending = 1; return; }
+                if (mode == CA_RESTART) {
+                    sc->rhat2 = rr;
+                } else {
+                    if (rr <= sc->tol2) { sc->pending = 1; return; }
+                    if (sc->iter >= sc->max_iter) { sc->max_hit = 1; sc->pending = 1; return; }
+                    if (mixed && rr <= update2 * sc->rr_last) { sc->pending = 1; return; }
+                    if (mixed && rr > 1e8 * sc->rr_last) { sc->diverged = 1; sc->done = 3; return; }
+                    if (mixed && sc->iter - sc->it_last >= stall) { sc->pending = 1; return; }
+                    if (fabs(rho) <= eps * sqrt(sc->rhat2 * rr)) {
+                        sc->restarts += 1;
+                        if (sc->restarts > 1000) { sc->done = 3; return; }
+                        sc->restart = 1;   // redo CA from this r with p = r
+                        return;
                     }
-                    sc->restart = 0;
-                    sc->parity ^= 1;
-                    sc->rho = rho;
-                    const double alpha_n = rho / rv;
-                    if (!isfinite(alpha_n) || alpha_n == 0.0) { sc->done = 3; return; }
-                    sc->alpha = alpha_n;
-                    publish(sc);
-                }))
-                return;
+                }
+                sc->restart = 0;
+                sc->parity ^= 1;
+                sc->rho = rho;
+                const double alpha_n = rho / rv;
+                if (!isfinite(alpha_n) || alpha_n == 0.0) { sc->done = 3; return; }
+                sc->alpha = alpha_n;
+                publish(sc);
+            };
+            bool ok;
+            if constexpr (sizeof(T) == 4) {
+                ok = grid_reduce_df<3>(a, epoch, dot, [&](const DF *tot) {
+                    double t64[3];
+                    for (int q = 0; q < 3; ++q) t64[q] = (double)tot[q].hi + (double)tot[q].lo;
+                    ca_last(t64);
+                    store_step_scalars<T>(a.sc, ls);
+                });
+            } else {
+                ok = grid_reduce<3>(a, epoch, dot, [&](double *tot) { ca_last(tot); store_step_scalars<T>(a.sc, ls); });
+            }
+            if (ok) take_scalars(a.sc, snap);
+            if (!ok) goto finish;
             stamp(a, it, 2);
         }
-        if (vload(&sc->done) || vload(&sc->pending) || vload(&sc->restart)) continue;
+        const int done1 = snap.done, pend1 = snap.pend, restart1 = snap.restart;
+        const int parb = snap.par;
+        const T alpha = snap.alpha;
+        if (done1 || pend1 || restart1) continue;
         // ---- phase B: s, t = A s; omega, beta ------------------------------
         {
-            T alpha;
-            if constexpr (sizeof(T) == 4) alpha = vload(&sc->alpha_f);
-            else alpha = (T)vload(&sc->alpha);
-            const int parb = vload(&sc->parity);
             const T *v_cur = (const T *)(parb ? a.v1 : a.v0);
             DotAcc<T> dot[5];
             phase_b2<G, T>(a, tile, v_cur, alpha, dot, pp);
             stamp(a, it, 3);
-            if (!grid_reduce<5>(a, epoch, dot, [&](double *tot) {
-                    sc->ts = tot[0];
-                    sc->tt = tot[1];
-                    sc->ss = tot[2];
-                    if (!isfinite(tot[0] + tot[1] + tot[2] + tot[3] + tot[4])) { sc->done = 4; return; }
-                    if (tot[2] <= sc->tol2) { sc->s_conv = 1; return; }
-                    if (tot[1] == 0.0) { sc->done = 3; return; }
-                    const double omega = tot[0] / tot[1];
-                    const double rho_next = tot[3] - omega * tot[4];
-                    sc->omega = omega;
-                    sc->beta = (rho_next / sc->rho) * (sc->alpha / omega);
-                    publish(sc);
-                }))
-                return;
+            auto b_last = [&](const double *tot) {
+                sc->ts = tot[0];
+                sc->tt = tot[1];
+                sc->ss = tot[2];
+                if (!isfinite(tot[0] + tot[1] + tot[2] + tot[3] + tot[4])) { sc->done = 4; return; }
+                if (tot[2] <= sc->tol2) { sc->s_conv = 1; return; }
+                if (tot[1] == 0.0) { sc->done = 3; return; }
+                const double omega = tot[0] / tot[1];
+                const double rho_next = tot[3] - omega * tot[4];
+                sc->omega = omega;
+                sc->beta = (rho_next / sc->rho) * (sc->alpha / omega);
+                publish(sc);
+            };
+            bool ok;
+            if constexpr (sizeof(T) == 4) {
+                ok = grid_reduce_df<5>(a, epoch, dot, [&](const DF *tot) {
+                    double t64[5];
+                    for (int q = 0; q < 5; ++q) t64[q] = (double)tot[q].hi + (double)tot[q].lo;
+                    b_last(t64);
+                    store_step_scalars<T>(a.sc, ls);
+                });
+            } else {
+                ok = grid_reduce<5>(a, epoch, dot, [&](double *tot) { b_last(tot); store_step_scalars<T>(a.sc, ls); });
+            }
+            if (ok) take_scalars(a.sc, snap);
+            if (!ok) goto finish;
             stamp(a, it, 4);
         }
     }
+finish:
+    if (blockIdx.x == 0 && threadIdx.x == 0) store_scalars(a.sc, ls);
 }
 
 // Grid of the persistent launch: every resident slot (at most one block per
@@ -2175,8 +2387,8 @@ using namespace mcd;
 
 extern "C" mcd_status mcd_trace_enable(int on) {
     if (on && !g_trace) {
-        MCD_CUDA_TRY(cudaMalloc(&g_trace, (512 + 6144) * sizeof(unsigned long long)));
-        MCD_CUDA_TRY(cudaMemset(g_trace, 0, (512 + 6144) * sizeof(unsigned long long)));
+        MCD_CUDA_TRY(cudaMalloc(&g_trace, (512 + 6144 + 2048) * sizeof(unsigned long long)));
+        MCD_CUDA_TRY(cudaMemset(g_trace, 0, (512 + 6144 + 2048) * sizeof(unsigned long long)));
     } else if (!on && g_trace) {
         cudaFree(g_trace);
         g_trace = nullptr;
@@ -2187,7 +2399,7 @@ extern "C" mcd_status mcd_trace_enable(int on) {
 extern "C" mcd_status mcd_trace_read(unsigned long long *host_out) {
     MCD_CHECK_ARG(host_out, "NULL argument");
     MCD_CHECK_ARG(g_trace, "tracing is not enabled");
-    MCD_CUDA_TRY(cudaMemcpy(host_out, g_trace, (512 + 6144) * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    MCD_CUDA_TRY(cudaMemcpy(host_out, g_trace, (512 + 6144 + 2048) * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     return MCD_OK;
 }
 

@@ -47,6 +47,10 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_relaxed_u32(unsigned *p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -153,6 +157,10 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
     two_sum_f(a.hi, b.hi, r.hi, e);
     r.lo = __fadd_rn(__fadd_rn(e, a.lo), b.lo);
     return r;
+}
+
+__device__ __forceinline__ DF df_shfl_down(DF x, int o) {
+    return DF{__shfl_down_sync(0xffffffffu, x.hi, o), __shfl_down_sync(0xffffffffu, x.lo, o)};
 }
 
 template <int NV>

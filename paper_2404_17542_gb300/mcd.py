@@ -672,13 +672,15 @@ def trace_enable(on: bool):
 
 
 def trace_read():
-    """Phase timestamps (64, 8) of block 0, and for iteration 10 the per-block
-    end of the first phase, SM ids and iteration start times, from the last
-    persistent launch."""
-    buf = (C.c_uint64 * (512 + 6144))()
+    """Phase timestamps (64, 8) of block 0; for iteration 10 the per-block end
+    of the first phase, SM ids and iteration start times; and the grid
+    barriers' stage stamps (256 epochs, 8 stages), from the last persistent
+    launch."""
+    buf = (C.c_uint64 * (512 + 6144 + 2048))()
     _check(lib().mcd_trace_read(buf))
     a = np.array(buf, dtype=np.uint64)
-    return a[:512].reshape(64, 8), a[512:512 + 2048], a[512 + 2048:512 + 4096], a[512 + 4096:]
+    return (a[:512].reshape(64, 8), a[512:512 + 2048], a[512 + 2048:512 + 4096], a[512 + 4096:512 + 6144],
+            a[6656:].reshape(256, 8))
 
 
 def launch_count() -> int:
