@@ -799,13 +799,14 @@ static mcd_status run_mixed(const mcd_stencils *st, double *x, const mcd_solve_p
 // true-residual (reliable) updates and the convergence test on the device.
 // Block b owns tiles [b T / G, (b + 1) T / G) for the whole launch (T tiles,
 // G blocks: the grid fills every resident slot, and the tile counts of the
-// blocks differ by at most one).  The three reductions
-// of an iteration are finished at grid barriers: each block writes its
-// partial sums, the last block to arrive adds them in block order (so results
-// are deterministic), updates the scalars and releases the others.  Waiting
-// blocks spin on a generation counter with a bounded number of polls; a
-// block that gives up records the timeout and leaves, and so do the others,
-// so the launch always ends.
+// blocks differ by at most one).  The reductions of an iteration are
+// finished at grid barriers: each block writes its partial sums and an
+// arrival flag; block 0 waits for every flag, adds the partials in block
+// order (so results are deterministic), updates the scalars (on a copy in
+// its shared memory in the two-barrier kernel) and releases the others
+// through one word per block on a line of its own.  Every wait is bounded:
+// a block that gives up records the timeout and leaves, and so do the
+// others, so the launch always ends.
 // ===========================================================================
 
 struct PArgs {
