@@ -1,0 +1,101 @@
+"""GPU tests of the persistent solver's grid barriers (Sec. 3.3 solve).
+
+- Both schedules (two barriers per iteration, the default, and three)
+  match the oracle's direct solve, in FP64 and mixed mode, within the
+  parity tests' tolerances.
+- Results are deterministic.  Block 0 adds the blocks' partial sums in
+  block order, so two solves of the same system give bit-identical fields
+  and iteration counts.
+- The barrier-stage stamps of the trace are causally ordered, per barrier:
+  - block 0 enters, publishes its partials, has every partial and updates
+    the scalars, in that order;
+  - the last block publishes its partials before block 0 has them all;
+  - every released block wakes after block 0's scalar update.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import mls, solve  # noqa: E402
+from paper_2404_17542_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mcd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_17542_gb300 import build
+    build.build()
+    from paper_2404_17542_gb300 import mcd as m
+    m.lib()
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def small():
+    # 160 x 160 cells: 5 x 10 tiles of 32 x 16, one per block
+    pb = inputs.manufactured_box(160, 2, seed=3)
+    W = mls.build_weights(pb.mesh, pb.pos, pb.mask)
+    A = solve.assemble(pb.mesh, W["row"])
+    b = solve.form_rhs(pb.mesh, W["kind"], W["QL"], pb.rhs, pb.bnd, W["rscale"])
+    return pb, solve.direct_solve(A, b)
+
+
+@pytest.fixture(scope="module")
+def large():
+    # 400 x 400 cells: 13 x 25 tiles (a ragged column) over at most 304
+    # blocks, so some blocks own two tiles
+    return inputs.manufactured_box(400, 2, seed=5)
+
+
+def stencils(mcd, pb):
+    return mcd.Stencils(pb.mesh, dev(pb.pos.ravel()), dev(pb.mask), want_derivs=False)
+
+
+SCHEDULES = [(0, 0), (1, 0), (0, 3), (1, 3)]   # (FP64 / mixed, default two-barrier / three-barrier)
+
+
+@pytest.mark.parametrize("mode,barriers", SCHEDULES)
+def test_schedules_match_oracle(mcd, small, mode, barriers):
+    pb, x = small
+    tol = 1e-11 if mode == 0 else 1e-10
+    p, info = stencils(mcd, pb).solve(dev(pb.rhs), dev(pb.bnd), tol=tol, mode=mode, barriers=barriers)
+    assert info["rel_res"] <= tol
+    got = p.cpu().numpy()
+    assert np.linalg.norm(got - x) / np.linalg.norm(x) <= (1e-8 if mode == 0 else 1e-6)
+
+
+@pytest.mark.parametrize("mode,barriers", SCHEDULES)
+def test_solves_are_bit_identical(mcd, large, mode, barriers):
+    st = stencils(mcd, large)
+    tol = 1e-11 if mode == 0 else 1e-10
+    runs = [st.solve(dev(large.rhs), dev(large.bnd), tol=tol, mode=mode, barriers=barriers) for _ in range(2)]
+    (p1, i1), (p2, i2) = runs
+    assert i1["rel_res"] <= tol
+    assert i1["iters"] == i2["iters"] and i1["fallback"] == i2["fallback"]
+    assert torch.equal(p1, p2)
+
+
+def test_barrier_trace_is_causally_ordered(mcd, large):
+    st = stencils(mcd, large)
+    mcd.trace_enable(True)
+    try:
+        _p, info = st.solve(dev(large.rhs), dev(large.bnd), tol=1e-10, mode=mcd.MIXED)
+        _ph, _end, _sm, _start, bar = mcd.trace_read()
+    finally:
+        mcd.trace_enable(False)
+    bar = bar.astype(np.int64)
+    epochs = [e for e in range(1, 256) if (bar[e] > 0).all()]
+    assert len(epochs) >= min(100, 2 * info["iters"])
+    for e in epochs:
+        t = bar[e]
+        assert t[0] <= t[1] <= t[2] <= t[3] <= t[4] <= t[5], (e, t)
+        assert t[6] <= t[2], (e, t)   # the last arrival precedes "every partial seen"
+        assert t[7] >= t[4], (e, t)   # wake-ups follow the scalar update
