@@ -2026,7 +2026,9 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
                     if (mixed && rr <= update2 * sc->rr_last) { sc->pending = 1; return; }
                     if (mixed && rr > 1e8 * sc->rr_last) { sc->diverged = 1; sc->done = 3; return; }
                     if (mixed && sc->iter - sc->it_last >= stall) { sc->pending = 1; return; }
-                    if (fabs(rho) <= eps * sqrt(sc->rhat2 * rr)) {
+                    // |rho| <= eps sqrt(|r^|^2 |r|^2), squared: no FP64
+                    // square root on the barrier's path
+                    if (rho * rho <= eps * eps * (sc->rhat2 * rr)) {
                         sc->restarts += 1;
                         if (sc->restarts > 1000) { sc->done = 3; return; }
                         sc->restart = 1;   // redo CA from this r with p = r
@@ -2039,7 +2041,7 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
                 const double alpha_n = rho / rv;
                 if (!isfinite(alpha_n) || alpha_n == 0.0) { sc->done = 3; return; }
                 sc->alpha = alpha_n;
-                publish(sc);
+                sc->alpha_f = (float)alpha_n;   // omega_f and beta_f are unchanged since phase B
             };
             bool ok;
             if constexpr (sizeof(T) == 4) {
