@@ -344,6 +344,21 @@ SOLVE_BYTES_PER_DP_ITER = 140
 BUILD_BYTES_PER_DP = 206
 
 
+def aggregate_ranks(ms, unknowns, world, device):
+    """Whole-job figures of N replicas: the slowest rank's timed milliseconds
+    (max over ranks) and the unknowns all ranks solved (sum).  Every rank
+    gets both.  With one rank, no collective runs."""
+    if world == 1:
+        return float(ms), float(unknowns)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(unknowns)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def gpu_arm(args):
     import torch
 
@@ -395,14 +410,7 @@ def gpu_arm(args):
     mcd.timing_enable(0)
     clk = clocks.stop()
 
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        u = torch.tensor([unknowns], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
-        ms_max, unknowns_all = float(t.item()), float(u.item())
-    else:
-        ms_max, unknowns_all = ms, float(unknowns)
+    ms_max, unknowns_all = aggregate_ranks(ms, unknowns, world, dev)
     value = unknowns_all / (ms_max / 1e3)
 
     # plain FP64 on the same steps
