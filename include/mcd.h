@@ -634,6 +634,17 @@ mcd_status mcd_timing_read(int kernel, int64_t *sampled, double *total_ms);
 mcd_status mcd_trace_enable(int on);
 mcd_status mcd_trace_read(unsigned long long *host_out);
 
+/* Self-test of the bounded device wait that the grid barriers of the
+ * persistent solvers use (failure detection without a GPU fault).  One
+ * thread polls a device word for the value 1, at most `polls` times: the
+ * first 256 back to back, then 64 ns apart.  With set_flag = 0 nothing sets
+ * the word, so the wait gives up.  The call then returns MCD_ETIMEOUT, and
+ * the context stays usable.  With set_flag = 1 the word holds 1 and the
+ * call returns MCD_OK.  polls must be in [1, 2^20], about a second at
+ * most; otherwise MCD_EINVAL.  The call allocates and frees 8 bytes of
+ * device memory and synchronises `stream`. */
+mcd_status mcd_selftest_bounded_wait(int set_flag, int64_t polls, mcd_stream_t stream);
+
 /* Number of kernels this library has launched since it was loaded. */
 int64_t mcd_launch_count(void);
 

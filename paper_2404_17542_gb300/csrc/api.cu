@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "krylov_common.cuh"
 
 namespace mcd {
 
@@ -56,9 +57,45 @@ KTimer::~KTimer() {
     if (active_) cudaEventRecord(b_, stream_);
 }
 
+// Probe of the grid barriers' bounded wait: thread 0 polls `word` for
+// `expect` with wait_eq and records 1 if it saw it, 0 if the wait gave up.
+__global__ void wait_probe_kernel(const unsigned *word, unsigned expect, long long polls, int *seen) {
+    if (threadIdx.x == 0) *seen = wait_eq(word, expect, polls) ? 1 : 0;
+}
+
 }  // namespace mcd
 
 using namespace mcd;
+
+extern "C" mcd_status mcd_selftest_bounded_wait(int set_flag, int64_t polls, mcd_stream_t stream) {
+    MCD_CHECK_ARG(polls >= 1 && polls <= (int64_t(1) << 20), "polls must be in [1, 2^20]");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned *buf = nullptr;   // [0] the polled word, [1] the result
+    if (cudaMalloc(&buf, 2 * sizeof(unsigned)) != cudaSuccess) {
+        set_error("bounded-wait self-test: cudaMalloc failed");
+        return MCD_ECUDA;
+    }
+    int seen = -1;
+    cudaError_t e = cudaMemsetAsync(buf, 0, 2 * sizeof(unsigned), s);
+    if (e == cudaSuccess && set_flag) e = cudaMemsetAsync(buf, 0x01, 1, s);   // word = 1 (little endian)
+    if (e == cudaSuccess) {
+        wait_probe_kernel<<<1, 32, 0, s>>>(buf, 1u, (long long)polls, reinterpret_cast<int *>(buf + 1));
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&seen, buf + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (e != cudaSuccess) {
+        set_error(std::string("bounded-wait self-test: ") + cudaGetErrorString(e));
+        return MCD_ECUDA;
+    }
+    if (seen != 1) {
+        set_error("bounded-wait self-test: the wait gave up after " + std::to_string(polls) + " polls");
+        return MCD_ETIMEOUT;
+    }
+    return MCD_OK;
+}
 
 extern "C" const char *mcd_last_error(void) { return g_last_error.c_str(); }
 

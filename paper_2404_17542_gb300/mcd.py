@@ -129,6 +129,7 @@ _SIGS = {
     "mcd_timing_enable": (C.c_int, [C.c_int]),
     "mcd_timing_read": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "mcd_launch_count": (C.c_int64, []),
+    "mcd_selftest_bounded_wait": (C.c_int, [C.c_int, C.c_int64, C.c_void_p]),
     "mcd_trace_enable": (C.c_int, [C.c_int]),
     "mcd_trace_read": (C.c_int, [C.POINTER(C.c_uint64)]),
     "mcd_last_error": (C.c_char_p, []),
@@ -681,6 +682,12 @@ def trace_read():
     a = np.array(buf, dtype=np.uint64)
     return (a[:512].reshape(64, 8), a[512:512 + 2048], a[512 + 2048:512 + 4096], a[512 + 4096:512 + 6144],
             a[6656:].reshape(256, 8))
+
+
+def selftest_bounded_wait(set_flag: bool, polls: int = 4096) -> int:
+    """Status of the bounded-wait self-test (MCD_OK when the polled word is
+    set, MCD_ETIMEOUT when nothing sets it); no exception either way."""
+    return int(lib().mcd_selftest_bounded_wait(1 if set_flag else 0, int(polls), None))
 
 
 def launch_count() -> int:

@@ -6,6 +6,9 @@
 - Results are deterministic.  Block 0 adds the blocks' partial sums in
   block order, so two solves of the same system give bit-identical fields
   and iteration counts.
+- The bounded wait of the barriers gives up with MCD_ETIMEOUT when nothing
+  sets the polled word (a flag that no one sets, no GPU fault), and the
+  context stays usable for a solve afterwards.
 - The barrier-stage stamps of the trace are causally ordered, per barrier:
   - block 0 enters, publishes its partials, has every partial and updates
     the scalars, in that order;
@@ -99,3 +102,13 @@ def test_barrier_trace_is_causally_ordered(mcd, large):
         assert t[0] <= t[1] <= t[2] <= t[3] <= t[4] <= t[5], (e, t)
         assert t[6] <= t[2], (e, t)   # the last arrival precedes "every partial seen"
         assert t[7] >= t[4], (e, t)   # wake-ups follow the scalar update
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(mcd, small):
+    assert mcd.selftest_bounded_wait(True) == mcd.OK
+    assert mcd.selftest_bounded_wait(False, polls=2048) == mcd.ETIMEOUT
+    assert b"gave up" in mcd.lib().mcd_last_error()
+    pb, x = small
+    p, info = stencils(mcd, pb).solve(dev(pb.rhs), dev(pb.bnd), tol=1e-10, mode=mcd.MIXED)
+    assert info["rel_res"] <= 1e-10
+    assert np.linalg.norm(p.cpu().numpy() - x) / np.linalg.norm(x) <= 1e-6

@@ -106,3 +106,9 @@ def test_ale_and_force_null_arguments(mcd):
     assert L.mcd_ale_interpolate(None, arr, 1, PH, PH, PH, PH, PH, PH, PH, PH, None, None) == mcd.EINVAL
     out = (C.c_double * 4)()
     assert L.mcd_fluid_force(None, None, 2, PH, PH, PH, PH, PH, PH, PH, 0.01, out, None) == mcd.EINVAL
+
+
+def test_bounded_wait_selftest_limits(mcd):
+    L = mcd.lib()
+    assert L.mcd_selftest_bounded_wait(0, 0, None) == mcd.EINVAL           # no polls
+    assert L.mcd_selftest_bounded_wait(0, (1 << 20) + 1, None) == mcd.EINVAL   # over about a second
