@@ -190,6 +190,19 @@ def boundary_velocity(mask, bodies_vel, pos=None):
     return ubc, vbc
 
 
+def rigid_acceleration(pos, centre, V0, V1, om0, om1, dt):
+    """dV/dt of a rigid body at the points pos (2, m) at t_{k+1} (Eqs.
+    (26)-(29)): the finite differences over the step of the translational
+    velocity (V0 -> V1) and of the angular velocity (om0 -> om1), with the
+    angular acceleration acting on r = x - centre, plus the centripetal
+    term omega x (omega x r) = -omega^2 r."""
+    rx, ry = pos[0] - centre[0], pos[1] - centre[1]
+    omd = (om1 - om0) / dt
+    ax = (V1[0] - V0[0]) / dt - omd * ry - om1 * om1 * rx
+    ay = (V1[1] - V0[1]) / dt + omd * rx - om1 * om1 * ry
+    return ax, ay
+
+
 def moving_step(mesh, pos_k, mask_k, u_k, v_k, Wv_k, bodies_k, bodies_k1, V_k, V_k1, dt, nu,
                 weight_kind=0, r_e=None, kappa=0.2, n_relax=10, band=None):
     """One moving-boundary fractional step in the order of Sec. 3.3.
@@ -229,12 +242,7 @@ def moving_step(mesh, pos_k, mask_k, u_k, v_k, Wv_k, bodies_k, bodies_k1, V_k, V
     bnd = np.zeros(mesh.N)
     for (bid, c, om1), (_b0, _c0, om0), V0, V1 in zip(frames_1, frames_k, V_k, V_k1):
         sel = mask1 == bid
-        # dV/dt of a rigid body (Eqs. (26)-(29)): the finite differences of
-        # V_trans and omega, plus omega x (omega x r) = -omega^2 r
-        rx, ry = pos1[0, sel] - c[0], pos1[1, sel] - c[1]
-        omd = (om1 - om0) / dt
-        ax = (V1[0] - V0[0]) / dt - omd * ry - om1 * om1 * rx
-        ay = (V1[1] - V0[1]) / dt + omd * rx - om1 * om1 * ry
+        ax, ay = rigid_acceleration(pos1[:, sel], c, V0, V1, om0, om1, dt)
         bnd[sel] = -(ax * normal[0, sel] + ay * normal[1, sel])
     A = solve.assemble(mesh, Wp["row"])
     b = solve.form_rhs(mesh, Wp["kind"], Wp["QL"], src, bnd, Wp["rscale"])
