@@ -51,21 +51,27 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mcd", choices=["mcd", "reference"])
-    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "batched", "cnn", "array", "flow"],
+    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "batched", "cnn", "array", "flow", "spmv", "tgv", "poisson3d"],
                     help="cylinder: the 1024^2 moving-cylinder step (the metric's workload); "
                          "batched: 256 independent Poisson systems of log-uniform size 32^2..512^2; "
                          "cnn: the warm-start network's inference and training step on an n^2 grid; "
                          "array: the 25-cylinder array (multiple stationary cylinders), 3x3 against "
                          "the expanded 9x9 stencil, on an n^2 grid (n = 128 is the paper's l0); "
                          "flow: full moving-boundary fractional steps (DP update, ALE interpolation, "
-                         "stencils, predict, PPE, projection, fluid force) of the oscillating cylinder")
+                         "stencils, predict, PPE, projection, fluid force) of the oscillating cylinder; "
+                         "spmv: the stencil SpMV (mcd_apply_laplacian, FP32 and FP64) on an n^2 jittered "
+                         "box whose rows and vectors exceed L2 (default n = 4096), and the persistent "
+                         "solve at 2048^2; tgv: the periodic Taylor-Green vortex, 512^2, 200 fractional "
+                         "steps, mixed against FP64, error against the closed form; poisson3d: the 128^3 "
+                         "manufactured Dirichlet problem (27-point stencils), mixed against FP64")
     ap.add_argument("--profile-solve", action="store_true",
                     help="run one mixed solve of the cylinder system from p = 0 (for a profiler) "
                          "and print its iteration count")
     ap.add_argument("--trace-solve", action="store_true",
                     help="one traced mixed cylinder solve at --n: per-phase and grid-barrier stage "
                          "times from the device timestamps (medians, us)")
-    ap.add_argument("--n", type=int, default=1024, help="background mesh cells per side")
+    ap.add_argument("--n", type=int, default=None,
+                    help="background mesh cells per side (default: 1024; spmv 4096, tgv 512, poisson3d 128)")
     ap.add_argument("--bodies", default="cylinder", choices=["cylinder", "passing", "passing-sdf", "wing"],
                     help="with --workload flow: the oscillating cylinder, the two cylinders passing "
                          "each other (analytic circles, or circles given as discrete SDF grids), or the "
@@ -82,7 +88,11 @@ def parse_args():
     ap.add_argument("--no-learned", action="store_true", help="time the mixed solve without the network")
     ap.add_argument("--train-steps", type=int, default=160, help="steps whose solves train the network")
     ap.add_argument("--train-epochs", type=int, default=10)
-    return ap.parse_args()
+    ap.add_argument("--tgv-steps", type=int, default=200, help="with --workload tgv: fractional steps per arm")
+    a = ap.parse_args()
+    if a.n is None:
+        a.n = {"spmv": 4096, "tgv": 512, "poisson3d": 128}.get(a.workload, 1024)
+    return a
 
 
 def dist_env():
@@ -308,9 +318,11 @@ def timed_steps(run, steps, mode, flush_buf, net=None):
     return total_ms, unknowns, infos
 
 
-def e2e_steps(run, steps, mode, net=None):
+def e2e_steps(run, steps, mode, flush_buf, net=None):
     """Steps through the public API with host buffers: the step's source field
-    is copied from pinned host memory and the pressure read back each step."""
+    is copied from pinned host memory and the pressure read back each step.
+    L2 is flushed before each step, outside the timed region, as in
+    timed_steps."""
     torch = run.torch
     stream = torch.cuda.current_stream()
     src = torch.from_numpy(run.src_host.copy()).pin_memory()
@@ -318,6 +330,7 @@ def e2e_steps(run, steps, mode, net=None):
     total_ms = 0.0
     unknowns = 0
     for _ in range(steps):
+        flush_l2(flush_buf)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -437,7 +450,7 @@ def gpu_arm(args):
     e2e = None
     if not args.no_e2e:
         run.restore(snap)
-        mse, unke, h2d, d2h = e2e_steps(run, args.steps, mcd.MIXED, net)
+        mse, unke, h2d, d2h = e2e_steps(run, args.steps, mcd.MIXED, flush_buf, net)
         e2e = {"value": unke / (mse / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
@@ -537,19 +550,46 @@ def oracle_state(n):
     return (pb, cyl, pos, m, np.zeros(pb.mesh.N), 0)
 
 
-def cpu_baseline(n=128, steps=2):
+def _oracle_sample(n, steps):
+    """One oracle instance: an untimed first step, then `steps` timed steps.
+    Returns (unknowns, seconds).  Runs in a spawned worker process."""
     state = oracle_state(n)
-    state, _u, _it = oracle_step(state)          # untimed first step
+    state, _u, _it = oracle_step(state)
     t0 = time.perf_counter()
     unknowns = 0
     for _ in range(steps):
         state, u, _it = oracle_step(state)
         unknowns += u
-    dt = time.perf_counter() - t0
-    return {"value": unknowns / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} oracle steps (DP update, MLS weights, Bi-CGSTAB to 1e-8) of the "
-                      f"same cylinder workload at {n}x{n} instead of the full mesh; "
-                      "single-threaded numpy/scipy"}
+    return unknowns, time.perf_counter() - t0
+
+
+def cpu_baseline(n=128, steps=2):
+    """The oracle on every host core: one independent instance of the bounded
+    sample per core (spawned processes, one BLAS thread each), throughput =
+    all instances' unknowns over the slowest instance's time."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    workers = max(1, min(cores, 64))
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            res = pool.starmap(_oracle_sample, [(n, steps)] * workers)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    unknowns = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    single = res[0][0] / res[0][1]
+    return {"value": unknowns / wall, "unit": UNIT, "cores": workers, "host_cores": cores, "kind": "oracle",
+            "single_core_value": single,
+            "sample": f"{workers} independent oracle instances (one per host core), each {steps} steps (DP "
+                      f"update, MLS weights, Bi-CGSTAB to 1e-8) of the same cylinder workload at {n}x{n} "
+                      "instead of the full mesh; numpy/scipy, one BLAS thread per process"}
 
 
 def reference_arm(args):
@@ -573,11 +613,11 @@ def reference_arm(args):
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"oscillating cylinder (D=0.1, KC=5, Re=100) {args.n}x{args.n} "
-                                   "moving-boundary PPE step",
+            "config": {"workload": f"oscillating cylinder (D=0.1, KC=5, Re=100) {n}x{n} "
+                                   "moving-boundary PPE step (a bounded sample of the 1024x1024 workload)",
                        "mesh": [n, n], "tol": args.tol, "mode": "oracle fp64"},
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
-                             "sample": sample},
+                             "host_cores": os.cpu_count(), "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -1002,6 +1042,300 @@ def flow_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# Algorithmic bytes per DP of one stencil SpMV y = A x: the S-slot rows, x
+# once, y once (neighbour reads of x are reuse, not new traffic).
+def spmv_bytes_per_dp(S, fp64):
+    w = 8 if fp64 else 4
+    return S * w + 2 * w
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)).get("hbm_gbs"), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def spmv_arm(args):
+    """The matrix-free stencil SpMV (mcd_apply_laplacian, Eq. (21) rows) where
+    HBM is the limit: an n x n jittered box (default 4096^2, 16.8 M DPs; FP32
+    rows + vectors 738 MB, FP64 1.48 GB, both above 3x L2), Gaussian MLS
+    rows.  Each dtype: --warmup untimed launches, then 10 x --steps launches
+    back to back between two CUDA events (the working set does not fit in L2,
+    so no flush is needed).  Then the persistent mixed and FP64 solves of the
+    2048^2 manufactured problem from p = 0 (working set above L2)."""
+    import torch
+
+    from paper_2404_17542_gb300 import build, inputs, mcd
+    build.build()
+    mcd.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    n = args.n
+    peak, peak_src = hbm_peak()
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+
+    def d(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    pb = inputs.manufactured_box(n, 2, seed=0)
+    N = pb.mesh.N
+    st = mcd.Stencils(pb.mesh, d(pb.pos.ravel()), d(pb.mask), precision=mcd.MIXED)
+    del pb
+    g = torch.Generator(device=dev).manual_seed(0)
+    reps = 10 * max(1, args.steps)
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = mcd.launch_count()
+    spmv = {}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        x = torch.rand(N, generator=g, device=dev, dtype=torch.float64).to(dt)
+        y = torch.empty_like(x)
+        for _ in range(max(3, args.warmup)):
+            st.apply(x, y)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            st.apply(x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        bpd = spmv_bytes_per_dp(9, dt == torch.float64)
+        gbs = bpd * N / (ms / 1e3) / 1e9
+        spmv[name] = {"ms_per_launch": round(ms, 4), "bytes_per_dp": bpd,
+                      "algorithmic_bytes_per_launch": bpd * N, "achieved_gbs": round(gbs, 1),
+                      "frac": round(gbs / peak, 4), "dps_per_s": N / (ms / 1e3)}
+        del x, y
+    launches = mcd.launch_count() - launches0
+    clk = clocks.stop()
+    st.close()
+    torch.cuda.synchronize()
+
+    # the persistent solve where its working set leaves L2
+    solve = {}
+    if not args.no_fp64:
+        m = 2048
+        pb = inputs.manufactured_box(m, 2, seed=0)
+        st = mcd.Stencils(pb.mesh, d(pb.pos.ravel()), d(pb.mask), precision=mcd.MIXED)
+        rhs, bnd = d(pb.rhs), d(pb.bnd)
+        p = torch.zeros(pb.mesh.N, dtype=torch.float64, device=dev)
+        for mode, nm in ((mcd.MIXED, "mixed"), (mcd.FP64, "fp64")):
+            p.zero_()
+            st.solve(rhs, bnd, p=p, tol=args.tol, mode=mode)          # warm-up
+            mcd.timing_enable(1)
+            p.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _p, info = st.solve(rhs, bnd, p=p, tol=args.tol, mode=mode)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            _nl, kms = mcd.timing_read(mcd.K_SOLVE)
+            mcd.timing_enable(0)
+            bpi = solve_bytes_per_dp_iter(9, mode == mcd.FP64)
+            ach = bpi * pb.mesh.N * info["iters"] / (kms / 1e3) / 1e9 if kms else None
+            err = float(torch.linalg.norm(p - d(pb.exact)) / torch.linalg.norm(d(pb.exact)))
+            solve[nm] = {"ms": round(ms, 3), "iters": info["iters"], "rel_res": info["rel_res"],
+                         "us_per_iteration": round(kms * 1e3 / max(1, info["iters"]), 2),
+                         "dps_per_s": info["unknowns"] / (ms / 1e3),
+                         "roofline": {"achieved": round(ach, 1) if ach else None, "peak": peak,
+                                      "frac": round(ach / peak, 4) if ach else None,
+                                      "bytes_per_dp_iteration": bpi},
+                         "err_vs_exact": err}
+        solve["workload"] = (f"manufactured sin(pi x) sin(pi y), 2048x2048 jittered box, Dirichlet walls, "
+                             f"from p = 0 to tol {args.tol:g}")
+        st.close()
+    line = {"metric": "stencil SpMV DP-rows/s (FP32 rows + vectors)", "value": spmv["f32"]["dps_per_s"],
+            "unit": "DP-rows/s", "n_gpus": 1, "steps": reps, "warmup": max(3, args.warmup),
+            "ms_per_step": spmv["f32"]["ms_per_launch"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (compensated sums)", "data": "synthetic",
+            "config": {"workload": f"mcd_apply_laplacian on a {n}x{n} jittered box (Gaussian MLS rows, "
+                                   "Dirichlet walls)", "dps": N, "l2_bytes": l2,
+                       "l2": f"working set {spmv_bytes_per_dp(9, False) * N / 1e6:.0f} MB (FP32) > 3x L2"},
+            "roofline": {"bound": "hbm", "achieved": spmv["f32"]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": spmv["f32"]["frac"], "traffic": None,
+                         "kernel": "spmv_kernel<float, 2>",
+                         "algorithmic": f"{spmv_bytes_per_dp(9, False)} B per DP x {N} DPs per launch",
+                         "peak_source": f"{peak_src} hbm_gbs"},
+            "spmv": spmv, "solve_2048": solve, "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def tgv_arm(args):
+    """Config C2: the periodic Taylor-Green vortex (Re = 100) on an n x n
+    jittered periodic cloud (default 512^2), --tgv-steps fractional steps
+    (predict, PPE, projection; Eqs. (20)-(22)) at dt = 0.2 l0, each PPE solve
+    warm-started from the previous pressure, DP 0 pinned to the closed form.
+    Mixed and plain FP64 each run all steps from t = 0, timed with CUDA
+    events over every step; the error against the closed form at the end."""
+    import torch
+
+    from paper_2404_17542_gb300 import build, inputs, mcd
+    build.build()
+    mcd.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    n = args.n
+    pb = inputs.tgv_box(n, seed=1)
+    nu = pb.meta["nu"]
+    # CFL 0.2 at U = 1, capped by the explicit viscous term of Eq. (20): the
+    # MLS Laplacian's spectrum reaches about -4/l0^2, so nu dt / l0^2 must
+    # stay below 1/2; 0.2 keeps a margin (at 512^2 this cap decides)
+    dt = min(0.2 * pb.mesh.l0, 0.2 * pb.mesh.l0 ** 2 / nu)
+    nsteps = args.tgv_steps
+    N = pb.mesh.N
+
+    def d(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    st = mcd.Stencils(pb.mesh, d(pb.pos.ravel()), d(pb.mask), precision=mcd.MIXED, want_derivs=True)
+    # boundary data: only DP 0 (the pinned DP) is not inner; its closed-form
+    # values for every step are uploaded once, outside the timed region
+    x0 = pb.pos[:, :1]
+    bc = np.array([[float(v[0]) for v in inputs.tgv_fields(x0, (k + 1) * dt, nu)] for k in range(nsteps)])
+    bc_dev = d(bc)
+    ue, ve, pe = inputs.tgv_fields(pb.pos, nsteps * dt, nu)
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = mcd.launch_count()
+    out = {}
+    for mode, nm in ((mcd.MIXED, "mixed"), (mcd.FP64, "fp64")):
+        if nm == "fp64" and args.no_fp64:
+            continue
+        u, v = d(pb.meta["u"]), d(pb.meta["v"])
+        P = torch.zeros(N, dtype=torch.float64, device=dev)
+        ubc, vbc, pbc = (torch.zeros(N, dtype=torch.float64, device=dev) for _ in range(3))
+        iters, unknowns = [], 0
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(nsteps):
+            ubc[:1].copy_(bc_dev[k, 0:1])
+            vbc[:1].copy_(bc_dev[k, 1:2])
+            pbc[:1].copy_(bc_dev[k, 2:3])
+            us, vs, src = st.flow_predict(u, v, ubc, vbc, nu, dt)
+            _p, info = st.solve(src, pbc, p=P, tol=args.tol, mode=mode)
+            u, v = st.flow_project(P, pbc, us, vs, ubc, vbc, dt)
+            iters.append(info["iters"])
+            unknowns += info["unknowns"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        Pm = P - P.mean()
+        pex = d(pe - pe.mean())
+        out[nm] = {"ms_total": round(ms, 2), "ms_per_step": round(ms / nsteps, 4),
+                   "dps_per_s": unknowns / (ms / 1e3), "iters_mean": statistics.mean(iters),
+                   "iters_max": max(iters),
+                   "err_u": float(torch.linalg.norm(u - d(ue)) / torch.linalg.norm(d(ue))),
+                   "err_v": float(torch.linalg.norm(v - d(ve)) / torch.linalg.norm(d(ve))),
+                   "err_p": float(torch.linalg.norm(Pm - pex) / torch.linalg.norm(pex))}
+    launches = (mcd.launch_count() - launches0) / max(1, len(out) * nsteps)
+    clk = clocks.stop()
+    line = {"metric": "DP-unknowns solved/s at rel.res 1e-8: learned+mixed vs plain FP64, same GB300",
+            "value": out["mixed"]["dps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": nsteps, "warmup": 0,
+            "ms_per_step": out["mixed"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 Krylov + f64 refinement", "data": "synthetic",
+            "config": {"workload": f"periodic Taylor-Green vortex, Re = 100, {n}x{n} jittered periodic cloud, "
+                                   f"{nsteps} fractional steps at dt = min(0.2 l0, 0.2 l0^2/nu) = {dt:.3g} (predict, PPE, projection), "
+                                   "PPE warm-started from the previous pressure, DP 0 pinned",
+                       "tol": args.tol, "l2": "not flushed (one continuous run of steps)"},
+            "mixed": out["mixed"], "fp64_plain": out.get("fp64"),
+            "speedup_vs_fp64": (out["fp64"]["ms_total"] / out["mixed"]["ms_total"]) if "fp64" in out else None,
+            "gpu_launches_per_step": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def poisson3d_arm(args):
+    """Config C3: the 128^3 manufactured Poisson problem (u = sin(pi x)
+    sin(pi y) sin(pi z), Dirichlet walls, one jittered DP per cell, 3x3x3
+    stencils, 10-term quadratic basis).  Each step is one solve from p = 0
+    (FP64 rows for the residual, FP32 rows for the recursion), mixed and
+    plain FP64, L2 flushed between steps; error against the closed form."""
+    import torch
+
+    from paper_2404_17542_gb300 import build, inputs, mcd
+    build.build()
+    mcd.lib()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    n = args.n
+    peak, peak_src = hbm_peak()
+
+    def d(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    pb = inputs.manufactured_box(n, 3, seed=2)
+    N = pb.mesh.N
+    pos, mask = d(pb.pos.ravel()), d(pb.mask)
+    st = mcd.Stencils(pb.mesh, pos, mask, precision=mcd.MIXED)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st.rebuild(pos, mask)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    rhs, bnd, exact = d(pb.rhs), d(pb.bnd), d(pb.exact)
+    p = torch.zeros(N, dtype=torch.float64, device=dev)
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    out = {}
+    launches = None
+    for mode, nm in ((mcd.MIXED, "mixed"), (mcd.FP64, "fp64")):
+        if nm == "fp64" and args.no_fp64:
+            continue
+        for _ in range(max(3, args.warmup)):
+            p.zero_()
+            st.solve(rhs, bnd, p=p, tol=args.tol, mode=mode)
+        mcd.timing_enable(1)
+        launches0 = mcd.launch_count()
+        tot, infos = 0.0, []
+        for _ in range(args.steps):
+            p.zero_()
+            flush_l2(flush_buf)
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            _p, info = st.solve(rhs, bnd, p=p, tol=args.tol, mode=mode)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            tot += a0.elapsed_time(a1)
+            infos.append(info)
+        if launches is None:
+            launches = (mcd.launch_count() - launches0) / args.steps
+        _nl, kms = mcd.timing_read(mcd.K_SOLVE)
+        mcd.timing_enable(0)
+        iters = sum(i["iters"] for i in infos)
+        bpi = solve_bytes_per_dp_iter(27, mode == mcd.FP64)
+        ach = bpi * N * iters / (kms / 1e3) / 1e9 if kms else None
+        out[nm] = {"ms_per_solve": round(tot / args.steps, 3), "dps_per_s": infos[0]["unknowns"] * args.steps / (tot / 1e3),
+                   "iters": infos[0]["iters"], "rel_res_max": max(i["rel_res"] for i in infos),
+                   "us_per_iteration": round(kms * 1e3 / max(1, iters), 2),
+                   "err_vs_exact": float(torch.linalg.norm(p - exact) / torch.linalg.norm(exact)),
+                   "roofline": {"bound": "hbm", "achieved": round(ach, 1) if ach else None, "peak": peak,
+                                "unit": "GB/s", "frac": round(ach / peak, 4) if ach else None,
+                                "kernel": f"bicg_persistent2<3, {'double' if mode == mcd.FP64 else 'float'}>",
+                                "algorithmic": f"{bpi} B per DP-iteration x {N} DPs x iterations",
+                                "peak_source": f"{peak_src} hbm_gbs"}}
+    clk = clocks.stop()
+    line = {"metric": METRIC, "value": out["mixed"]["dps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": out["mixed"]["ms_per_solve"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 Krylov + f64 refinement", "data": "synthetic",
+            "config": {"workload": f"3D Poisson {n}^3, jittered DPs, 27-point quadratic MLS (Gaussian), "
+                                   "u = sin(pi x) sin(pi y) sin(pi z), Dirichlet walls, solve from p = 0",
+                       "tol": args.tol, "l2": "flushed between steps (256 MB write)"},
+            "build_ms": round(build_ms, 3), "mixed": out["mixed"], "fp64_plain": out.get("fp64"),
+            "speedup_vs_fp64": (out["mixed"]["dps_per_s"] / out["fp64"]["dps_per_s"]) if "fp64" in out else None,
+            "roofline": out["mixed"]["roofline"], "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def profile_solve(args):
     """One mixed solve of the cylinder system at step 1 from p = 0 (or, with
     --workload array, of the 25-cylinder array system, gap 12, on the stencil
@@ -1099,6 +1433,12 @@ def main():
         array_arm(args)
     elif args.workload == "flow":
         flow_arm(args)
+    elif args.workload == "spmv":
+        spmv_arm(args)
+    elif args.workload == "tgv":
+        tgv_arm(args)
+    elif args.workload == "poisson3d":
+        poisson3d_arm(args)
     else:
         gpu_arm(args)
 
