@@ -1,25 +1,27 @@
 #!/usr/bin/env python
 """Benchmark of the MCD pressure-Poisson hot path on one GB300 per rank.
 
-Workload: the oscillating-cylinder moving-boundary problem (2D unit box,
-1024x1024 background mesh, rigid cylinder D = 0.1 oscillating along x with
-KC = 5, Re = 100; Dirichlet p = 0 on the box walls, Neumann dP/dn = -a.n on
-the body).  One step is one pass of the hot path:
+Workload (the metric's): the oscillating-cylinder moving-boundary problem
+(2D unit box, 1024x1024 background mesh, rigid cylinder D = 0.1 oscillating
+along x with KC = 5, Re = 100, fluid at rest at t = 0; Dirichlet p = 0 on
+the box walls, Neumann dP/dn = -dV/dt . n on the body).  One step is one
+full moving-boundary fractional step through the C ABI (mcd_flow_step):
     DP update (remask + 10 relaxation sweeps in the 5 l0 band)
-    -> body normals and Neumann data
-    -> MLS stencil build (FP64 rows + FP32 copy)
-    -> right-hand side assembly
-    -> learned warm start: the previous step's pressure corrected by the
-       bf16 convolutional network (trained beforehand, untimed, on the
-       first steps of the same run) along its residual-minimising step
-    -> mixed-precision Bi-CGSTAB solve to ||b - A p|| <= 1e-8 ||b|| (FP64
-       residual).
+    -> ALE interpolation of u, v and of the pressure guess (Appendix A)
+    -> velocity and pressure MLS stencils (FP64 rows + FP32 copy)
+    -> u* and the PPE source (1/dt) div u*
+    -> learned warm start: the ALE pressure guess corrected by the bf16
+       convolutional network (trained, untimed, on the run's first 500 steps)
+       along its residual-minimising step
+    -> mixed-precision Bi-CGSTAB to ||b - A p|| <= 1e-8 ||b|| (FP64 residual)
+    -> projection and fluid force.
 Metric: DP-unknowns (non-void DPs) solved per second.  The same steps are
-also run with the plain FP64 Bi-CGSTAB warm-started from the previous
-pressure (`fp64_plain`) and with the mixed solve without the network
-(`mixed_no_net`).
+also run with the plain FP64 Bi-CGSTAB from the same ALE guess
+(`fp64_plain`) and with the mixed solve without the network
+(`mixed_no_net`); `e2e` reads the pressure back to host memory each step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --workload spmv | tgv | poisson3d | batched | cnn | array | flow
 
 Multi-GPU: replicas only (each rank runs its own instance; no data-path
 collective; max-over-ranks timing).
@@ -86,7 +88,9 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="time the mixed solve without the network")
-    ap.add_argument("--train-steps", type=int, default=160, help="steps whose solves train the network")
+    ap.add_argument("--train-steps", type=int, default=500, help="steps whose solves train the network")
+    ap.add_argument("--total-steps", type=int, default=2000,
+                    help="headline: length of the run over which the --steps timed steps are spread")
     ap.add_argument("--train-epochs", type=int, default=10)
     ap.add_argument("--tgv-steps", type=int, default=200, help="with --workload tgv: fractional steps per arm")
     a = ap.parse_args()
@@ -251,98 +255,127 @@ class CylinderRun:
         return info
 
 
-def train_warm_start(run, steps, epochs, lr=1e-3, seed=3):
-    """Network of the learned warm start, trained on the solves of the next
-    `steps` steps of the run (plain mixed solves from the previous pressure):
-    features of (b, p_prev, p_prev - p_prev2), target p_new - p_prev.
-    Leaves run.dprev set to the last increment.  Returns (net, info)."""
-    torch, mcd, inputs = run.torch, run.mcd, run.inputs
+class FlowRun:
+    """The oscillating-cylinder run of the headline (D = 0.1, KC = 5,
+    Re = 100 in the unit box, fluid at rest at t = 0): full moving-boundary
+    fractional steps through mcd_flow_step (mcd.AleFlow).  The PPE source is
+    the step's own (1/dt) div u*, the Neumann datum -dV/dt . n with dV/dt the
+    Eq. (29) difference, and every solve starts from the step-k pressure
+    carried to the new DP positions by the ALE interpolation (Eq. (19),
+    Appendix A).  dt = min(0.2 l0 / U, 0.2 l0^2 / nu)."""
+
+    def __init__(self, n, dev, mcd, inputs, tol):
+        import torch
+        self.torch, self.mcd = torch, mcd
+        cyl = inputs.Cylinder()
+        pb = inputs.cylinder_box(n, cyl)
+        self.cyl, self.mesh, self.N, self.n, self.dev = cyl, pb.mesh, pb.mesh.N, n, dev
+        D, U = 2 * cyl.radius, 1.0
+        self.nu = U * D / 100.0
+        self.dt = min(0.2 * pb.mesh.l0 / U, 0.2 * pb.mesh.l0 ** 2 / self.nu)
+        self.flow = mcd.AleFlow(pb.mesh, torch.from_numpy(pb.pos.ravel().copy()).to(dev),
+                                torch.from_numpy(pb.mask.copy()).to(dev), self.bodies_at, self.nu, self.dt,
+                                precision=mcd.MIXED, mode=mcd.MIXED, tol=tol, ale_pressure=True)
+        self.dprev = torch.zeros(self.N, dtype=torch.float64, device=dev)   # last increment (network input)
+        self.k = 0
+
+    def bodies_at(self, t):
+        c = self.cyl
+        return [(c.body_id, c.centre(t), c.radius)], [c.velocity(t)]
+
+    def step(self, mode, net=None, precond=None):
+        """One step; the solve info (with a network the solve starts from its
+        warm start and updates self.dprev; precond: the network applied at
+        the restarts of the solve's refinement cycles)."""
+        info = self.flow.step(mode=mode, net=net, dprev=self.dprev if net is not None else None,
+                              precond=precond)
+        self.k += 1
+        return info["solve"]
+
+    def snapshot(self):
+        return (self.flow.snapshot(), self.dprev.clone(), self.k)
+
+    def restore(self, snap):
+        fs, dp, k = snap
+        self.flow.restore(fs)
+        self.dprev.copy_(dp)
+        self.k = k
+
+
+def train_nets(run, steps, epochs, precond=True, lr=1e-3, seed=3):
+    """The networks of the learned part, trained on the first `steps` steps
+    of the run (plain mixed solves, untimed).  Each step's system at its ALE
+    guess gives one sample per network, target P - guess:
+      warm start     features of (b, guess, the last increment);
+      preconditioner features of (b, guess) without an increment (the
+                     residual -> correction map it applies at the restarts
+                     of a solve's refinement cycles).
+    Leaves run.dprev set to the last increment.  Returns (net, precond net
+    or None, info)."""
+    torch, mcd = run.torch, run.mcd
+    from paper_2404_17542_gb300 import inputs
     t0 = time.perf_counter()
     net = mcd.Net(inputs.cnn_flatten(*inputs.cnn_weights(seed)))
-    samples = []
-    p_m1 = run.p.clone()
+    pre = mcd.Net(inputs.cnn_flatten(*inputs.cnn_weights(seed + 1))) if precond else None
+    samples, psamples = [], []
+    dprev = torch.zeros(run.N, dtype=torch.float64, device=run.dev)
     for k in range(steps):
-        p_prev = run.p.clone()
-        dprev = p_prev - p_m1
         run.step(mcd.MIXED)
-        b = run.st.assemble_rhs(run.rhs, run.neu)
+        st = run.flow.stencils(mcd.FLOW_PRESSURE)
+        b = run.flow.array(mcd.FLOW_B)
+        guess = run.flow.array(mcd.FLOW_GUESS)
         if k >= 2:
-            samples.append(net.features(run.st, b, p_prev, dprev, run.p))
-        p_m1 = p_prev
-    run.dprev.copy_(run.p - p_m1)
+            samples.append(net.features(st, b, guess, dprev, run.flow.P))
+            if pre is not None:
+                psamples.append(pre.features(st, b, guess, None, run.flow.P))
+        dprev = run.flow.P - guess
+    run.dprev.copy_(dprev)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     loss = torch.zeros(1, dtype=torch.float64, device=run.dev)
     rng = np.random.default_rng(seed)
-    hist = []
+    info = {"train_steps": steps, "samples": len(samples), "epochs": epochs, "lr": lr, "data_s": round(t_data, 2)}
     t1 = time.perf_counter()
-    for ep in range(epochs):
-        tot = 0.0
-        for i in rng.permutation(len(samples)):
-            x, tg, wt = samples[i]
-            net.train_step(x, tg, wt, run.n, run.n, lr, loss)
-            tot += float(loss.item()) if ep in (0, epochs - 1) else 0.0
-        if ep in (0, epochs - 1):
-            hist.append(tot / max(1, len(samples)))
+    for name, nn, S in (("warm_start", net, samples), ("precond", pre, psamples)):
+        if nn is None:
+            continue
+        hist = []
+        for ep in range(epochs):
+            tot = 0.0
+            for i in rng.permutation(len(S)):
+                x, tg, wt = S[i]
+                nn.train_step(x, tg, wt, run.n, run.n, lr, loss)
+                tot += float(loss.item()) if ep in (0, epochs - 1) else 0.0
+            if ep in (0, epochs - 1):
+                hist.append(tot / max(1, len(S)))
+        info[f"{name}_loss_first_epoch"] = hist[0] if hist else None
+        info[f"{name}_loss_last_epoch"] = hist[-1] if hist else None
     torch.cuda.synchronize()
-    return net, {"train_steps": steps, "samples": len(samples), "epochs": epochs, "lr": lr,
-                 "data_s": round(t_data, 2), "train_s": round(time.perf_counter() - t1, 2),
-                 "loss_first_epoch": hist[0] if hist else None, "loss_last_epoch": hist[-1] if hist else None}
+    info["train_s"] = round(time.perf_counter() - t1, 2)
+    return net, pre, info
 
 
 def flush_l2(buf):
     buf.zero_()
 
 
-def timed_steps(run, steps, mode, flush_buf, net=None):
-    """Run `steps` steps, each bracketed by CUDA events on the current stream
-    with an L2 flush between steps.  Returns (total ms, unknowns, infos)."""
-    torch = run.torch
-    mcd = run.mcd
-    stream = torch.cuda.current_stream()
-    total_ms = 0.0
-    unknowns = 0
-    infos = []
-    for _ in range(steps):
-        flush_l2(flush_buf)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        info = run.step(mode, net)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        unknowns += info["unknowns"]
-        infos.append(info)
-    return total_ms, unknowns, infos
-
-
-def e2e_steps(run, steps, mode, flush_buf, net=None):
-    """Steps through the public API with host buffers: the step's source field
-    is copied from pinned host memory and the pressure read back each step.
-    L2 is flushed before each step, outside the timed region, as in
-    timed_steps."""
+def timed_step(run, mode, flush_buf, net=None, host_out=None, precond=None):
+    """One step bracketed by CUDA events on the current stream, after an L2
+    flush (outside the events).  With host_out (pinned) the step's pressure
+    is read back inside the timed region.  Returns (ms, solve info)."""
     torch = run.torch
     stream = torch.cuda.current_stream()
-    src = torch.from_numpy(run.src_host.copy()).pin_memory()
-    out = torch.empty(run.N, dtype=torch.float64).pin_memory()
-    total_ms = 0.0
-    unknowns = 0
-    for _ in range(steps):
-        flush_l2(flush_buf)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        run.rhs.copy_(src, non_blocking=True)
-        info = run.step(mode, net)
-        out.copy_(run.p, non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        unknowns += info["unknowns"]
-    return total_ms, unknowns, src.numel() * 8, out.numel() * 8
+    flush_l2(flush_buf)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    info = run.step(mode, net, precond)
+    if host_out is not None:
+        host_out.copy_(run.flow.P, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), info
 
 
 # Algorithmic bytes of the persistent Bi-CGSTAB solve per DP and iteration
@@ -350,9 +383,10 @@ def e2e_steps(run, steps, mode, flush_buf, net=None):
 #   phase A reads r, p, v, r^ (16) + 9 FP32 weights (36), writes p, v (8)  = 60
 #   phase B reads r, v (8) + weights (36), writes s, t (8)                  = 52
 #   phase C reads x, p, s, t, r^ (20), writes x, r (8)                      = 28
-# i.e. 140 B per DP-iteration; halo re-reads and the true-residual updates
-# are not counted.  The stencil build reads positions and masks (17 B) and
-# writes FP64 + FP32 rows, Neumann weights, row scale and kind (206 B).
+# i.e. 140 B per DP-iteration; halo re-reads, the low word of the
+# double-float correction and the true-residual updates are not counted.
+# The stencil build reads positions and masks (17 B) and writes FP64 + FP32
+# rows, Neumann weights, row scale and kind (206 B).
 SOLVE_BYTES_PER_DP_ITER = 140
 BUILD_BYTES_PER_DP = 206
 
@@ -373,6 +407,14 @@ def aggregate_ranks(ms, unknowns, world, device):
 
 
 def gpu_arm(args):
+    """The headline: the oscillating cylinder at --n (1024^2).  Steps
+    1..--train-steps run plain mixed solves whose systems train the network
+    (untimed); --warmup learned steps follow; then --steps sample points are
+    spread evenly over the rest of the --total-steps run.  At each sample
+    point the same step is timed for every arm from one snapshot (learned +
+    mixed, plain FP64, mixed without the network, and end to end with the
+    pressure read back to host memory), after which the run continues,
+    untimed, on the learned + mixed path to the next sample point."""
     import torch
 
     from paper_2404_17542_gb300 import build, inputs, mcd
@@ -386,73 +428,102 @@ def gpu_arm(args):
     build.build()
     mcd.lib()
 
-    run = CylinderRun(args.n, dev, mcd, inputs, args.tol)
+    run = FlowRun(args.n, dev, mcd, inputs, args.tol)
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    host_p = torch.empty(run.N, dtype=torch.float64).pin_memory()
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # the learned warm start: trained (untimed) on the first steps of the run
-    net, learned = None, None
+    net, pre, learned = None, None, None
     if not args.no_learned:
-        net, learned = train_warm_start(run, args.train_steps, args.train_epochs)
-
-    # warm-up
+        net, pre, learned = train_nets(run, args.train_steps, args.train_epochs)
+    else:
+        for _ in range(args.train_steps):
+            run.step(mcd.MIXED)
     for _ in range(args.warmup):
         run.step(mcd.MIXED, net)
-    snap = run.snapshot()
+    K = args.steps
+    gap = max(1, (args.total_steps - run.k) // K)
 
-    # timed region: mixed path
+    arms = {"main": [], "fp64": [], "no_net": [], "e2e": [], "precond": []}
+    ktimes = {}
+    launches = 0
     clocks = ClockSampler(local)
     clocks.start()
-    mcd.timing_enable(1)
-    launches0 = mcd.launch_count()
     barrier()
     wall0 = time.perf_counter()
-    ms, unknowns, infos = timed_steps(run, args.steps, mcd.MIXED, flush_buf, net)
+    for _i in range(K):
+        snap = run.snapshot()
+        # the headline arm, with the kernel sampler on for this step alone
+        mcd.timing_enable(1)
+        l0 = mcd.launch_count()
+        ms, info = timed_step(run, mcd.MIXED, flush_buf, net)
+        launches += mcd.launch_count() - l0
+        for kid, name in enumerate(mcd.KERNEL_NAMES):
+            n_, t_ = mcd.timing_read(kid)
+            if n_:
+                a_ = ktimes.setdefault(name, [0, 0.0])
+                a_[0] += n_
+                a_[1] += t_
+        mcd.timing_enable(0)
+        arms["main"].append((ms, info, run.k))
+        if not args.no_fp64:
+            run.restore(snap)
+            arms["fp64"].append(timed_step(run, mcd.FP64, flush_buf))
+        if net is not None:
+            run.restore(snap)
+            arms["no_net"].append(timed_step(run, mcd.MIXED, flush_buf))
+        if not args.no_e2e:
+            run.restore(snap)
+            arms["e2e"].append(timed_step(run, mcd.MIXED, flush_buf, net, host_out=host_p))
+        if pre is not None:
+            run.restore(snap)
+            arms["precond"].append(timed_step(run, mcd.MIXED, flush_buf, net, precond=pre))
+        run.restore(snap)
+        for _ in range(gap):
+            run.step(mcd.MIXED, net)
     barrier()
     wall = time.perf_counter() - wall0
-    launches = mcd.launch_count() - launches0
-    ktimes = {}
-    for kid, name in enumerate(mcd.KERNEL_NAMES):
-        n, t = mcd.timing_read(kid)
-        if n:
-            ktimes[name] = (n, t)
-    mcd.timing_enable(0)
     clk = clocks.stop()
 
+    main = arms["main"]
+    ms = sum(m for m, _i, _k in main)
+    unknowns = sum(i["unknowns"] for _m, i, _k in main)
+    infos = [i for _m, i, _k in main]
     ms_max, unknowns_all = aggregate_ranks(ms, unknowns, world, dev)
     value = unknowns_all / (ms_max / 1e3)
 
-    # plain FP64 on the same steps
-    fp64 = None
-    if not args.no_fp64:
-        run.restore(snap)
-        ms64, unk64, infos64 = timed_steps(run, args.steps, mcd.FP64, flush_buf)
-        fp64 = {"value": unk64 / (ms64 / 1e3), "ms_per_step": ms64 / args.steps,
-                "iters_per_step": statistics.mean(i["iters"] for i in infos64),
-                "rel_res_max": max(i["rel_res"] for i in infos64)}
-
-    # the mixed solve without the network on the same steps
-    no_net = None
-    if net is not None:
-        run.restore(snap)
-        msn, unkn, infosn = timed_steps(run, args.steps, mcd.MIXED, flush_buf)
-        no_net = {"value": unkn / (msn / 1e3), "ms_per_step": msn / args.steps,
-                  "iters_per_step": statistics.mean(i["iters"] for i in infosn)}
+    def summary(rows):
+        if not rows:
+            return None
+        t = sum(m for m, _i in rows)
+        return {"value": sum(i["unknowns"] for _m, i in rows) / (t / 1e3), "ms_per_step": t / len(rows),
+                "iters_per_step": statistics.mean(i["iters"] for _m, i in rows),
+                "rel_res_max": max(i["rel_res"] for _m, i in rows),
+                "fp64_finishes": sum(i["fallback"] for _m, i in rows)}
+    fp64 = summary(arms["fp64"])
+    no_net = summary(arms["no_net"])
+    with_pre = summary(arms["precond"])
+    if with_pre is not None:
+        with_pre["net_corrections_per_step"] = statistics.mean(i["net_corrections"] for _m, i in arms["precond"])
+    if learned is not None:
         learned["iters_per_step"] = statistics.mean(i["iters"] for i in infos)
+        learned["iters_per_step_without_net"] = no_net["iters_per_step"] if no_net else None
         learned["rel_res_guess_mean"] = statistics.mean(i["rel_res_guess"] for i in infos)
         learned["rel_res_start_mean"] = statistics.mean(i["rel_res_start"] for i in infos)
-
-    # end to end through the public API with host buffers
+        learned["iters_gain_vs_no_net"] = (no_net["iters_per_step"] / learned["iters_per_step"]) if no_net else None
     e2e = None
-    if not args.no_e2e:
-        run.restore(snap)
-        mse, unke, h2d, d2h = e2e_steps(run, args.steps, mcd.MIXED, flush_buf, net)
-        e2e = {"value": unke / (mse / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+    if arms["e2e"]:
+        te = sum(m for m, _i in arms["e2e"])
+        import ctypes
+        body_bytes = 2 * ctypes.sizeof(mcd.c_body)      # the step's inputs: body states at t_k, t_k+1
+        e2e = {"value": sum(i["unknowns"] for _m, i in arms["e2e"]) / (te / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": body_bytes, "d2h_bytes_per_step": run.N * 8,
+               "note": "mcd_flow_step from host body states (passed by value), the step's pressure copied "
+                       "to pinned host memory inside the timed region"}
 
     # roofline of the dominant kernel: the persistent Bi-CGSTAB solve
     peak, peak_src = measured_peaks()
@@ -486,26 +557,34 @@ def gpu_arm(args):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 Krylov + f64 refinement",
             "data": "synthetic",
-            "config": {"workload": f"oscillating cylinder (D=0.1, KC=5, Re=100) {args.n}x{args.n} "
-                                   "moving-boundary PPE step",
-                       "mesh": [args.n, args.n], "tol": args.tol, "mode": "mixed",
+            "config": {"workload": f"oscillating cylinder (D=0.1, KC=5, Re=100) {args.n}x{args.n}, full "
+                                   "moving-boundary fractional step (DP update, ALE, stencils, predict, "
+                                   "PPE, projection, force)",
+                       "mesh": [args.n, args.n], "tol": args.tol, "mode": "mixed", "dt": run.dt,
+                       "ppe_source": "(1/dt) div u* of the step (Eq. (21))",
                        "learned_warm_start": net is not None,
-                       "warm_start": ("previous step pressure + network correction" if net is not None
-                                      else "previous step pressure"),
-                       "l2": "flushed between steps (256 MB write)",
+                       "warm_start": ("step-k pressure at the new positions (ALE, Appendix A) + network "
+                                      "correction" if net is not None else
+                                      "step-k pressure at the new positions (ALE, Appendix A)"),
+                       "schedule": f"train on steps 1-{args.train_steps}, {args.warmup} warm-up steps, "
+                                   f"{K} timed steps every {gap} steps up to step {args.total_steps}",
+                       "timed_steps": [k for _m, _i, k in main],
+                       "l2": "flushed before each timed step (256 MB write)",
                        "parallelism": f"replicas x{world}"},
             "iters_per_step": statistics.mean(i["iters"] for i in infos),
-            "refinements_per_step": statistics.mean(i["refinements"] for i in infos),
+            "updates_per_step": statistics.mean(i["refinements"] for i in infos),
+            "dropped_cycles_per_step": statistics.mean(i["discarded"] for i in infos),
+            "fp64_finishes": sum(i["fallback"] for i in infos),
             "rel_res_max": max(i["rel_res"] for i in infos),
-            "unknowns_per_step": unknowns / args.steps,
+            "unknowns_per_step": unknowns / K,
             "wall_s": wall,
             "fp64_plain": fp64,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
-            "mixed_no_net": no_net, "learned": learned,
+            "mixed_no_net": no_net, "learned_with_precond": with_pre, "learned": learned,
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
             "clocks": clk,
         }
@@ -517,53 +596,53 @@ def gpu_arm(args):
 # ---------------------------------------------------------------------------
 # the oracle on host cores (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_step(state, tol=1e-8):
-    """One oracle pass of the same hot path on a smaller cylinder instance."""
-    from oracle import mask as omask
-    from oracle import mls, solve
-    pb, cyl, pos, m, p, k = state
-    mesh = pb.mesh
-    dt = 0.2 * mesh.l0
-    k += 1
-    t = k * dt
-    c = cyl.centre(t)
-    pos, m, _prev = omask.update_dps(mesh, pos, m, c, cyl.radius, body_id=cyl.body_id, n_relax=10)
-    normal = omask.circle_normals(pos, m, c, cyl.body_id)
-    a = cyl.acceleration(t)
-    bnd = np.where(m == cyl.body_id, -(a[0] * normal[0] + a[1] * normal[1]), 0.0)
-    W = mls.build_weights(mesh, pos, m, normal, pb.bc_kind)
-    A = solve.assemble(mesh, W["row"])
-    from paper_2404_17542_gb300 import inputs
-    rhs = inputs.ppe_source(pos, 0.0)
-    b = solve.form_rhs(mesh, W["kind"], W["QL"], rhs, bnd, W["rscale"])
-    x, it, rel = solve.bicgstab(A, b, x0=p, tol=tol)
-    return (pb, cyl, pos, m, x, k), int((m != 0).sum()), it
-
-
 def oracle_state(n):
+    """The oracle's copy of the headline run at n x n: DPs arranged for the
+    cylinder at t = 0, fluid at rest, the step-k velocity weights."""
     from oracle import mask as omask
+    from oracle import mls
     from paper_2404_17542_gb300 import inputs
-    pb = inputs.cylinder_box(n)
-    cyl = pb.meta["cylinder"]
-    pos, m, _ = omask.update_dps(pb.mesh, pb.pos, pb.mask, cyl.centre(0.0), cyl.radius,
-                                 body_id=cyl.body_id, band=0.0, n_relax=4)
-    return (pb, cyl, pos, m, np.zeros(pb.mesh.N), 0)
+    cyl = inputs.Cylinder()
+    pb = inputs.cylinder_box(n, cyl)
+    nu = 2 * cyl.radius / 100.0
+    dt = min(0.2 * pb.mesh.l0, 0.2 * pb.mesh.l0 ** 2 / nu)
+    pos, m, _ = omask.update_dps_bodies(pb.mesh, pb.pos, pb.mask, [(cyl.body_id, cyl.centre(0.0), cyl.radius)],
+                                        0.2, 10, 0.0)
+    z = np.zeros(pb.mesh.N)
+    return {"mesh": pb.mesh, "cyl": cyl, "pos": pos, "mask": m, "u": z, "v": z.copy(),
+            "Wv": mls.build_weights(pb.mesh, pos, m), "t": 0.0, "nu": nu, "dt": dt}
+
+
+def oracle_step(s):
+    """One oracle pass of the headline's step: oracle.ale.moving_step (DP
+    update, ALE, MLS weights, predict, the PPE by a direct sparse solve,
+    projection, force).  Returns the unknowns (non-void DPs)."""
+    from oracle import ale
+    cyl, t, dt = s["cyl"], s["t"], s["dt"]
+    bk = [(cyl.body_id, cyl.centre(t), cyl.radius)]
+    b1 = [(cyl.body_id, cyl.centre(t + dt), cyl.radius)]
+    o = ale.moving_step(s["mesh"], s["pos"], s["mask"], s["u"], s["v"], s["Wv"], bk, b1, [cyl.velocity(t)],
+                        [cyl.velocity(t + dt)], dt, s["nu"])
+    s.update(pos=o["pos"], mask=o["mask"], u=o["u"], v=o["v"], Wv=o["Wv"], t=t + dt)
+    return int((o["mask"] != 0).sum())
+
+
+ORACLE_N = 96
 
 
 def _oracle_sample(n, steps):
     """One oracle instance: an untimed first step, then `steps` timed steps.
     Returns (unknowns, seconds).  Runs in a spawned worker process."""
-    state = oracle_state(n)
-    state, _u, _it = oracle_step(state)
+    s = oracle_state(n)
+    oracle_step(s)
     t0 = time.perf_counter()
     unknowns = 0
     for _ in range(steps):
-        state, u, _it = oracle_step(state)
-        unknowns += u
+        unknowns += oracle_step(s)
     return unknowns, time.perf_counter() - t0
 
 
-def cpu_baseline(n=128, steps=2):
+def cpu_baseline(n=ORACLE_N, steps=4):
     """The oracle on every host core: one independent instance of the bounded
     sample per core (spawned processes, one BLAS thread each), throughput =
     all instances' unknowns over the slowest instance's time."""
@@ -587,35 +666,35 @@ def cpu_baseline(n=128, steps=2):
     single = res[0][0] / res[0][1]
     return {"value": unknowns / wall, "unit": UNIT, "cores": workers, "host_cores": cores, "kind": "oracle",
             "single_core_value": single,
-            "sample": f"{workers} independent oracle instances (one per host core), each {steps} steps (DP "
-                      f"update, MLS weights, Bi-CGSTAB to 1e-8) of the same cylinder workload at {n}x{n} "
-                      "instead of the full mesh; numpy/scipy, one BLAS thread per process"}
+            "sample": f"{workers} independent oracle instances (one per host core), each {steps} full "
+                      f"moving-boundary steps (oracle.ale.moving_step: DP update, ALE, MLS weights, predict, "
+                      f"direct PPE solve, projection, force) of the same cylinder run at {n}x{n} instead of "
+                      "1024x1024; numpy/scipy, one BLAS thread per process"}
 
 
 def reference_arm(args):
     rank, world, _local = dist_env()
     if rank != 0:
         return
-    n = 96
-    state = oracle_state(n)
+    n = ORACLE_N
+    s = oracle_state(n)
     for _ in range(args.warmup):
-        state, _u, _it = oracle_step(state, args.tol)
+        oracle_step(s)
     t0 = time.perf_counter()
     unknowns = 0
     for _ in range(args.steps):
-        state, u, _it = oracle_step(state, args.tol)
-        unknowns += u
+        unknowns += oracle_step(s)
     dt = time.perf_counter() - t0
     value = unknowns / dt
-    sample = (f"each step one oracle pass (DP update, MLS weights, Bi-CGSTAB to {args.tol}) of "
-              f"the cylinder workload at {n}x{n}; single-threaded numpy/scipy")
+    sample = (f"each step one oracle pass of the full moving-boundary step (oracle.ale.moving_step, direct "
+              f"PPE solve) of the cylinder run at {n}x{n}; single-threaded numpy/scipy")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"oscillating cylinder (D=0.1, KC=5, Re=100) {n}x{n} "
-                                   "moving-boundary PPE step (a bounded sample of the 1024x1024 workload)",
-                       "mesh": [n, n], "tol": args.tol, "mode": "oracle fp64"},
+            "config": {"workload": f"oscillating cylinder (D=0.1, KC=5, Re=100) {n}x{n}, full "
+                                   "moving-boundary fractional step (a bounded sample of the 1024x1024 run)",
+                       "mesh": [n, n], "tol": "direct solve", "mode": "oracle fp64"},
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
                              "host_cores": os.cpu_count(), "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

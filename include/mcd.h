@@ -190,20 +190,40 @@ typedef struct mcd_net mcd_net;   /* learned warm start, declared below */
  *              keeps the Krylov direction); needs an MCD_MIXED handle.
  * inner_tol    (MIXED) reliable-update factor in (0, 1): an FP64 residual
  *              is taken once the FP32 residual has fallen by this factor
- *              since the last one (checked every few iterations).
+ *              since the last one (0.3 is the tested choice).  A recursion
+ *              whose residual grows 100-fold since the last update while
+ *              residuals are replaced (1e4-fold when restarting) has
+ *              diverged: its correction is dropped and it restarts; after 64
+ *              such cycles the solve finishes in FP64.
  * max_refine   cap on FP64 restarts (FP64 mode).
  * net          NULL, or a network whose correction is added to the guess
  *              before the Krylov solve (mcd_net_warm_start; 2D only).
  * check_every  Krylov iterations between host convergence checks (0: auto).
  * update_restart (MIXED) 1: restart the FP32 recurrence (fresh shadow
- *              residual, p = r) at every reliable update; 0: keep p.
+ *              residual, p = r) at every reliable update; 0 (adaptive):
+ *              residual replacement, the recurrence continues with p, v and
+ *              the shadow residual kept and beta recomputed from the replaced
+ *              residual (restarts still follow the first update, an ||s||
+ *              stop or a breakdown), until a cycle diverges; from then on
+ *              the solve restarts at every update, as with 1.
  * barriers     grid barriers per Bi-CGSTAB iteration of the persistent solve:
  *              2 (default; x, r update fused into the next p, v = A p phase,
  *              beta from the recurrence r^.s - omega r^.t) or 3 (textbook).
  * net_dprev    with net: device float64 [N] or NULL, in and out: the
  *              increment the warm start reads (the pressure of the last
  *              step minus the one before); after a converged solve it
- *              holds this solve's increment, p(out) - p(in), for the next. */
+ *              holds this solve's increment, p(out) - p(in), for the next.
+ * precond      NULL, or a network used as the preconditioner of the
+ *              iterative refinement (MCD_MIXED, two-barrier persistent
+ *              schedule only): every FP64 true-residual update that does not
+ *              meet tol and restarts the FP32 recursion (the first update, a
+ *              cycle dropped after diverging, an ||s|| stop or a breakdown;
+ *              every update with update_restart = 1) begins a refinement
+ *              cycle whose d0 is the network's correction of that residual
+ *              (features without an increment: channel 6 is 0), added along
+ *              its residual-minimising step before the recursion restarts.
+ *              The residual never grows (mcd_solve_info.net_corrections
+ *              counts the applications). */
 typedef struct {
     double tol;
     int max_iter;
@@ -215,18 +235,25 @@ typedef struct {
     int update_restart;
     double *net_dprev;
     int barriers;
+    const mcd_net *precond;
 } mcd_solve_params;
 
 typedef struct {
     int iters;          /* Krylov iterations done */
-    int refinements;    /* FP64 residual updates after the first */
+    int refinements;    /* FP64 true-residual updates (reliable updates) */
     int restarts;       /* Bi-CGSTAB restarts after a rho breakdown */
     double rel_res;     /* final ||b - A p|| / ||b|| in FP64 */
     double b_norm;      /* ||b||_2 */
     int64_t unknowns;   /* non-void DPs of the system (DP unknowns solved) */
     double rel_res_guess;  /* with a net: ||b - A p|| / ||b|| of the guess, else -1 */
     double rel_res_start;  /* with a net: the same after the warm start, else -1 */
-    int fallback;       /* MIXED: 1 if the FP32 recursion failed and FP64 finished */
+    int fallback;       /* MIXED: nonzero if the FP32 recursion failed and FP64
+                           finished; why: 1 more than 64 cycles diverged, 2 breakdown
+                           restarts exhausted, 3 r^.v breakdown (alpha), 4 t = 0,
+                           5 a non-finite dot, 6 max_iter, 7 other */
+    int net_corrections;   /* with precond: network corrections applied */
+    int discarded;      /* MIXED: FP32 cycles whose residual grew 100-fold; their
+                           correction was dropped and the recursion restarted */
 } mcd_solve_info;
 
 /* mcd_solve_pressure - solve A p = b (b from mcd_assemble_rhs(rhs, bnd)).
@@ -434,6 +461,109 @@ mcd_status mcd_fluid_force(const mcd_stencils *pres, const mcd_stencils *vel, in
                            const double *pos_dev, const int8_t *mask_dev, const double *normal_dev,
                            const double *P_dev, const double *bnd_dev, const double *u_dev,
                            const double *v_dev, double mu, double *out_host, mcd_stream_t stream);
+
+/* -------------------------------------------------------------------------
+ * The moving-boundary fractional step (Sec. 3.3), one call per time step
+ * ---------------------------------------------------------------------- */
+typedef struct mcd_flow mcd_flow;   /* opaque: stencils and work arrays of a run */
+
+/* nu           kinematic viscosity (the force uses mu = nu: unit density).
+ * weight_kind, r_e   MLS weight of the velocity and pressure stencils (r_e
+ *              0: l0); r_s = l0; 3x3 stencils.
+ * precision    pressure stencils: MCD_FP64 or MCD_MIXED (needed by MIXED
+ *              solves).
+ * kappa, n_relax, band, alpha   the DP update of every step (as in
+ *              mcd_update_dps; band <= 0: 5 l0, the band of Sec. 2.4).
+ * ale_pressure 1: the PPE's initial guess is the step-k pressure carried to
+ *              the new DP positions by the same ALE interpolation as the
+ *              velocity (Eq. (19) and Appendix A: the role-changed DPs get
+ *              the shifted-support value of Eq. (A.2)); 0: the step-k
+ *              pressure as it is.
+ * forces       1: compute the fluid force on every body (Eqs. (30)-(31)). */
+typedef struct {
+    double nu;
+    int weight_kind;
+    double r_e;
+    int precision;
+    double kappa;
+    int n_relax;
+    double band;
+    double alpha;
+    int ale_pressure;
+    int forces;
+} mcd_flow_params;
+
+typedef struct {
+    mcd_solve_info solve;      /* the step's PPE solve */
+    int ale_fallbacks;         /* velocity ALE: role-changed DPs without an inner
+                                  shifted centre (they keep u^k; Appendix A) */
+    int ale_fallbacks_p;       /* the same for the pressure guess */
+    int nbodies;
+    double force[MCD_MAX_BODIES][2];   /* F of body b (order of the body list) */
+    double perimeter[MCD_MAX_BODIES];  /* sum of dGamma of its DPs (Eq. (31)) */
+    int skipped[MCD_MAX_BODIES];       /* its DPs whose shifted centre is not inner */
+} mcd_flow_info;
+
+/* mcd_flow_create - state of a moving-boundary run on the 2D mesh `mesh`
+ * (3x3 stencils): arranges the DPs of pos_dev (float64 [2][N], in/out) and
+ * mask_dev (int8 [N], in/out; walls already marked) for `bodies` over the
+ * whole mesh (mcd_update_dps with band 0) and builds the velocity stencils
+ * the first step's ALE interpolation reads.  The body ids and their order
+ * are fixed for the run (1..MCD_MAX_BODIES bodies; their pressure boundary is
+ * Neumann, every other boundary id Dirichlet).  Allocates about 20 N doubles
+ * plus two stencil handles.  Asynchronous; *out receives the handle. */
+mcd_status mcd_flow_create(const mcd_mesh *mesh, const mcd_flow_params *prm, const mcd_body *bodies,
+                           int nbodies, double *pos_dev, int8_t *mask_dev, mcd_flow **out,
+                           mcd_stream_t stream);
+void mcd_flow_destroy(mcd_flow *f);
+
+/* mcd_flow_restart - continue a run from a saved cloud (checkpoint / resume,
+ * or repeating steps from a snapshot): rebuilds the velocity stencils of
+ * pos_dev / mask_dev, the step-k weights the next step's ALE interpolation
+ * reads.  The caller restores its own u, v, P with the cloud.
+ * Asynchronous. */
+mcd_status mcd_flow_restart(mcd_flow *f, const double *pos_dev, const int8_t *mask_dev, mcd_stream_t stream);
+
+/* mcd_flow_step - one fractional step from t_k to t_{k+1} = t_k + dt in the
+ * order of Sec. 3.3:
+ *  1. every body's dV/dt = (vel^{k+1} - vel^k) / dt and
+ *     d omega/dt = (omega^{k+1} - omega^k) / dt (Eq. (29)); the acc and
+ *     omega_dot fields of the lists are not read;
+ *  2. DP update to bodies_k1 (mcd_update_dps with the run's parameters);
+ *  3. u~ = u^k(x^{k+1}) (mcd_ale_interpolate with the step-k velocity
+ *     stencils and bodies_k; with ale_pressure also the PPE's guess);
+ *  4. velocity stencils of the new cloud, the bodies' normals and Neumann
+ *     data dP/dn = -dV/dt . n (Eq. (23)), pressure stencils;
+ *  5. boundary velocities V + omega x r on the body DPs, 0 on the walls
+ *     (Eqs. (24)-(25)); u* and src = (1/dt) div u* (Eqs. (20)-(21));
+ *  6. the PPE (mcd_solve_pressure with `solve`, walls P = 0) and
+ *     u^{k+1} = u* - dt grad P (Eq. (22));
+ *  7. (forces = 1) the force on every body (Eqs. (30)-(31)).
+ * bodies_k, bodies_k1: the bodies at t_k and t_{k+1} (positions, posture,
+ * velocities vel and omega), the ids of mcd_flow_create in the same order.
+ * pos_dev, mask_dev: the cloud of the last step (in), of this step (out);
+ * u_dev, v_dev, P_dev: float64 [N] fields of step k in, k+1 out (P_dev is
+ * also the solve's warm start).  info: host, may be NULL.  Synchronises the
+ * stream.  A failed solve returns its status before the projection (the
+ * cloud and the stencils are already those of step k+1). */
+mcd_status mcd_flow_step(mcd_flow *f, const mcd_body *bodies_k, const mcd_body *bodies_k1, int nbodies,
+                         double dt, const mcd_solve_params *solve, double *pos_dev, int8_t *mask_dev,
+                         double *u_dev, double *v_dev, double *P_dev, mcd_flow_info *info,
+                         mcd_stream_t stream);
+
+/* The stencil handles of the run's current cloud (owned by the run; valid
+ * until its next step or mcd_flow_destroy), e.g. for mcd_net_features on
+ * the pressure system of the last step.  NULL for an unknown `which`. */
+enum { MCD_FLOW_VELOCITY = 0, MCD_FLOW_PRESSURE = 1 };
+const mcd_stencils *mcd_flow_stencils(const mcd_flow *f, int which);
+
+/* Copy an array of the last step into dst_dev (device float64; [N], or
+ * [2][N] for the normals): MCD_FLOW_B the assembled PPE right-hand side,
+ * MCD_FLOW_GUESS the solve's initial guess, MCD_FLOW_BND the boundary data
+ * (Neumann data on the bodies), MCD_FLOW_SRC (1/dt) div u*, MCD_FLOW_NORMAL
+ * the body normals.  Asynchronous. */
+enum { MCD_FLOW_B = 0, MCD_FLOW_GUESS = 1, MCD_FLOW_BND = 2, MCD_FLOW_SRC = 3, MCD_FLOW_NORMAL = 4 };
+mcd_status mcd_flow_copy(const mcd_flow *f, int which, double *dst_dev, mcd_stream_t stream);
 
 /* -------------------------------------------------------------------------
  * Batched systems (an addition: the paper solves one system at a time)
@@ -644,6 +774,14 @@ mcd_status mcd_trace_read(unsigned long long *host_out);
  * most; otherwise MCD_EINVAL.  The call allocates and frees 8 bytes of
  * device memory and synchronises `stream`. */
 mcd_status mcd_selftest_bounded_wait(int set_flag, int64_t polls, mcd_stream_t stream);
+
+/* Staging of the persistent solve's operands (a measurement switch, not
+ * part of the method): on = 1 (the default) lets the two-barrier FP32 solve
+ * of 2D 3x3 stencils on non-periodic meshes stage each tile's rows and
+ * vectors in shared memory with TMA copies, two tiles in flight per block;
+ * on = 0 makes it load them directly.  Results are the same either way (the
+ * same arithmetic in the same order).  Process-wide; affects later solves. */
+mcd_status mcd_solver_set_staging(int on);
 
 /* Number of kernels this library has launched since it was loaded. */
 int64_t mcd_launch_count(void);

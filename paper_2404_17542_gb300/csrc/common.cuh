@@ -283,6 +283,7 @@ struct mcd_stencils {
     int8_t *kind;        // [N]
     uint16_t *off16;     // [N][2] bf16 DP offsets (x - x_cell) / l0 (2D; network features)
     unsigned long long *bad_dp;  // device: smallest failing DP, ~0ull if none
+    int *spmv_err;       // device: nonzero if a TMA-streamed SpMV gave up waiting for its copies
     mcd::Workspace *ws;
 };
 

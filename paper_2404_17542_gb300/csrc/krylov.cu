@@ -54,7 +54,14 @@ struct Scalars {
     int phase_err;    // a grid barrier gave up (timeout)
     double rr_last;   // recursive-precision ||r||^2 at the last true residual
     int it_last;      // iteration of the last true residual
-    int diverged;     // MIXED: the FP32 recursion diverged (its correction dropped)
+    int diverged;     // why the recursion stopped: 1 diverged (correction dropped), 2 breakdown
+                      // restarts exhausted, 3 alpha breakdown, 4 t = 0, 5 non-finite dot
+    int replace;      // next CA: r was replaced by the true residual; keep p, v, r^
+    int net_fresh;    // the network just corrected x64: this update continues (no exit)
+    int discard;      // MIXED: the cycle's recursion diverged: drop its correction, restart
+    int divergences;  // cycles dropped so far
+    int updates;      // true-residual updates (persistent schedule)
+    int no_replace;   // a replaced recursion diverged: restart at every later update
 };
 
 // Refresh the FP32 copies (called by the single thread that updates them).
@@ -87,6 +94,7 @@ struct Workspace {
     // FP32 Krylov vectors
     float *fr = nullptr, *frh = nullptr, *fp[2] = {nullptr, nullptr}, *fv[2] = {nullptr, nullptr},
           *fs = nullptr, *ft = nullptr, *fd = nullptr;
+    float *fdlo = nullptr;        // low part of the double-float correction (persistent MIXED)
     double *partials = nullptr;  // [4][max(nblk, nblk1)]
     unsigned int *counter = nullptr;
     Scalars *sc = nullptr;
@@ -102,7 +110,7 @@ void free_workspace(mcd_stencils *st) {
     cudaFree(w->dr); cudaFree(w->drh); cudaFree(w->dp[0]); cudaFree(w->dp[1]);
     cudaFree(w->dv[0]); cudaFree(w->dv[1]); cudaFree(w->ds); cudaFree(w->dt);
     cudaFree(w->fr); cudaFree(w->frh); cudaFree(w->fp[0]); cudaFree(w->fp[1]);
-    cudaFree(w->fv[0]); cudaFree(w->fv[1]); cudaFree(w->fs); cudaFree(w->ft); cudaFree(w->fd);
+    cudaFree(w->fv[0]); cudaFree(w->fv[1]); cudaFree(w->fs); cudaFree(w->ft); cudaFree(w->fd); cudaFree(w->fdlo);
     cudaFree(w->partials); cudaFree(w->counter); cudaFree(w->sc); cudaFree(w->bar);
     cudaFreeHost(w->h_sc);
     delete w;
@@ -564,6 +572,7 @@ static mcd_status ensure_workspace(mcd_stencils *st, int mode) {
         chk(cudaMalloc(&w->fs, N * sizeof(float)));
         chk(cudaMalloc(&w->ft, N * sizeof(float)));
         chk(cudaMalloc(&w->fd, N * sizeof(float)));
+        chk(cudaMalloc(&w->fdlo, N * sizeof(float)));
         if (e == cudaSuccess) e = cudaMemset(w->frh, 0, N * sizeof(float));
     }
     if (e != cudaSuccess) {
@@ -817,6 +826,7 @@ struct PArgs {
     const double *b;         // FP64 right-hand side
     double *x64;             // FP64 solution
     void *x, *r, *rh, *p0, *p1, *v0, *v1, *s, *t;   // T vectors (x = correction in MIXED)
+    float *xlo;              // MIXED two-barrier: low part of the correction (x, xlo), else NULL
     Scalars *sc;
     double *partials;
     int pstride;
@@ -830,8 +840,16 @@ struct PArgs {
     int iter_budget;         // iterations this launch may run
     long long spin_limit;
     unsigned long long *trace;   // non-NULL: block 0 stamps phase times here
+    int net_exit;                // MIXED with a preconditioner network: leave the launch at each
+                                 // true-residual update (done = 5) for the host to apply it
     int tma_rows;                // wide stencils: rows streamed by TMA (tmap_rows)
     CUtensorMap tmap_rows;       // rows as a [S][n_y][n_x] tensor, box one tile x 9 slots
+    int tma3;                    // 2D 3x3 FP32: phase operands staged by TMA (maps3)
+    struct {
+        CUtensorMap rows;        // [9][n_y][n_x], box 32 x 16 x 9
+        CUtensorMap halo[7];     // s, t, p0, p1, v0, v1, r as [n_y][n_x], box 40 x 18
+        CUtensorMap point[3];    // r^, x, xlo, box 32 x 16
+    } maps3;
 };
 
 __device__ __forceinline__ int tile_first(const PArgs &a, int block) {
@@ -880,7 +898,7 @@ __device__ __forceinline__ void release_all(const PArgs &a, unsigned epoch) {
 
 // Scalars of one step of the two-barrier kernel, as its block sees them.
 template <typename T> struct ScalarSnap {
-    int done, perr, pend, par, restart, sconv;
+    int done, perr, pend, par, restart, sconv, replace, discard;
     T alpha, omega, beta;
 };
 
@@ -893,6 +911,8 @@ __device__ __forceinline__ void take_scalars(const Scalars *sc, ScalarSnap<T> &s
         sn.par = vload(&sc->parity);
         sn.restart = vload(&sc->restart);
         sn.sconv = vload(&sc->s_conv);
+        sn.replace = vload(&sc->replace);
+        sn.discard = vload(&sc->discard);
         if constexpr (sizeof(T) == 4) {
             sn.alpha = vload(&sc->alpha_f);
             sn.omega = vload(&sc->omega_f);
@@ -925,6 +945,8 @@ __device__ __forceinline__ void store_step_scalars(Scalars *g, const Scalars &l)
     g->parity = l.parity;
     g->restart = l.restart;
     g->s_conv = l.s_conv;
+    g->replace = l.replace;
+    g->discard = l.discard;
     if constexpr (sizeof(T) == 4) {
         g->alpha_f = l.alpha_f;
         g->omega_f = l.omega_f;
@@ -1327,8 +1349,36 @@ __device__ void phase_fold(const PArgs &a) {
             int lx, ly, lz;
             const int64_t k = tile_dp<G>(g, tid, q, x0, y0, z0, lx, ly, lz);
             if (k < 0) continue;
-            a.x64[k] += (double)__ldcg(x + k);
+            double add = (double)__ldcg(x + k);
+            if (a.xlo) {
+                add += (double)__ldcg(a.xlo + k);
+                a.xlo[k] = 0.0f;
+            }
+            a.x64[k] += add;
             x[k] = (T)0;
+        }
+    }
+}
+
+// Discard (MIXED): x = 0 (and its low part) over the block's own DPs: the
+// correction of a cycle whose recursion diverged is dropped, not folded.
+template <int G, typename T>
+__device__ void phase_discard(const PArgs &a) {
+    using TL = Tile<G>;
+    const Geo &g = a.ta.g;
+    T *x = (T *)a.x;
+    const int tid = threadIdx.x;
+    const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
+    for (int tl = tb; tl < te; ++tl) {
+        int x0, y0, z0;
+        tile_origin<G>(a.ta, tl, x0, y0, z0);
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            int lx, ly, lz;
+            const int64_t k = tile_dp<G>(g, tid, q, x0, y0, z0, lx, ly, lz);
+            if (k < 0) continue;
+            x[k] = (T)0;
+            if (a.xlo) a.xlo[k] = 0.0f;
         }
     }
 }
@@ -1576,6 +1626,7 @@ template <typename T> struct RowPipe {
     uint64_t *mbar;      // NB transaction barriers
     unsigned parity;     // bit b: parity of buffer b's next completion
     bool failed;
+    unsigned outstanding;   // staged phases (thread 0): bit b set while buffer b has a copy in flight
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -1704,7 +1755,30 @@ __device__ void pipe_stencil(const PArgs &a, RowPipe<T> &pp, int tb, int i0, int
     }
 }
 
-enum { CA_NORMAL = 0, CA_RESTART = 1, CA_SCONV = 2 };
+// The correction of a MIXED solve as a double-float pair (x, xlo):
+// x + xlo + alpha p + omega s with both products split exactly (fma) and
+// the sums by TwoSum, renormalised so |xlo| <= ulp(x) / 2.  A rounding
+// error e in the correction moves the true residual by A e, amplified by
+// the condition number of A (1e5-1e6 on these meshes); kept in one FP32
+// word the correction would separate the true residual from the recursive
+// one by ~1e-2 of the residual at the last update, which is what limits how
+// far an FP32 cycle can run and whether a replaced residual keeps the
+// recursion going.
+__device__ __forceinline__ void add_correction(float *xlo, float *x, int64_t k, float xh, float xl, float alpha,
+                                               float p, float omega, float s) {
+    DF acc{xh, xl};
+    df_add_prod(acc, alpha, p);
+    df_add_prod(acc, omega, s);
+    float hi, lo;
+    two_sum_f(acc.hi, acc.lo, hi, lo);
+    x[k] = hi;
+    xlo[k] = lo;
+}
+
+// CA_REPLACE: r already holds the true residual that replaced the recursive
+// one (reliable update with residual replacement); x and r are not updated,
+// p = r + beta (p_old - omega v_old) continues the recursion.
+enum { CA_NORMAL = 0, CA_RESTART = 1, CA_SCONV = 2, CA_REPLACE = 3 };
 
 template <int G, typename T>
 __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old, T *p_new, T *v_new,
@@ -1724,6 +1798,7 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
     const int tid = threadIdx.x;
     const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
     const bool tma = (S > 27) && a.tma_rows && mode != CA_SCONV;
+    const bool rep = mode == CA_REPLACE;
     const int total = RowPipe<T>::SL * (te - tb);
     if (tma) pipe_start<G, T>(a, pp, tb, total);
     for (int tl = tb; tl < te; ++tl) {
@@ -1733,15 +1808,17 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
         int lx[TL::R], ly[TL::R], lz[TL::R];
         T w[TL::R][PREF ? S : 1];
         T rh[TL::R], xo[TL::R], po[TL::R], so[TL::R], to[TL::R];
+        float xl[TL::R];
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
             k[q] = tile_dp<G>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
             const bool in = k[q] >= 0;
             if (PREF && mode != CA_SCONV) load_row<S, T>(row, g.N, k[q], w[q]);
             rh[q] = (mode != CA_RESTART && in) ? __ldcg(rhat + k[q]) : (T)0;
-            xo[q] = (mode != CA_RESTART && in) ? __ldcg(x + k[q]) : (T)0;
-            po[q] = (mode != CA_RESTART && in) ? __ldcg(p_old + k[q]) : (T)0;
-            so[q] = (mode != CA_RESTART && in) ? __ldcg(s + k[q]) : (T)0;
+            xo[q] = (mode != CA_RESTART && !rep && in) ? __ldcg(x + k[q]) : (T)0;
+            xl[q] = (a.xlo && mode != CA_RESTART && !rep && in) ? __ldcg(a.xlo + k[q]) : 0.0f;
+            po[q] = (mode != CA_RESTART && !rep && in) ? __ldcg(p_old + k[q]) : (T)0;
+            so[q] = (mode != CA_RESTART && in) ? __ldcg((rep ? (const T *)r : s) + k[q]) : (T)0;
             to[q] = (mode == CA_NORMAL && in) ? __ldcg(t + k[q]) : (T)0;
         }
         if (mode == CA_SCONV) {
@@ -1749,7 +1826,11 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
 #pragma unroll
             for (int q = 0; q < TL::R; ++q) {
                 if (k[q] < 0) continue;
-                x[k[q]] = xo[q] + alpha * po[q];
+                if (a.xlo) {
+                    if constexpr (sizeof(T) == 4) add_correction(a.xlo, x, k[q], xo[q], xl[q], alpha, po[q], 0.0f, 0.0f);
+                } else {
+                    x[k[q]] = xo[q] + alpha * po[q];
+                }
                 r[k[q]] = so[q];
                 dot[1].add(so[q], so[q]);
                 dot[2].add(rh[q], so[q]);
@@ -1767,8 +1848,9 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
                 if (mode == CA_RESTART) {
                     h1[u] = __ldcg(r + j);
                 } else {
-                    h1[u] = __ldcg(s + j);
-                    h2[u] = __ldcg(t + j);
+                    // CA_REPLACE: r_j = r[j] (h2 = 0 makes r_j = h1 exactly)
+                    h1[u] = __ldcg((rep ? (const T *)r : s) + j);
+                    if (!rep) h2[u] = __ldcg(t + j);
                     h3[u] = __ldcg(p_old + j);
                     h4[u] = __ldcg(v_old + j);
                 }
@@ -1798,9 +1880,15 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
                 rk = pk;   // p = r on a restart
                 rq = pk;
                 rhat[k[q]] = pk;
+            } else if (rep) {
+                rk = so[q];   // the replaced residual, already stored
             } else {
                 rk = so[q] - omega * to[q];
-                x[k[q]] = xo[q] + alpha * po[q] + omega * so[q];
+                if (a.xlo) {
+                    if constexpr (sizeof(T) == 4) add_correction(a.xlo, x, k[q], xo[q], xl[q], alpha, po[q], omega, so[q]);
+                } else {
+                    x[k[q]] = xo[q] + alpha * po[q] + omega * so[q];
+                }
                 r[k[q]] = rk;
             }
             p_new[k[q]] = pk;
@@ -1909,6 +1997,231 @@ __device__ void phase_b2(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T>
     }
 }
 
+// ---- TMA-staged phases of the two-barrier kernel (2D 3x3, FP32) ----------
+// A block's phase walks its tiles with two stages in flight: while all
+// threads work on tile i from shared memory, thread 0 has tile i + 1's
+// operands on the way.  A stage holds everything the tile's phase reads: the
+// nine weight slots of its 32 x 16 DPs (one 3D copy of the rows), 40 x 18
+// halo boxes of the vectors the stencil is applied to (x from x0 - 4 so that
+// each copy starts on a 16-byte boundary, y from y0 - 1), and 32 x 16 boxes
+// of the point vectors.  Copies past the mesh fill zeros: on a non-periodic
+// mesh those neighbours carry zero weight, and every value formed there is
+// finite.  The arithmetic per DP is that of phase_ca / phase_b2.
+struct Stage3 {
+    static constexpr int TX = 32, TY = 16, HXB = 40, HYB = 18;
+    static constexpr unsigned W_BYTES = 9u * TX * TY * 4u;      // 18432
+    static constexpr unsigned H_BYTES = HXB * HYB * 4u;         // 2880
+    static constexpr unsigned H_PAD = 2944u;                    // 128-byte multiple
+    static constexpr unsigned P_BYTES = TX * TY * 4u;           // 2048
+    static constexpr unsigned CA_TX = W_BYTES + 4u * H_BYTES + 3u * P_BYTES;
+    static constexpr unsigned B_TX = W_BYTES + 2u * H_BYTES + P_BYTES;
+    static constexpr unsigned BYTES = W_BYTES + 4u * H_PAD + 3u * P_BYTES;
+    static constexpr int NB = 2;
+    static constexpr unsigned halo_off(int q) { return W_BYTES + (unsigned)q * H_PAD; }
+    static constexpr unsigned point_off(int q) { return W_BYTES + 4u * H_PAD + (unsigned)q * P_BYTES; }
+};
+static_assert(Tile<2>::X == Stage3::TX && Tile<2>::Y == Stage3::TY, "stage boxes are one 2D tile");
+enum { H_S = 0, H_T = 1, H_P0 = 2, H_P1 = 3, H_V0 = 4, H_V1 = 5, H_R = 6 };
+enum { PT_RH = 0, PT_X = 1, PT_XLO = 2 };
+
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mb) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mb)
+        : "memory");
+}
+
+// Thread 0: tile `tl` of a phase into stage buffer b.  ca: phase CA (halos
+// s, t, p_old, v_old; points r^, x, xlo), else phase B (halos r, v; point
+// r^).  par: the p / v buffer the phase reads (p_old, v_old in CA; v in B).
+__device__ __forceinline__ void stage_issue(const PArgs &a, RowPipe<float> &pp, int b, int tl, bool ca,
+                                            int par) {
+    pp.outstanding |= 1u << b;
+    int x0, y0, z0;
+    tile_origin<2>(a.ta, tl, x0, y0, z0);
+    const uint32_t mb = smem_addr(pp.mbar + b);
+    const uint32_t dst = smem_addr(pp.buf) + (uint32_t)b * Stage3::BYTES;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of the buffer
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
+                 "r"(ca ? Stage3::CA_TX : Stage3::B_TX)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(dst), "l"(reinterpret_cast<uint64_t>(&a.maps3.rows)), "r"(x0), "r"(y0), "r"(0), "r"(mb)
+        : "memory");
+    const int hx = x0 - 4, hy = y0 - 1;
+    if (ca) {
+        tma_2d(dst + Stage3::halo_off(0), &a.maps3.halo[H_S], hx, hy, mb);
+        tma_2d(dst + Stage3::halo_off(1), &a.maps3.halo[H_T], hx, hy, mb);
+        tma_2d(dst + Stage3::halo_off(2), &a.maps3.halo[par ? H_P1 : H_P0], hx, hy, mb);
+        tma_2d(dst + Stage3::halo_off(3), &a.maps3.halo[par ? H_V1 : H_V0], hx, hy, mb);
+        tma_2d(dst + Stage3::point_off(0), &a.maps3.point[PT_RH], x0, y0, mb);
+        tma_2d(dst + Stage3::point_off(1), &a.maps3.point[PT_X], x0, y0, mb);
+        tma_2d(dst + Stage3::point_off(2), &a.maps3.point[PT_XLO], x0, y0, mb);
+    } else {
+        tma_2d(dst + Stage3::halo_off(0), &a.maps3.halo[H_R], hx, hy, mb);
+        tma_2d(dst + Stage3::halo_off(1), &a.maps3.halo[par ? H_V1 : H_V0], hx, hy, mb);
+        tma_2d(dst + Stage3::point_off(0), &a.maps3.point[PT_RH], x0, y0, mb);
+    }
+}
+
+// Wait (bounded) for stage b; a timeout raises the solve's error word and
+// the phase runs on (its results are discarded with the launch).
+__device__ __forceinline__ void stage_wait(const PArgs &a, RowPipe<float> &pp, int b) {
+    if (pp.failed) return;
+    if (pipe_wait(pp, b, a.spin_limit)) {
+        pp.outstanding &= ~(1u << b);
+    } else {
+        pp.failed = true;
+        atomicExch(&a.sc->phase_err, 5);
+    }
+}
+
+// After a timeout: thread 0 waits (bounded) for the copies it still has in
+// flight, so that none lands in shared memory the block no longer owns.
+__device__ __forceinline__ void stage_drain(const PArgs &a, RowPipe<float> &pp) {
+    if (threadIdx.x != 0 || !pp.failed) return;
+    for (int b = 0; b < Stage3::NB; ++b)
+        if (pp.outstanding & (1u << b)) {
+            pipe_wait(pp, b, a.spin_limit);
+            pp.outstanding &= ~(1u << b);
+        }
+}
+
+// Phase CA (normal iterations) from staged operands: x, r of the last
+// iteration; p = r + beta (p_old - omega v_old) on tile + halo; v = A p.
+__device__ void phase_ca_staged(const PArgs &a, float *tile, int par, float alpha, float omega, float beta,
+                                DotAcc<float> (&dot)[3], RowPipe<float> &pp) {
+    using HD = HaloDims<2>;
+    using TL = Tile<2>;
+    const Geo &g = a.ta.g;
+    float *x = (float *)a.x;
+    float *r = (float *)a.r;
+    float *p_new = (float *)(par ? a.p0 : a.p1);
+    float *v_new = (float *)(par ? a.v0 : a.v1);
+    const int tid = threadIdx.x;
+    const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
+    const int total = te - tb;
+    if (tid == 0 && !pp.failed)
+        for (int i = 0; i < Stage3::NB && i < total; ++i) stage_issue(a, pp, i, tb + i, true, par);
+    for (int i = 0; i < total; ++i) {
+        const int b = i % Stage3::NB;
+        stage_wait(a, pp, b);
+        const unsigned char *st = reinterpret_cast<const unsigned char *>(pp.buf) + (size_t)b * Stage3::BYTES;
+        const float *W = reinterpret_cast<const float *>(st);
+        const float *S = reinterpret_cast<const float *>(st + Stage3::halo_off(0));
+        const float *T = reinterpret_cast<const float *>(st + Stage3::halo_off(1));
+        const float *PO = reinterpret_cast<const float *>(st + Stage3::halo_off(2));
+        const float *VO = reinterpret_cast<const float *>(st + Stage3::halo_off(3));
+        const float *RH = reinterpret_cast<const float *>(st + Stage3::point_off(0));
+        const float *X = reinterpret_cast<const float *>(st + Stage3::point_off(1));
+        const float *XL = reinterpret_cast<const float *>(st + Stage3::point_off(2));
+        int x0, y0, z0;
+        tile_origin<2>(a.ta, tb + i, x0, y0, z0);
+        for (int h = tid; h < HD::H; h += 256) {
+            const int hy = h / HD::HX, hx = h - hy * HD::HX;
+            const int hi = hy * Stage3::HXB + hx + 3;
+            const float rj = S[hi] - omega * T[hi];
+            tile[h] = rj + beta * (PO[hi] - omega * VO[hi]);
+        }
+        int64_t k[TL::R];
+        int lx[TL::R], ly[TL::R], lz[TL::R];
+        float w[TL::R][9], so[TL::R], to[TL::R], po[TL::R], rh[TL::R], xo[TL::R], xl[TL::R];
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            k[q] = tile_dp<2>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+            const int pi = ly[q] * Stage3::TX + lx[q];
+            const int hc = (ly[q] + 1) * Stage3::HXB + lx[q] + 4;
+#pragma unroll
+            for (int sl = 0; sl < 9; ++sl) w[q][sl] = W[sl * (Stage3::TX * Stage3::TY) + pi];
+            so[q] = S[hc]; to[q] = T[hc]; po[q] = PO[hc];
+            rh[q] = RH[pi]; xo[q] = X[pi]; xl[q] = XL[pi];
+        }
+        __syncthreads();   // the halo tile is complete and stage b is read: refill it
+        if (tid == 0 && !pp.failed && i + Stage3::NB < total) stage_issue(a, pp, b, tb + i + Stage3::NB, true, par);
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            if (k[q] < 0) continue;
+            const float pk = tile[tile_centre<2>(lx[q], ly[q], 0)];
+            const float rk = so[q] - omega * to[q];
+            add_correction(a.xlo, x, k[q], xo[q], xl[q], alpha, po[q], omega, so[q]);
+            r[k[q]] = rk;
+            p_new[k[q]] = pk;
+            const float vk = (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN)
+                                 ? pk
+                                 : stencil_apply<2, float>(w[q], tile, lx[q], ly[q], 0);
+            v_new[k[q]] = vk;
+            dot[0].add(rh[q], vk);
+            dot[1].add(rk, rk);
+            dot[2].add(rh[q], rk);
+        }
+        __syncthreads();   // the halo tile is free for the next tile
+    }
+    stage_drain(a, pp);
+}
+
+// Phase B from staged operands: s = r - alpha v (tile + halo), t = A s;
+// dots t.s, t.t, s.s, r^.s, r^.t.
+__device__ void phase_b2_staged(const PArgs &a, float *tile, int parb, float alpha, DotAcc<float> (&dot)[5],
+                                RowPipe<float> &pp) {
+    using HD = HaloDims<2>;
+    using TL = Tile<2>;
+    const Geo &g = a.ta.g;
+    float *s_out = (float *)a.s;
+    float *t_out = (float *)a.t;
+    const int tid = threadIdx.x;
+    const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
+    const int total = te - tb;
+    if (tid == 0 && !pp.failed)
+        for (int i = 0; i < Stage3::NB && i < total; ++i) stage_issue(a, pp, i, tb + i, false, parb);
+    for (int i = 0; i < total; ++i) {
+        const int b = i % Stage3::NB;
+        stage_wait(a, pp, b);
+        const unsigned char *st = reinterpret_cast<const unsigned char *>(pp.buf) + (size_t)b * Stage3::BYTES;
+        const float *W = reinterpret_cast<const float *>(st);
+        const float *R = reinterpret_cast<const float *>(st + Stage3::halo_off(0));
+        const float *V = reinterpret_cast<const float *>(st + Stage3::halo_off(1));
+        const float *RH = reinterpret_cast<const float *>(st + Stage3::point_off(0));
+        int x0, y0, z0;
+        tile_origin<2>(a.ta, tb + i, x0, y0, z0);
+        for (int h = tid; h < HD::H; h += 256) {
+            const int hy = h / HD::HX, hx = h - hy * HD::HX;
+            const int hi = hy * Stage3::HXB + hx + 3;
+            tile[h] = R[hi] - alpha * V[hi];
+        }
+        int64_t k[TL::R];
+        int lx[TL::R], ly[TL::R], lz[TL::R];
+        float w[TL::R][9], rh[TL::R];
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            k[q] = tile_dp<2>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+            const int pi = ly[q] * Stage3::TX + lx[q];
+#pragma unroll
+            for (int sl = 0; sl < 9; ++sl) w[q][sl] = W[sl * (Stage3::TX * Stage3::TY) + pi];
+            rh[q] = RH[pi];
+        }
+        __syncthreads();
+        if (tid == 0 && !pp.failed && i + Stage3::NB < total) stage_issue(a, pp, b, tb + i + Stage3::NB, false, parb);
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            if (k[q] < 0) continue;
+            const float sk = tile[tile_centre<2>(lx[q], ly[q], 0)];
+            s_out[k[q]] = sk;
+            const float tk = (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN)
+                                 ? sk
+                                 : stencil_apply<2, float>(w[q], tile, lx[q], ly[q], 0);
+            t_out[k[q]] = tk;
+            dot[0].add(tk, sk);
+            dot[1].add(tk, tk);
+            dot[2].add(sk, sk);
+            dot[3].add(rh[q], sk);
+            dot[4].add(rh[q], tk);
+        }
+        __syncthreads();
+    }
+    stage_drain(a, pp);
+}
+
 // Wide stencils ask for two blocks per SM explicitly (their accumulators
 // otherwise lead the register allocator to spill); a minimum of 0 leaves the
 // compact stencils as the compiler places them.
@@ -1917,15 +2230,23 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
     using HD = HaloDims<G>;
     __shared__ T tile[HD::H];
     extern __shared__ __align__(128) unsigned char pipe_smem[];
-    __shared__ __align__(8) uint64_t pipe_mbar[Shape<G>::S > 27 ? RowPipe<T>::NB : 1];
+    __shared__ __align__(8) uint64_t pipe_mbar[Shape<G>::S > 27 ? RowPipe<T>::NB : Stage3::NB];
     RowPipe<T> pp;
     pp.buf = reinterpret_cast<T *>(pipe_smem);
     pp.mbar = pipe_mbar;
     pp.parity = 0;
     pp.failed = false;
+    pp.outstanding = 0;
     if constexpr (Shape<G>::S > 27) {
         if (a.tma_rows && threadIdx.x == 0) {
             for (int b = 0; b < RowPipe<T>::NB; ++b)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(pipe_mbar + b)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    } else if constexpr (G == 2 && sizeof(T) == 4) {
+        if (a.tma3 && threadIdx.x == 0) {
+            for (int b = 0; b < Stage3::NB; ++b)
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(pipe_mbar + b)) : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
@@ -1948,13 +2269,16 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
     take_scalars(a.sc, snap);
     for (;;) {
         const int done0 = snap.done, perr0 = snap.perr, pend0 = snap.pend;
-        const int par = snap.par, restart0 = snap.restart, sconv0 = snap.sconv;
+        const int par = snap.par, restart0 = snap.restart, sconv0 = snap.sconv, replace0 = snap.replace;
         const T alpha0 = snap.alpha, omega0 = snap.omega, beta0 = snap.beta;
         if (done0 || perr0) goto finish;
         if (pend0) {
             // ---- true residual (reliable) update: as in the three-barrier kernel
             if (a.mixed) {
-                phase_fold<G, T>(a);
+                if (snap.discard)
+                    phase_discard<G, T>(a);
+                else
+                    phase_fold<G, T>(a);
                 DotAcc<double> none[1];
                 if (!grid_reduce<1>(a, epoch, none, [&](double *) {})) goto finish;
             }
@@ -1972,6 +2296,8 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
                 all[3].v = dt[1].v;
             }
             const double tol = a.tol;
+            const int update_mode = a.update_mode;
+            const int net_exit = a.net_exit;
             auto tr_last = [&](double *tot) {
                     sc->rr64 = tot[0];
                     sc->bb64 = tot[1];
@@ -1983,6 +2309,34 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
                     if (sc->max_hit) { sc->done = 2; return; }
                     sc->rr_last = tot[3];
                     sc->it_last = sc->iter;
+                    sc->updates += 1;
+                    const bool corrected = sc->net_fresh != 0 || sc->discard != 0;
+                    const bool keep = update_mode == 2 && !sc->no_replace && !corrected && !sc->restart &&
+                                      !sc->s_conv && sc->rho != 0.0 && sc->omega != 0.0;
+                    // an update that restarts the recursion (the first, after a
+                    // dropped cycle, an ||s|| stop or a breakdown; every update
+                    // of the restarting schedule) begins a new refinement
+                    // cycle: with a preconditioner network the host adds the
+                    // network's correction of this residual first (done = 5)
+                    // and relaunches with net_fresh set
+                    if (net_exit && !sc->net_fresh && !keep) { sc->done = 5; return; }
+                    sc->net_fresh = 0;
+                    sc->discard = 0;
+                    // residual replacement (update_mode 2): r now holds the
+                    // true residual; the recursion continues from the last
+                    // complete iteration with beta recomputed from
+                    // rho' = r^.r, keeping p, v and r^.  Otherwise (update
+                    // mode 1, the first update, after an ||s|| stop or a
+                    // restart) the recursion restarts from r.
+                    if (keep) {
+                        const double beta = (tot[2] / sc->rho) * (sc->alpha / sc->omega);
+                        if (isfinite(beta)) {
+                            sc->beta = beta;
+                            sc->replace = 1;
+                            publish(sc);
+                            return;
+                        }
+                    }
                     sc->restart = 1;
                     sc->s_conv = 0;
                     sc->alpha = sc->beta = sc->omega = 0.0;
@@ -2002,35 +2356,64 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
         T *v_old = (T *)(par ? a.v1 : a.v0), *v_new = (T *)(par ? a.v0 : a.v1);
         // ---- phase CA: x, r of the last iteration; p, v = A p; alpha ------
         {
-            const int mode = restart0 ? CA_RESTART : (sconv0 ? CA_SCONV : CA_NORMAL);
+            const int mode = restart0 ? CA_RESTART : (replace0 ? CA_REPLACE : (sconv0 ? CA_SCONV : CA_NORMAL));
             DotAcc<T> dot[3];
-            phase_ca<G, T>(a, tile, p_old, v_old, p_new, v_new, alpha0, omega0, beta0, mode, dot, pp);
+            if constexpr (G == 2 && sizeof(T) == 4) {
+                if (a.tma3 && mode == CA_NORMAL)
+                    phase_ca_staged(a, tile, par, alpha0, omega0, beta0, dot, pp);
+                else
+                    phase_ca<G, T>(a, tile, p_old, v_old, p_new, v_new, alpha0, omega0, beta0, mode, dot, pp);
+            } else {
+                phase_ca<G, T>(a, tile, p_old, v_old, p_new, v_new, alpha0, omega0, beta0, mode, dot, pp);
+            }
             stamp(a, it, 1);
             stamp_block(a, it);
             const int stall = a.stall;
             const double eps = a.eps_breakdown;
             const double update2 = a.update2;
             const int mixed = a.mixed;
+            const int update_mode_ca = a.update_mode;
             auto ca_last = [&](const double *tot) {
                 const double rv = tot[0], rr = tot[1], rho = tot[2];
                 sc->rv = rv;
                 sc->rr = rr;
-                if (mode != CA_RESTART) sc->iter += 1;   // iteration k finished (x, r)
-                if (!isfinite(rv + rr + rho)) { sc->done = 4; return; }
-                if (mode == CA_SCONV) { sc->s_conv = 0; sc->pending = 1; return; }
+                sc->replace = 0;
+                // iteration k finished (x, r); a replacement CA finishes none
+                if (mode == CA_NORMAL || mode == CA_SCONV) sc->iter += 1;
+                if (!isfinite(rv + rr + rho)) { sc->diverged = 5; sc->done = 4; return; }
+                // s_conv stays set: the update that follows restarts (this
+                // iteration computed no omega to continue from)
+                if (mode == CA_SCONV) { sc->pending = 1; return; }
                 if (mode == CA_RESTART) {
                     sc->rhat2 = rr;
                 } else {
                     if (rr <= sc->tol2) { sc->pending = 1; return; }
                     if (sc->iter >= sc->max_iter) { sc->max_hit = 1; sc->pending = 1; return; }
                     if (mixed && rr <= update2 * sc->rr_last) { sc->pending = 1; return; }
-                    if (mixed && rr > 1e8 * sc->rr_last) { sc->diverged = 1; sc->done = 3; return; }
+                    // a recursion whose residual grew since the last true
+                    // residual beyond what its schedule allows has diverged:
+                    // its correction is dropped, the recursion restarts from
+                    // the last folded iterate, and every later update of the
+                    // solve restarts too (the solve finishes in FP64 after 64
+                    // such cycles)
+                    // growth that counts as divergence: 100-fold in norm while
+                    // residuals are replaced; the restarting schedule's short
+                    // cycles spike higher on their own (1e4-fold)
+                    const bool replacing = update_mode_ca == 2 && !sc->no_replace;
+                    if (mixed && rr > (replacing ? 1e4 : 1e8) * sc->rr_last) {
+                        sc->divergences += 1;
+                        if (sc->divergences > 64) { sc->diverged = 1; sc->done = 3; return; }
+                        sc->discard = 1;
+                        sc->no_replace = 1;   // this system is beyond the FP32 rows' reach for replacement
+                        sc->pending = 1;
+                        return;
+                    }
                     if (mixed && sc->iter - sc->it_last >= stall) { sc->pending = 1; return; }
                     // |rho| <= eps sqrt(|r^|^2 |r|^2), squared: no FP64
                     // square root on the barrier's path
                     if (rho * rho <= eps * eps * (sc->rhat2 * rr)) {
                         sc->restarts += 1;
-                        if (sc->restarts > 1000) { sc->done = 3; return; }
+                        if (sc->restarts > 1000) { sc->diverged = 2; sc->done = 3; return; }
                         sc->restart = 1;   // redo CA from this r with p = r
                         return;
                     }
@@ -2039,7 +2422,7 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
                 sc->parity ^= 1;
                 sc->rho = rho;
                 const double alpha_n = rho / rv;
-                if (!isfinite(alpha_n) || alpha_n == 0.0) { sc->done = 3; return; }
+                if (!isfinite(alpha_n) || alpha_n == 0.0) { sc->diverged = 3; sc->done = 3; return; }
                 sc->alpha = alpha_n;
                 sc->alpha_f = (float)alpha_n;   // omega_f and beta_f are unchanged since phase B
             };
@@ -2066,15 +2449,22 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
         {
             const T *v_cur = (const T *)(parb ? a.v1 : a.v0);
             DotAcc<T> dot[5];
-            phase_b2<G, T>(a, tile, v_cur, alpha, dot, pp);
+            if constexpr (G == 2 && sizeof(T) == 4) {
+                if (a.tma3)
+                    phase_b2_staged(a, tile, parb, alpha, dot, pp);
+                else
+                    phase_b2<G, T>(a, tile, v_cur, alpha, dot, pp);
+            } else {
+                phase_b2<G, T>(a, tile, v_cur, alpha, dot, pp);
+            }
             stamp(a, it, 3);
             auto b_last = [&](const double *tot) {
                 sc->ts = tot[0];
                 sc->tt = tot[1];
                 sc->ss = tot[2];
-                if (!isfinite(tot[0] + tot[1] + tot[2] + tot[3] + tot[4])) { sc->done = 4; return; }
+                if (!isfinite(tot[0] + tot[1] + tot[2] + tot[3] + tot[4])) { sc->diverged = 5; sc->done = 4; return; }
                 if (tot[2] <= sc->tol2) { sc->s_conv = 1; return; }
-                if (tot[1] == 0.0) { sc->done = 3; return; }
+                if (tot[1] == 0.0) { sc->diverged = 4; sc->done = 3; return; }
                 const double omega = tot[0] / tot[1];
                 const double rho_next = tot[3] - omega * tot[4];
                 sc->omega = omega;
@@ -2107,7 +2497,10 @@ finish:
 // wide stencil, none otherwise.
 template <int G, typename T>
 static size_t pipe_smem_bytes(bool tma) {
-    return (Shape<G>::S > 27 && tma) ? (size_t)RowPipe<T>::NB * RowPipe<T>::BYTES : 0;
+    if (!tma) return 0;
+    if (Shape<G>::S > 27) return (size_t)RowPipe<T>::NB * RowPipe<T>::BYTES;
+    if (G == 2 && sizeof(T) == 4) return (size_t)Stage3::NB * Stage3::BYTES;
+    return 0;
 }
 
 template <int G, typename T, int B>
@@ -2169,6 +2562,59 @@ static bool encode_row_map(const Geo &g, const void *row, CUtensorMap *map) {
     return r == CUDA_SUCCESS;
 }
 
+// Process-wide switch of the staged phases (mcd_solver_set_staging).
+static int g_no_stage = 0;
+static bool st_no_stage() { return g_no_stage != 0; }
+
+// Tensor maps of the staged 2D 3x3 FP32 phases: the rows as [9][n_y][n_x]
+// (box 32 x 16 x 9), the halo vectors with a 40 x 18 box, the point vectors
+// with a 32 x 16 box.  False (the phases then load directly) on a periodic
+// mesh (a copy cannot wrap), when n_x is not a multiple of 4 (16-byte row
+// strides), on meshes smaller than a halo box, or without the encoder.
+static bool encode_stage_maps(const Geo &g, const float *row, const void *const *halo, const void *const *point,
+                              PArgs &a) {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    if (!fn || g.dim != 2 || g.per[0] || g.per[1] || g.n[0] % 4 != 0) return false;
+    if (g.n[0] < Stage3::HXB || g.n[1] < Stage3::HYB) return false;
+    const cuuint64_t nx = (cuuint64_t)g.n[0], ny = (cuuint64_t)g.n[1];
+    const cuuint32_t ones[3] = {1, 1, 1};
+    auto aligned = [](const void *p) { return ((uintptr_t)p % 16) == 0; };
+    {
+        if (!aligned(row)) return false;
+        const cuuint64_t dims[3] = {nx, ny, 9};
+        const cuuint64_t str[2] = {nx * 4, nx * ny * 4};
+        const cuuint32_t box[3] = {(cuuint32_t)Stage3::TX, (cuuint32_t)Stage3::TY, 9};
+        if (fn(&a.maps3.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(row), dims, str, box, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    const cuuint64_t dims[2] = {nx, ny};
+    const cuuint64_t str[1] = {nx * 4};
+    for (int q = 0; q < 7 + 3; ++q) {
+        const void *ptr = q < 7 ? halo[q] : point[q - 7];
+        if (!ptr || !aligned(ptr)) return false;
+        const cuuint32_t hbox[2] = {(cuuint32_t)Stage3::HXB, (cuuint32_t)Stage3::HYB};
+        const cuuint32_t pbox[2] = {(cuuint32_t)Stage3::TX, (cuuint32_t)Stage3::TY};
+        CUtensorMap *m = q < 7 ? &a.maps3.halo[q] : &a.maps3.point[q - 7];
+        if (fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(ptr), dims, str, q < 7 ? hbox : pbox, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
 // Run the whole solve in persistent launches (each bounded by an iteration
 // budget and the barrier spin limit).  On return w->h_sc holds the final
 // scalars.  x64 is the FP64 solution; in FP64 mode it is also the iterate.
@@ -2177,7 +2623,7 @@ static unsigned long long *g_trace = nullptr;
 
 template <int G, typename T>
 static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_solve_params *prm,
-                                 mcd_status &result, cudaStream_t stream) {
+                                 mcd_status &result, int &net_corrections, cudaStream_t stream) {
     Workspace *w = st->ws;
     const Geo &g = st->geo;
     const bool mixed = sizeof(T) == 4;
@@ -2194,8 +2640,15 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
                                                &a.tmap_rows))
                      ? 1
                      : 0;
-    const size_t dyn_smem = two ? pipe_smem_bytes<G, T>(a.tma_rows != 0) : 0;
-    const int grid = two ? persistent_grid<G, T, 2>(a.ta.ntiles, a.tma_rows != 0)
+    a.tma3 = 0;
+    if (G == 2 && mixed && two && !st_no_stage()) {
+        const void *halo[7] = {w->fs, w->ft, w->fp[0], w->fp[1], w->fv[0], w->fv[1], w->fr};
+        const void *point[3] = {w->frh, w->fd, w->fdlo};
+        a.tma3 = encode_stage_maps(g, st->row32, halo, point, a) ? 1 : 0;
+    }
+    const bool staged = a.tma_rows != 0 || a.tma3 != 0;
+    const size_t dyn_smem = two ? pipe_smem_bytes<G, T>(staged) : 0;
+    const int grid = two ? persistent_grid<G, T, 2>(a.ta.ntiles, staged)
                          : persistent_grid<G, T, 3>(a.ta.ntiles, false);
     a.grid = grid;
     a.row64 = st->row64;
@@ -2204,10 +2657,13 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
     if (mixed) {
         a.row = st->row32;
         a.x = w->fd; a.r = w->fr; a.rh = w->frh;
+        a.xlo = two ? w->fdlo : nullptr;
         a.p0 = w->fp[0]; a.p1 = w->fp[1]; a.v0 = w->fv[0]; a.v1 = w->fv[1];
         a.s = w->fs; a.t = w->ft;
         MCD_CUDA_TRY(cudaMemsetAsync(w->fd, 0, g.N * sizeof(float), stream));
+        MCD_CUDA_TRY(cudaMemsetAsync(w->fdlo, 0, g.N * sizeof(float), stream));
     } else {
+        a.xlo = nullptr;
         a.row = st->row64;
         a.x = x64; a.r = w->dr; a.rh = w->drh;
         a.p0 = w->dp[0]; a.p1 = w->dp[1]; a.v0 = w->dv[0]; a.v1 = w->dv[1];
@@ -2218,7 +2674,7 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
     a.pstride = w->pstride;
     a.bar = w->bar;
     a.mixed = mixed ? 1 : 0;
-    a.update_mode = mixed ? (prm->update_restart == 2 ? 2 : 1) : 1;
+    a.update_mode = mixed ? (prm->update_restart == 1 ? 1 : 2) : 1;
     const double upd = (prm->inner_tol > 0.0 && prm->inner_tol < 1.0) ? prm->inner_tol : 0.3;
     a.update2 = upd * upd;
     a.stall = 1024;
@@ -2227,6 +2683,7 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
     a.iter_budget = 4096;
     a.spin_limit = 1ll << 21;   // about 1.5 s of polls (L2 round trip + 64 ns sleep)
     a.trace = g_trace;
+    a.net_exit = (mixed && two && prm->precond) ? 1 : 0;
     const size_t bar_bytes = barrier_bytes(grid);
     // start with a true-residual update of the initial guess
     int one = 1;
@@ -2245,6 +2702,20 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
         if (s != MCD_OK) return s;
         const Scalars &h = *w->h_sc;
         if (h.phase_err) { result = MCD_ETIMEOUT; return MCD_OK; }
+        if (h.done == 5) {
+            // d0 of this refinement: the network's correction of the FP64
+            // residual b - A x64, along its residual-minimising step
+            s = net_warm_start(prm->precond, st, w->b, nullptr, x64, nullptr, stream);
+            if (s != MCD_OK) return s;
+            net_corrections += 1;
+            const int zero = 0;
+            MCD_CUDA_TRY(cudaMemcpyAsync(&w->sc->done, &zero, sizeof(int), cudaMemcpyHostToDevice, stream));
+            MCD_CUDA_TRY(cudaMemcpyAsync(&w->sc->pending, &one, sizeof(int), cudaMemcpyHostToDevice, stream));
+            MCD_CUDA_TRY(cudaMemcpyAsync(&w->sc->restart, &one, sizeof(int), cudaMemcpyHostToDevice, stream));
+            MCD_CUDA_TRY(cudaMemcpyAsync(&w->sc->net_fresh, &one, sizeof(int), cudaMemcpyHostToDevice, stream));
+            --launch;   // not a launch of the iteration budget: every cycle runs >= 1 iteration
+            continue;
+        }
         if (h.done == 1) { result = MCD_OK; return MCD_OK; }
         if (h.done == 2) { result = MCD_ENOCONV; return MCD_OK; }
         if (h.done == 3) { result = MCD_EBREAKDOWN; return MCD_OK; }
@@ -2285,11 +2756,11 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
 
     mcd_status result = MCD_ENOCONV;
     int outer = 0;
-    int mixed_iters = 0, fallback = 0;
+    int mixed_iters = 0, fallback = 0, net_corr = 0, mixed_div = 0, mixed_upd = 0;
     if (prm->check_every >= 0) {
         // persistent cooperative solve (the default)
-        s = (prm->mode == MCD_FP64) ? run_persistent<G, double>(st, p, prm, result, stream)
-                                    : run_persistent<G, float>(st, p, prm, result, stream);
+        s = (prm->mode == MCD_FP64) ? run_persistent<G, double>(st, p, prm, result, net_corr, stream)
+                                    : run_persistent<G, float>(st, p, prm, result, net_corr, stream);
         if (s != MCD_OK) return s;
         if (prm->mode == MCD_MIXED && result != MCD_OK && result != MCD_ETIMEOUT) {
             // the FP32 recursion failed (diverged or broke down): finish in
@@ -2297,7 +2768,9 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
             // never touched
             const Scalars &hm = *w->h_sc;
             mixed_iters = hm.iter;
-            fallback = 1;
+            mixed_div = hm.divergences;
+            mixed_upd = hm.updates;
+            fallback = (result == MCD_ENOCONV) ? 6 : (hm.diverged > 0 ? hm.diverged : 7);
             Scalars re;
             memset(&re, 0, sizeof(re));
             re.max_iter = std::max(1, init.max_iter - hm.iter);
@@ -2305,7 +2778,7 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
             MCD_CUDA_TRY(cudaMemcpyAsync(w->sc, &re, sizeof(re), cudaMemcpyHostToDevice, stream));
             s = ensure_workspace(const_cast<mcd_stencils *>(st), MCD_FP64);
             if (s != MCD_OK) return s;
-            s = run_persistent<G, double>(st, p, prm, result, stream);
+            s = run_persistent<G, double>(st, p, prm, result, net_corr, stream);
             if (s != MCD_OK) return s;
         }
     } else if (prm->mode == MCD_FP64) {
@@ -2359,6 +2832,9 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
         info->iters = h.iter + mixed_iters;
         info->refinements = outer;
         info->fallback = fallback;
+        info->net_corrections = net_corr;
+        info->discarded = mixed_div + h.divergences;
+        if (prm->check_every >= 0) info->refinements = mixed_upd + h.updates;
         info->restarts = h.restarts;
         info->b_norm = sqrt(h.bb64);
         info->rel_res = h.bb64 > 0.0 ? sqrt(h.rr64 / h.bb64) : 0.0;
@@ -2388,6 +2864,11 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
 
 using namespace mcd;
 
+extern "C" mcd_status mcd_solver_set_staging(int on) {
+    g_no_stage = on ? 0 : 1;
+    return MCD_OK;
+}
+
 extern "C" mcd_status mcd_trace_enable(int on) {
     if (on && !g_trace) {
         MCD_CUDA_TRY(cudaMalloc(&g_trace, (512 + 6144 + 2048) * sizeof(unsigned long long)));
@@ -2416,6 +2897,8 @@ extern "C" mcd_status mcd_solve_pressure(const mcd_stencils *st, const double *r
     MCD_CHECK_ARG(prm->mode != MCD_MIXED || st->row32, "MIXED solve needs an MCD_MIXED stencil handle");
     MCD_CHECK_ARG(prm->mode != MCD_MIXED || (prm->inner_tol > 0.0 && prm->inner_tol < 1.0),
                   "inner_tol must be in (0, 1)");
+    MCD_CHECK_ARG(!prm->precond || (prm->mode == MCD_MIXED && prm->barriers != 3 && prm->check_every >= 0),
+                  "a preconditioner network needs a MIXED solve on the two-barrier persistent schedule");
     mcd_status s = mcd_stencils_check(st, nullptr, stream);
     if (s != MCD_OK) return s;
     s = ensure_workspace(const_cast<mcd_stencils *>(st), prm->mode);

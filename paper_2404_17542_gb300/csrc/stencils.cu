@@ -13,9 +13,13 @@
 //
 // FP64 throughout: the FP64 rows are the matrix the refinement residual is
 // judged on; the FP32 copy used by the inner Krylov solve is their rounding.
+#include <cuda.h>
 #include <math.h>
 
 #include <string.h>
+
+#include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -453,6 +457,340 @@ __global__ void __launch_bounds__(256) spmv_kernel(Geo g, const T *__restrict__ 
     y[k] = acc;
 }
 
+// The 2D 3x3 SpMV, tiled for HBM: one block of 256 threads per tile of
+// (32 VEC) x 8 cells; thread (tx, ty) owns the VEC consecutive cells
+// (i0 + VEC tx + v, j0 + ty), v < VEC.  x of the tile and its one-cell halo
+// is staged in shared memory (wrapped on periodic axes, clamped otherwise,
+// which is how neighbour() maps a missing neighbour: onto the cell itself),
+// each slot's weights of the VEC cells arrive in one 16-byte streaming load,
+// and y leaves in one 16-byte store.  Per cell the products and the order of
+// their sum are those of spmv_kernel.  VEC > 1 needs n0 % VEC == 0.
+__device__ __forceinline__ int halo_coord(int v, int n, int per) {
+    if (v < 0) return per ? v + n : 0;
+    if (v >= n) return per ? v - n : n - 1;
+    return v;
+}
+
+template <typename T, int VEC>
+__global__ void __launch_bounds__(256) spmv2d_tiled(Geo g, const T *__restrict__ row,
+                                                    const T *__restrict__ x, T *__restrict__ y) {
+    constexpr int TX = 32 * VEC, TY = 8;
+    constexpr int OFF = 16 / sizeof(T);    // shared column of cell i0: 16-byte aligned
+    constexpr int XS = TX + 2 * OFF;
+    constexpr int C = 4;
+    constexpr bool diff_form = sizeof(T) == 4;
+    __shared__ __align__(16) T xs[TY + 2][XS];
+    const int n0 = g.n[0], n1 = g.n[1];
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int i = i0 + VEC * tx, j = j0 + ty;
+    const bool in = i < n0 && j < n1;
+    const int64_t N = g.N;
+    const int64_t k = (int64_t)i + (int64_t)n0 * j;
+    // the weights first: their loads are in flight while x is staged
+    T w[9][VEC];
+#pragma unroll
+    for (int sl = 0; sl < 9; ++sl) {
+        const T *src = row + (int64_t)sl * N + k;
+        if (!in) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) w[sl][v] = (T)0;
+        } else if constexpr (VEC == 4) {
+            const float4 v4 = __ldcs(reinterpret_cast<const float4 *>(src));
+            w[sl][0] = v4.x; w[sl][1] = v4.y; w[sl][2] = v4.z; w[sl][3] = v4.w;
+        } else if constexpr (VEC == 2) {
+            const double2 v2 = __ldcs(reinterpret_cast<const double2 *>(src));
+            w[sl][0] = v2.x; w[sl][1] = v2.y;
+        } else {
+            w[sl][0] = __ldcs(src);
+        }
+    }
+    for (int h = threadIdx.x; h < (TY + 2) * (TX + 2); h += 256) {
+        const int hy = h / (TX + 2), hx = h - hy * (TX + 2);
+        // columns and rows past the mesh's own halo (ragged tiles) are
+        // clamped into it: they are loaded but never used
+        const int gx = halo_coord(min(i0 + hx - 1, n0), n0, g.per[0]);
+        const int gy = halo_coord(min(j0 + hy - 1, n1), n1, g.per[1]);
+        xs[hy][OFF - 1 + hx] = __ldg(x + (int64_t)gx + (int64_t)n0 * gy);
+    }
+    __syncthreads();
+    if (!in) return;
+    T xr[3][VEC + 2];
+#pragma unroll
+    for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+        for (int c = 0; c < VEC + 2; ++c) xr[dj][c] = xs[ty + dj][OFF - 1 + VEC * tx + c];
+    T out[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+        const T xi = xr[1][v + 1];
+        if constexpr (diff_form) {
+            float hi = (float)w[C][v] * (float)xi, lo = 0.0f;
+#pragma unroll
+            for (int sl = 0; sl < 9; ++sl) {
+                if (sl == C) continue;
+                const float wv = (float)w[sl][v];
+                const float d = __fsub_rn((float)xr[sl / 3][v + 1 + sl % 3 - 1], (float)xi);
+                const float pr = __fmul_rn(wv, d);
+                const float pe = __fmaf_rn(wv, d, -pr);
+                const float sum = __fadd_rn(hi, pr);
+                const float bb = __fsub_rn(sum, hi);
+                lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(pr, bb)), pe));
+                hi = sum;
+            }
+            out[v] = (T)__fadd_rn(hi, lo);
+        } else {
+            T acc = (T)0;
+#pragma unroll
+            for (int sl = 0; sl < 9; ++sl) acc = fma(w[sl][v], xr[sl / 3][v + 1 + sl % 3 - 1], acc);
+            out[v] = acc;
+        }
+    }
+    if constexpr (VEC == 4) {
+        __stcs(reinterpret_cast<float4 *>(y + k), make_float4(out[0], out[1], out[2], out[3]));
+    } else if constexpr (VEC == 2) {
+        __stcs(reinterpret_cast<double2 *>(y + k), make_double2(out[0], out[1]));
+    } else {
+        y[k] = out[0];
+    }
+}
+
+// The 2D 3x3 SpMV streamed by TMA (non-periodic meshes): a persistent
+// launch, two blocks per SM, whose blocks take tiles of TX x 8 cells in turn
+// (tile blockIdx.x + k gridDim.x).  Thread 0 keeps NS stages in flight; a
+// stage is two cp.async.bulk.tensor copies completing on its mbarrier: the
+// tile's nine weight slots (box TX x 8 x 9 of the rows as a [9][n1][n0]
+// tensor) and x over the tile and its halo (box (TX + 2 HP) x 10 of x as a
+// [n1][n0] tensor, from column i0 - HP so that the copy starts on a 16-byte
+// boundary).  Copies reaching past the mesh fill zeros; a missing neighbour
+// carries zero weight (the build leaves it out of the fit), so it adds
+// nothing, as in spmv_kernel.  Per cell the arithmetic and its order are
+// spmv_kernel's.  Every wait is bounded: on a timeout the block raises *err,
+// stops issuing, waits (bounded) for the copies it has in flight and returns.
+template <typename T> struct SpmvTma {
+    static constexpr int VEC = 16 / (int)sizeof(T);   // cells per thread: 4 (FP32), 2 (FP64)
+    static constexpr int TX = 32 * VEC, TY = 8;
+    static constexpr int HP = VEC;                      // x columns loaded on each side
+    static constexpr int XW = TX + 2 * HP;              // x box width (544 bytes)
+    static constexpr unsigned ROWS_BYTES = 9u * TY * TX * sizeof(T);
+    static constexpr unsigned X_BYTES = (TY + 2u) * XW * sizeof(T);
+    static constexpr unsigned X_PAD = (X_BYTES + 127u) / 128u * 128u;
+    static constexpr unsigned STAGE = ROWS_BYTES + X_PAD;   // 128-byte aligned stages
+    static constexpr int NS = 2;
+    static constexpr size_t SMEM = (size_t)NS * STAGE;
+};
+
+__device__ __forceinline__ uint32_t spmv_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool spmv_wait(uint64_t *mbar, uint32_t parity, long long limit) {
+    const uint32_t mb = spmv_smem(mbar);
+    uint32_t done = 0;
+    for (long long polls = 0; !done; ++polls) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mb), "r"(parity)
+            : "memory");
+        if (!done && polls >= limit) return false;
+    }
+    return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) spmv2d_tma(const __grid_constant__ CUtensorMap rows_map,
+                                                     const __grid_constant__ CUtensorMap x_map, int n0, int n1,
+                                                     int tiles_x, int ntiles, T *__restrict__ y, int *err,
+                                                     long long spin_limit) {
+    using P = SpmvTma<T>;
+    constexpr int VEC = P::VEC, TX = P::TX, TY = P::TY, XW = P::XW, C = 4;
+    constexpr bool diff_form = sizeof(T) == 4;
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[P::NS];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x;
+    const int mine = (blockIdx.x < ntiles) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (tid == 0) {
+        for (int b = 0; b < P::NS; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(spmv_smem(mbar + b)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int k) {   // thread 0: tile k of this block into stage k % NS
+        const int t = (int)blockIdx.x + k * (int)gridDim.x;
+        const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
+        unsigned char *st = smem + (size_t)(k % P::NS) * P::STAGE;
+        const uint32_t mb = spmv_smem(mbar + k % P::NS);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
+                     "r"(P::ROWS_BYTES + P::X_BYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];" ::"r"(spmv_smem(st)),
+            "l"(reinterpret_cast<uint64_t>(&rows_map)), "r"(x0), "r"(y0), "r"(0), "r"(mb)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+            "[%4];" ::"r"(spmv_smem(st + P::ROWS_BYTES)),
+            "l"(reinterpret_cast<uint64_t>(&x_map)), "r"(x0 - P::HP), "r"(y0 - 1), "r"(mb)
+            : "memory");
+    };
+    if (tid == 0)
+        for (int k = 0; k < P::NS && k < mine; ++k) issue(k);
+    const int tx = tid & 31, ty = tid >> 5;
+    int k = 0;
+    for (; k < mine; ++k) {
+        const int b = k % P::NS;
+        const bool ok = spmv_wait(mbar + b, (uint32_t)((k / P::NS) & 1), spin_limit);
+        if (__syncthreads_or(!ok)) break;
+        const int t = (int)blockIdx.x + k * (int)gridDim.x;
+        const int i = (t % tiles_x) * TX + VEC * tx, j = (t / tiles_x) * TY + ty;
+        const T *W = reinterpret_cast<const T *>(smem + (size_t)b * P::STAGE);
+        const T *X = reinterpret_cast<const T *>(smem + (size_t)b * P::STAGE + P::ROWS_BYTES);
+        T w[9][VEC];
+#pragma unroll
+        for (int sl = 0; sl < 9; ++sl) {
+            const V wv = *reinterpret_cast<const V *>(W + (sl * TY + ty) * TX + VEC * tx);
+            if constexpr (VEC == 4) {
+                w[sl][0] = wv.x; w[sl][1] = wv.y; w[sl][2] = wv.z; w[sl][3] = wv.w;
+            } else {
+                w[sl][0] = wv.x; w[sl][1] = wv.y;
+            }
+        }
+        // x of cells i - 1 .. i + VEC of rows j - 1 .. j + 1: three aligned
+        // vectors per row (the thread's own and its two neighbours')
+        T xr[3][VEC + 2];
+#pragma unroll
+        for (int dj = 0; dj < 3; ++dj) {
+            const T *row = X + (ty + dj) * XW;
+            const V lo = *reinterpret_cast<const V *>(row + VEC * tx);
+            const V mid = *reinterpret_cast<const V *>(row + VEC * (tx + 1));
+            const V hi = *reinterpret_cast<const V *>(row + VEC * (tx + 2));
+            if constexpr (VEC == 4) {
+                xr[dj][0] = lo.w; xr[dj][1] = mid.x; xr[dj][2] = mid.y; xr[dj][3] = mid.z; xr[dj][4] = mid.w;
+                xr[dj][5] = hi.x;
+            } else {
+                xr[dj][0] = lo.y; xr[dj][1] = mid.x; xr[dj][2] = mid.y; xr[dj][3] = hi.x;
+            }
+        }
+        __syncthreads();   // every thread has its operands: stage b may be refilled
+        if (tid == 0 && k + P::NS < mine) issue(k + P::NS);
+        if (i >= n0 || j >= n1) continue;
+        T out[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const T xi = xr[1][v + 1];
+            if constexpr (diff_form) {
+                float hi = (float)w[C][v] * (float)xi, lo = 0.0f;
+#pragma unroll
+                for (int sl = 0; sl < 9; ++sl) {
+                    if (sl == C) continue;
+                    const float wv = (float)w[sl][v];
+                    const float d = __fsub_rn((float)xr[sl / 3][v + 1 + sl % 3 - 1], (float)xi);
+                    const float pr = __fmul_rn(wv, d);
+                    const float pe = __fmaf_rn(wv, d, -pr);
+                    const float sum = __fadd_rn(hi, pr);
+                    const float bb = __fsub_rn(sum, hi);
+                    lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(pr, bb)), pe));
+                    hi = sum;
+                }
+                out[v] = (T)__fadd_rn(hi, lo);
+            } else {
+                T acc = (T)0;
+#pragma unroll
+                for (int sl = 0; sl < 9; ++sl) acc = fma(w[sl][v], xr[sl / 3][v + 1 + sl % 3 - 1], acc);
+                out[v] = acc;
+            }
+        }
+        const int64_t kk = (int64_t)i + (int64_t)n0 * j;
+        if constexpr (VEC == 4) {
+            __stcs(reinterpret_cast<float4 *>(y + kk), make_float4(out[0], out[1], out[2], out[3]));
+        } else {
+            __stcs(reinterpret_cast<double2 *>(y + kk), make_double2(out[0], out[1]));
+        }
+    }
+    if (k < mine && tid == 0) {
+        // a wait gave up: report it and let the copies in flight land
+        // (bounded) before the block's shared memory is released
+        atomicExch(err, 1);
+        for (int q = k; q < mine && q < k + P::NS; ++q)
+            if (!spmv_wait(mbar + q % P::NS, (uint32_t)((q / P::NS) & 1), spin_limit)) break;
+    }
+}
+
+typedef CUresult (*SpmvEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static SpmvEncodeFn spmv_encoder() {
+    static SpmvEncodeFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<SpmvEncodeFn>(ptr);
+    }
+    return fn;
+}
+
+// Launch spmv2d_tma if the layout allows it (non-periodic 2D 3x3, n0 a
+// multiple of the vector width, 16-byte aligned arrays); false otherwise.
+template <typename T>
+static bool launch_spmv_tma(const mcd_stencils *st, const T *row, const T *x, T *y, cudaStream_t stream) {
+    using P = SpmvTma<T>;
+    const Geo &g = st->geo;
+    if (st->shape != 2 || g.per[0] || g.per[1] || g.n[0] % P::VEC != 0) return false;
+    if ((uintptr_t)row % 16 || (uintptr_t)x % 16 || (uintptr_t)y % 16) return false;
+    SpmvEncodeFn enc = spmv_encoder();
+    if (!enc) return false;
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    const cuuint64_t n0 = (cuuint64_t)g.n[0], n1 = (cuuint64_t)g.n[1], es = sizeof(T);
+    CUtensorMap rows_map, x_map;
+    const cuuint64_t rdims[3] = {n0, n1, 9};
+    const cuuint64_t rstr[2] = {n0 * es, n0 * n1 * es};
+    const cuuint32_t rbox[3] = {(cuuint32_t)P::TX, (cuuint32_t)P::TY, 9};
+    const cuuint32_t ones[3] = {1, 1, 1};
+    if (enc(&rows_map, dt, 3, const_cast<T *>(row), rdims, rstr, rbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t xdims[2] = {n0, n1};
+    const cuuint64_t xstr[1] = {n0 * es};
+    const cuuint32_t xbox[2] = {(cuuint32_t)P::XW, (cuuint32_t)(P::TY + 2)};
+    if (enc(&x_map, dt, 2, const_cast<T *>(x), xdims, xstr, xbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    static int sms[64] = {0};
+    static bool attr_set[2][64] = {{false}};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return false;
+    if (!attr_set[sizeof(T) == 8][dev]) {
+        if (cudaFuncSetAttribute(spmv2d_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM) !=
+            cudaSuccess)
+            return false;
+        attr_set[sizeof(T) == 8][dev] = true;
+    }
+    const int tiles_x = (g.n[0] + P::TX - 1) / P::TX, tiles_y = (g.n[1] + P::TY - 1) / P::TY;
+    const int ntiles = tiles_x * tiles_y;
+    const int grid = std::min(ntiles, 2 * sms[dev]);
+    {
+        KTimer kt(MCD_K_OTHER, stream);
+        spmv2d_tma<T><<<grid, 256, P::SMEM, stream>>>(rows_map, x_map, g.n[0], g.n[1], tiles_x, ntiles, y,
+                                                      st->spmv_err, 1ll << 22);
+    }
+    return true;
+}
+
 // b: inner DP f - sum QL * bnd (Neumann neighbours); boundary DP rscale * bnd.
 template <int G>
 __global__ void rhs_kernel(Geo g, const int8_t *__restrict__ kind, const double *__restrict__ ql,
@@ -501,6 +839,7 @@ static void free_arrays(mcd_stencils *st) {
     cudaFree(st->kind);
     cudaFree(st->off16);
     cudaFree(st->bad_dp);
+    cudaFree(st->spmv_err);
 }
 
 static bool same_layout(const mcd_stencils *st, const mcd_mesh &m, const mcd_mls_params &p) {
@@ -581,6 +920,8 @@ extern "C" mcd_status mcd_build_stencils(const mcd_mesh *mesh, const double *pos
         chk(dmalloc(&h->kind, (size_t)N));
         if (mesh->dim == 2) chk(dmalloc(&h->off16, (size_t)2 * N));
         chk(dmalloc(&h->bad_dp, 1));
+        chk(dmalloc(&h->spmv_err, 1));
+        if (e == cudaSuccess) chk(cudaMemset(h->spmv_err, 0, sizeof(int)));
         if (e != cudaSuccess) {
             free_arrays(h);
             delete h;
@@ -629,8 +970,14 @@ extern "C" mcd_status mcd_stencils_check(const mcd_stencils *st, int64_t *first_
                                          mcd_stream_t stream) {
     MCD_CHECK_ARG(st, "NULL handle");
     unsigned long long bad = 0;
+    int spmv_err = 0;
     MCD_CUDA_TRY(cudaMemcpyAsync(&bad, st->bad_dp, sizeof(bad), cudaMemcpyDeviceToHost, stream));
+    MCD_CUDA_TRY(cudaMemcpyAsync(&spmv_err, st->spmv_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
     MCD_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (spmv_err) {
+        set_error("a TMA-streamed SpMV of this handle gave up waiting for its copies (bounded wait)");
+        return MCD_ETIMEOUT;
+    }
     const bool fail = bad != ~0ull;
     if (first_bad_dp) *first_bad_dp = fail ? (int64_t)bad : -1;
     if (fail) {
@@ -690,11 +1037,19 @@ extern "C" mcd_status mcd_apply_laplacian(const mcd_stencils *st, const void *x_
     const int64_t N = st->geo.N;
     const int threads = 256;
     const unsigned blocks = (unsigned)((N + threads - 1) / threads);
+    const int n0 = st->geo.n[0], n1 = st->geo.n[1];
+    const bool tiled = st->shape == 2 && (n1 + 7) / 8 <= 65535;
     if (dtype == MCD_DT_F64) {
         const double *row = st->row64;
         const double *x = (const double *)x_dev;
         double *y = (double *)y_dev;
-        if (st->shape == 2)
+        if (launch_spmv_tma<double>(st, row, x, y, stream))
+            ;
+        else if (tiled && n0 % 2 == 0)
+            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv2d_tiled<double, 2><<<dim3((n0 + 63) / 64, (n1 + 7) / 8), threads, 0, stream>>>(st->geo, row, x, y));
+        else if (tiled)
+            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv2d_tiled<double, 1><<<dim3((n0 + 31) / 32, (n1 + 7) / 8), threads, 0, stream>>>(st->geo, row, x, y));
+        else if (st->shape == 2)
             MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<double, 2><<<blocks, threads, 0, stream>>>(st->geo, row, x, y));
         else if (st->shape == 3)
             MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<double, 3><<<blocks, threads, 0, stream>>>(st->geo, row, x, y));
@@ -705,7 +1060,13 @@ extern "C" mcd_status mcd_apply_laplacian(const mcd_stencils *st, const void *x_
         const float *row = st->row32;
         const float *x = (const float *)x_dev;
         float *y = (float *)y_dev;
-        if (st->shape == 2)
+        if (launch_spmv_tma<float>(st, row, x, y, stream))
+            ;
+        else if (tiled && n0 % 4 == 0)
+            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv2d_tiled<float, 4><<<dim3((n0 + 127) / 128, (n1 + 7) / 8), threads, 0, stream>>>(st->geo, row, x, y));
+        else if (tiled)
+            MCD_KLAUNCH(MCD_K_OTHER, stream, spmv2d_tiled<float, 1><<<dim3((n0 + 31) / 32, (n1 + 7) / 8), threads, 0, stream>>>(st->geo, row, x, y));
+        else if (st->shape == 2)
             MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<float, 2><<<blocks, threads, 0, stream>>>(st->geo, row, x, y));
         else if (st->shape == 3)
             MCD_KLAUNCH(MCD_K_OTHER, stream, spmv_kernel<float, 3><<<blocks, threads, 0, stream>>>(st->geo, row, x, y));

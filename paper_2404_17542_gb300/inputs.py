@@ -498,6 +498,31 @@ def cnn_weights(seed: int, c_in: int = 7, width: int = 32, layers: int = 4,
     return ws, bs
 
 
+def cnn_weights_extrapolating(seed: int, scale: float = 0.1, c_in: int = 7, width: int = 32,
+                              layers: int = 4, channel: int = 6):
+    """Initial weights whose network already computes y = x[channel] (the
+    input's increment channel) exactly, plus He-normal weights times `scale`
+    everywhere else: two hidden channels carry relu(x) and relu(-x) through
+    the centre taps, the last layer takes their difference (weights +-1 and
+    0, exact in bf16).  Training starts from that map instead of from noise."""
+    ws, bs = cnn_weights(seed, c_in, width, layers)
+    for w in ws:
+        w *= scale
+    ws[0][0, :, :, :] = 0.0
+    ws[0][1, :, :, :] = 0.0
+    ws[0][0, channel, 1, 1] = 1.0
+    ws[0][1, channel, 1, 1] = -1.0
+    for w in ws[1:-1]:
+        w[0:2, :, :, :] = 0.0
+        w[:, 0:2, :, :] = 0.0
+        w[0, 0, 1, 1] = 1.0
+        w[1, 1, 1, 1] = 1.0
+    ws[-1][:, 0:2, :, :] = 0.0
+    ws[-1][0, 0, 1, 1] = 1.0
+    ws[-1][0, 1, 1, 1] = -1.0
+    return ws, bs
+
+
 def cnn_flatten(ws, bs):
     """Flat float32 parameter vector: per layer W[o][c][dj][di], then b[o]."""
     parts = []

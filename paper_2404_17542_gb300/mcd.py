@@ -49,13 +49,14 @@ class c_solve_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("mode", C.c_int),
                 ("inner_tol", C.c_double), ("max_refine", C.c_int), ("net", C.c_void_p),
                 ("check_every", C.c_int), ("update_restart", C.c_int), ("net_dprev", C.c_void_p),
-                ("barriers", C.c_int)]
+                ("barriers", C.c_int), ("precond", C.c_void_p)]
 
 
 class c_solve_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("restarts", C.c_int),
                 ("rel_res", C.c_double), ("b_norm", C.c_double), ("unknowns", C.c_int64),
-                ("rel_res_guess", C.c_double), ("rel_res_start", C.c_double), ("fallback", C.c_int)]
+                ("rel_res_guess", C.c_double), ("rel_res_start", C.c_double), ("fallback", C.c_int),
+                ("net_corrections", C.c_int), ("discarded", C.c_int)]
 
 
 class c_batch_tuning(C.Structure):
@@ -72,6 +73,21 @@ class c_body(C.Structure):
                 ("vel", C.c_double * 3), ("acc", C.c_double * 3), ("theta", C.c_double),
                 ("omega", C.c_double), ("omega_dot", C.c_double), ("sdf_dev", C.c_void_p),
                 ("sdf_n", C.c_int * 2), ("sdf_origin", C.c_double * 2), ("sdf_h", C.c_double)]
+
+
+class c_flow_params(C.Structure):
+    _fields_ = [("nu", C.c_double), ("weight_kind", C.c_int), ("r_e", C.c_double), ("precision", C.c_int),
+                ("kappa", C.c_double), ("n_relax", C.c_int), ("band", C.c_double), ("alpha", C.c_double),
+                ("ale_pressure", C.c_int), ("forces", C.c_int)]
+
+
+MAX_BODIES = 64
+
+
+class c_flow_info(C.Structure):
+    _fields_ = [("solve", c_solve_info), ("ale_fallbacks", C.c_int), ("ale_fallbacks_p", C.c_int),
+                ("nbodies", C.c_int), ("force", (C.c_double * 2) * MAX_BODIES),
+                ("perimeter", C.c_double * MAX_BODIES), ("skipped", C.c_int * MAX_BODIES)]
 
 
 _lib = None
@@ -126,9 +142,19 @@ _SIGS = {
     "mcd_batch_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(c_batch_tuning)]),
     "mcd_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(c_solve_params),
                                      C.c_int, C.c_char_p, C.POINTER(C.c_double), C.c_void_p]),
+    "mcd_flow_create": (C.c_int, [C.POINTER(c_mesh), C.POINTER(c_flow_params), C.c_void_p, C.c_int,
+                                  C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.c_void_p]),
+    "mcd_flow_destroy": (None, [C.c_void_p]),
+    "mcd_flow_restart": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mcd_flow_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                C.POINTER(c_solve_params)] + [C.c_void_p] * 5
+                      + [C.POINTER(c_flow_info), C.c_void_p]),
+    "mcd_flow_stencils": (C.c_void_p, [C.c_void_p, C.c_int]),
+    "mcd_flow_copy": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mcd_timing_enable": (C.c_int, [C.c_int]),
     "mcd_timing_read": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "mcd_launch_count": (C.c_int64, []),
+    "mcd_solver_set_staging": (C.c_int, [C.c_int]),
     "mcd_selftest_bounded_wait": (C.c_int, [C.c_int, C.c_int64, C.c_void_p]),
     "mcd_trace_enable": (C.c_int, [C.c_int]),
     "mcd_trace_read": (C.c_int, [C.POINTER(C.c_uint64)]),
@@ -256,8 +282,8 @@ class Stencils:
         return b
 
     def solve(self, rhs, bnd, p=None, tol=1e-8, mode=MIXED, max_iter=200000, inner_tol=0.3,
-              max_refine=60, check_every=64, update_restart=1, raise_on_error=True, net=None,
-              dprev=None, barriers=0):
+              max_refine=60, check_every=64, update_restart=0, raise_on_error=True, net=None,
+              dprev=None, barriers=0, precond=None):
         """Solve the PPE; returns (p, info dict).  p is updated in place if given.
         net (a Net) adds its warm-start correction to p first; dprev (or
         None) is the last pressure increment it reads, and is overwritten
@@ -268,7 +294,7 @@ class Stencils:
                             max_refine=max_refine, net=None if net is None else net.handle,
                             check_every=check_every, update_restart=int(update_restart),
                             net_dprev=None if dprev is None else _ptr(dprev, torch.float64, self.N),
-                            barriers=int(barriers))
+                            barriers=int(barriers), precond=None if precond is None else precond.handle)
         info = c_solve_info()
         st = lib().mcd_solve_pressure(self.handle, _ptr(rhs, torch.float64, self.N),
                                       _ptr(bnd, torch.float64, self.N), _ptr(p, torch.float64, self.N),
@@ -276,7 +302,7 @@ class Stencils:
         d = dict(status=st, iters=info.iters, refinements=info.refinements, restarts=info.restarts,
                  rel_res=info.rel_res, b_norm=info.b_norm, unknowns=info.unknowns,
                  rel_res_guess=info.rel_res_guess, rel_res_start=info.rel_res_start,
-                 fallback=info.fallback)
+                 fallback=info.fallback, net_corrections=info.net_corrections, discarded=info.discarded)
         if st != OK and raise_on_error:
             raise McdError(st, lib().mcd_last_error().decode())
         return p, d
@@ -314,6 +340,27 @@ class Stencils:
             self.close()
         except Exception:
             pass
+
+
+class StencilsView(Stencils):
+    """A stencil handle owned by the library (e.g. a flow run's pressure
+    stencils): the array and solve helpers of Stencils, nothing to free."""
+
+    def __init__(self, handle, mesh, support=1):
+        self.mesh = mesh
+        self.cmesh = make_mesh(mesh)
+        self.N = int(np.prod([mesh.n[d] for d in range(mesh.dim)]))
+        self.dim = mesh.dim
+        self.support = support
+        self.S = (2 * support + 1) ** mesh.dim
+        self.nb = 5 if mesh.dim == 2 else 9
+        self.handle = C.c_void_p(handle)
+
+    def rebuild(self, pos, mask, normal=None):
+        raise RuntimeError("a library-owned stencil handle is rebuilt by its owner")
+
+    def close(self):
+        self.handle = C.c_void_p(None)
 
 
 class Batch:
@@ -690,6 +737,11 @@ def selftest_bounded_wait(set_flag: bool, polls: int = 4096) -> int:
     return int(lib().mcd_selftest_bounded_wait(1 if set_flag else 0, int(polls), None))
 
 
+def solver_set_staging(on: bool):
+    """Stage the persistent solve's tile operands with TMA (default) or not."""
+    _check(lib().mcd_solver_set_staging(1 if on else 0))
+
+
 def launch_count() -> int:
     return int(lib().mcd_launch_count())
 
@@ -698,75 +750,125 @@ def version():
     return lib().mcd_version().decode()
 
 
+FLOW_B, FLOW_GUESS, FLOW_BND, FLOW_SRC, FLOW_NORMAL = range(5)
+FLOW_VELOCITY, FLOW_PRESSURE = 0, 1
+
+
 class AleFlow:
-    """Moving-boundary fractional steps on the device, in the order of
-    Sec. 3.3; every stage is one call of the C ABI.
+    """Moving-boundary fractional steps (Sec. 3.3) through mcd_flow_step:
+    one library call per step does the DP update, the ALE interpolation,
+    the stencils, predict, the PPE, the projection and the forces, and forms
+    the bodies' dV/dt and d omega/dt by the differences of Eq. (29).
 
     bodies_at(t) -> ([bodies], [(vx, vy)]): the bodies at time t (circles
     (id, centre, radius) or SdfBody objects with their posture angle and
-    angular velocity) and their translational velocities.  dV/dt and
-    d omega/dt of the Neumann datum are the finite differences of Eq. (29).  The state (DP
-    positions and masks, u, v, P) lives in device tensors; the velocity
-    stencils of the current step are kept for the next step's ALE
-    interpolation.  Per step:
-      1. DP update to the bodies at t + dt (band 5 l0);
-      2. u~ = u(x^{k+1}) (Eq. (19), Appendix A);
-      3. velocity and pressure stencils of the new cloud;
-      4. boundary velocities, u* and the PPE source (Eqs. (20)-(21));
-      5. the PPE with dP/dn = -(V^{k+1} - V^k)/dt . n on the bodies
-         (Eqs. (23), (29)), warm-started from the previous P;
-      6. u^{k+1} = u* - dt grad P (Eq. (22));
-      7. the force on every body (Eqs. (30)-(31)), mu = nu.
+    angular velocity) and their translational velocities.  The state (DP
+    positions and masks, u, v, P) lives in device tensors.  With
+    ale_pressure the PPE starts from the step-k pressure carried to the new
+    positions (Eq. (19), Appendix A), else from the step-k pressure.
     """
 
     def __init__(self, mesh, pos, mask, bodies_at, nu, dt, t0=0.0, weight_kind=W_GAUSS, r_e=None,
-                 precision=MIXED, mode=MIXED, tol=1e-8, kappa=0.2, n_relax=10, band=None):
+                 precision=MIXED, mode=MIXED, tol=1e-8, kappa=0.2, n_relax=10, band=None,
+                 ale_pressure=True, forces=True):
         self.mesh, self.bodies_at, self.nu, self.dt, self.t = mesh, bodies_at, nu, dt, t0
-        self.kappa, self.n_relax = kappa, n_relax
-        self.band = 5.0 * mesh.l0 if band is None else band
         self.mode, self.tol = mode, tol
-        self.kw = dict(weight_kind=weight_kind, r_e=r_e)
-        self.precision = precision
         self.N = mesh.n[0] * mesh.n[1]
         dev = pos.device
         self.pos, self.mask = pos, mask
-        self.prev = torch.empty_like(mask)
-        geo, _vel = bodies_at(t0)
-        update_dps_bodies(mesh, geo, self.pos, self.mask, self.prev, kappa, n_relax, band=0.0)
-        self.vel = Stencils(mesh, self.pos, self.mask, want_derivs=True, precision=FP64, **self.kw)
-        self.pres = None
+        self.cmesh = make_mesh(mesh)
+        self.prm = c_flow_params(nu=float(nu), weight_kind=int(weight_kind),
+                                 r_e=float(0.0 if r_e is None else r_e), precision=int(precision),
+                                 kappa=float(kappa), n_relax=int(n_relax),
+                                 band=float(0.0 if band is None else band), alpha=0.0,
+                                 ale_pressure=int(bool(ale_pressure)), forces=int(bool(forces)))
+        geo, vel = bodies_at(t0)
+        self.ids = [body_id(b) for b in geo]
+        arr = make_bodies(geo, vels=vel)
+        self.handle = C.c_void_p(None)
+        _check(lib().mcd_flow_create(C.byref(self.cmesh), C.byref(self.prm), arr, len(geo),
+                                     _ptr(pos, torch.float64, 2 * self.N), _ptr(mask, torch.int8, self.N),
+                                     C.byref(self.handle), _stream()))
         z = lambda: torch.zeros(self.N, dtype=torch.float64, device=dev)  # noqa: E731
         self.u, self.v, self.P = z(), z(), z()
         self.info = {}
 
-    def step(self):
-        mesh, dt = self.mesh, self.dt
+    def step(self, mode=None, net=None, dprev=None, tol=None, raise_on_error=True, precond=None,
+             update_restart=0):
+        """One step; returns {solve, fallbacks, fallbacks_p, forces}.  net /
+        dprev: the learned warm start of the solve, precond: the network that
+        preconditions its refinement (as in Stencils.solve)."""
         geo_k, V_k = self.bodies_at(self.t)
-        geo_1, V_1 = self.bodies_at(self.t + dt)
-        for bk, b1 in zip(geo_k, geo_1):
-            if isinstance(b1, SdfBody):   # d omega / dt of Eq. (29)
-                b1.omega_dot = (b1.omega - bk.omega) / dt
-        pos_k, mask_k = self.pos.clone(), self.mask.clone()
-        update_dps_bodies(mesh, geo_1, self.pos, self.mask, self.prev, self.kappa, self.n_relax, self.band)
-        ut, vt, fallbacks = ale_interpolate(self.vel, geo_k, pos_k, self.pos, mask_k, self.mask, self.u, self.v)
-        self.vel.rebuild(self.pos, self.mask)
-        accs = [((b[0] - a[0]) / dt, (b[1] - a[1]) / dt) for a, b in zip(V_k, V_1)]
-        normal, bnd = bodies_boundary(mesh, geo_1, self.pos, self.mask, accs=accs)
-        if self.pres is None:
-            bc = np.zeros(128, dtype=np.uint8)
-            for body in geo_1:
-                bc[body_id(body)] = BC_NEUMANN
-            self.pres = Stencils(mesh, self.pos, self.mask, normal, bc_kind=bc, want_derivs=True,
-                                 precision=self.precision, **self.kw)
-        else:
-            self.pres.rebuild(self.pos, self.mask, normal)
-        ubc, vbc = bodies_velocity(mesh, geo_1, V_1, self.pos, self.mask)
-        us, vs, src = self.vel.flow_predict(ut, vt, ubc, vbc, self.nu, dt)
-        _p, info = self.pres.solve(src, bnd, p=self.P, tol=self.tol, mode=self.mode)
-        self.u, self.v = self.pres.flow_project(self.P, bnd, us, vs, ubc, vbc, dt)
-        forces = {body_id(b): fluid_force(self.pres, self.vel, body_id(b), self.pos, self.mask, normal, self.P,
-                                          bnd, self.u, self.v, self.nu) for b in geo_1}
-        self.t += dt
-        self.normal, self.bnd = normal, bnd
-        self.info = dict(solve=info, fallbacks=fallbacks, forces=forces)
+        geo_1, V_1 = self.bodies_at(self.t + self.dt)
+        bk = make_bodies(geo_k, vels=V_k)
+        b1 = make_bodies(geo_1, vels=V_1)
+        sp = c_solve_params(tol=float(self.tol if tol is None else tol),
+                            max_iter=200000, mode=int(self.mode if mode is None else mode), inner_tol=0.3,
+                            max_refine=60, net=None if net is None else net.handle, check_every=64,
+                            update_restart=int(update_restart),
+                            net_dprev=None if dprev is None else _ptr(dprev, torch.float64, self.N),
+                            barriers=0, precond=None if precond is None else precond.handle)
+        fi = c_flow_info()
+        f64 = torch.float64
+        st = lib().mcd_flow_step(self.handle, bk, b1, len(geo_k), float(self.dt), C.byref(sp),
+                                 _ptr(self.pos, f64, 2 * self.N), _ptr(self.mask, torch.int8, self.N),
+                                 _ptr(self.u, f64, self.N), _ptr(self.v, f64, self.N), _ptr(self.P, f64, self.N),
+                                 C.byref(fi), _stream())
+        si = fi.solve
+        solve = dict(status=st, iters=si.iters, refinements=si.refinements, restarts=si.restarts,
+                     rel_res=si.rel_res, b_norm=si.b_norm, unknowns=si.unknowns,
+                     rel_res_guess=si.rel_res_guess, rel_res_start=si.rel_res_start, fallback=si.fallback,
+                     net_corrections=si.net_corrections, discarded=si.discarded)
+        if st != OK and raise_on_error:
+            raise McdError(st, lib().mcd_last_error().decode())
+        forces = {bid: ((fi.force[b][0], fi.force[b][1]), fi.perimeter[b], fi.skipped[b])
+                  for b, bid in enumerate(self.ids)}
+        self.t += self.dt
+        self.info = dict(solve=solve, fallbacks=fi.ale_fallbacks, fallbacks_p=fi.ale_fallbacks_p, forces=forces)
         return self.info
+
+    def snapshot(self):
+        """Copies of the run's state (cloud, fields, time)."""
+        return (self.pos.clone(), self.mask.clone(), self.u.clone(), self.v.clone(), self.P.clone(), self.t)
+
+    def restore(self, snap):
+        """Continue from a snapshot: its state, and the velocity stencils of
+        its cloud rebuilt for the next step's ALE interpolation."""
+        pos, mask, u, v, P, t = snap
+        for dst, src in ((self.pos, pos), (self.mask, mask), (self.u, u), (self.v, v), (self.P, P)):
+            dst.copy_(src)
+        self.t = t
+        _check(lib().mcd_flow_restart(self.handle, _ptr(self.pos, torch.float64, 2 * self.N),
+                                      _ptr(self.mask, torch.int8, self.N), _stream()))
+
+    def stencils(self, which=FLOW_PRESSURE):
+        """The run's current velocity or pressure stencils (library-owned)."""
+        h = lib().mcd_flow_stencils(self.handle, int(which))
+        return StencilsView(h, self.mesh)
+
+    def array(self, which, out=None):
+        """Copy of an array of the last step (FLOW_B, FLOW_GUESS, FLOW_BND,
+        FLOW_SRC: [N]; FLOW_NORMAL: [2][N])."""
+        n = 2 * self.N if which == FLOW_NORMAL else self.N
+        out = torch.empty(n, dtype=torch.float64, device=self.u.device) if out is None else out
+        _check(lib().mcd_flow_copy(self.handle, int(which), _ptr(out, torch.float64, n), _stream()))
+        return out
+
+    @property
+    def normal(self):
+        return self.array(FLOW_NORMAL)
+
+    @property
+    def bnd(self):
+        return self.array(FLOW_BND)
+
+    def close(self):
+        if self.handle and self.handle.value:
+            lib().mcd_flow_destroy(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -54,15 +54,17 @@ def test_binding_struct_sizes_match_c(libpath, tmp_path):
     from paper_2404_17542_gb300 import mcd
     src = tmp_path / "sizes.c"
     src.write_text('#include "mcd.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(mcd_mesh),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mcd_mesh),'
                    ' sizeof(mcd_mls_params), sizeof(mcd_solve_params), sizeof(mcd_solve_info),'
-                   ' sizeof(mcd_body)); return 0;}\n')
+                   ' sizeof(mcd_body), sizeof(mcd_flow_params), sizeof(mcd_flow_info),'
+                   ' offsetof(mcd_flow_info, skipped)); return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     sizes = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                             check=True).stdout.split()]
     assert sizes == [C.sizeof(mcd.c_mesh), C.sizeof(mcd.c_mls_params), C.sizeof(mcd.c_solve_params),
-                     C.sizeof(mcd.c_solve_info), C.sizeof(mcd.c_body)]
+                     C.sizeof(mcd.c_solve_info), C.sizeof(mcd.c_body), C.sizeof(mcd.c_flow_params),
+                     C.sizeof(mcd.c_flow_info), mcd.c_flow_info.skipped.offset]
 
 
 def test_no_cpu_fallback_in_product_path():
