@@ -315,7 +315,9 @@ def train_nets(run, steps, epochs, precond=True, lr=1e-3, seed=3):
     torch, mcd = run.torch, run.mcd
     from paper_2404_17542_gb300 import inputs
     t0 = time.perf_counter()
-    net = mcd.Net(inputs.cnn_flatten(*inputs.cnn_weights(seed)))
+    # the warm-start network starts as linear extrapolation in time (its
+    # output equals its increment channel) and learns corrections to it
+    net = mcd.Net(inputs.cnn_flatten(*inputs.cnn_weights_extrapolating(seed)))
     pre = mcd.Net(inputs.cnn_flatten(*inputs.cnn_weights(seed + 1))) if precond else None
     samples, psamples = [], []
     dprev = torch.zeros(run.N, dtype=torch.float64, device=run.dev)
@@ -731,11 +733,11 @@ def batched_arm(args):
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def timed(mode, graph, steps):
+    def timed(mode, graph, steps, **kw):
         tot, res = 0.0, None
         for _ in range(args.warmup):
             p.zero_()
-            bt.solve(rhs, bnd, p=p, tol=args.tol, mode=mode, graph=graph)
+            bt.solve(rhs, bnd, p=p, tol=args.tol, mode=mode, graph=graph, **kw)
         for _ in range(steps):
             p.zero_()
             flush_buf.zero_()
@@ -743,7 +745,7 @@ def batched_arm(args):
             e1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            _p, res = bt.solve(rhs, bnd, p=p, tol=args.tol, mode=mode, graph=graph)
+            _p, res = bt.solve(rhs, bnd, p=p, tol=args.tol, mode=mode, graph=graph, **kw)
             e1.record(stream)
             torch.cuda.synchronize()
             tot += e0.elapsed_time(e1)
@@ -755,6 +757,35 @@ def batched_arm(args):
     launches = (mcd.launch_count() - launches0) / max(1, args.steps + args.warmup)
     clk = clocks.stop()
     ms64, res64 = timed(mcd.FP64, True, max(1, args.steps // 2))
+    ms_rs, res_rs = timed(mcd.MIXED, True, max(1, args.steps // 2), update_restart=1)
+    # the learned warm start: a network trained on the batch's own systems
+    # (features at the zero guess, target the FP64 solution), applied to
+    # every system's guess before the mixed solve
+    learned = None
+    if not args.no_learned:
+        t0 = time.perf_counter()
+        p.zero_()
+        bt.solve(rhs, bnd, p=p, tol=1e-10, mode=mcd.FP64)
+        net = mcd.Net(inputs.cnn_flatten(*inputs.cnn_weights(4)))
+        samples = []
+        for i, pb in enumerate(probs):
+            o0, o1 = int(bt.offsets[i]), int(bt.offsets[i + 1])
+            sti = bt.stencils(i)
+            bi = sti.assemble_rhs(rhs[o0:o1].contiguous(), bnd[o0:o1].contiguous())
+            zero = torch.zeros(o1 - o0, dtype=torch.float64, device=dev)
+            samples.append((sti.mesh.n[0], sti.mesh.n[1]) + net.features(sti, bi, zero, None, p[o0:o1].contiguous()))
+        rng = np.random.default_rng(4)
+        for _ep in range(args.train_epochs):
+            for j in rng.permutation(len(samples)):
+                nx, ny, x, tg, wt = samples[j]
+                net.train_step(x, tg, wt, nx, ny, 1e-3)
+        del samples
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        ms_l, res_l = timed(mcd.MIXED, True, max(1, args.steps // 2), net=net)
+        learned = {"value": bt.N / (ms_l / 1e3), "ms_per_step": ms_l, "iters_max": int(res_l["iters"].max()),
+                   "iters_mean": float(res_l["iters"].mean()), "train_s": round(t_train, 1),
+                   "epochs": args.train_epochs}
     # per-system plain FP64 solves with the single-system solver
     sts = [(mcd.Stencils(pb.mesh, d(pb.pos.ravel()), d(pb.mask), precision=mcd.FP64), d(pb.rhs), d(pb.bnd),
             torch.zeros(pb.mesh.N, dtype=torch.float64, device=dev)) for pb in probs]
@@ -776,13 +807,21 @@ def batched_arm(args):
             "vs_baseline": None, "dtype": "f32 Krylov + f64 refinement", "data": "synthetic",
             "config": {"workload": "256 independent 2D Poisson systems, sizes log-uniform 32^2..512^2 "
                                    "(seed 4), degree-4 polynomial Dirichlet data",
-                       "dps": bt.N, "tol": args.tol, "mode": "mixed", "graph": True,
+                       "dps": bt.N, "tol": args.tol, "mode": "mixed (adaptive residual replacement)",
+                       "graph": True,
                        "tiling": {"rows": rows, "ctas_per_sm": cps, "autotune_ms_per_sweep": tune_ms},
                        "l2": "flushed between steps (256 MB write)"},
             "iters_max": int(res["iters"].max()), "iters_mean": float(res["iters"].mean()),
             "rel_res_max": float(res["rel_res"].max()),
+            "iters_total": int(res["iters"].sum()), "dropped_cycles": int(res["discarded"].sum()),
+            "fp64_finishes": int((res["fallback"] != 0).sum()),
             "batched_fp64": {"value": bt.N / (ms64 / 1e3), "ms_per_step": ms64,
-                             "iters_max": int(res64["iters"].max())},
+                             "iters_max": int(res64["iters"].max()), "iters_total": int(res64["iters"].sum())},
+            "batched_mixed_restarting": {"value": bt.N / (ms_rs / 1e3), "ms_per_step": ms_rs,
+                                         "iters_total": int(res_rs["iters"].sum()),
+                                         "fp64_finishes": int((res_rs["fallback"] != 0).sum())},
+            "batched_learned_mixed": learned,
+            "speedup_vs_batched_fp64": ms64 / ms,
             "per_system_fp64": {"value": bt.N / (ms_each / 1e3), "ms_per_step": ms_each,
                                 "iters_max": int(max(its))},
             "speedup_vs_per_system_fp64": ms_each / ms,

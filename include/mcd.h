@@ -192,9 +192,10 @@ typedef struct mcd_net mcd_net;   /* learned warm start, declared below */
  *              is taken once the FP32 residual has fallen by this factor
  *              since the last one (0.3 is the tested choice).  A recursion
  *              whose residual grows 100-fold since the last update while
- *              residuals are replaced (1e4-fold when restarting) has
- *              diverged: its correction is dropped and it restarts; after 64
- *              such cycles the solve finishes in FP64.
+ *              residuals are replaced has diverged: its correction is dropped
+ *              and the solve continues on the restarting schedule; one that
+ *              grows 1e4-fold while restarting ends the FP32 solve, which
+ *              finishes in FP64 from the last folded iterate.
  * max_refine   cap on FP64 restarts (FP64 mode).
  * net          NULL, or a network whose correction is added to the guess
  *              before the Krylov solve (mcd_net_warm_start; 2D only).
@@ -222,8 +223,10 @@ typedef struct mcd_net mcd_net;   /* learned warm start, declared below */
  *              cycle whose d0 is the network's correction of that residual
  *              (features without an increment: channel 6 is 0), added along
  *              its residual-minimising step before the recursion restarts.
- *              The residual never grows (mcd_solve_info.net_corrections
- *              counts the applications). */
+ *              The residual never grows; a correction that cuts it by less
+ *              than 10 % ends the network's part in that solve, which goes
+ *              on plain (mcd_solve_info.net_corrections counts the
+ *              applications). */
 typedef struct {
     double tol;
     int max_iter;
@@ -248,7 +251,7 @@ typedef struct {
     double rel_res_guess;  /* with a net: ||b - A p|| / ||b|| of the guess, else -1 */
     double rel_res_start;  /* with a net: the same after the warm start, else -1 */
     int fallback;       /* MIXED: nonzero if the FP32 recursion failed and FP64
-                           finished; why: 1 more than 64 cycles diverged, 2 breakdown
+                           finished; why: 1 a restarted cycle diverged, 2 breakdown
                            restarts exhausted, 3 r^.v breakdown (alpha), 4 t = 0,
                            5 a non-finite dot, 6 max_iter, 7 other */
     int net_corrections;   /* with precond: network corrections applied */
@@ -590,6 +593,7 @@ typedef struct {
     int updates;       /* true-residual updates after the first */
     double rel_res;    /* ||b - A p|| / ||b|| (FP64) at the last update */
     int fallback;      /* MIXED: 1 if the FP32 recursion failed and FP64 finished */
+    int discarded;     /* MIXED: cycles dropped after diverging (see mcd_solve_params) */
 } mcd_batch_result;
 
 /* meshes: host [count], each 2D.  Returns MCD_ENOTSUP for a 3D mesh or a
@@ -615,10 +619,12 @@ mcd_status mcd_batch_check(const mcd_batch *bt, int64_t *first_bad_dp, mcd_strea
  * lockstep sweeps with per-system scalars and convergence, the work of the
  * systems still running spread over all CTAs each sweep.  prm: tol (per
  * system, ||b_i - A_i p_i|| <= tol ||b_i||), max_iter (per system), mode
- * (MCD_MIXED: FP32 recursion with FP64 true-residual updates, inner_tol as
- * in mcd_solve_pressure, and systems whose FP32 recursion fails finished by
- * a second launch in FP64 from their last folded iterate; MCD_FP64), net
- * must be NULL.  p_dev: initial guess
+ * (MCD_MIXED: FP32 recursion with FP64 true-residual updates, inner_tol and
+ * update_restart as in mcd_solve_pressure -- per system -- and systems whose
+ * FP32 recursion fails finished by a second launch in FP64 from their last
+ * folded iterate; MCD_FP64), net: NULL or the learned warm start, applied
+ * to each system's guess (features without an increment) before the solve.
+ * p_dev: initial guess
  * in, solutions out.  use_graph: capture the launches in a CUDA graph on the
  * first call and replay it while the arguments and tuning stay the same.
  * results: host [count] or NULL.  Synchronises the stream.  Returns MCD_OK
@@ -626,6 +632,12 @@ mcd_status mcd_batch_check(const mcd_batch *bt, int64_t *first_bad_dp, mcd_strea
 mcd_status mcd_batch_solve(mcd_batch *bt, const double *rhs_dev, const double *bnd_dev,
                            double *p_dev, const mcd_solve_params *prm, int use_graph,
                            mcd_batch_result *results, mcd_stream_t stream);
+
+/* System i of the batch as a stencil handle over the batch's arrays (owned
+ * by the batch; valid after mcd_batch_build until mcd_batch_destroy), e.g.
+ * for mcd_net_features or mcd_apply_laplacian on that system; NULL for a
+ * bad index. */
+const mcd_stencils *mcd_batch_stencils(const mcd_batch *bt, int i);
 
 mcd_status mcd_batch_set_tuning(mcd_batch *bt, const mcd_batch_tuning *t);
 mcd_status mcd_batch_get_tuning(const mcd_batch *bt, mcd_batch_tuning *t);

@@ -62,6 +62,9 @@ struct BScal {
     int restart, restarts, s_conv, pending, max_hit, parity, mode;
     int updates;   // true-residual updates after the first
     int it_last;   // iteration of the last true residual
+    int discard;   // MIXED: the cycle diverged: drop its correction (UPDATE slot A)
+    int no_replace;   // a replaced recursion diverged: restart at every later update
+    int discarded;    // cycles dropped
 };
 
 struct BState {
@@ -91,6 +94,7 @@ struct BArgs {
     int mixed;
     double tol2_factor;       // tol^2
     double update2;           // MIXED: update once rr <= update2 rr_last
+    int replace;              // MIXED: residual replacement until a cycle diverges (adaptive)
     int stall;                // MIXED: update after this many iterations without one
     double eps_breakdown;
     int budget;               // sweeps this launch may run
@@ -258,7 +262,7 @@ __device__ void tile_c(const BGeo &g, int64_t t, T *x, T *r, const T *rhat, cons
 }
 
 template <typename T, int R>
-__device__ void tile_fold(const BGeo &g, int64_t t, double *x64, T *x) {
+__device__ void tile_fold(const BGeo &g, int64_t t, double *x64, T *x, bool discard) {
     const int tid = threadIdx.x;
     int x0, y0;
     bt_origin<R>(g, t, x0, y0);
@@ -267,16 +271,16 @@ __device__ void tile_fold(const BGeo &g, int64_t t, double *x64, T *x) {
         int lx, ly;
         const int64_t k = bt_dp<R>(g, tid, q, x0, y0, lx, ly);
         if (k < 0) continue;
-        x64[k] += (double)__ldcg(x + k);
+        if (!discard) x64[k] += (double)__ldcg(x + k);
         x[k] = (T)0;
     }
 }
 
 // r = b - A64 x64 stored in the recursion's precision; dots ||r64||^2 and
-// ||b||^2 (FP64) and r.r of the stored residual.
+// ||b||^2 (FP64), r.r and r^.r of the stored residual.
 template <typename T, int R>
 __device__ void tile_true_residual(const BGeo &g, int64_t t, const double *row64, const double *b,
-                                   const double *x64, T *r, DotAcc<T> (&rr)[1], double (&d64)[2]) {
+                                   const double *x64, T *r, const T *rhat, DotAcc<T> (&rr)[2], double (&d64)[2]) {
     const int tid = threadIdx.x;
     int x0, y0;
     bt_origin<R>(g, t, x0, y0);
@@ -300,6 +304,7 @@ __device__ void tile_true_residual(const BGeo &g, int64_t t, const double *row64
         d64[0] += rk * rk;
         d64[1] += bk * bk;
         rr[0].add(rt, rt);
+        rr[1].add(__ldcg(rhat + k), rt);
     }
 }
 
@@ -498,7 +503,9 @@ __global__ void __launch_bounds__(256) bicg_batch(const __grid_constant__ BArgs 
                                  v_old, p_new, v_new, beta, omega, restart, dot);
                 flush<T, 3>(dot, accA + (size_t)4 * sys);
             } else if (mode == MODE_UPDATE && a.mixed) {
-                for (int64_t t = t0; t < t1; ++t) tile_fold<T, R>(g, t, a.x64 + g.off, (T *)a.x + g.off);
+                const bool discard = __ldcg(&c->discard) != 0;
+                for (int64_t t = t0; t < t1; ++t)
+                    tile_fold<T, R>(g, t, a.x64 + g.off, (T *)a.x + g.off, discard);
             }
         });
         if (!barrier(a, epoch, [&](int th) {
@@ -539,13 +546,17 @@ __global__ void __launch_bounds__(256) bicg_batch(const __grid_constant__ BArgs 
                                  (T *)a.t + g.off, alpha, dot);
                 flush<T, 3>(dot, accB + (size_t)4 * sys);
             } else if (mode == MODE_UPDATE) {
-                DotAcc<T> rr[1];
+                DotAcc<T> rr[2];
                 double d64[2] = {0.0, 0.0};
                 for (int64_t t = t0; t < t1; ++t)
                     tile_true_residual<T, R>(g, t, a.row64 + 9 * g.off, a.b + g.off, a.x64 + g.off,
-                                             (T *)a.r + g.off, rr, d64);
+                                             (T *)a.r + g.off, (const T *)a.rh + g.off, rr, d64);
                 flush64(d64, accB + (size_t)4 * sys);
-                flush<T, 1>(rr, accB + (size_t)4 * sys + 3);
+                DotAcc<T> r1[1], r2[1];
+                r1[0] = rr[0];
+                r2[0] = rr[1];
+                flush<T, 1>(r1, accB + (size_t)4 * sys + 3);
+                flush<T, 1>(r2, accB + (size_t)4 * sys + 2);
             }
         });
         if (!barrier(a, epoch, [&](int th) {
@@ -575,10 +586,27 @@ __global__ void __launch_bounds__(256) bicg_batch(const __grid_constant__ BArgs 
                         else {
                             c->rr_last = rr;
                             c->it_last = c->iter;
-                            c->restart = 1;
-                            c->s_conv = 0;
-                            c->alpha = c->beta = c->omega = 0.0;
-                            publish(c);
+                            // residual replacement (as in the single-system
+                            // solve): keep p, v and r^ and continue with beta
+                            // from rho' = r^.r of the replaced residual, unless
+                            // this update restarts (the first, after a dropped
+                            // cycle or an ||s|| stop, or once a replaced
+                            // recursion of this system has diverged)
+                            const double rho_new = __ldcg(ac + 2);
+                            const bool keep = a.replace && !first && !c->no_replace && !c->discard &&
+                                              !c->restart && !c->s_conv && c->rho != 0.0 && c->omega != 0.0;
+                            const double beta = keep ? (rho_new / c->rho) * (c->alpha / c->omega) : 0.0;
+                            c->discard = 0;
+                            if (keep && isfinite(beta)) {
+                                c->beta = beta;
+                                c->rho = rho_new;
+                                publish(c);
+                            } else {
+                                c->restart = 1;
+                                c->s_conv = 0;
+                                c->alpha = c->beta = c->omega = 0.0;
+                                publish(c);
+                            }
                         }
                     }
                     ac[0] = ac[1] = ac[2] = ac[3] = 0.0;
@@ -627,7 +655,15 @@ __global__ void __launch_bounds__(256) bicg_batch(const __grid_constant__ BArgs 
                             // residual grown by 1e4 since the last true residual
                             // is a diverged recursion; no update for `stall`
                             // iterations forces one
-                            else if (a.mixed && rr > 1e8 * c->rr_last) c->done = 3;
+                            else if (a.mixed && a.replace && !c->no_replace && rr > 1e4 * c->rr_last) {
+                                // a replaced recursion that grew 100-fold has
+                                // diverged: drop its correction, restart from
+                                // then on
+                                c->discard = 1;
+                                c->no_replace = 1;
+                                c->discarded += 1;
+                                c->pending = 1;
+                            } else if (a.mixed && rr > 1e8 * c->rr_last) c->done = 3;
                             else if (a.mixed && c->iter - c->it_last >= a.stall) c->pending = 1;
                             else if (fabs(rho_new) <= a.eps_breakdown * sqrt(c->rhat2 * rr)) {
                                 c->restarts += 1;
@@ -735,6 +771,9 @@ struct mcd_batch {
     double *rscale = nullptr;
     int8_t *kind = nullptr;
     unsigned long long *bad = nullptr;
+    uint16_t *off16 = nullptr;    // [N][2] bf16 DP offsets of every system (network features)
+    int *spmv_err = nullptr;      // error word of the systems' SpMVs
+    std::vector<mcd_stencils> views;   // system i as a stencil handle over the arrays above
     // solve
     BGeo *bgeo_d = nullptr;
     int bgeo_rows = 0;            // tiling the bgeo table holds
@@ -890,6 +929,7 @@ mcd_status make_launch(mcd_batch *bt, double *p, const mcd_solve_params *prm, La
     a.tol2_factor = prm->tol * prm->tol;
     const double upd = (prm->inner_tol > 0.0 && prm->inner_tol < 1.0) ? prm->inner_tol : 0.3;
     a.update2 = upd * upd;
+    a.replace = (mixed && prm->update_restart != 1) ? 1 : 0;
     a.stall = 1024;
     a.eps_breakdown = mixed ? 1e-12 : 1e-14;
     const long long mi = prm->max_iter > 0 ? prm->max_iter : (1 << 30);
@@ -1035,6 +1075,7 @@ mcd_status finish_solve(mcd_batch *bt, Launch &L, mcd_batch_result *results, cud
             results[i].updates = c.updates;
             results[i].rel_res = c.bb64 > 0.0 ? sqrt(c.rr64 / c.bb64) : 0.0;
             results[i].fallback = 0;
+            results[i].discarded = c.discarded;
         }
         if (si != MCD_OK && worst == MCD_OK) worst = si;
     }
@@ -1047,10 +1088,6 @@ mcd_status check_params(const mcd_batch *bt, const mcd_solve_params *prm) {
     MCD_CHECK_ARG(prm->tol > 0.0, "tol must be positive");
     MCD_CHECK_ARG(prm->mode == MCD_FP64 || prm->mode == MCD_MIXED, "unknown mode");
     MCD_CHECK_ARG(prm->mode != MCD_MIXED || bt->row32, "MIXED solve needs an MCD_MIXED batch");
-    if (prm->net) {
-        set_error("the batched solve takes no network warm start");
-        return MCD_ENOTSUP;
-    }
     return MCD_OK;
 }
 
@@ -1116,6 +1153,9 @@ extern "C" mcd_status mcd_batch_create(const mcd_mesh *meshes, int count, const 
     chk(cudaMalloc(&bt->rscale, (size_t)at * sizeof(double)));
     chk(cudaMalloc(&bt->kind, (size_t)at));
     chk(cudaMalloc(&bt->bad, sizeof(unsigned long long)));
+    chk(cudaMalloc(&bt->off16, (size_t)2 * at * sizeof(uint16_t)));
+    chk(cudaMalloc(&bt->spmv_err, sizeof(int)));
+    if (bt->spmv_err) chk(cudaMemset(bt->spmv_err, 0, sizeof(int)));
     if (e == cudaSuccess) chk(cudaMemcpy(bt->geo_d, geo.data(), count * sizeof(Geo), cudaMemcpyHostToDevice));
     if (e == cudaSuccess)
         chk(cudaMemcpy(bt->off_d, bt->off.data(), (count + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
@@ -1126,6 +1166,30 @@ extern "C" mcd_status mcd_batch_create(const mcd_mesh *meshes, int count, const 
         set_error(std::string("batch allocation: ") + cudaGetErrorString(e));
         return MCD_ENOMEM;
     }
+    // system i as a stencil handle over the batch's own arrays (the
+    // network warm start and mcd_apply_laplacian run on it unchanged)
+    bt->views.resize(count);
+    for (int i = 0; i < count; ++i) {
+        mcd_stencils &v = bt->views[i];
+        memset(&v, 0, sizeof(v));
+        const int64_t o = bt->off[i];
+        v.mesh = meshes[i];
+        v.prm = *prm;
+        v.geo = make_geo(meshes[i]);
+        v.S = 9;
+        v.support = 1;
+        v.shape = 2;
+        v.nb = 5;
+        v.has_neumann = 0;
+        v.row64 = bt->row64 + 9 * o;
+        v.row32 = bt->row32 ? bt->row32 + 9 * o : nullptr;
+        v.rscale = bt->rscale + o;
+        v.kind = bt->kind + o;
+        v.off16 = bt->off16 + 2 * o;
+        v.bad_dp = bt->bad;
+        v.spmv_err = bt->spmv_err;
+        v.ws = nullptr;
+    }
     *out = bt;
     return MCD_OK;
 }
@@ -1135,6 +1199,7 @@ extern "C" void mcd_batch_destroy(mcd_batch *bt) {
     if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
     cudaFree(bt->geo_d); cudaFree(bt->off_d); cudaFree(bt->blk_d);
     cudaFree(bt->row64); cudaFree(bt->row32); cudaFree(bt->rscale); cudaFree(bt->kind); cudaFree(bt->bad);
+    cudaFree(bt->off16); cudaFree(bt->spmv_err);
     cudaFree(bt->bgeo_d); cudaFree(bt->b);
     for (int i = 0; i < 9; ++i) { cudaFree(bt->f[i]); cudaFree(bt->d[i]); }
     cudaFree(bt->sc); cudaFreeHost(bt->h_sc); cudaFree(bt->acc); cudaFree(bt->active); cudaFree(bt->prefix);
@@ -1167,7 +1232,14 @@ extern "C" mcd_status mcd_batch_build(mcd_batch *bt, const double *pos_dev, cons
     d.kind = bt->kind;
     d.bad = bt->bad;
     MCD_CUDA_TRY(launch_build_batch(d, stream));
+    for (int i = 0; i < bt->nsys; ++i)
+        MCD_CUDA_TRY(cnn_store_offsets(&bt->views[i], pos_dev + 2 * bt->off[i], mask_dev + bt->off[i], stream));
     return MCD_OK;
+}
+
+extern "C" const mcd_stencils *mcd_batch_stencils(const mcd_batch *bt, int i) {
+    if (!bt || i < 0 || i >= bt->nsys) return nullptr;
+    return &bt->views[i];
 }
 
 extern "C" mcd_status mcd_batch_check(const mcd_batch *bt, int64_t *first_bad_dp, mcd_stream_t stream) {
@@ -1194,6 +1266,21 @@ extern "C" mcd_status mcd_batch_solve(mcd_batch *bt, const double *rhs_dev, cons
     if (s != MCD_OK) return s;
     s = ensure_solver(bt, prm->mode);
     if (s != MCD_OK) return s;
+    if (prm->net) {
+        // the learned warm start of every system, on its assembled right-hand
+        // side (the prep kernel, which the solve then runs again unchanged:
+        // it touches only the Dirichlet and void entries of the guess)
+        const int64_t N = bt->N;
+        float *x32 = prm->mode == MCD_MIXED ? bt->f[0] : nullptr;
+        MCD_KLAUNCH(MCD_K_OTHER, stream, prep_kernel<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(
+                                             N, bt->kind, rhs_dev, bnd_dev, bt->b, p_dev, x32));
+        MCD_LAUNCH_CHECK();
+        for (int i = 0; i < bt->nsys; ++i) {
+            s = net_warm_start(prm->net, &bt->views[i], bt->b + bt->off[i], nullptr, p_dev + bt->off[i], nullptr,
+                               stream);
+            if (s != MCD_OK) return s;
+        }
+    }
     Launch L;
     s = run_solve(bt, rhs_dev, bnd_dev, p_dev, prm, use_graph != 0, stream, L);
     if (s != MCD_OK) return s;
@@ -1232,10 +1319,11 @@ extern "C" mcd_status mcd_batch_solve(mcd_batch *bt, const double *rhs_dev, cons
     mcd_status worst = MCD_OK;
     for (int i = 0; i < bt->nsys; ++i) {
         if (sub[i]) {
-            const int mixed_iters = res[i].iters;
+            const int mixed_iters = res[i].iters, dropped = res[i].discarded;
             res[i] = r64[i];
             res[i].iters += mixed_iters;
             res[i].fallback = 1;
+            res[i].discarded = dropped;
         }
         if (res[i].status != MCD_OK && worst == MCD_OK) worst = (mcd_status)res[i].status;
     }

@@ -2391,20 +2391,22 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
                     if (sc->iter >= sc->max_iter) { sc->max_hit = 1; sc->pending = 1; return; }
                     if (mixed && rr <= update2 * sc->rr_last) { sc->pending = 1; return; }
                     // a recursion whose residual grew since the last true
-                    // residual beyond what its schedule allows has diverged:
-                    // its correction is dropped, the recursion restarts from
-                    // the last folded iterate, and every later update of the
-                    // solve restarts too (the solve finishes in FP64 after 64
-                    // such cycles)
+                    // residual beyond what its schedule allows has diverged.
+                    // Replacing residuals: the cycle's correction is dropped,
+                    // the recursion restarts from the last folded iterate and
+                    // every later update of the solve restarts.  Restarting:
+                    // the solve finishes in FP64 from the last folded iterate.
                     // growth that counts as divergence: 100-fold in norm while
                     // residuals are replaced; the restarting schedule's short
                     // cycles spike higher on their own (1e4-fold)
                     const bool replacing = update_mode_ca == 2 && !sc->no_replace;
                     if (mixed && rr > (replacing ? 1e4 : 1e8) * sc->rr_last) {
                         sc->divergences += 1;
-                        if (sc->divergences > 64) { sc->diverged = 1; sc->done = 3; return; }
+                        // the restarting schedule would rerun the same cycle
+                        // bit for bit: its divergence ends the FP32 solve
+                        if (!replacing) { sc->diverged = 1; sc->done = 3; return; }
                         sc->discard = 1;
-                        sc->no_replace = 1;   // this system is beyond the FP32 rows' reach for replacement
+                        sc->no_replace = 1;
                         sc->pending = 1;
                         return;
                     }
@@ -2704,10 +2706,14 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
         if (h.phase_err) { result = MCD_ETIMEOUT; return MCD_OK; }
         if (h.done == 5) {
             // d0 of this refinement: the network's correction of the FP64
-            // residual b - A x64, along its residual-minimising step
-            s = net_warm_start(prm->precond, st, w->b, nullptr, x64, nullptr, stream);
+            // residual b - A x64, along its residual-minimising step.  A
+            // correction that cuts the residual by less than 10 % ends the
+            // network's part in this solve (the plain solve goes on)
+            double ns[8] = {0.0};
+            s = net_warm_start(prm->precond, st, w->b, nullptr, x64, ns, stream);
             if (s != MCD_OK) return s;
             net_corrections += 1;
+            if (!(ns[4] > 0.0 && ns[6] < 0.81 * ns[3])) a.net_exit = 0;
             const int zero = 0;
             MCD_CUDA_TRY(cudaMemcpyAsync(&w->sc->done, &zero, sizeof(int), cudaMemcpyHostToDevice, stream));
             MCD_CUDA_TRY(cudaMemcpyAsync(&w->sc->pending, &one, sizeof(int), cudaMemcpyHostToDevice, stream));
@@ -2811,9 +2817,13 @@ static mcd_status solve_impl(const mcd_stencils *st, const double *rhs, const do
     // on the interior block with the Neumann rows held fixed.  Their values
     // now follow from their own rows; then the full FP64 residual decides.
     if (result == MCD_OK && st->has_neumann) {
+        // Jacobi sweeps on the Neumann rows converge geometrically; the
+        // interior block may have stopped just below tol, leaving them a thin
+        // margin, so the rounds grow (8, 8, 16, 16, ... 256: about 1000
+        // sweeps at most) until the full residual meets tol
         result = MCD_ENOCONV;
-        for (int round = 0; round < 6; ++round) {
-            s = neumann_sweeps<G>(st, p, 8, stream);
+        for (int round = 0; round < 12; ++round) {
+            s = neumann_sweeps<G>(st, p, 8 << (round / 2), stream);
             if (s != MCD_OK) return s;
             s = residual<G>(st, p, prm->tol, 0, stream);
             if (s != MCD_OK) return s;

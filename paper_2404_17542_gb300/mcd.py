@@ -65,7 +65,7 @@ class c_batch_tuning(C.Structure):
 
 class c_batch_result(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("updates", C.c_int), ("rel_res", C.c_double),
-                ("fallback", C.c_int)]
+                ("fallback", C.c_int), ("discarded", C.c_int)]
 
 
 class c_body(C.Structure):
@@ -138,6 +138,7 @@ _SIGS = {
     "mcd_batch_check": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
     "mcd_batch_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(c_solve_params),
                                   C.c_int, C.c_void_p, C.c_void_p]),
+    "mcd_batch_stencils": (C.c_void_p, [C.c_void_p, C.c_int]),
     "mcd_batch_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(c_batch_tuning)]),
     "mcd_batch_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(c_batch_tuning)]),
     "mcd_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(c_solve_params),
@@ -403,13 +404,14 @@ class Batch:
         return st, bad.value
 
     def solve(self, rhs, bnd, p=None, tol=1e-8, mode=MIXED, max_iter=200000, inner_tol=0.3, graph=False,
-              raise_on_error=True):
+              raise_on_error=True, update_restart=0, net=None):
         """Solve every system; returns (p, dict of per-system arrays status,
         iters, updates, rel_res)."""
         if p is None:
             p = torch.zeros(self.N, dtype=torch.float64, device=rhs.device)
         sp = c_solve_params(tol=tol, max_iter=max_iter, mode=mode, inner_tol=inner_tol, max_refine=0,
-                            net=None, check_every=0, update_restart=1, net_dprev=None)
+                            net=None if net is None else net.handle, check_every=0,
+                            update_restart=int(update_restart), net_dprev=None)
         n = len(self.meshes)
         res = (c_batch_result * n)()
         f64 = torch.float64
@@ -417,11 +419,18 @@ class Batch:
                                    _ptr(p, f64, self.N), C.byref(sp), 1 if graph else 0,
                                    C.cast(res, C.c_void_p), _stream())
         out = {k: np.array([getattr(r, k) for r in res])
-               for k in ("status", "iters", "updates", "rel_res", "fallback")}
+               for k in ("status", "iters", "updates", "rel_res", "fallback", "discarded")}
         out["return"] = st
         if st != OK and raise_on_error:
             raise McdError(st, lib().mcd_last_error().decode())
         return p, out
+
+    def stencils(self, i):
+        """System i as a (library-owned) stencil handle."""
+        h = lib().mcd_batch_stencils(self.handle, int(i))
+        if not h:
+            raise McdError(EINVAL, f"no system {i}")
+        return StencilsView(h, self.meshes[i])
 
     def set_tuning(self, rows, ctas_per_sm):
         t = c_batch_tuning(rows=int(rows), ctas_per_sm=int(ctas_per_sm))
@@ -794,7 +803,7 @@ class AleFlow:
         self.info = {}
 
     def step(self, mode=None, net=None, dprev=None, tol=None, raise_on_error=True, precond=None,
-             update_restart=0):
+             update_restart=1):
         """One step; returns {solve, fallbacks, fallbacks_p, forces}.  net /
         dprev: the learned warm start of the solve, precond: the network that
         preconditions its refinement (as in Stencils.solve)."""
