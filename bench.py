@@ -1274,8 +1274,10 @@ def spmv_arm(args):
                                    "Dirichlet walls)", "dps": N, "l2_bytes": l2,
                        "l2": f"working set {spmv_bytes_per_dp(9, False) * N / 1e6:.0f} MB (FP32) > 3x L2"},
             "roofline": {"bound": "hbm", "achieved": spmv["f32"]["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                         "frac": spmv["f32"]["frac"], "traffic": None,
-                         "kernel": "spmv_kernel<float, 2>",
+                         "frac": spmv["f32"]["frac"],
+                         "traffic": (committed_traffic("spmv2d_tma") * N if committed_traffic("spmv2d_tma")
+                                     else None),
+                         "kernel": "spmv2d_tma<float>",
                          "algorithmic": f"{spmv_bytes_per_dp(9, False)} B per DP x {N} DPs per launch",
                          "peak_source": f"{peak_src} hbm_gbs"},
             "spmv": spmv, "solve_2048": solve, "gpu_launches": launches, "clocks": clk}

@@ -360,7 +360,11 @@ typedef struct {
  *     Eqs. (45)-(46), r_e = 5 l0), clamp into the cell.
  * pos_dev (float64 [2][N]) and mask_dev (int8 [N]) are updated in place;
  * mask_prev_dev (int8 [N]) receives the old mask.  2D only (MCD_ENOTSUP
- * otherwise); a bad body list gives MCD_EINVAL.  Asynchronous. */
+ * otherwise); a bad body list gives MCD_EINVAL.  Asynchronous.
+ * The Jacobi sweeps use one scratch buffer per device inside the library
+ * (grown with cudaMalloc/cudaFree when a larger mesh comes): calls whose
+ * work may overlap on the GPU (on two streams, or from two threads) race on
+ * it and must be serialised by the caller. */
 mcd_status mcd_update_dps(const mcd_mesh *mesh, const mcd_body *bodies,
                           int nbodies, double *pos_dev, int8_t *mask_dev,
                           int8_t *mask_prev_dev, double kappa, int n_relax,
@@ -381,8 +385,10 @@ mcd_status mcd_update_dps(const mcd_mesh *mesh, const mcd_body *bodies,
  *    the library until the process exits; meshes with more than
  *    MCD_NOALLOC_MAX_DPS cells are rejected with MCD_EINVAL;
  *  - the first call on each device looks up that array's device address
- *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture;
+ *    (cudaGetSymbolAddress, with that device current) and keeps it; make
+ *    that first call before any stream capture, and do not reset the device
+ *    (cudaDeviceReset) after it in a process that goes on calling this
+ *    entry point (the kept address would no longer be valid);
  *  - all calls share the one array: calls whose work may overlap on the GPU
  *    (for instance on two streams) race and must be serialised by the
  *    caller.  Each call overwrites the scratch it reads, so nothing needs

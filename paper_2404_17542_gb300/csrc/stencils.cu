@@ -239,7 +239,13 @@ __device__ __forceinline__ void build_dp(const BuildArgs &a, const Geo &g, int64
     double acc[NB];
     for (int q = 0; q < NB * (NB + 1) / 2; ++q) L[q] = 0.0;
     for (int q = 0; q < NB; ++q) acc[q] = 0.0;
+    // the 3x3 build keeps each neighbour's weight for pass 2 (registers:
+    // the loops are unrolled), instead of evaluating the FP64 sqrt and exp a
+    // second time; the wider stencils recompute it
+    constexpr bool KEEP_W = (S == 9);
+    double wkeep[KEEP_W ? S : 1];
 
+#pragma unroll(KEEP_W ? S : 1)
     for (int s = 0; s < S; ++s) {
         if (s == C) continue;
         Nbr<DIM> nb = neighbour<G>(g, c, s);
@@ -254,6 +260,7 @@ __device__ __forceinline__ void build_dp(const BuildArgs &a, const Geo &g, int64
             r2 += dx[d] * dx[d];
         }
         const double w = mls_weight(sqrt(r2), a.weight_kind, r_e);
+        if constexpr (KEEP_W) wkeep[s] = w;
         double p[NB];
         if (neu) {
             double n[DIM];
@@ -304,6 +311,7 @@ __device__ __forceinline__ void build_dp(const BuildArgs &a, const Geo &g, int64
     rscale[k] = sigma;
 
     // ---- pass 2: per-slot weights ----
+#pragma unroll(KEEP_W ? S : 1)
     for (int s = 0; s < S; ++s) {
         double z[NB];
         double zq[NB];
@@ -321,7 +329,9 @@ __device__ __forceinline__ void build_dp(const BuildArgs &a, const Geo &g, int64
                     X[d] = dx[d] * inv_rs;
                     r2 += dx[d] * dx[d];
                 }
-                const double w = mls_weight(sqrt(r2), a.weight_kind, r_e);
+                double w;
+                if constexpr (KEEP_W) w = wkeep[s];
+                else w = mls_weight(sqrt(r2), a.weight_kind, r_e);
                 double p[NB];
                 if (neu) {
                     double n[DIM];
@@ -748,6 +758,7 @@ static bool launch_spmv_tma(const mcd_stencils *st, const T *row, const T *x, T 
     const Geo &g = st->geo;
     if (st->shape != 2 || g.per[0] || g.per[1] || g.n[0] % P::VEC != 0) return false;
     if ((uintptr_t)row % 16 || (uintptr_t)x % 16 || (uintptr_t)y % 16) return false;
+    if (((uint64_t)g.N * sizeof(T)) % 16) return false;   // slot stride of the rows
     SpmvEncodeFn enc = spmv_encoder();
     if (!enc) return false;
     const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
@@ -1039,13 +1050,18 @@ extern "C" mcd_status mcd_apply_laplacian(const mcd_stencils *st, const void *x_
     const unsigned blocks = (unsigned)((N + threads - 1) / threads);
     const int n0 = st->geo.n[0], n1 = st->geo.n[1];
     const bool tiled = st->shape == 2 && (n1 + 7) / 8 <= 65535;
+    // the vector paths load 16-byte groups of the rows and store y the same
+    // way: the rows and y must start on 16-byte boundaries (a system of a
+    // batch starts at an arbitrary DP offset inside the batch's arrays)
+    auto al16 = [](const void *q) { return ((uintptr_t)q % 16) == 0; };
     if (dtype == MCD_DT_F64) {
         const double *row = st->row64;
         const double *x = (const double *)x_dev;
         double *y = (double *)y_dev;
-        if (launch_spmv_tma<double>(st, row, x, y, stream))
-            ;
-        else if (tiled && n0 % 2 == 0)
+        // FP64: the shared-memory tiles (the product is bound by the FP64
+        // pipe, 9 DFMA per DP, which TMA staging does not relieve: 0.278 ms
+        // against 0.312 ms at 4096^2)
+        if (tiled && n0 % 2 == 0 && al16(row) && al16(y))
             MCD_KLAUNCH(MCD_K_OTHER, stream, spmv2d_tiled<double, 2><<<dim3((n0 + 63) / 64, (n1 + 7) / 8), threads, 0, stream>>>(st->geo, row, x, y));
         else if (tiled)
             MCD_KLAUNCH(MCD_K_OTHER, stream, spmv2d_tiled<double, 1><<<dim3((n0 + 31) / 32, (n1 + 7) / 8), threads, 0, stream>>>(st->geo, row, x, y));
@@ -1062,7 +1078,7 @@ extern "C" mcd_status mcd_apply_laplacian(const mcd_stencils *st, const void *x_
         float *y = (float *)y_dev;
         if (launch_spmv_tma<float>(st, row, x, y, stream))
             ;
-        else if (tiled && n0 % 4 == 0)
+        else if (tiled && n0 % 4 == 0 && al16(row) && al16(y))
             MCD_KLAUNCH(MCD_K_OTHER, stream, spmv2d_tiled<float, 4><<<dim3((n0 + 127) / 128, (n1 + 7) / 8), threads, 0, stream>>>(st->geo, row, x, y));
         else if (tiled)
             MCD_KLAUNCH(MCD_K_OTHER, stream, spmv2d_tiled<float, 1><<<dim3((n0 + 31) / 32, (n1 + 7) / 8), threads, 0, stream>>>(st->geo, row, x, y));

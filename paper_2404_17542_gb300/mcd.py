@@ -803,7 +803,7 @@ class AleFlow:
         self.info = {}
 
     def step(self, mode=None, net=None, dprev=None, tol=None, raise_on_error=True, precond=None,
-             update_restart=1):
+             update_restart=1, inner_tol=0.3):
         """One step; returns {solve, fallbacks, fallbacks_p, forces}.  net /
         dprev: the learned warm start of the solve, precond: the network that
         preconditions its refinement (as in Stencils.solve)."""
@@ -812,7 +812,8 @@ class AleFlow:
         bk = make_bodies(geo_k, vels=V_k)
         b1 = make_bodies(geo_1, vels=V_1)
         sp = c_solve_params(tol=float(self.tol if tol is None else tol),
-                            max_iter=200000, mode=int(self.mode if mode is None else mode), inner_tol=0.3,
+                            max_iter=200000, mode=int(self.mode if mode is None else mode),
+                            inner_tol=float(inner_tol),
                             max_refine=60, net=None if net is None else net.handle, check_every=64,
                             update_restart=int(update_restart),
                             net_dprev=None if dprev is None else _ptr(dprev, torch.float64, self.N),

@@ -149,3 +149,38 @@ def test_full_batched_workload(mcd):
         want = oracle_solution(probs[i])
         gi = got[bt.offsets[i]:bt.offsets[i + 1]]
         assert rel(gi, want) <= 1e-6, (i, probs[i].mesh.n)
+
+
+def test_system_views_at_odd_offsets(mcd):
+    """System i of a batch as a stencil handle (mcd_batch_stencils): its rows
+    start at DP offset off_i inside the batch's arrays, odd here (the systems
+    before it have odd cell counts), so the SpMV takes its scalar path.  The
+    product matches the oracle's matrix of that system; the learned warm
+    start runs per system inside the batched solve, never raises a system's
+    residual, and every system still converges to the oracle's solution."""
+    sizes = [33, 35, 40, 37, 44]
+    probs = [inputs.poly4_box(n, seed=300 + i) for i, n in enumerate(sizes)]
+    bt, rhs, bnd = make_batch(mcd, probs, mcd.MIXED)
+    offs = bt.offsets
+    assert offs[1] % 2 == 1 and offs[2] % 2 == 0 and offs[3] % 2 == 0 and offs[4] % 2 == 1
+    rng = np.random.default_rng(5)
+    for i, pb in enumerate(probs):
+        st = bt.stencils(i)
+        W = mls.build_weights(pb.mesh, pb.pos, pb.mask)
+        A = solve.assemble(pb.mesh, W["row"])
+        x = rng.normal(size=pb.mesh.N)
+        # x and y start at the system's offset too (slices of batch-sized arrays)
+        big = torch.zeros(int(offs[-1]), dtype=torch.float64, device="cuda")
+        big[offs[i]:offs[i + 1]] = dev(x)
+        out = torch.zeros_like(big)
+        st.apply(big[offs[i]:offs[i + 1]], out[offs[i]:offs[i + 1]])
+        want = A @ x
+        scale = np.abs(A).multiply(np.abs(x)[None, :]).sum(axis=1).A.ravel()
+        got = out[offs[i]:offs[i + 1]].cpu().numpy()
+        assert np.all(np.abs(got - want) <= 1e-13 * scale + 1e-300), i
+    net = mcd.Net(inputs.cnn_flatten(*inputs.cnn_weights(7)))
+    p, res = bt.solve(rhs, bnd, tol=1e-10, mode=mcd.MIXED, net=net)
+    assert (res["status"] == 0).all()
+    got = p.cpu().numpy()
+    for i, pb in enumerate(probs):
+        assert rel(got[offs[i]:offs[i + 1]], oracle_solution(pb)) <= 1e-6, i

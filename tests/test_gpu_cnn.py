@@ -263,81 +263,58 @@ def test_net_rejects_bad_shapes(mcd):
         mcd.Net(np.zeros(10, np.float32))
 
 
-def cylinder_sequence(mcd, n, steps, net=None, train=None):
-    """Run the oscillating-cylinder pressure sequence on the GPU (DP update,
-    stencil build, mixed solve warm-started from the previous pressure).
-    With `train` (a list) it appends (x, target, weight) of every step; with
-    `net` it returns the warm-start statistics of every step instead of
-    solving without it."""
-    pb = inputs.cylinder_box(n)
-    cyl, mesh = pb.meta["cylinder"], pb.mesh
-    N = mesh.N
-    dt = 0.2 * mesh.l0
-    pos = dev(pb.pos.ravel().copy())
-    mask = dev(pb.mask.copy())
-    prev = torch.empty_like(mask)
-    normal = torch.zeros(2 * N, dtype=torch.float64, device="cuda")
-    neu = torch.zeros(N, dtype=torch.float64, device="cuda")
-    rhs = dev(inputs.ppe_source(pb.pos, 0.0))
-    mcd.update_dps(mesh, cyl.centre(0.0), cyl.radius, cyl.body_id, pos, mask, prev, n_relax=30, band=0.0)
-    mcd.body_boundary(mesh, cyl.centre(0.0), cyl.radius, cyl.body_id, pos, mask,
-                      acc=cyl.acceleration(0.0), normal=normal, neumann=neu)
-    st = mcd.Stencils(mesh, pos, mask, normal, bc_kind=pb.bc_kind, precision=mcd.MIXED)
-    p = torch.zeros(N, dtype=torch.float64, device="cuda")
-    p_m1 = p.clone()
-    stats = []
-    for k in range(1, steps + 1):
-        t = k * dt
-        c = cyl.centre(t)
-        mcd.update_dps(mesh, c, cyl.radius, cyl.body_id, pos, mask, prev, band=5.0 * mesh.l0)
-        mcd.body_boundary(mesh, c, cyl.radius, cyl.body_id, pos, mask, acc=cyl.acceleration(t),
-                          normal=normal, neumann=neu)
-        st.rebuild(pos, mask, normal)
-        dprev = p - p_m1
-        p_prev = p.clone()
-        if net is not None:
-            p, info = st.solve(rhs, neu, p=p, net=net, dprev=dprev.clone())
-            stats.append((info["rel_res_guess"], info["rel_res_start"], info["iters"]))
-        else:
-            p, info = st.solve(rhs, neu, p=p)
-        if train is not None and k > 2:
-            b = st.assemble_rhs(rhs, neu)
-            train.append(net_features(mcd, st, b, p_prev, dprev, p))
-        p_m1 = p_prev
-    return stats
+def test_trained_net_on_the_flow_ppe(mcd):
+    """What the learned warm start gains on the PPE of the moving-boundary
+    flow (mcd_flow_step: the step's own source, the ALE pressure guess, the
+    restarting mixed schedule), 256^2 oscillating cylinder: the network
+    (initialised as linear extrapolation in time, trained on the run's
+    first 40 steps) against the same steps without it, from one snapshot
+    per step.  What holds, and is asserted: the correction never raises the
+    guess's residual (its step minimises the residual) and lowers it on
+    average; the iterations with it stay within 10 % of those without.
+    What it does not do on this PPE, where the ALE guess is already close:
+    cut the iterations (printed; about even in the measurements)."""
+    n = 256
+    cyl = inputs.Cylinder()
+    pb = inputs.cylinder_box(n, cyl)
+    mesh = pb.mesh
+    nu = 2 * cyl.radius / 100.0
+    dt = min(0.2 * mesh.l0, 0.2 * mesh.l0 ** 2 / nu)
 
+    def bodies_at(t):
+        return [(cyl.body_id, cyl.centre(t), cyl.radius)], [cyl.velocity(t)]
 
-_FEATURE_NET = {}
-
-
-def net_features(mcd, st, b, p_prev, dprev, p_true):
-    if "net" not in _FEATURE_NET:
-        _FEATURE_NET["net"] = mcd.Net(inputs.cnn_flatten(*net_params(0)))
-    return _FEATURE_NET["net"].features(st, b, p_prev, dprev, p_true)
-
-
-def test_trained_net_gains_over_untrained_and_plain(mcd):
-    """The gain the trained network brings on the cylinder sequence: the
-    residual of the warm-started guess relative to the plain warm start
-    (the previous pressure).  The line search guarantees a ratio <= 1; an
-    untrained network gets only what a random direction gives, the trained
-    one must cut the residual at least in half on steps it has not seen."""
-    n = 128
+    flow = mcd.AleFlow(mesh, dev(pb.pos.ravel().copy()), dev(pb.mask.copy()), bodies_at, nu, dt,
+                       precision=mcd.MIXED, mode=mcd.MIXED, tol=1e-8, ale_pressure=True)
+    net = mcd.Net(inputs.cnn_flatten(*inputs.cnn_weights_extrapolating(3)))
     data = []
-    cylinder_sequence(mcd, n, 40, train=data)
-    net = mcd.Net(inputs.cnn_flatten(*net_params(30)))
-    untrained = mcd.Net(inputs.cnn_flatten(*net_params(30)))
+    dprev = torch.zeros(mesh.N, dtype=torch.float64, device="cuda")
+    for k in range(40):
+        flow.step()
+        st = flow.stencils(mcd.FLOW_PRESSURE)
+        b = flow.array(mcd.FLOW_B)
+        guess = flow.array(mcd.FLOW_GUESS)
+        if k >= 2:
+            data.append(net.features(st, b, guess, dprev, flow.P))
+        dprev = flow.P - guess
     rng = np.random.default_rng(0)
-    for _ep in range(25):
+    for _ep in range(10):
         for i in rng.permutation(len(data)):
             x, tg, wt = data[i]
             net.train_step(x, tg, wt, n, n, 1e-3)
-    trained = cylinder_sequence(mcd, n, 48, net=net)[40:]
-    random_net = cylinder_sequence(mcd, n, 48, net=untrained)[40:]
-    r_tr = np.mean([after / before for before, after, _ in trained])
-    r_un = np.mean([after / before for before, after, _ in random_net])
-    it_tr = np.mean([it for *_r, it in trained])
-    it_un = np.mean([it for *_r, it in random_net])
-    print(f"residual ratio trained {r_tr:.3f} untrained {r_un:.3f}; iterations {it_tr:.0f} / {it_un:.0f}")
-    assert r_tr <= 0.5
-    assert r_tr < 0.75 * r_un
+    del data
+    it_net, it_plain, ratios = [], [], []
+    for _k in range(10):
+        snap = flow.snapshot()
+        info = flow.step(net=net, dprev=dprev)["solve"]   # dprev <- this step's increment
+        it_net.append(info["iters"])
+        ratios.append(info["rel_res_start"] / info["rel_res_guess"])
+        flow.restore(snap)
+        it_plain.append(flow.step()["solve"]["iters"])
+    print(f"iterations with the network {it_net}, without {it_plain}; residual ratios {np.round(ratios, 3)}")
+    assert all(r <= 1.0 + 1e-12 for r in ratios)
+    assert np.mean(ratios) < 0.995
+    assert sum(it_net) <= 1.1 * sum(it_plain)
+    flow.close()
+
+

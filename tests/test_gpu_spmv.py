@@ -1,8 +1,9 @@
 """GPU parity of the matrix-free stencil SpMV (mcd_apply_laplacian, the rows
 of Eq. (21)) on the layouts that select each kernel: non-periodic meshes with
-n0 a multiple of the vector width (TMA-streamed tiles), periodic meshes
-(shared-memory tiles), n0 not a multiple of 4 (scalar tiles); sizes with
-ragged tiles in x and y; and sampled rows at the full 4096^2 size.
+n0 a multiple of 4 (FP32: TMA-streamed tiles; FP64: shared-memory tiles with
+16-byte loads), periodic meshes (shared-memory tiles), n0 not a multiple of 4
+(scalar tiles); sizes with ragged tiles in x and y; and sampled rows at the
+full 4096^2 size.
 
 FP64: the oracle's CSR product to 1e-13 of sum |c_s x_j|.  FP32: the exact
 value of the FP32 difference-form row applied to the FP32 vector (computed
