@@ -357,6 +357,16 @@ def train_nets(run, steps, epochs, precond=True, lr=1e-3, seed=3):
     return net, pre, info
 
 
+def fp64_finish_counts(infos):
+    """How many solves finished in FP64 after the FP32 recursion failed, and
+    why (mcd_solve_info.fallback: 1 diverged, 2 restarts exhausted, 3 alpha
+    not finite or 0, 4 t.t = 0, 5 non-finite dot products, 6 iteration
+    limit, 7 other)."""
+    codes = [int(i["fallback"]) for i in infos]
+    return {"fp64_finishes": sum(1 for c in codes if c),
+            "fp64_finish_reasons": {str(c): codes.count(c) for c in sorted(set(codes)) if c}}
+
+
 def flush_l2(buf):
     buf.zero_()
 
@@ -505,7 +515,7 @@ def gpu_arm(args):
         return {"value": sum(i["unknowns"] for _m, i in rows) / (t / 1e3), "ms_per_step": t / len(rows),
                 "iters_per_step": statistics.mean(i["iters"] for _m, i in rows),
                 "rel_res_max": max(i["rel_res"] for _m, i in rows),
-                "fp64_finishes": sum(i["fallback"] for _m, i in rows)}
+                **fp64_finish_counts(i for _m, i in rows)}
     fp64 = summary(arms["fp64"])
     no_net = summary(arms["no_net"])
     with_pre = summary(arms["precond"])
@@ -580,7 +590,7 @@ def gpu_arm(args):
             "iters_per_step": statistics.mean(i["iters"] for i in infos),
             "updates_per_step": statistics.mean(i["refinements"] for i in infos),
             "dropped_cycles_per_step": statistics.mean(i["discarded"] for i in infos),
-            "fp64_finishes": sum(i["fallback"] for i in infos),
+            **fp64_finish_counts(infos),
             "rel_res_max": max(i["rel_res"] for i in infos),
             "unknowns_per_step": unknowns / K,
             "wall_s": wall,

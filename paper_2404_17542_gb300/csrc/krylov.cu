@@ -62,6 +62,10 @@ struct Scalars {
     int divergences;  // cycles dropped so far
     int updates;      // true-residual updates (persistent schedule)
     int no_replace;   // a replaced recursion diverged: restart at every later update
+    // FP32 kernel: the recursion's scalars as double-float pairs (hi, lo),
+    // updated on the FP32 pipe at every barrier; the doubles above are
+    // refreshed from them at true-residual updates and when a launch ends
+    float2 rho_d, alpha_d, omega_d, rhat2_d, tol2_d, rr_last_d, rr_d, rv_d, ts_d, tt_d, ss_d;
 };
 
 // Refresh the FP32 copies (called by the single thread that updates them).
@@ -957,6 +961,53 @@ __device__ __forceinline__ void store_step_scalars(Scalars *g, const Scalars &l)
         g->beta = l.beta;
     }
 }
+
+// ---- double-float scalar arithmetic (the FP32 kernel's scalar update) -----
+// One thread of block 0 updates the recursion's scalars at every barrier.
+// In FP64 that chain of divisions costs about 2 us on this GPU's 1/64-rate
+// FP64 pipe; the same quantities as unevaluated float pairs take a few
+// dozen FP32 operations.  Products are split with fma, sums by TwoSum, and
+// a quotient is q1 + (a - q1 b) / b (about 44 significant bits), enough for
+// the cancellation in rho' = r^.s - omega r^.t.  The operations assume
+// normalised pairs (|lo| <= ulp(hi) / 2).  The grid's totals are not: their
+// low words collect the rounding errors of every partial sum, and where a
+// dot product cancels (r^.r, r^.t) the low word can reach a good fraction
+// of the high one; df_norm renormalises them first.
+__device__ __forceinline__ DF df_norm(DF a) {
+    float s, e;
+    two_sum_f(a.hi, a.lo, s, e);
+    return DF{s, e};
+}
+__device__ __forceinline__ DF df_quick(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_quick(p, e);
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) {
+    float s, e;
+    two_sum_f(a.hi, -b.hi, s, e);
+    // after cancellation of the high words the low words' difference can
+    // exceed s: TwoSum, not the quick form
+    return df_norm(DF{s, __fadd_rn(e, __fsub_rn(a.lo, b.lo))});
+}
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const DF r = df_sub(a, df_mul(b, DF{q1, 0.0f}));
+    return df_quick(q1, __fdiv_rn(r.hi, b.hi));
+}
+__device__ __forceinline__ float2 df_pack(DF a) { return make_float2(a.hi, a.lo); }
+__device__ __forceinline__ DF df_unpack(float2 a) { return DF{a.x, a.y}; }
+__device__ __forceinline__ float2 df_from(double d) {
+    const float h = (float)d;
+    return make_float2(h, (float)(d - (double)h));
+}
+__device__ __forceinline__ double df_value(float2 a) { return (double)a.x + (double)a.y; }
 
 // Grid barrier that finishes the NV-value reduction: returns false if a wait
 // gave up.  Every block writes its partial sums and then its arrival flag
@@ -2304,15 +2355,28 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
                     sc->rr = tot[3];
                     sc->tol2 = tol * tol * tot[1];
                     sc->pending = 0;
+                    if constexpr (sizeof(T) == 4) {
+                        sc->tol2_d = df_from(sc->tol2);
+                        sc->rr_d = df_from(tot[3]);
+                    }
                     if (!isfinite(tot[0] + tot[1])) { sc->done = 4; return; }
                     if (tot[0] <= sc->tol2) { sc->done = 1; return; }
                     if (sc->max_hit) { sc->done = 2; return; }
                     sc->rr_last = tot[3];
                     sc->it_last = sc->iter;
                     sc->updates += 1;
+                    // the recursion's scalars (kept as double-float pairs by
+                    // the FP32 kernel)
+                    double rho_c = sc->rho, alpha_c = sc->alpha, omega_c = sc->omega;
+                    if constexpr (sizeof(T) == 4) {
+                        sc->rr_last_d = df_from(tot[3]);
+                        rho_c = df_value(sc->rho_d);
+                        alpha_c = df_value(sc->alpha_d);
+                        omega_c = df_value(sc->omega_d);
+                    }
                     const bool corrected = sc->net_fresh != 0 || sc->discard != 0;
                     const bool keep = update_mode == 2 && !sc->no_replace && !corrected && !sc->restart &&
-                                      !sc->s_conv && sc->rho != 0.0 && sc->omega != 0.0;
+                                      !sc->s_conv && rho_c != 0.0 && omega_c != 0.0;
                     // an update that restarts the recursion (the first, after a
                     // dropped cycle, an ||s|| stop or a breakdown; every update
                     // of the restarting schedule) begins a new refinement
@@ -2329,17 +2393,21 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
                     // mode 1, the first update, after an ||s|| stop or a
                     // restart) the recursion restarts from r.
                     if (keep) {
-                        const double beta = (tot[2] / sc->rho) * (sc->alpha / sc->omega);
+                        const double beta = (tot[2] / rho_c) * (alpha_c / omega_c);
                         if (isfinite(beta)) {
                             sc->beta = beta;
                             sc->replace = 1;
-                            publish(sc);
+                            if constexpr (sizeof(T) == 4)
+                                sc->beta_f = (float)beta;   // alpha_f, omega_f stay those of the last iteration
+                            else
+                                publish(sc);
                             return;
                         }
                     }
                     sc->restart = 1;
                     sc->s_conv = 0;
                     sc->alpha = sc->beta = sc->omega = 0.0;
+                    if constexpr (sizeof(T) == 4) sc->alpha_d = sc->omega_d = make_float2(0.0f, 0.0f);
                     publish(sc);
                 };
             if (!grid_reduce<4>(a, epoch, all, [&](double *tot) { tr_last(tot); store_scalars(a.sc, ls); }))
@@ -2428,12 +2496,52 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
                 sc->alpha = alpha_n;
                 sc->alpha_f = (float)alpha_n;   // omega_f and beta_f are unchanged since phase B
             };
+            // the same tests and updates on the FP32 pipe (double-float
+            // scalars; a threshold test reads the high word)
+            auto ca_last_df = [&](const DF *tot) {
+                const DF rv = df_norm(tot[0]), rr = df_norm(tot[1]), rho = df_norm(tot[2]);
+                sc->rv_d = df_pack(rv);
+                sc->rr_d = df_pack(rr);
+                sc->replace = 0;
+                if (mode == CA_NORMAL || mode == CA_SCONV) sc->iter += 1;
+                if (!isfinite(rv.hi + rr.hi + rho.hi)) { sc->diverged = 5; sc->done = 4; return; }
+                if (mode == CA_SCONV) { sc->pending = 1; return; }
+                if (mode == CA_RESTART) {
+                    sc->rhat2_d = df_pack(rr);
+                } else {
+                    const float rrf = rr.hi, last = sc->rr_last_d.x;
+                    if (rrf <= sc->tol2_d.x) { sc->pending = 1; return; }
+                    if (sc->iter >= sc->max_iter) { sc->max_hit = 1; sc->pending = 1; return; }
+                    if (rrf <= (float)update2 * last) { sc->pending = 1; return; }
+                    const bool replacing = update_mode_ca == 2 && !sc->no_replace;
+                    if (rrf > (replacing ? 1e4f : 1e8f) * last) {
+                        sc->divergences += 1;
+                        if (!replacing) { sc->diverged = 1; sc->done = 3; return; }
+                        sc->discard = 1;
+                        sc->no_replace = 1;
+                        sc->pending = 1;
+                        return;
+                    }
+                    if (sc->iter - sc->it_last >= stall) { sc->pending = 1; return; }
+                    if (fabsf(rho.hi) <= (float)eps * sqrtf(sc->rhat2_d.x) * sqrtf(rrf)) {
+                        sc->restarts += 1;
+                        if (sc->restarts > 1000) { sc->diverged = 2; sc->done = 3; return; }
+                        sc->restart = 1;
+                        return;
+                    }
+                }
+                sc->restart = 0;
+                sc->parity ^= 1;
+                sc->rho_d = df_pack(rho);
+                const DF alpha_n = df_div(rho, rv);
+                if (!isfinite(alpha_n.hi) || alpha_n.hi == 0.0f) { sc->diverged = 3; sc->done = 3; return; }
+                sc->alpha_d = df_pack(alpha_n);
+                sc->alpha_f = alpha_n.hi;   // omega_f and beta_f are unchanged since phase B
+            };
             bool ok;
             if constexpr (sizeof(T) == 4) {
                 ok = grid_reduce_df<3>(a, epoch, dot, [&](const DF *tot) {
-                    double t64[3];
-                    for (int q = 0; q < 3; ++q) t64[q] = (double)tot[q].hi + (double)tot[q].lo;
-                    ca_last(t64);
+                    ca_last_df(tot);
                     store_step_scalars<T>(a.sc, ls);
                 });
             } else {
@@ -2473,12 +2581,30 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
                 sc->beta = (rho_next / sc->rho) * (sc->alpha / omega);
                 publish(sc);
             };
+            auto b_last_df = [&](const DF *tot_raw) {
+                DF tot[5];
+                for (int q = 0; q < 5; ++q) tot[q] = df_norm(tot_raw[q]);
+                sc->ts_d = df_pack(tot[0]);
+                sc->tt_d = df_pack(tot[1]);
+                sc->ss_d = df_pack(tot[2]);
+                if (!isfinite(tot[0].hi + tot[1].hi + tot[2].hi + tot[3].hi + tot[4].hi)) {
+                    sc->diverged = 5;
+                    sc->done = 4;
+                    return;
+                }
+                if (tot[2].hi <= sc->tol2_d.x) { sc->s_conv = 1; return; }
+                if (tot[1].hi == 0.0f) { sc->diverged = 4; sc->done = 3; return; }
+                const DF omega = df_div(tot[0], tot[1]);
+                const DF rho_next = df_sub(tot[3], df_mul(omega, tot[4]));
+                const DF beta = df_mul(df_div(rho_next, df_unpack(sc->rho_d)), df_div(df_unpack(sc->alpha_d), omega));
+                sc->omega_d = df_pack(omega);
+                sc->omega_f = omega.hi;
+                sc->beta_f = beta.hi;
+            };
             bool ok;
             if constexpr (sizeof(T) == 4) {
                 ok = grid_reduce_df<5>(a, epoch, dot, [&](const DF *tot) {
-                    double t64[5];
-                    for (int q = 0; q < 5; ++q) t64[q] = (double)tot[q].hi + (double)tot[q].lo;
-                    b_last(t64);
+                    b_last_df(tot);
                     store_step_scalars<T>(a.sc, ls);
                 });
             } else {
@@ -2490,7 +2616,21 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
         }
     }
 finish:
-    if (blockIdx.x == 0 && threadIdx.x == 0) store_scalars(a.sc, ls);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if constexpr (sizeof(T) == 4) {
+            // the doubles the host reads for its diagnostics
+            ls.rho = df_value(ls.rho_d);
+            ls.alpha = df_value(ls.alpha_d);
+            ls.omega = df_value(ls.omega_d);
+            ls.rv = df_value(ls.rv_d);
+            ls.rr = df_value(ls.rr_d);
+            ls.rhat2 = df_value(ls.rhat2_d);
+            ls.ts = df_value(ls.ts_d);
+            ls.tt = df_value(ls.tt_d);
+            ls.ss = df_value(ls.ss_d);
+        }
+        store_scalars(a.sc, ls);
+    }
 }
 
 // Grid of the persistent launch: every resident slot (at most one block per
