@@ -84,6 +84,12 @@ def parse_args():
     ap.add_argument("--support", type=int, default=1, choices=[1, 4],
                     help="with --profile-solve --workload array: 1 = 3x3 stencil, 4 = 9x9 stencil")
     ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--update-restart", type=int, default=0, choices=[0, 1],
+                    help="with --profile-solve / --trace-solve: the mixed solve's update schedule "
+                         "(0 adaptive, 1 restarting as in the flow step)")
+    ap.add_argument("--barriers", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="with --profile-solve / --trace-solve: grid barriers per Bi-CGSTAB iteration "
+                         "(0: the library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -200,10 +206,11 @@ def committed_traffic(kernel):
 class CylinderRun:
     """State of one oscillating-cylinder instance on the device."""
 
-    def __init__(self, n, dev, mcd, inputs, tol):
+    def __init__(self, n, dev, mcd, inputs, tol, barriers=0, update_restart=0):
         import torch
         self.torch, self.mcd, self.inputs = torch, mcd, inputs
-        self.n, self.dev, self.tol = n, dev, tol
+        self.n, self.dev, self.tol, self.barriers = n, dev, tol, barriers
+        self.update_restart = update_restart
         pb = inputs.cylinder_box(n)
         self.pb, self.cyl, self.mesh = pb, pb.meta["cylinder"], pb.mesh
         N = self.mesh.N
@@ -251,7 +258,8 @@ class CylinderRun:
                           acc=self.cyl.acceleration(t), normal=self.normal, neumann=self.neu)
         self.st.rebuild(self.pos, self.mask, self.normal)
         _p, info = self.st.solve(self.rhs, self.neu, p=self.p, tol=self.tol, mode=mode, net=net,
-                                 dprev=self.dprev if net is not None else None)
+                                 dprev=self.dprev if net is not None else None, barriers=self.barriers,
+                                 update_restart=self.update_restart)
         return info
 
 
@@ -390,13 +398,16 @@ def timed_step(run, mode, flush_buf, net=None, host_out=None, precond=None):
     return e0.elapsed_time(e1), info
 
 
-# Algorithmic bytes of the persistent Bi-CGSTAB solve per DP and iteration
-# (FP32 recursion, 2D, 9-point rows):
-#   phase A reads r, p, v, r^ (16) + 9 FP32 weights (36), writes p, v (8)  = 60
-#   phase B reads r, v (8) + weights (36), writes s, t (8)                  = 52
-#   phase C reads x, p, s, t, r^ (20), writes x, r (8)                      = 28
-# i.e. 140 B per DP-iteration; halo re-reads, the low word of the
-# double-float correction and the true-residual updates are not counted.
+# Algorithmic bytes of the persistent Bi-CGSTAB solve per DP and iteration,
+# FP32 recursion on 2D 9-point rows, two grid barriers per iteration (the
+# kernel the step runs, bicg_persistent2): phase CA reads s, t, p, v (16 B),
+# r^ and the double-float correction x, xlo (12 B) and the 9 FP32 weights
+# (36 B) and writes x, xlo, r, p, v (20 B); phase B reads r, v, r^ (12 B)
+# and the weights (36 B) and writes s, t (8 B): 140 B per DP-iteration.
+# Halo re-reads, the phases that restart or replace the recursion and the
+# true-residual updates are not counted.  (The one-barrier schedule,
+# barriers = 1, moves 96 B: reads r, p, v, u, q, r^, x, xlo and the
+# weights, writes r, p, v, u, q, x, xlo.)
 # The stencil build reads positions and masks (17 B) and writes FP64 + FP32
 # rows, Neumann weights, row scale and kind (206 B).
 SOLVE_BYTES_PER_DP_ITER = 140
@@ -558,7 +569,9 @@ def gpu_arm(args):
             per_unit = per_unit * units / n_launch
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": per_unit,
-                "kernel": name, "launches": n_launch, "avg_launch_ms": round(t_ms / n_launch, 3),
+                "kernel": ("bicg_persistent2 (two grid barriers per iteration)" if name == "bicg_persistent"
+                           else name),
+                "launches": n_launch, "avg_launch_ms": round(t_ms / n_launch, 3),
                 "algorithmic_bytes_per_launch": algo / n_launch, "algorithmic_bytes": unit_note,
                 "peak_source": f"{peak_src} hbm_gbs",
                 "kernel_share": {k: round(v[1] / total, 4) for k, v in ktimes.items()}}
@@ -1490,11 +1503,11 @@ def profile_solve(args):
         m = mask.cpu().numpy()
         rhs = torch.from_numpy(np.where(m == -1, pb.rhs, 0.0)).to(dev)
         bnd = torch.zeros_like(rhs)
-        _p, info = st.solve(rhs, bnd, tol=args.tol, mode=mcd.MIXED)
+        _p, info = st.solve(rhs, bnd, tol=args.tol, mode=mcd.MIXED, barriers=args.barriers)
         print(json.dumps({"iters": info["iters"], "fallback": info["fallback"], "dps": pb.mesh.N,
                           "rel_res": info["rel_res"], "support": args.support}), flush=True)
         return
-    run = CylinderRun(args.n, torch.device("cuda", 0), mcd, inputs, args.tol)
+    run = CylinderRun(args.n, torch.device("cuda", 0), mcd, inputs, args.tol, args.barriers, args.update_restart)
     info = run.step(mcd.MIXED)
     print(json.dumps({"iters": info["iters"], "fallback": info["fallback"], "dps": run.N,
                       "rel_res": info["rel_res"]}), flush=True)
@@ -1512,31 +1525,51 @@ def trace_solve(args):
     from paper_2404_17542_gb300 import build, inputs, mcd
     build.build()
     mcd.lib()
-    run = CylinderRun(args.n, torch.device("cuda", 0), mcd, inputs, args.tol)
+    run = CylinderRun(args.n, torch.device("cuda", 0), mcd, inputs, args.tol, args.barriers, args.update_restart)
     run.step(mcd.MIXED)
     mcd.trace_enable(True)
+    mcd.timing_enable(1)
     try:
         info = run.step(mcd.MIXED)
         ph, _end, _sm, start, bar = mcd.trace_read()
+        n_solve, solve_ms = mcd.timing_read(mcd.K_SOLVE)
     finally:
         mcd.trace_enable(False)
+        mcd.timing_enable(0)
     ph = ph.astype(np.int64)
     bar = bar.astype(np.int64)
-    rows = [r for r in range(4, 63) if (ph[r, :5] > 0).all() and ph[r + 1, 0] > 0]
+    # one grid barrier per iteration stamps slots 0-2 (start, phase done,
+    # reduced); two barriers stamp 0-4
+    one = not (ph[4:63, 3] > 0).any()
+    width = 3 if one else 5
+    rows = [r for r in range(4, 63) if (ph[r, :width] > 0).all() and ph[r + 1, 0] > 0]
     epochs = [e for e in range(10, 256) if (bar[e] > 0).all()]
 
     def med(vals):
         return round(float(np.median(vals)) / 1000.0, 3) if len(vals) else None
 
+    if one:
+        block0 = {"work": med([ph[r, 1] - ph[r, 0] for r in rows]),
+                  "barrier": med([ph[r, 2] - ph[r, 1] for r in rows])}
+    else:
+        block0 = {"ca_work": med([ph[r, 1] - ph[r, 0] for r in rows]),
+                  "ca_barrier": med([ph[r, 2] - ph[r, 1] for r in rows]),
+                  "b_work": med([ph[r, 3] - ph[r, 2] for r in rows]),
+                  "b_barrier": med([ph[r, 4] - ph[r, 3] for r in rows])}
     s = start[:2048].astype(np.int64)
     s = s[s > 0]
     print(json.dumps({
         "n": args.n, "iters": info["iters"], "fallback": info["fallback"],
+        "barriers_per_iteration": 1 if one else 2,
         "iteration_us": med([ph[r + 1, 0] - ph[r, 0] for r in rows]),
-        "block0_us": {"ca_work": med([ph[r, 1] - ph[r, 0] for r in rows]),
-                      "ca_barrier": med([ph[r, 2] - ph[r, 1] for r in rows]),
-                      "b_work": med([ph[r, 3] - ph[r, 2] for r in rows]),
-                      "b_barrier": med([ph[r, 4] - ph[r, 3] for r in rows])},
+        "iteration_us_p90": (round(float(np.percentile([ph[r + 1, 0] - ph[r, 0] for r in rows], 90)) / 1000.0, 3)
+                             if rows else None),
+        # the whole solve: persistent launches' time over all iterations
+        # (true-residual updates and restarts included)
+        "solve_us_per_iteration": round(solve_ms * 1000.0 / max(1, info["iters"]), 3),
+        "solve_launches": n_solve,
+        "updates": info["refinements"],
+        "block0_us": block0,
         "barrier_us": {"last_arrival_to_all_partials": med([bar[e, 2] - bar[e, 6] for e in epochs]),
                        "block0_reduction": med([bar[e, 3] - bar[e, 2] for e in epochs]),
                        "scalar_update": med([bar[e, 4] - bar[e, 3] for e in epochs]),

@@ -208,15 +208,22 @@ typedef struct mcd_net mcd_net;   /* learned warm start, declared below */
  *              stop or a breakdown), until a cycle diverges; from then on
  *              the solve restarts at every update, as with 1.
  * barriers     grid barriers per Bi-CGSTAB iteration of the persistent solve:
- *              2 (default; x, r update fused into the next p, v = A p phase,
- *              beta from the recurrence r^.s - omega r^.t) or 3 (textbook).
+ *              0 (default) or 2: two, the x, r update fused into the next
+ *              p, v = A p phase, beta from the recurrence r^.s - omega r^.t;
+ *              1: one where it applies (MCD_MIXED on a non-periodic 2D 3x3
+ *              mesh with n_x a multiple of 4 and at least 40 x 20 cells),
+ *              else two: each phase finishes iteration k and forms
+ *              p', v' = A p', q' = A v', u' = A r' of k+1, and one reduction
+ *              gives alpha, omega and beta, the last two as polynomials in
+ *              alpha of its dot products (slower than two barriers on this
+ *              GPU: more work per phase); 3: textbook.
  * net_dprev    with net: device float64 [N] or NULL, in and out: the
  *              increment the warm start reads (the pressure of the last
  *              step minus the one before); after a converged solve it
  *              holds this solve's increment, p(out) - p(in), for the next.
  * precond      NULL, or a network used as the preconditioner of the
- *              iterative refinement (MCD_MIXED, two-barrier persistent
- *              schedule only): every FP64 true-residual update that does not
+ *              iterative refinement (MCD_MIXED, one- or two-barrier
+ *              persistent schedule): every FP64 true-residual update that does not
  *              meet tol and restarts the FP32 recursion (the first update, a
  *              cycle dropped after diverging, an ||s|| stop or a breakdown;
  *              every update with update_restart = 1) begins a refinement

@@ -85,6 +85,7 @@ struct BArgs {
     const double *b;
     double *x64;
     void *x, *r, *rh, *p0, *p1, *v0, *v1, *s, *t;
+    float *xlo;               // MIXED: low word of the double-float correction (x, xlo)
     BScal *sc;
     double *acc;              // [3 slots][nsys][4] FP64 accumulators
     int *active;              // [2][nsys] work lists (system ids)
@@ -235,8 +236,8 @@ __device__ void tile_b(const BGeo &g, int64_t t, T *tile, const T *row, const T 
 }
 
 template <typename T, int R>
-__device__ void tile_c(const BGeo &g, int64_t t, T *x, T *r, const T *rhat, const T *p, const T *s, const T *tv,
-                       T alpha, T omega, int sconv, DotAcc<T> (&dot)[2]) {
+__device__ void tile_c(const BGeo &g, int64_t t, T *x, float *xlo, T *r, const T *rhat, const T *p, const T *s,
+                       const T *tv, T alpha, T omega, int sconv, DotAcc<T> (&dot)[2]) {
     const int tid = threadIdx.x;
     int x0, y0;
     bt_origin<R>(g, t, x0, y0);
@@ -248,6 +249,25 @@ __device__ void tile_c(const BGeo &g, int64_t t, T *x, T *r, const T *rhat, cons
         const T xv = __ldcg(x + k), pv = __ldcg(p + k), sv = __ldcg(s + k), tt = __ldcg(tv + k);
         const T hv = __ldcg(rhat + k);
         T rk;
+        if constexpr (sizeof(T) == 4) {
+            if (xlo) {
+                // the correction as a double-float pair: the increments are
+                // split exactly and added by TwoSum, so the fold adds an
+                // error of order eps^2 |x| rather than eps |x|
+                DF acc{xv, __ldcg(xlo + k)};
+                df_add_prod(acc, alpha, pv);
+                if (!sconv) df_add_prod(acc, omega, sv);
+                float hi, lo;
+                two_sum_f(acc.hi, acc.lo, hi, lo);
+                x[k] = hi;
+                xlo[k] = lo;
+                rk = sconv ? sv : sv - omega * tt;
+                r[k] = rk;
+                dot[0].add(hv, rk);
+                dot[1].add(rk, rk);
+                continue;
+            }
+        }
         if (sconv) {
             x[k] = xv + alpha * pv;
             rk = sv;
@@ -262,7 +282,7 @@ __device__ void tile_c(const BGeo &g, int64_t t, T *x, T *r, const T *rhat, cons
 }
 
 template <typename T, int R>
-__device__ void tile_fold(const BGeo &g, int64_t t, double *x64, T *x, bool discard) {
+__device__ void tile_fold(const BGeo &g, int64_t t, double *x64, T *x, float *xlo, bool discard) {
     const int tid = threadIdx.x;
     int x0, y0;
     bt_origin<R>(g, t, x0, y0);
@@ -271,7 +291,12 @@ __device__ void tile_fold(const BGeo &g, int64_t t, double *x64, T *x, bool disc
         int lx, ly;
         const int64_t k = bt_dp<R>(g, tid, q, x0, y0, lx, ly);
         if (k < 0) continue;
-        if (!discard) x64[k] += (double)__ldcg(x + k);
+        double add = (double)__ldcg(x + k);
+        if (xlo) {
+            add += (double)__ldcg(xlo + k);
+            xlo[k] = 0.0f;
+        }
+        if (!discard) x64[k] += add;
         x[k] = (T)0;
     }
 }
@@ -505,7 +530,8 @@ __global__ void __launch_bounds__(256) bicg_batch(const __grid_constant__ BArgs 
             } else if (mode == MODE_UPDATE && a.mixed) {
                 const bool discard = __ldcg(&c->discard) != 0;
                 for (int64_t t = t0; t < t1; ++t)
-                    tile_fold<T, R>(g, t, a.x64 + g.off, (T *)a.x + g.off, discard);
+                    tile_fold<T, R>(g, t, a.x64 + g.off, (T *)a.x + g.off, a.xlo ? a.xlo + g.off : nullptr,
+                                    discard);
             }
         });
         if (!barrier(a, epoch, [&](int th) {
@@ -626,7 +652,8 @@ __global__ void __launch_bounds__(256) bicg_batch(const __grid_constant__ BArgs 
                 const T *p_new = (const T *)(par ? a.p0 : a.p1) + g.off;
                 DotAcc<T> dot[2];
                 for (int64_t t = t0; t < t1; ++t)
-                    tile_c<T, R>(g, t, (T *)a.x + g.off, (T *)a.r + g.off, (const T *)a.rh + g.off, p_new,
+                    tile_c<T, R>(g, t, (T *)a.x + g.off, a.xlo ? a.xlo + g.off : nullptr, (T *)a.r + g.off,
+                                 (const T *)a.rh + g.off, p_new,
                                  (const T *)a.s + g.off, (const T *)a.t + g.off, alpha, omega, sconv, dot);
                 flush<T, 2>(dot, accC + (size_t)4 * sys);
             }
@@ -687,7 +714,7 @@ __global__ void __launch_bounds__(256) bicg_batch(const __grid_constant__ BArgs 
 // the FP32 correction is zeroed.
 __global__ void prep_kernel(int64_t N, const int8_t *__restrict__ kind, const double *__restrict__ rhs,
                             const double *__restrict__ bnd, double *__restrict__ b, double *__restrict__ p,
-                            float *__restrict__ x32) {
+                            float *__restrict__ x32, float *__restrict__ x32lo) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     const int8_t kd = kind[k];
@@ -698,6 +725,7 @@ __global__ void prep_kernel(int64_t N, const int8_t *__restrict__ kind, const do
     if (kd == KIND_DIRICHLET) p[k] = bk;
     else if (kd == KIND_VOID) p[k] = 0.0;
     if (x32) x32[k] = 0.0f;
+    if (x32lo) x32lo[k] = 0.0f;
 }
 
 // Scalars of every system reset to "true-residual update next", full work
@@ -778,7 +806,7 @@ struct mcd_batch {
     BGeo *bgeo_d = nullptr;
     int bgeo_rows = 0;            // tiling the bgeo table holds
     double *b = nullptr;
-    float *f[9] = {};             // x r rh p0 p1 v0 v1 s t (FP32)
+    float *f[10] = {};            // x r rh p0 p1 v0 v1 s t (FP32), xlo (low word of the correction)
     double *d[9] = {};            // the same in FP64 (FP64 mode; x unused)
     BScal *sc = nullptr;
     BScal *h_sc = nullptr;
@@ -864,7 +892,7 @@ mcd_status ensure_solver(mcd_batch *bt, int mode) {
         chk(cudaMallocHost(&bt->h_state, sizeof(BState)));
     }
     if (mode == MCD_MIXED && !bt->f[0])
-        for (int i = 0; i < 9; ++i) chk(cudaMalloc(&bt->f[i], N * sizeof(float)));
+        for (int i = 0; i < 10; ++i) chk(cudaMalloc(&bt->f[i], N * sizeof(float)));
     if (mode == MCD_FP64 && !bt->d[1])
         for (int i = 1; i < 9; ++i) chk(cudaMalloc(&bt->d[i], N * sizeof(double)));
     const int need = 4 * device_sms();   // largest grid any tiling launches
@@ -914,7 +942,9 @@ mcd_status make_launch(mcd_batch *bt, double *p, const mcd_solve_params *prm, La
         a.row = bt->row32;
         a.x = bt->f[0]; a.r = bt->f[1]; a.rh = bt->f[2]; a.p0 = bt->f[3]; a.p1 = bt->f[4];
         a.v0 = bt->f[5]; a.v1 = bt->f[6]; a.s = bt->f[7]; a.t = bt->f[8];
+        a.xlo = bt->f[9];
     } else {
+        a.xlo = nullptr;
         a.row = bt->row64;
         a.x = p; a.r = bt->d[1]; a.rh = bt->d[2]; a.p0 = bt->d[3]; a.p1 = bt->d[4];
         a.v0 = bt->d[5]; a.v1 = bt->d[6]; a.s = bt->d[7]; a.t = bt->d[8];
@@ -947,12 +977,13 @@ mcd_status enqueue_solve(mcd_batch *bt, const double *rhs, const double *bnd, do
     const int64_t N = bt->N;
     const unsigned eb = (unsigned)((N + 255) / 256);
     float *x32 = prm->mode == MCD_MIXED ? bt->f[0] : nullptr;
+    float *x32lo = prm->mode == MCD_MIXED ? bt->f[9] : nullptr;
     const int max_iter = prm->max_iter > 0 ? prm->max_iter : (1 << 30);
     if (capture) {
-        prep_kernel<<<eb, 256, 0, s>>>(N, bt->kind, rhs, bnd, bt->b, p, x32);
+        prep_kernel<<<eb, 256, 0, s>>>(N, bt->kind, rhs, bnd, bt->b, p, x32, x32lo);
         init_kernel<<<1, 256, 0, s>>>(L.args, max_iter, subset);
     } else {
-        MCD_KLAUNCH(MCD_K_OTHER, s, prep_kernel<<<eb, 256, 0, s>>>(N, bt->kind, rhs, bnd, bt->b, p, x32));
+        MCD_KLAUNCH(MCD_K_OTHER, s, prep_kernel<<<eb, 256, 0, s>>>(N, bt->kind, rhs, bnd, bt->b, p, x32, x32lo));
         MCD_KLAUNCH(MCD_K_OTHER, s, init_kernel<<<1, 256, 0, s>>>(L.args, max_iter, subset));
     }
     MCD_LAUNCH_CHECK();
@@ -1201,7 +1232,8 @@ extern "C" void mcd_batch_destroy(mcd_batch *bt) {
     cudaFree(bt->row64); cudaFree(bt->row32); cudaFree(bt->rscale); cudaFree(bt->kind); cudaFree(bt->bad);
     cudaFree(bt->off16); cudaFree(bt->spmv_err);
     cudaFree(bt->bgeo_d); cudaFree(bt->b);
-    for (int i = 0; i < 9; ++i) { cudaFree(bt->f[i]); cudaFree(bt->d[i]); }
+    for (int i = 0; i < 9; ++i) cudaFree(bt->d[i]);
+    for (int i = 0; i < 10; ++i) cudaFree(bt->f[i]);
     cudaFree(bt->sc); cudaFreeHost(bt->h_sc); cudaFree(bt->acc); cudaFree(bt->active); cudaFree(bt->prefix);
     cudaFree(bt->subset);
     cudaFree(bt->state); cudaFreeHost(bt->h_state); cudaFree(bt->bar);
@@ -1272,8 +1304,9 @@ extern "C" mcd_status mcd_batch_solve(mcd_batch *bt, const double *rhs_dev, cons
         // it touches only the Dirichlet and void entries of the guess)
         const int64_t N = bt->N;
         float *x32 = prm->mode == MCD_MIXED ? bt->f[0] : nullptr;
+        float *x32lo = prm->mode == MCD_MIXED ? bt->f[9] : nullptr;
         MCD_KLAUNCH(MCD_K_OTHER, stream, prep_kernel<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(
-                                             N, bt->kind, rhs_dev, bnd_dev, bt->b, p_dev, x32));
+                                             N, bt->kind, rhs_dev, bnd_dev, bt->b, p_dev, x32, x32lo));
         MCD_LAUNCH_CHECK();
         for (int i = 0; i < bt->nsys; ++i) {
             s = net_warm_start(prm->net, &bt->views[i], bt->b + bt->off[i], nullptr, p_dev + bt->off[i], nullptr,

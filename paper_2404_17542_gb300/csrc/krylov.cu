@@ -99,7 +99,8 @@ struct Workspace {
     float *fr = nullptr, *frh = nullptr, *fp[2] = {nullptr, nullptr}, *fv[2] = {nullptr, nullptr},
           *fs = nullptr, *ft = nullptr, *fd = nullptr;
     float *fdlo = nullptr;        // low part of the double-float correction (persistent MIXED)
-    double *partials = nullptr;  // [4][max(nblk, nblk1)]
+    float *fr1 = nullptr, *fu1 = nullptr, *fq1 = nullptr;   // one-barrier kernel: second r, u, q
+    double *partials = nullptr;  // [12][max(nblk, nblk1)]
     unsigned int *counter = nullptr;
     Scalars *sc = nullptr;
     Scalars *h_sc = nullptr;     // pinned host mirror
@@ -115,6 +116,7 @@ void free_workspace(mcd_stencils *st) {
     cudaFree(w->dv[0]); cudaFree(w->dv[1]); cudaFree(w->ds); cudaFree(w->dt);
     cudaFree(w->fr); cudaFree(w->frh); cudaFree(w->fp[0]); cudaFree(w->fp[1]);
     cudaFree(w->fv[0]); cudaFree(w->fv[1]); cudaFree(w->fs); cudaFree(w->ft); cudaFree(w->fd); cudaFree(w->fdlo);
+    cudaFree(w->fr1); cudaFree(w->fu1); cudaFree(w->fq1);
     cudaFree(w->partials); cudaFree(w->counter); cudaFree(w->sc); cudaFree(w->bar);
     cudaFreeHost(w->h_sc);
     delete w;
@@ -542,7 +544,7 @@ static mcd_status ensure_workspace(mcd_stencils *st, int mode) {
         auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
         chk(cudaMalloc(&w->b, N * sizeof(double)));
         chk(cudaMalloc(&w->r64, N * sizeof(double)));
-        chk(cudaMalloc(&w->partials, 5 * (size_t)w->pstride * sizeof(double)));
+        chk(cudaMalloc(&w->partials, 12 * (size_t)w->pstride * sizeof(double)));
         chk(cudaMalloc(&w->counter, sizeof(unsigned int)));
         chk(cudaMalloc(&w->sc, sizeof(Scalars)));
         chk(cudaMalloc(&w->bar, barrier_bytes(w->pstride)));
@@ -577,6 +579,11 @@ static mcd_status ensure_workspace(mcd_stencils *st, int mode) {
         chk(cudaMalloc(&w->ft, N * sizeof(float)));
         chk(cudaMalloc(&w->fd, N * sizeof(float)));
         chk(cudaMalloc(&w->fdlo, N * sizeof(float)));
+        if (st->geo.dim == 2) {
+            chk(cudaMalloc(&w->fr1, N * sizeof(float)));
+            chk(cudaMalloc(&w->fu1, N * sizeof(float)));
+            chk(cudaMalloc(&w->fq1, N * sizeof(float)));
+        }
         if (e == cudaSuccess) e = cudaMemset(w->frh, 0, N * sizeof(float));
     }
     if (e != cudaSuccess) {
@@ -854,7 +861,17 @@ struct PArgs {
         CUtensorMap halo[7];     // s, t, p0, p1, v0, v1, r as [n_y][n_x], box 40 x 18
         CUtensorMap point[3];    // r^, x, xlo, box 32 x 16
     } maps3;
+    // one grid barrier per iteration (bicg_persistent1; 2D 3x3 FP32 with maps3)
+    int one;
+    void *r1, *u0, *u1, *q0, *q1;   // second r buffer; u = A r and q~ = sigma A v, two of each
+    float q_scale, q_unscale;       // sigma = 2^k close to l0^2, and 1 / sigma (exact scalings)
+    struct {
+        CUtensorMap rows;        // [9][n_y][n_x], box 40 x 18 x 9 from (x0 - 4, y0 - 1)
+        CUtensorMap vec[10];     // r0, r1, p0, p1, v0, v1, u0, u1, q0, q1: box 40 x 20 from (x0 - 4, y0 - 2)
+    } maps1;
 };
+
+static_assert(sizeof(PArgs) <= 4096, "PArgs is passed as one kernel parameter block");
 
 __device__ __forceinline__ int tile_first(const PArgs &a, int block) {
     return (int)((int64_t)block * a.ta.ntiles / a.grid);
@@ -1438,11 +1455,12 @@ __device__ void phase_discard(const PArgs &a) {
 // stored in the recursion's precision; Neumann rows read 0 (interior block).
 // Dots ||r64||^2, ||b||^2, r^.r, r.r.
 template <int G, typename T>
-__device__ void phase_true_residual(const PArgs &a, DotAcc<double> (&d64)[2], DotAcc<T> (&dt)[2]) {
+__device__ void phase_true_residual(const PArgs &a, DotAcc<double> (&d64)[2], DotAcc<T> (&dt)[2],
+                                    T *r_out = nullptr) {
     using TL = Tile<G>;
     constexpr int S = Shape<G>::S;
     const Geo &g = a.ta.g;
-    T *r = (T *)a.r;
+    T *r = r_out ? r_out : (T *)a.r;
     const T *rhat = (const T *)a.rh;
     const int tid = threadIdx.x;
     const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
@@ -2273,6 +2291,110 @@ __device__ void phase_b2_staged(const PArgs &a, float *tile, int parb, float alp
     stage_drain(a, pp);
 }
 
+// The scalar step of a true-residual update (block 0, thread 0), from the
+// totals ||r64||^2, ||b||^2, r^.r, r.r (the last two in the recursion's
+// precision) of r = b - A64 x64: convergence, and whether the recursion goes
+// on with the replaced residual or restarts from it.
+template <typename T>
+__device__ void tr_last_update(Scalars *sc, const double *tot, double tol, int update_mode, int net_exit) {
+    sc->rr64 = tot[0];
+    sc->bb64 = tot[1];
+    sc->rr = tot[3];
+    sc->tol2 = tol * tol * tot[1];
+    sc->pending = 0;
+    if constexpr (sizeof(T) == 4) {
+        sc->tol2_d = df_from(sc->tol2);
+        sc->rr_d = df_from(tot[3]);
+    }
+    if (!isfinite(tot[0] + tot[1])) { sc->done = 4; return; }
+    if (tot[0] <= sc->tol2) { sc->done = 1; return; }
+    if (sc->max_hit) { sc->done = 2; return; }
+    sc->rr_last = tot[3];
+    sc->it_last = sc->iter;
+    sc->updates += 1;
+    // the recursion's scalars (kept as double-float pairs by the FP32
+    // kernels)
+    double rho_c = sc->rho, alpha_c = sc->alpha, omega_c = sc->omega;
+    if constexpr (sizeof(T) == 4) {
+        sc->rr_last_d = df_from(tot[3]);
+        rho_c = df_value(sc->rho_d);
+        alpha_c = df_value(sc->alpha_d);
+        omega_c = df_value(sc->omega_d);
+    }
+    const bool corrected = sc->net_fresh != 0 || sc->discard != 0;
+    const bool keep = update_mode == 2 && !sc->no_replace && !corrected && !sc->restart && !sc->s_conv &&
+                      rho_c != 0.0 && omega_c != 0.0;
+    // an update that restarts the recursion (the first, after a dropped
+    // cycle, an ||s|| stop or a breakdown; every update of the restarting
+    // schedule) begins a new refinement cycle: with a preconditioner network
+    // the host adds the network's correction of this residual first
+    // (done = 5) and relaunches with net_fresh set
+    if (net_exit && !sc->net_fresh && !keep) { sc->done = 5; return; }
+    sc->net_fresh = 0;
+    sc->discard = 0;
+    // residual replacement (update_mode 2): r now holds the true residual;
+    // the recursion continues from the last complete iteration with beta
+    // recomputed from rho' = r^.r, keeping p, v and r^.  Otherwise (update
+    // mode 1, the first update, after an ||s|| stop or a restart) the
+    // recursion restarts from r.
+    if (keep) {
+        const double beta = (tot[2] / rho_c) * (alpha_c / omega_c);
+        if (isfinite(beta)) {
+            sc->beta = beta;
+            sc->replace = 1;
+            if constexpr (sizeof(T) == 4)
+                sc->beta_f = (float)beta;   // alpha_f, omega_f stay those of the last iteration
+            else
+                publish(sc);
+            return;
+        }
+    }
+    sc->restart = 1;
+    sc->s_conv = 0;
+    sc->alpha = sc->beta = sc->omega = 0.0;
+    if constexpr (sizeof(T) == 4) sc->alpha_d = sc->omega_d = make_float2(0.0f, 0.0f);
+    publish(sc);
+}
+
+// True-residual (reliable) update of the persistent two- and one-barrier
+// kernels: fold the correction into x64 (or drop it after a diverged cycle),
+// r_out = b - A64 x64 in the recursion's precision, then tr_last_update.
+// False if a barrier wait gave up.
+template <int G, typename T>
+__device__ bool true_residual_update(const PArgs &a, unsigned &epoch, Scalars &ls, ScalarSnap<T> &snap, T *r_out) {
+    if (a.mixed) {
+        if (snap.discard)
+            phase_discard<G, T>(a);
+        else
+            phase_fold<G, T>(a);
+        DotAcc<double> none[1];
+        if (!grid_reduce<1>(a, epoch, none, [&](double *) {})) return false;
+    }
+    DotAcc<double> d64[2];
+    DotAcc<T> dt[2];
+    phase_true_residual<G, T>(a, d64, dt, r_out);
+    DotAcc<double> all[4];
+    all[0].v = d64[0].v;
+    all[1].v = d64[1].v;
+    if constexpr (sizeof(T) == 4) {
+        all[2].v = (double)dt[0].v.hi + (double)dt[0].v.lo;
+        all[3].v = (double)dt[1].v.hi + (double)dt[1].v.lo;
+    } else {
+        all[2].v = dt[0].v;
+        all[3].v = dt[1].v;
+    }
+    const double tol = a.tol;
+    const int update_mode = a.update_mode;
+    const int net_exit = a.net_exit;
+    if (!grid_reduce<4>(a, epoch, all, [&](double *tot) {
+            tr_last_update<T>(&ls, tot, tol, update_mode, net_exit);
+            store_scalars(a.sc, ls);
+        }))
+        return false;
+    take_scalars(a.sc, snap);
+    return true;
+}
+
 // Wide stencils ask for two blocks per SM explicitly (their accumulators
 // otherwise lead the register allocator to spill); a minimum of 0 leaves the
 // compact stencils as the compiler places them.
@@ -2324,95 +2446,8 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
         const T alpha0 = snap.alpha, omega0 = snap.omega, beta0 = snap.beta;
         if (done0 || perr0) goto finish;
         if (pend0) {
-            // ---- true residual (reliable) update: as in the three-barrier kernel
-            if (a.mixed) {
-                if (snap.discard)
-                    phase_discard<G, T>(a);
-                else
-                    phase_fold<G, T>(a);
-                DotAcc<double> none[1];
-                if (!grid_reduce<1>(a, epoch, none, [&](double *) {})) goto finish;
-            }
-            DotAcc<double> d64[2];
-            DotAcc<T> dt[2];
-            phase_true_residual<G, T>(a, d64, dt);
-            DotAcc<double> all[4];
-            all[0].v = d64[0].v;
-            all[1].v = d64[1].v;
-            if constexpr (sizeof(T) == 4) {
-                all[2].v = (double)dt[0].v.hi + (double)dt[0].v.lo;
-                all[3].v = (double)dt[1].v.hi + (double)dt[1].v.lo;
-            } else {
-                all[2].v = dt[0].v;
-                all[3].v = dt[1].v;
-            }
-            const double tol = a.tol;
-            const int update_mode = a.update_mode;
-            const int net_exit = a.net_exit;
-            auto tr_last = [&](double *tot) {
-                    sc->rr64 = tot[0];
-                    sc->bb64 = tot[1];
-                    sc->rr = tot[3];
-                    sc->tol2 = tol * tol * tot[1];
-                    sc->pending = 0;
-                    if constexpr (sizeof(T) == 4) {
-                        sc->tol2_d = df_from(sc->tol2);
-                        sc->rr_d = df_from(tot[3]);
-                    }
-                    if (!isfinite(tot[0] + tot[1])) { sc->done = 4; return; }
-                    if (tot[0] <= sc->tol2) { sc->done = 1; return; }
-                    if (sc->max_hit) { sc->done = 2; return; }
-                    sc->rr_last = tot[3];
-                    sc->it_last = sc->iter;
-                    sc->updates += 1;
-                    // the recursion's scalars (kept as double-float pairs by
-                    // the FP32 kernel)
-                    double rho_c = sc->rho, alpha_c = sc->alpha, omega_c = sc->omega;
-                    if constexpr (sizeof(T) == 4) {
-                        sc->rr_last_d = df_from(tot[3]);
-                        rho_c = df_value(sc->rho_d);
-                        alpha_c = df_value(sc->alpha_d);
-                        omega_c = df_value(sc->omega_d);
-                    }
-                    const bool corrected = sc->net_fresh != 0 || sc->discard != 0;
-                    const bool keep = update_mode == 2 && !sc->no_replace && !corrected && !sc->restart &&
-                                      !sc->s_conv && rho_c != 0.0 && omega_c != 0.0;
-                    // an update that restarts the recursion (the first, after a
-                    // dropped cycle, an ||s|| stop or a breakdown; every update
-                    // of the restarting schedule) begins a new refinement
-                    // cycle: with a preconditioner network the host adds the
-                    // network's correction of this residual first (done = 5)
-                    // and relaunches with net_fresh set
-                    if (net_exit && !sc->net_fresh && !keep) { sc->done = 5; return; }
-                    sc->net_fresh = 0;
-                    sc->discard = 0;
-                    // residual replacement (update_mode 2): r now holds the
-                    // true residual; the recursion continues from the last
-                    // complete iteration with beta recomputed from
-                    // rho' = r^.r, keeping p, v and r^.  Otherwise (update
-                    // mode 1, the first update, after an ||s|| stop or a
-                    // restart) the recursion restarts from r.
-                    if (keep) {
-                        const double beta = (tot[2] / rho_c) * (alpha_c / omega_c);
-                        if (isfinite(beta)) {
-                            sc->beta = beta;
-                            sc->replace = 1;
-                            if constexpr (sizeof(T) == 4)
-                                sc->beta_f = (float)beta;   // alpha_f, omega_f stay those of the last iteration
-                            else
-                                publish(sc);
-                            return;
-                        }
-                    }
-                    sc->restart = 1;
-                    sc->s_conv = 0;
-                    sc->alpha = sc->beta = sc->omega = 0.0;
-                    if constexpr (sizeof(T) == 4) sc->alpha_d = sc->omega_d = make_float2(0.0f, 0.0f);
-                    publish(sc);
-                };
-            if (!grid_reduce<4>(a, epoch, all, [&](double *tot) { tr_last(tot); store_scalars(a.sc, ls); }))
-                goto finish;
-            take_scalars(a.sc, snap);
+            // ---- true residual (reliable) update
+            if (!true_residual_update<G, T>(a, epoch, ls, snap, (T *)a.r)) goto finish;
             continue;
         }
         if (iters >= a.iter_budget) goto finish;
@@ -2633,6 +2668,367 @@ finish:
     }
 }
 
+// ---- one grid barrier per iteration (2D 3x3 FP32, operands staged by TMA) --
+// Bi-CGSTAB needs alpha before s = r - alpha v and t = A s, and omega
+// before r' = s - omega t: two reductions per iteration in its textbook
+// order.  Here each phase finishes iteration k and prepares iteration k+1
+// up to its reduction, with three stencils instead of two:
+//   x += alpha p + omega s,  r' = s - omega t     (s = r - alpha v, t = u - alpha q)
+//   p' = r' + beta (p - omega v),  v' = A p',  q' = A v',  u' = A r'.
+// t = A s = A r - alpha A v = u - alpha q holds for the stored u and q, so
+// the dot products that fix omega and the next rho are polynomials in alpha
+// of dot products of r', v', u', q', r^ from the same phase:
+//   r^.v', r^.r', r'.r', u'.r', u'.v' + q'.r', q'.v', u'.u', u'.q', q'.q',
+//   r^.u', r^.q'
+// give alpha = r^.r' / r^.v' and, with s = r' - alpha v', t = u' - alpha q',
+//   t.s = u'.r' - alpha (u'.v' + q'.r') + alpha^2 q'.v',
+//   t.t = u'.u' - 2 alpha u'.q' + alpha^2 q'.q',
+//   rho'' = r^.s - omega r^.t,
+// so one reduction per iteration yields alpha, omega and beta.  alpha and
+// the residual tests use direct dot products; omega and beta come from the
+// polynomials, evaluated in double-float.  q' = A A p' carries the square of
+// the rows' O(1 / l0^2) scale, and q'.q' would leave the FP32 range on fine
+// meshes: q~ = sigma q' is stored instead, sigma = 2^k close to l0^2, and
+// alpha~ = alpha / sigma multiplies it (both scalings exact), so
+// t = u - alpha~ q~ and
+//   t.t = u'.u' - 2 alpha~ u'.q~ + alpha~^2 q~.q~.  The phase needs p' two cells
+// beyond the tile (v' one beyond, q' on it): each tile is staged with a
+// two-cell halo of r, p, v, u, q and a one-cell halo of the rows.
+struct Stage1 {
+    static constexpr int TX = 32, TY = 16;
+    static constexpr int WX = 40, WY = 18;    // rows box, from (x0 - 4, y0 - 1)
+    static constexpr int HX = 40, HY = 20;    // vector boxes, from (x0 - 4, y0 - 2)
+    static constexpr int WS = WX * WY;        // slot stride of the rows box
+    static constexpr unsigned W_BYTES = 9u * WX * WY * 4u;   // 25920
+    static constexpr unsigned W_PAD = 26112u;                 // 128-byte multiple
+    static constexpr unsigned H_BYTES = HX * HY * 4u;         // 3200 (25 x 128)
+    static constexpr unsigned P_BYTES = TX * TY * 4u;         // 2048
+    static constexpr unsigned BYTES = W_PAD + 5u * H_BYTES + 3u * P_BYTES;
+    static constexpr int NB = 2;
+    static constexpr unsigned halo_off(int q) { return W_PAD + (unsigned)q * H_BYTES; }
+    static constexpr unsigned point_off(int q) { return W_PAD + 5u * H_BYTES + (unsigned)q * P_BYTES; }
+};
+static_assert(Tile<2>::X == Stage1::TX && Tile<2>::Y == Stage1::TY, "stage boxes are one 2D tile");
+static_assert(Stage1::BYTES % 128 == 0 && Stage1::W_PAD >= Stage1::W_BYTES, "128-byte aligned stage buffers");
+enum { B1_R = 0, B1_P = 1, B1_V = 2, B1_U = 3, B1_Q = 4 };
+enum { ONE_NORMAL = 0, ONE_REPLACE = 1, ONE_RESTART = 2 };
+
+// Copies of one tile for a phase of mode `mode` reading buffer pair `par`:
+// normal r, p, v, u, q halos and r^, x, xlo; replacement (r holds the true
+// residual) r, p, v and r^; restart r alone.
+__device__ __forceinline__ unsigned stage1_tx(int mode) {
+    return Stage1::W_BYTES + (mode == ONE_NORMAL ? 5u * Stage1::H_BYTES + 3u * Stage1::P_BYTES
+                              : mode == ONE_REPLACE ? 3u * Stage1::H_BYTES + Stage1::P_BYTES
+                                                    : Stage1::H_BYTES);
+}
+
+__device__ __forceinline__ void stage1_issue(const PArgs &a, RowPipe<float> &pp, int b, int tl, int mode, int par) {
+    pp.outstanding |= 1u << b;
+    int x0, y0, z0;
+    tile_origin<2>(a.ta, tl, x0, y0, z0);
+    const uint32_t mb = smem_addr(pp.mbar + b);
+    const uint32_t dst = smem_addr(pp.buf) + (uint32_t)b * Stage1::BYTES;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads and writes of the buffer
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(stage1_tx(mode)) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(dst), "l"(reinterpret_cast<uint64_t>(&a.maps1.rows)), "r"(x0 - 4), "r"(y0 - 1), "r"(0), "r"(mb)
+        : "memory");
+    const int hx = x0 - 4, hy = y0 - 2;
+    tma_2d(dst + Stage1::halo_off(B1_R), &a.maps1.vec[0 + par], hx, hy, mb);
+    if (mode == ONE_RESTART) return;
+    tma_2d(dst + Stage1::halo_off(B1_P), &a.maps1.vec[2 + par], hx, hy, mb);
+    tma_2d(dst + Stage1::halo_off(B1_V), &a.maps1.vec[4 + par], hx, hy, mb);
+    tma_2d(dst + Stage1::point_off(PT_RH), &a.maps3.point[PT_RH], x0, y0, mb);
+    if (mode == ONE_REPLACE) return;
+    tma_2d(dst + Stage1::halo_off(B1_U), &a.maps1.vec[6 + par], hx, hy, mb);
+    tma_2d(dst + Stage1::halo_off(B1_Q), &a.maps1.vec[8 + par], hx, hy, mb);
+    tma_2d(dst + Stage1::point_off(PT_X), &a.maps3.point[PT_X], x0, y0, mb);
+    tma_2d(dst + Stage1::point_off(PT_XLO), &a.maps3.point[PT_XLO], x0, y0, mb);
+}
+
+// (A y)_k of the FP32 difference-form row whose weights sit in the staged
+// rows box at wi and y in a vector box (row stride 40) at yi: the
+// compensated sum of stencil_apply, term for term in the same order.
+__device__ __forceinline__ float box_stencil(const float *W, int wi, const float *Y, int yi) {
+    const float yk = Y[yi];
+    float hi = W[4 * Stage1::WS + wi] * yk, lo = 0.0f;   // centre weight is 0 or 1: exact
+#pragma unroll
+    for (int s = 0; s < 9; ++s) {
+        if (s == 4) continue;
+        const int o = (s % 3 - 1) + Stage1::HX * (s / 3 - 1);
+        const float w = W[s * Stage1::WS + wi];
+        const float d = __fsub_rn(Y[yi + o], yk);
+        const float p = __fmul_rn(w, d);
+        const float pe = __fmaf_rn(w, d, -p);
+        float e;
+        two_sum(hi, p, hi, e);
+        lo = __fadd_rn(lo, __fadd_rn(e, pe));
+    }
+    return __fadd_rn(hi, lo);
+}
+
+// One phase of the one-barrier schedule over the block's tiles.  Reads the
+// buffers of parity par, writes those of par ^ 1 (r', p', v', u', q'; r^ on
+// a restart) and the correction x, xlo.  Dot products as listed above.
+__device__ void phase_one(const PArgs &a, int par, int mode, float alpha, float omega, float beta,
+                          DotAcc<float> (&dot)[11], RowPipe<float> &pp) {
+    const Geo &g = a.ta.g;
+    const int n0 = g.n[0], n1 = g.n[1];
+    const int np = par ^ 1;
+    float *x = (float *)a.x;
+    float *r_new = (float *)(np ? a.r1 : a.r);
+    float *p_new = (float *)(np ? a.p1 : a.p0);
+    float *v_new = (float *)(np ? a.v1 : a.v0);
+    float *u_new = (float *)(np ? a.u1 : a.u0);
+    float *q_new = (float *)(np ? a.q1 : a.q0);
+    float *rh_out = (float *)a.rh;
+    const int8_t *kind = a.ta.kind;
+    const float qs = a.q_scale, qu = a.q_unscale;
+    const float alpha_q = alpha * qu;   // exact: qu is a power of two
+    const int tid = threadIdx.x;
+    const int tb = tile_first(a, blockIdx.x), te = tile_first(a, blockIdx.x + 1);
+    const int total = te - tb;
+    if (tid == 0 && !pp.failed)
+        for (int i = 0; i < Stage1::NB && i < total; ++i) stage1_issue(a, pp, i, tb + i, mode, par);
+    for (int i = 0; i < total; ++i) {
+        const int b = i % Stage1::NB;
+        stage_wait(a, pp, b);
+        unsigned char *st = reinterpret_cast<unsigned char *>(pp.buf) + (size_t)b * Stage1::BYTES;
+        const float *W = reinterpret_cast<const float *>(st);
+        float *R = reinterpret_cast<float *>(st + Stage1::halo_off(B1_R));
+        float *P = reinterpret_cast<float *>(st + Stage1::halo_off(B1_P));
+        float *V = reinterpret_cast<float *>(st + Stage1::halo_off(B1_V));
+        const float *U = reinterpret_cast<const float *>(st + Stage1::halo_off(B1_U));
+        const float *Q = reinterpret_cast<const float *>(st + Stage1::halo_off(B1_Q));
+        const float *RH = reinterpret_cast<const float *>(st + Stage1::point_off(PT_RH));
+        const float *X = reinterpret_cast<const float *>(st + Stage1::point_off(PT_X));
+        const float *XL = reinterpret_cast<const float *>(st + Stage1::point_off(PT_XLO));
+        int x0, y0, z0;
+        tile_origin<2>(a.ta, tb + i, x0, y0, z0);
+        // (1) r' and p' on the tile and two rings of halo (in place); the
+        // tile's correction, r' and p'.  Cells past the mesh hold zeros.
+        for (int h = tid; h < 36 * 20; h += 256) {
+            const int hy = h / 36, hx = h - hy * 36;
+            const int bi = hy * Stage1::HX + hx + 2;
+            const float rk = R[bi];
+            float rn = rk, pn = rk, sk = 0.0f, pk = 0.0f;
+            if (mode != ONE_RESTART) {
+                const float vk = V[bi];
+                pk = P[bi];
+                if (mode == ONE_NORMAL) {
+                    sk = __fmaf_rn(-alpha, vk, rk);
+                    const float tk = __fmaf_rn(-alpha_q, Q[bi], U[bi]);
+                    rn = __fmaf_rn(-omega, tk, sk);
+                }
+                pn = __fmaf_rn(beta, __fmaf_rn(-omega, vk, pk), rn);
+            }
+            const int lx = hx - 2, ly = hy - 2;
+            if (lx >= 0 && lx < Stage1::TX && ly >= 0 && ly < Stage1::TY && x0 + lx < n0 && y0 + ly < n1) {
+                const int64_t k = (int64_t)(x0 + lx) + (int64_t)n0 * (y0 + ly);
+                const int pi = ly * Stage1::TX + lx;
+                if (mode == ONE_NORMAL) add_correction(a.xlo, x, k, X[pi], XL[pi], alpha, pk, omega, sk);
+                r_new[k] = rn;
+                p_new[k] = pn;
+                if (mode == ONE_RESTART) rh_out[k] = rn;
+            }
+            R[bi] = rn;
+            P[bi] = pn;
+        }
+        __syncthreads();
+        // (2) v' = A p' on the tile and one ring of halo (into the v box)
+        for (int h = tid; h < 34 * 18; h += 256) {
+            const int hy = h / 34, hx = h - hy * 34;
+            const int bi = (hy + 1) * Stage1::HX + hx + 3;
+            const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+            float vn = 0.0f;
+            if (gx >= 0 && gx < n0 && gy >= 0 && gy < n1) {
+                const int64_t k = (int64_t)gx + (int64_t)n0 * gy;
+                vn = (kind && kind[k] == KIND_NEUMANN) ? P[bi] : box_stencil(W, hy * Stage1::WX + hx + 3, P, bi);
+            }
+            V[bi] = vn;
+        }
+        __syncthreads();
+        // (3) the tile: q' = A v', u' = A r', stores and dot products
+#pragma unroll
+        for (int c0 = 0; c0 < Stage1::TX * Stage1::TY; c0 += 256) {
+            const int c = c0 + tid;
+            const int lx = c % Stage1::TX, ly = c / Stage1::TX;
+            if (x0 + lx >= n0 || y0 + ly >= n1) continue;
+            const int64_t k = (int64_t)(x0 + lx) + (int64_t)n0 * (y0 + ly);
+            const int bi = (ly + 2) * Stage1::HX + lx + 4;
+            const int wi = (ly + 1) * Stage1::WX + lx + 4;
+            const float vk = V[bi], rk = R[bi];
+            const bool neu = kind && kind[k] == KIND_NEUMANN;
+            const float qk = qs * (neu ? vk : box_stencil(W, wi, V, bi));   // q~ = sigma A v'
+            const float uk = (mode == ONE_RESTART || neu) ? (mode == ONE_RESTART ? vk : rk) : box_stencil(W, wi, R, bi);
+            v_new[k] = vk;
+            q_new[k] = qk;
+            u_new[k] = uk;
+            const float rh = (mode == ONE_RESTART) ? rk : RH[ly * Stage1::TX + lx];
+            dot[0].add(rh, vk);
+            dot[1].add(rh, rk);
+            dot[2].add(rk, rk);
+            dot[3].add(uk, rk);
+            dot[4].add(uk, vk);
+            dot[4].add(qk * qu, rk);   // q'.r' itself: its size is that of u'.v'
+            dot[5].add(qk, vk);
+            dot[6].add(uk, uk);
+            dot[7].add(uk, qk);
+            dot[8].add(qk, qk);
+            dot[9].add(rh, uk);
+            dot[10].add(rh, qk);
+        }
+        __syncthreads();   // stage b is read: refill it
+        if (tid == 0 && !pp.failed && i + Stage1::NB < total) stage1_issue(a, pp, b, tb + i + Stage1::NB, mode, par);
+    }
+    stage_drain(a, pp);
+}
+
+__global__ void __launch_bounds__(256, 2) bicg_persistent1(const __grid_constant__ PArgs a) {
+    extern __shared__ __align__(128) unsigned char pipe_smem[];
+    __shared__ __align__(8) uint64_t pipe_mbar[Stage1::NB];
+    RowPipe<float> pp;
+    pp.buf = reinterpret_cast<float *>(pipe_smem);
+    pp.mbar = pipe_mbar;
+    pp.parity = 0;
+    pp.failed = false;
+    pp.outstanding = 0;
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < Stage1::NB; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(pipe_mbar + b)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // block 0 updates its shared-memory copy of the scalars, as in
+    // bicg_persistent2
+    __shared__ Scalars ls;
+    if (threadIdx.x == 0) ls = *a.sc;
+    Scalars *sc = &ls;
+    int iters = 0;
+    unsigned epoch = 0;
+    __shared__ ScalarSnap<float> snap;
+    take_scalars(a.sc, snap);
+    for (;;) {
+        if (snap.done || snap.perr) goto finish;
+        const int par = snap.par;
+        if (snap.pend) {
+            // true residual into the r buffer the next phase reads
+            if (!true_residual_update<2, float>(a, epoch, ls, snap, (float *)(par ? a.r1 : a.r))) goto finish;
+            continue;
+        }
+        if (iters >= a.iter_budget) goto finish;
+        const int it = iters;
+        ++iters;
+        stamp(a, it, 0);
+        stamp_block_start(a, it);
+        const int mode = snap.restart ? ONE_RESTART : (snap.replace ? ONE_REPLACE : ONE_NORMAL);
+        DotAcc<float> dot[11];
+        phase_one(a, par, mode, snap.alpha, snap.omega, snap.beta, dot, pp);
+        stamp(a, it, 1);
+        stamp_block(a, it);
+        const int stall = a.stall;
+        const float eps = (float)a.eps_breakdown;
+        const float update2 = (float)a.update2;
+        const int update_mode = a.update_mode;
+        const float q_unscale = a.q_unscale;
+        auto one_last = [&](const DF *raw) {
+            DF t[11];
+#pragma unroll
+            for (int q = 0; q < 11; ++q) t[q] = df_norm(raw[q]);
+            const DF rv = t[0], rho = t[1], rr = t[2];
+            sc->rv_d = df_pack(rv);
+            sc->rr_d = df_pack(rr);
+            sc->replace = 0;
+            // a normal phase completes an iteration (x and r'); a replaced
+            // or restarted one only rebuilds the directions
+            if (mode == ONE_NORMAL) sc->iter += 1;
+            bool fin = true;
+#pragma unroll
+            for (int q = 0; q < 11; ++q) fin = fin && isfinite(t[q].hi);
+            if (!fin) { sc->diverged = 5; sc->done = 4; return; }
+            if (mode == ONE_RESTART) {
+                sc->rhat2_d = df_pack(rr);
+            } else {
+                // the tests of bicg_persistent2 on r' (x is up to date: a
+                // true-residual update may follow at once)
+                const float rrf = rr.hi, last = sc->rr_last_d.x;
+                if (rrf <= sc->tol2_d.x) { sc->pending = 1; return; }
+                if (sc->iter >= sc->max_iter) { sc->max_hit = 1; sc->pending = 1; return; }
+                if (rrf <= update2 * last) { sc->pending = 1; return; }
+                const bool replacing = update_mode == 2 && !sc->no_replace;
+                if (rrf > (replacing ? 1e4f : 1e8f) * last) {
+                    sc->divergences += 1;
+                    if (!replacing) { sc->diverged = 1; sc->done = 3; return; }
+                    sc->discard = 1;
+                    sc->no_replace = 1;
+                    sc->pending = 1;
+                    return;
+                }
+                if (sc->iter - sc->it_last >= stall) { sc->pending = 1; return; }
+                if (fabsf(rho.hi) <= eps * sqrtf(sc->rhat2_d.x) * sqrtf(rrf)) {
+                    sc->restarts += 1;
+                    if (sc->restarts > 1000) { sc->diverged = 2; sc->done = 3; return; }
+                    sc->restart = 1;
+                    sc->parity ^= 1;   // restart from the r' this phase wrote
+                    return;
+                }
+            }
+            sc->restart = 0;
+            sc->parity ^= 1;
+            const DF alpha = df_div(rho, rv);
+            if (!isfinite(alpha.hi) || alpha.hi == 0.0f) { sc->diverged = 3; sc->done = 3; return; }
+            // alpha~ = alpha / sigma: t[5], t[7], t[8], t[10] hold dot
+            // products with q~ = sigma q'
+            const DF alq = DF{alpha.hi * q_unscale, alpha.lo * q_unscale};
+            const DF ts = df_norm(df_add(df_sub(t[3], df_mul(alpha, t[4])), df_mul(alpha, df_mul(alq, t[5]))));
+            const DF tt = df_norm(df_add(df_sub(t[6], df_mul(DF{2.0f * alq.hi, 2.0f * alq.lo}, t[7])),
+                                         df_mul(df_mul(alq, alq), t[8])));
+            sc->rho_d = df_pack(rho);
+            sc->alpha_d = df_pack(alpha);
+            sc->alpha_f = alpha.hi;
+            sc->ts_d = df_pack(ts);
+            sc->tt_d = df_pack(tt);
+            if (!(tt.hi > 0.0f)) {
+                // t = A s vanishes to rounding, so s does: the next phase
+                // takes r'' = s and the residual tests follow
+                sc->omega_d = make_float2(0.0f, 0.0f);
+                sc->omega_f = 0.0f;
+                sc->beta_f = 0.0f;
+                return;
+            }
+            const DF omega = df_div(ts, tt);
+            const DF rs = df_sub(rho, df_mul(alpha, rv));        // r^.s
+            const DF rt = df_sub(t[9], df_mul(alq, t[10]));      // r^.t
+            const DF rho_next = df_sub(rs, df_mul(omega, rt));
+            const DF beta = df_mul(df_div(rho_next, rho), df_div(alpha, omega));
+            sc->omega_d = df_pack(omega);
+            sc->omega_f = omega.hi;
+            sc->beta_f = beta.hi;
+        };
+        if (!grid_reduce_df<11>(a, epoch, dot, [&](const DF *tot) {
+                one_last(tot);
+                store_step_scalars<float>(a.sc, ls);
+            }))
+            goto finish;
+        take_scalars(a.sc, snap);
+        stamp(a, it, 2);
+    }
+finish:
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ls.rho = df_value(ls.rho_d);
+        ls.alpha = df_value(ls.alpha_d);
+        ls.omega = df_value(ls.omega_d);
+        ls.rv = df_value(ls.rv_d);
+        ls.rr = df_value(ls.rr_d);
+        ls.rhat2 = df_value(ls.rhat2_d);
+        ls.ts = df_value(ls.ts_d);
+        ls.tt = df_value(ls.tt_d);
+        ls.ss = df_value(ls.ss_d);
+        store_scalars(a.sc, ls);
+    }
+}
+
 // Grid of the persistent launch: every resident slot (at most one block per
 // tile).
 // Dynamic shared memory of the two-barrier kernel: the TMA row buffers of a
@@ -2757,6 +3153,67 @@ static bool encode_stage_maps(const Geo &g, const float *row, const void *const 
     return true;
 }
 
+// Tensor maps of the one-barrier kernel: the rows as [9][n_y][n_x] with a
+// 40 x 18 x 9 box (the tile and one ring of halo, from x0 - 4 so that the
+// copy starts on a 16-byte boundary) and the ten vectors with a 40 x 20 box
+// (two rings).  Needs what encode_stage_maps needs and a mesh of at least
+// 40 x 20 cells.
+static bool encode_one_maps(const Geo &g, const float *row, const void *const *vec, PArgs &a) {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    if (!fn || g.dim != 2 || g.per[0] || g.per[1] || g.n[0] % 4 != 0) return false;
+    if (g.n[0] < Stage1::HX || g.n[1] < Stage1::HY) return false;
+    const cuuint64_t nx = (cuuint64_t)g.n[0], ny = (cuuint64_t)g.n[1];
+    const cuuint32_t ones[3] = {1, 1, 1};
+    auto aligned = [](const void *p) { return p && ((uintptr_t)p % 16) == 0; };
+    if (!aligned(row)) return false;
+    {
+        const cuuint64_t dims[3] = {nx, ny, 9};
+        const cuuint64_t str[2] = {nx * 4, nx * ny * 4};
+        const cuuint32_t box[3] = {(cuuint32_t)Stage1::WX, (cuuint32_t)Stage1::WY, 9};
+        if (fn(&a.maps1.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(row), dims, str, box, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    const cuuint64_t dims[2] = {nx, ny};
+    const cuuint64_t str[1] = {nx * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)Stage1::HX, (cuuint32_t)Stage1::HY};
+    for (int q = 0; q < 10; ++q) {
+        if (!aligned(vec[q])) return false;
+        if (fn(&a.maps1.vec[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(vec[q]), dims, str, box, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
+// Grid of the one-barrier kernel: every resident slot (at most one block
+// per tile).
+static int persistent_grid_one(int ntiles) {
+    static int occ = 0;
+    if (!occ) {
+        const size_t dyn = (size_t)Stage1::NB * Stage1::BYTES;
+        cudaFuncSetAttribute(bicg_persistent1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, bicg_persistent1, 256, dyn) != cudaSuccess ||
+            blocks < 1)
+            blocks = 1;
+        occ = blocks;
+    }
+    return std::min(ntiles, std::max(1, occ * sm_count()));
+}
+
 // Run the whole solve in persistent launches (each bounded by an iteration
 // budget and the barrier spin limit).  On return w->h_sc holds the final
 // scalars.  x64 is the FP64 solution; in FP64 mode it is also the iterate.
@@ -2789,9 +3246,27 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
         a.tma3 = encode_stage_maps(g, st->row32, halo, point, a) ? 1 : 0;
     }
     const bool staged = a.tma_rows != 0 || a.tma3 != 0;
-    const size_t dyn_smem = two ? pipe_smem_bytes<G, T>(staged) : 0;
-    const int grid = two ? persistent_grid<G, T, 2>(a.ta.ntiles, staged)
-                         : persistent_grid<G, T, 3>(a.ta.ntiles, false);
+    // one grid barrier per iteration on request (barriers = 1) where the
+    // staged 2D 3x3 FP32 phases run.  Not the default: its phase does more
+    // work per tile than the two phases it replaces (three stencils and a
+    // deeper halo), and on the 1024^2 cylinder an iteration took 56.6 us
+    // against 52.0 us for the two-barrier schedule on the same GPU
+    a.one = 0;
+    if (G == 2 && mixed && a.tma3 && prm->barriers == 1 && w->fr1) {
+        const void *vec[10] = {w->fr, w->fr1, w->fp[0], w->fp[1], w->fv[0], w->fv[1], w->fs, w->fu1, w->ft, w->fq1};
+        a.one = encode_one_maps(g, st->row32, vec, a) ? 1 : 0;
+    }
+    a.q_scale = ldexpf(1.0f, (int)std::lround(std::log2(g.l0 * g.l0)));
+    a.q_unscale = 1.0f / a.q_scale;
+    a.r1 = w->fr1;
+    a.u0 = w->fs;
+    a.u1 = w->fu1;
+    a.q0 = w->ft;
+    a.q1 = w->fq1;
+    const size_t dyn_smem = a.one ? (size_t)Stage1::NB * Stage1::BYTES : two ? pipe_smem_bytes<G, T>(staged) : 0;
+    const int grid = a.one ? persistent_grid_one(a.ta.ntiles)
+                     : two ? persistent_grid<G, T, 2>(a.ta.ntiles, staged)
+                           : persistent_grid<G, T, 3>(a.ta.ntiles, false);
     a.grid = grid;
     a.row64 = st->row64;
     a.b = w->b;
@@ -2837,7 +3312,9 @@ static mcd_status run_persistent(const mcd_stencils *st, double *x64, const mcd_
         MCD_CUDA_TRY(cudaMemsetAsync(w->bar, 0, bar_bytes, stream));
         {
             KTimer kt(MCD_K_SOLVE, stream);
-            const void *kern = two ? (const void *)bicg_persistent2<G, T> : (const void *)bicg_persistent<G, T>;
+            const void *kern = a.one ? (const void *)bicg_persistent1
+                               : two ? (const void *)bicg_persistent2<G, T>
+                                     : (const void *)bicg_persistent<G, T>;
             MCD_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(256), args, dyn_smem, stream));
         }
         mcd_status s = read_scalars(w, stream);
@@ -3048,7 +3525,7 @@ extern "C" mcd_status mcd_solve_pressure(const mcd_stencils *st, const double *r
     MCD_CHECK_ARG(prm->mode != MCD_MIXED || (prm->inner_tol > 0.0 && prm->inner_tol < 1.0),
                   "inner_tol must be in (0, 1)");
     MCD_CHECK_ARG(!prm->precond || (prm->mode == MCD_MIXED && prm->barriers != 3 && prm->check_every >= 0),
-                  "a preconditioner network needs a MIXED solve on the two-barrier persistent schedule");
+                  "a preconditioner network needs a MIXED solve on the one- or two-barrier persistent schedule");
     mcd_status s = mcd_stencils_check(st, nullptr, stream);
     if (s != MCD_OK) return s;
     s = ensure_workspace(const_cast<mcd_stencils *>(st), prm->mode);

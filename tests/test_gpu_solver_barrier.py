@@ -1,8 +1,12 @@
 """GPU tests of the persistent solver's grid barriers (Sec. 3.3 solve).
 
-- Both schedules (two barriers per iteration, the default, and three)
-  match the oracle's direct solve, in FP64 and mixed mode, within the
-  parity tests' tolerances.
+- Every schedule matches the oracle's direct solve, in FP64 and mixed mode,
+  within the parity tests' tolerances: two grid barriers per iteration (the
+  default), one (mixed, non-periodic 2D 3x3 meshes) and three.  The
+  one-barrier schedule is Bi-CGSTAB with its reductions merged (omega and
+  beta from dot-product polynomials in alpha, t from the recurrence
+  u - alpha q); in FP32 those recurrences round differently, and its
+  iteration count stays within 25 % of the two-barrier count.
 - Results are deterministic.  Block 0 adds the blocks' partial sums in
   block order, so two solves of the same system give bit-identical fields
   and iteration counts.
@@ -62,7 +66,8 @@ def stencils(mcd, pb):
     return mcd.Stencils(pb.mesh, dev(pb.pos.ravel()), dev(pb.mask), want_derivs=False)
 
 
-SCHEDULES = [(0, 0), (1, 0), (0, 3), (1, 3)]   # (FP64 / mixed, default two-barrier / three-barrier)
+# (FP64 / mixed, barriers: 0 default (two), 1 (mixed: one), 3)
+SCHEDULES = [(0, 0), (1, 0), (1, 1), (0, 3), (1, 3)]
 
 
 @pytest.mark.parametrize("mode,barriers", SCHEDULES)
@@ -96,7 +101,7 @@ def test_barrier_trace_is_causally_ordered(mcd, large):
         mcd.trace_enable(False)
     bar = bar.astype(np.int64)
     epochs = [e for e in range(1, 256) if (bar[e] > 0).all()]
-    assert len(epochs) >= min(100, 2 * info["iters"])
+    assert len(epochs) >= min(100, info["iters"])
     for e in epochs:
         t = bar[e]
         assert t[0] <= t[1] <= t[2] <= t[3] <= t[4] <= t[5], (e, t)
@@ -143,3 +148,28 @@ def test_staged_operands_match_direct_loads(mcd, shape):
         x = solve.direct_solve(A, b)
         got = p1.cpu().numpy()
         assert np.linalg.norm(got - x) <= 1e-6 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("shape", [(1000, 700), (404, 397)])
+def test_one_barrier_schedule(mcd, shape):
+    """The one-barrier schedule against the two-barrier default on the same
+    system: both meet tol and the oracle, and the iteration counts agree
+    within 25 % (4667 against 4003 at 1000 x 700).  Repeat solves are
+    bit-identical.  1000 x 700: blocks own several tiles; 404 x 397: ragged
+    tiles, where the two-cell halo copies reach past the mesh."""
+    pb = inputs.manufactured_box(shape, 2, seed=9)
+    st = mcd.Stencils(pb.mesh, dev(pb.pos.ravel()), dev(pb.mask), precision=mcd.MIXED)
+    p1, i1 = st.solve(dev(pb.rhs), dev(pb.bnd), tol=1e-10, mode=mcd.MIXED, barriers=1)
+    p1b, i1b = st.solve(dev(pb.rhs), dev(pb.bnd), tol=1e-10, mode=mcd.MIXED, barriers=1)
+    p2, i2 = st.solve(dev(pb.rhs), dev(pb.bnd), tol=1e-10, mode=mcd.MIXED)
+    assert torch.equal(p1, p1b) and i1["iters"] == i1b["iters"]
+    assert i1["rel_res"] <= 1e-10 and i2["rel_res"] <= 1e-10
+    assert i1["fallback"] == 0
+    assert abs(i1["iters"] - i2["iters"]) <= 0.25 * i2["iters"], (i1["iters"], i2["iters"])
+    assert np.linalg.norm((p1 - p2).cpu().numpy()) <= 1e-6 * np.linalg.norm(p2.cpu().numpy())
+    if shape[0] * shape[1] <= 404 * 397:
+        W = mls.build_weights(pb.mesh, pb.pos, pb.mask)
+        A = solve.assemble(pb.mesh, W["row"])
+        b = solve.form_rhs(pb.mesh, W["kind"], W["QL"], pb.rhs, pb.bnd, W["rscale"])
+        x = solve.direct_solve(A, b)
+        assert np.linalg.norm(p1.cpu().numpy() - x) / np.linalg.norm(x) <= 1e-6
