@@ -1525,8 +1525,16 @@ def trace_solve(args):
     from paper_2404_17542_gb300 import build, inputs, mcd
     build.build()
     mcd.lib()
-    run = CylinderRun(args.n, torch.device("cuda", 0), mcd, inputs, args.tol, args.barriers, args.update_restart)
-    run.step(mcd.MIXED)
+    if args.workload == "flow":
+        # the headline's own solve: a full moving-boundary step (restarting
+        # schedule, ALE pressure guess) after --warmup steps from rest
+        run = FlowRun(args.n, torch.device("cuda", 0), mcd, inputs, args.tol)
+        for _ in range(max(1, args.warmup)):
+            run.step(mcd.MIXED)
+    else:
+        run = CylinderRun(args.n, torch.device("cuda", 0), mcd, inputs, args.tol, args.barriers,
+                          args.update_restart)
+        run.step(mcd.MIXED)
     mcd.trace_enable(True)
     mcd.timing_enable(1)
     try:
@@ -1561,6 +1569,7 @@ def trace_solve(args):
     print(json.dumps({
         "n": args.n, "iters": info["iters"], "fallback": info["fallback"],
         "barriers_per_iteration": 1 if one else 2,
+        "staged_tiles": bool(int(ph[0, 7]) & 2),
         "iteration_us": med([ph[r + 1, 0] - ph[r, 0] for r in rows]),
         "iteration_us_p90": (round(float(np.percentile([ph[r + 1, 0] - ph[r, 0] for r in rows], 90)) / 1000.0, 3)
                              if rows else None),

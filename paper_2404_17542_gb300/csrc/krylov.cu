@@ -885,9 +885,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Phase timestamps of block 0 for the first 64 iterations of a launch:
 // slots 0 start, 1 A done, 2 A reduced, 3 B done, 4 B reduced, 5 C done,
-// 6 C reduced.
+// 6 C reduced.  Slot 7 of iteration 0 records the launch's operand path:
+// bit 0 set, bit 1 TMA-staged 3x3 tiles, bit 2 TMA row stream, bit 3 one
+// barrier per iteration.
 __device__ __forceinline__ void stamp(const PArgs &a, int it, int slot) {
-    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && it < 64) a.trace[it * 8 + slot] = global_ns();
+    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && it < 64) {
+        a.trace[it * 8 + slot] = global_ns();
+        if (it == 0 && slot == 0)
+            a.trace[7] = 1ull | (a.tma3 ? 2ull : 0ull) | (a.tma_rows ? 4ull : 0ull) | (a.one ? 8ull : 0ull);
+    }
 }
 
 // Per-block stamps of iteration 10: start (after the previous barrier),
