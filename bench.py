@@ -90,6 +90,9 @@ def parse_args():
     ap.add_argument("--barriers", type=int, default=0, choices=[0, 1, 2, 3],
                     help="with --profile-solve / --trace-solve: grid barriers per Bi-CGSTAB iteration "
                          "(0: the library default)")
+    ap.add_argument("--tilings", action="store_true",
+                    help="with --workload batched: time every tiling (rows x CTAs per SM) in both precisions, "
+                         "one JSON line each, instead of the bench line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -729,6 +732,38 @@ def reference_arm(args):
 import numpy as np  # noqa: E402  (used by the oracle legs)
 
 
+TUNE_SWEEPS = 5000   # longer than any solve of the batched workload
+
+
+def batched_tilings(args, bt, rhs, bnd, p, mcd):
+    """Every tiling of the batched solve (tile rows x CTAs per SM, clamped by
+    the kernel's occupancy) in both precisions: one whole solve each after a
+    warm-up solve, L2 flushed, CUDA events; one JSON line per tiling."""
+    import torch
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=p.device)
+    stream = torch.cuda.current_stream()
+    for mode, name in ((mcd.MIXED, "mixed"), (mcd.FP64, "fp64")):
+        for rows in (1, 2, 4):
+            for cps in (1, 2, 3, 4):
+                bt.set_tuning(rows, cps)
+                ms = []
+                for _ in range(2):
+                    p.zero_()
+                    flush_buf.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    _p, res = bt.solve(rhs, bnd, p=p, tol=args.tol, mode=mode, graph=True)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                print(json.dumps({"workload": "batched", "mode": name, "rows": rows, "ctas_per_sm": cps,
+                                  "ms": round(ms[-1], 1), "iters_max": int(res["iters"].max()),
+                                  "iters_total": int(res["iters"].sum()),
+                                  "dp_unknowns_per_s": bt.N / (ms[-1] / 1e3)}), flush=True)
+
+
 def batched_arm(args):
     """One line for the batched workload: 256 degree-4 polynomial Poisson
     systems, sizes floor(exp U(ln 32, ln 512)) per side (seed 4), all solved
@@ -752,7 +787,12 @@ def batched_arm(args):
     bnd = d(np.concatenate([pb.bnd for pb in probs]))
     bt.build(pos, mask)
     p = torch.zeros(bt.N, dtype=torch.float64, device=dev)
-    tune_ms = bt.autotune(rhs, bnd, p, tol=args.tol, sweeps=30)
+    if args.tilings:
+        return batched_tilings(args, bt, rhs, bnd, p, mcd)
+    # the autotuner times whole solves (the sweep budget exceeds any solve's
+    # length): the first sweeps, with every system running, favour other
+    # tilings than the rest of the solve, where the large systems run alone
+    tune_ms = bt.autotune(rhs, bnd, p, tol=args.tol, sweeps=TUNE_SWEEPS)
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -779,7 +819,12 @@ def batched_arm(args):
     ms, res = timed(mcd.MIXED, True, args.steps)
     launches = (mcd.launch_count() - launches0) / max(1, args.steps + args.warmup)
     clk = clocks.stop()
+    # the FP64 batch on its own autotuned tiling, then the mixed tiling again
+    rows, cps = bt.tuning()
+    tune_ms64 = bt.autotune(rhs, bnd, p, tol=args.tol, mode=mcd.FP64, sweeps=TUNE_SWEEPS)
+    rows64, cps64 = bt.tuning()
     ms64, res64 = timed(mcd.FP64, True, max(1, args.steps // 2))
+    bt.set_tuning(rows, cps)
     ms_rs, res_rs = timed(mcd.MIXED, True, max(1, args.steps // 2), update_restart=1)
     # the learned warm start: a network trained on the batch's own systems
     # (features at the zero guess, target the FP64 solution), applied to
@@ -824,7 +869,6 @@ def batched_arm(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_each = e0.elapsed_time(e1)
-    rows, cps = bt.tuning()
     line = {"metric": METRIC, "value": bt.N / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 Krylov + f64 refinement", "data": "synthetic",
@@ -839,7 +883,8 @@ def batched_arm(args):
             "iters_total": int(res["iters"].sum()), "dropped_cycles": int(res["discarded"].sum()),
             "fp64_finishes": int((res["fallback"] != 0).sum()),
             "batched_fp64": {"value": bt.N / (ms64 / 1e3), "ms_per_step": ms64,
-                             "iters_max": int(res64["iters"].max()), "iters_total": int(res64["iters"].sum())},
+                             "iters_max": int(res64["iters"].max()), "iters_total": int(res64["iters"].sum()),
+                             "tiling": {"rows": rows64, "ctas_per_sm": cps64, "autotune_ms_per_sweep": tune_ms64}},
             "batched_mixed_restarting": {"value": bt.N / (ms_rs / 1e3), "ms_per_step": ms_rs,
                                          "iters_total": int(res_rs["iters"].sum()),
                                          "fp64_finishes": int((res_rs["fallback"] != 0).sum())},

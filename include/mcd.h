@@ -594,7 +594,9 @@ mcd_status mcd_flow_copy(const mcd_flow *f, int which, double *dst_dev, mcd_stre
 typedef struct mcd_batch mcd_batch;
 
 /* Tiling of the batched solve: tiles of 32 x (8 rows) DPs per CTA step, and
- * CTAs per SM of the persistent launch (0: the default, 2). */
+ * CTAs per SM of the persistent launch (0: as many as fit, at most 4; the
+ * FP32 kernels with 1 or 2 rows and the FP64 kernel with 1 row are built to
+ * fit 4). */
 typedef struct {
     int rows;          /* 1, 2 or 4 */
     int ctas_per_sm;   /* 0 .. 4 */
@@ -657,7 +659,10 @@ mcd_status mcd_batch_get_tuning(const mcd_batch *bt, mcd_batch_tuning *t);
 
 /* mcd_batch_autotune - time `sweeps` sweeps of the solve for every tiling
  * (rows 1, 2, 4 x 1 .. 4 CTAs per SM within the kernel's occupancy) and keep
- * the fastest per sweep.  cache_path (may be NULL): a text file of
+ * the fastest per sweep.  A budget longer than the solve times whole solves,
+ * which is what the choice should rest on: the per-sweep cost of a tiling
+ * changes as small systems converge and large ones run alone.
+ * cache_path (may be NULL): a text file of
  * "<device, sizes and mode key> | rows ctas_per_sm ms" lines; a matching
  * line is used without timing, a new result is appended.  p_dev is
  * overwritten (it is the iterate of the trial solves).  best_ms_per_sweep:

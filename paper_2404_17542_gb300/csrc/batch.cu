@@ -489,8 +489,16 @@ __device__ void for_segments(const BArgs &a, int na, int list, int64_t M, F fn) 
     }
 }
 
+// Occupancy: the block's tile loop waits on its loads once per tile, so more
+// resident blocks hide more of that latency.  The tilings whose registers fit
+// 64 per thread without spilling (FP32 with 1 or 2 rows, FP64 with 1) ask for
+// four blocks per SM; the others leave the count to the compiler.
+template <typename T, int R> struct BatchOcc {
+    static constexpr int min_blocks = (R == 1 || (R == 2 && sizeof(T) == 4)) ? 4 : 0;
+};
+
 template <typename T, int R>
-__global__ void __launch_bounds__(256) bicg_batch(const __grid_constant__ BArgs a) {
+__global__ void __launch_bounds__(256, BatchOcc<T, R>::min_blocks) bicg_batch(const __grid_constant__ BArgs a) {
     __shared__ T tile[BT<R>::H];
     __shared__ int s_na, s_list, s_err;
     __shared__ long long s_M;
@@ -926,7 +934,7 @@ mcd_status make_launch(mcd_batch *bt, double *p, const mcd_solve_params *prm, La
         set_error("batch kernel cannot be resident on this device");
         return MCD_ECUDA;
     }
-    const int cps = bt->tune.ctas_per_sm > 0 ? std::min(bt->tune.ctas_per_sm, occ) : std::min(occ, 2);
+    const int cps = std::min(bt->tune.ctas_per_sm > 0 ? bt->tune.ctas_per_sm : 4, occ);
     L.grid = std::min(cps, 4) * device_sms();
     L.kernel = k;
     BArgs &a = L.args;
