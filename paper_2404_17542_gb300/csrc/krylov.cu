@@ -2193,18 +2193,25 @@ __device__ void phase_ca_staged(const PArgs &a, float *tile, int par, float alph
         const float *XL = reinterpret_cast<const float *>(st + Stage3::point_off(2));
         int x0, y0, z0;
         tile_origin<2>(a.ta, tb + i, x0, y0, z0);
+        // the DPs' roles first: these are the phase's only global loads, and
+        // issued here their latency overlaps the halo fill below
+        int64_t k[TL::R];
+        int lx[TL::R], ly[TL::R], lz[TL::R];
+        bool neu[TL::R];
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            k[q] = tile_dp<2>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+            neu[q] = a.ta.kind && k[q] >= 0 && __ldg(a.ta.kind + k[q]) == KIND_NEUMANN;
+        }
         for (int h = tid; h < HD::H; h += 256) {
             const int hy = h / HD::HX, hx = h - hy * HD::HX;
             const int hi = hy * Stage3::HXB + hx + 3;
             const float rj = S[hi] - omega * T[hi];
             tile[h] = rj + beta * (PO[hi] - omega * VO[hi]);
         }
-        int64_t k[TL::R];
-        int lx[TL::R], ly[TL::R], lz[TL::R];
         float w[TL::R][9], so[TL::R], to[TL::R], po[TL::R], rh[TL::R], xo[TL::R], xl[TL::R];
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
-            k[q] = tile_dp<2>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
             const int pi = ly[q] * Stage3::TX + lx[q];
             const int hc = (ly[q] + 1) * Stage3::HXB + lx[q] + 4;
 #pragma unroll
@@ -2222,9 +2229,7 @@ __device__ void phase_ca_staged(const PArgs &a, float *tile, int par, float alph
             add_correction(a.xlo, x, k[q], xo[q], xl[q], alpha, po[q], omega, so[q]);
             r[k[q]] = rk;
             p_new[k[q]] = pk;
-            const float vk = (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN)
-                                 ? pk
-                                 : stencil_apply<2, float>(w[q], tile, lx[q], ly[q], 0);
+            const float vk = neu[q] ? pk : stencil_apply<2, float>(w[q], tile, lx[q], ly[q], 0);
             v_new[k[q]] = vk;
             dot[0].add(rh[q], vk);
             dot[1].add(rk, rk);
@@ -2259,17 +2264,22 @@ __device__ void phase_b2_staged(const PArgs &a, float *tile, int parb, float alp
         const float *RH = reinterpret_cast<const float *>(st + Stage3::point_off(0));
         int x0, y0, z0;
         tile_origin<2>(a.ta, tb + i, x0, y0, z0);
+        int64_t k[TL::R];
+        int lx[TL::R], ly[TL::R], lz[TL::R];
+        bool neu[TL::R];
+#pragma unroll
+        for (int q = 0; q < TL::R; ++q) {
+            k[q] = tile_dp<2>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
+            neu[q] = a.ta.kind && k[q] >= 0 && __ldg(a.ta.kind + k[q]) == KIND_NEUMANN;
+        }
         for (int h = tid; h < HD::H; h += 256) {
             const int hy = h / HD::HX, hx = h - hy * HD::HX;
             const int hi = hy * Stage3::HXB + hx + 3;
             tile[h] = R[hi] - alpha * V[hi];
         }
-        int64_t k[TL::R];
-        int lx[TL::R], ly[TL::R], lz[TL::R];
         float w[TL::R][9], rh[TL::R];
 #pragma unroll
         for (int q = 0; q < TL::R; ++q) {
-            k[q] = tile_dp<2>(g, tid, q, x0, y0, z0, lx[q], ly[q], lz[q]);
             const int pi = ly[q] * Stage3::TX + lx[q];
 #pragma unroll
             for (int sl = 0; sl < 9; ++sl) w[q][sl] = W[sl * (Stage3::TX * Stage3::TY) + pi];
@@ -2282,9 +2292,7 @@ __device__ void phase_b2_staged(const PArgs &a, float *tile, int parb, float alp
             if (k[q] < 0) continue;
             const float sk = tile[tile_centre<2>(lx[q], ly[q], 0)];
             s_out[k[q]] = sk;
-            const float tk = (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN)
-                                 ? sk
-                                 : stencil_apply<2, float>(w[q], tile, lx[q], ly[q], 0);
+            const float tk = neu[q] ? sk : stencil_apply<2, float>(w[q], tile, lx[q], ly[q], 0);
             t_out[k[q]] = tk;
             dot[0].add(tk, sk);
             dot[1].add(tk, tk);
