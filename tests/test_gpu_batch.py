@@ -87,7 +87,7 @@ def test_batch_tilings_and_graph_agree(mcd, small_batch):
     ref, _ = bt.solve(rhs, bnd, tol=1e-10)
     ref = ref.cpu().numpy()
     for rows in (1, 2, 4):
-        for cps in (1, 2):
+        for cps in (1, 2, 4):   # 4: the 64-register builds (FP32 1-2 rows) at full occupancy
             bt.set_tuning(rows, cps)
             p, res = bt.solve(rhs, bnd, tol=1e-10, graph=(rows == 2))
             assert np.all(res["status"] == 0)
