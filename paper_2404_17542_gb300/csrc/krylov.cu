@@ -2165,8 +2165,8 @@ __device__ __forceinline__ void stage_drain(const PArgs &a, RowPipe<float> &pp) 
 
 // Phase CA (normal iterations) from staged operands: x, r of the last
 // iteration; p = r + beta (p_old - omega v_old) on tile + halo; v = A p.
-__device__ void phase_ca_staged(const PArgs &a, float *tile, int par, float alpha, float omega, float beta,
-                                DotAcc<float> (&dot)[3], RowPipe<float> &pp) {
+__device__ void phase_ca_staged(const PArgs &a, float *tile0, float *tile1, int par, float alpha, float omega,
+                                float beta, DotAcc<float> (&dot)[3], RowPipe<float> &pp) {
     using HD = HaloDims<2>;
     using TL = Tile<2>;
     const Geo &g = a.ta.g;
@@ -2179,8 +2179,14 @@ __device__ void phase_ca_staged(const PArgs &a, float *tile, int par, float alph
     const int total = te - tb;
     if (tid == 0 && !pp.failed)
         for (int i = 0; i < Stage3::NB && i < total; ++i) stage_issue(a, pp, i, tb + i, true, par);
+    // Consecutive tiles build their halo tiles in alternate buffers: a thread
+    // that fills tile i + 1's halo has passed no barrier since it read tile
+    // i's, but every thread reading buffer (i & 1) in tile i finished before
+    // the barrier of tile i + 1, which any thread passes before it refills
+    // that buffer in tile i + 2.  One __syncthreads per tile.
     for (int i = 0; i < total; ++i) {
         const int b = i % Stage3::NB;
+        float *tile = (i & 1) ? tile1 : tile0;
         stage_wait(a, pp, b);
         const unsigned char *st = reinterpret_cast<const unsigned char *>(pp.buf) + (size_t)b * Stage3::BYTES;
         const float *W = reinterpret_cast<const float *>(st);
@@ -2235,15 +2241,14 @@ __device__ void phase_ca_staged(const PArgs &a, float *tile, int par, float alph
             dot[1].add(rk, rk);
             dot[2].add(rh[q], rk);
         }
-        __syncthreads();   // the halo tile is free for the next tile
     }
     stage_drain(a, pp);
 }
 
 // Phase B from staged operands: s = r - alpha v (tile + halo), t = A s;
 // dots t.s, t.t, s.s, r^.s, r^.t.
-__device__ void phase_b2_staged(const PArgs &a, float *tile, int parb, float alpha, DotAcc<float> (&dot)[5],
-                                RowPipe<float> &pp) {
+__device__ void phase_b2_staged(const PArgs &a, float *tile0, float *tile1, int parb, float alpha,
+                                DotAcc<float> (&dot)[5], RowPipe<float> &pp) {
     using HD = HaloDims<2>;
     using TL = Tile<2>;
     const Geo &g = a.ta.g;
@@ -2254,8 +2259,10 @@ __device__ void phase_b2_staged(const PArgs &a, float *tile, int parb, float alp
     const int total = te - tb;
     if (tid == 0 && !pp.failed)
         for (int i = 0; i < Stage3::NB && i < total; ++i) stage_issue(a, pp, i, tb + i, false, parb);
+    // alternate halo buffers, one __syncthreads per tile (as in phase CA)
     for (int i = 0; i < total; ++i) {
         const int b = i % Stage3::NB;
+        float *tile = (i & 1) ? tile1 : tile0;
         stage_wait(a, pp, b);
         const unsigned char *st = reinterpret_cast<const unsigned char *>(pp.buf) + (size_t)b * Stage3::BYTES;
         const float *W = reinterpret_cast<const float *>(st);
@@ -2300,7 +2307,6 @@ __device__ void phase_b2_staged(const PArgs &a, float *tile, int parb, float alp
             dot[3].add(rh[q], sk);
             dot[4].add(rh[q], tk);
         }
-        __syncthreads();
     }
     stage_drain(a, pp);
 }
@@ -2416,6 +2422,8 @@ template <int G, typename T>
 __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent2(const __grid_constant__ PArgs a) {
     using HD = HaloDims<G>;
     __shared__ T tile[HD::H];
+    // the staged FP32 phases alternate between tile and tile_alt
+    __shared__ T tile_alt[(G == 2 && sizeof(T) == 4) ? HD::H : 1];
     extern __shared__ __align__(128) unsigned char pipe_smem[];
     __shared__ __align__(8) uint64_t pipe_mbar[Shape<G>::S > 27 ? RowPipe<T>::NB : Stage3::NB];
     RowPipe<T> pp;
@@ -2477,7 +2485,7 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
             DotAcc<T> dot[3];
             if constexpr (G == 2 && sizeof(T) == 4) {
                 if (a.tma3 && mode == CA_NORMAL)
-                    phase_ca_staged(a, tile, par, alpha0, omega0, beta0, dot, pp);
+                    phase_ca_staged(a, tile, tile_alt, par, alpha0, omega0, beta0, dot, pp);
                 else
                     phase_ca<G, T>(a, tile, p_old, v_old, p_new, v_new, alpha0, omega0, beta0, mode, dot, pp);
             } else {
@@ -2610,7 +2618,7 @@ __global__ void __launch_bounds__(256, Shape<G>::S > 27 ? 2 : 0) bicg_persistent
             DotAcc<T> dot[5];
             if constexpr (G == 2 && sizeof(T) == 4) {
                 if (a.tma3)
-                    phase_b2_staged(a, tile, parb, alpha, dot, pp);
+                    phase_b2_staged(a, tile, tile_alt, parb, alpha, dot, pp);
                 else
                     phase_b2<G, T>(a, tile, v_cur, alpha, dot, pp);
             } else {
