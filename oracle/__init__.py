@@ -13,6 +13,12 @@ Modules (each function cites the passage of arXiv 2404.17542 it restates):
   solve    sparse assembly of the pressure-Poisson system (Eq. (21)) and a
            textbook BiCGSTAB (Sec. 3.3)
   flow     projection-method driver pieces (Sec. 3.3, Eqs. (20)-(23))
+  ale      the moving-boundary step: ALE interpolation (Eq. (19), Appendix A),
+           boundary velocities and rigid accelerations (Eqs. (24)-(29)), the
+           fluid force (Eqs. (30)-(31)) and the whole step in the order of
+           Sec. 3.3 (moving_step)
+  sdf      discrete signed-distance bodies and their MLS interpolation
+           (Sec. 2.5)
   cnn      FP64 forward/backward of the small convolutional network used as
            the learned warm start (an addition: the paper has no network)
 
