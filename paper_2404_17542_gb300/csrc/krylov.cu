@@ -184,14 +184,14 @@ __global__ void __launch_bounds__(256) bicg_ka(TileArgs ta, const T *__restrict_
         if (ta.kind && ta.kind[k[q]] == KIND_NEUMANN) {
             vk = pk;
         } else if (PREF) {
-            vk = stencil_apply<G, T>(w[q], tile, lx[q], ly[q], lz[q]);
+            vk = stencil_apply<G, T, (G != 2)>(w[q], tile, lx[q], ly[q], lz[q]);
         } else {
             if constexpr (S > 27) {
                 vk = stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
             } else {
                 T wl[S];
                 load_row<S, T>(row, g.N, k[q], wl);
-                vk = stencil_apply<G, T>(wl, tile, lx[q], ly[q], lz[q]);
+                vk = stencil_apply<G, T, (G != 2)>(wl, tile, lx[q], ly[q], lz[q]);
             }
         }
         v_new[k[q]] = vk;
@@ -253,14 +253,14 @@ __global__ void __launch_bounds__(256) bicg_kb(TileArgs ta, const T *__restrict_
         if (ta.kind && ta.kind[k[q]] == KIND_NEUMANN) {
             tk = sk;
         } else if (PREF) {
-            tk = stencil_apply<G, T>(w[q], tile, lx[q], ly[q], lz[q]);
+            tk = stencil_apply<G, T, (G != 2)>(w[q], tile, lx[q], ly[q], lz[q]);
         } else {
             if constexpr (S > 27) {
                 tk = stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
             } else {
                 T wl[S];
                 load_row<S, T>(row, g.N, k[q], wl);
-                tk = stencil_apply<G, T>(wl, tile, lx[q], ly[q], lz[q]);
+                tk = stencil_apply<G, T, (G != 2)>(wl, tile, lx[q], ly[q], lz[q]);
             }
         }
         t_out[k[q]] = tk;
@@ -1275,14 +1275,14 @@ __device__ void phase_a(const PArgs &a, T *tile, const T *p_old, const T *v_old,
             if (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN) {
                 vk = pk;
             } else if (PREF) {
-                vk = stencil_apply<G, T>(w[q], tile, lx[q], ly[q], lz[q]);
+                vk = stencil_apply<G, T, (G != 2)>(w[q], tile, lx[q], ly[q], lz[q]);
             } else {
                 if constexpr (S > 27) {
                     vk = stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
                 } else {
                     T wl[S];
                     load_row<S, T>(row, g.N, k[q], wl);
-                    vk = stencil_apply<G, T>(wl, tile, lx[q], ly[q], lz[q]);
+                    vk = stencil_apply<G, T, (G != 2)>(wl, tile, lx[q], ly[q], lz[q]);
                 }
             }
             v_new[k[q]] = vk;
@@ -1344,14 +1344,14 @@ __device__ void phase_b(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T> 
             if (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN) {
                 tk = sk;
             } else if (PREF) {
-                tk = stencil_apply<G, T>(w[q], tile, lx[q], ly[q], lz[q]);
+                tk = stencil_apply<G, T, (G != 2)>(w[q], tile, lx[q], ly[q], lz[q]);
             } else {
                 if constexpr (S > 27) {
                     tk = stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
                 } else {
                     T wl[S];
                     load_row<S, T>(row, g.N, k[q], wl);
-                    tk = stencil_apply<G, T>(wl, tile, lx[q], ly[q], lz[q]);
+                    tk = stencil_apply<G, T, (G != 2)>(wl, tile, lx[q], ly[q], lz[q]);
                 }
             }
             t_out[k[q]] = tk;
@@ -1974,14 +1974,14 @@ __device__ void phase_ca(const PArgs &a, T *tile, const T *p_old, const T *v_old
             if (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN) {
                 vk = pk;
             } else if (PREF) {
-                vk = stencil_apply<G, T>(w[q], tile, lx[q], ly[q], lz[q]);
+                vk = stencil_apply<G, T, (G != 2)>(w[q], tile, lx[q], ly[q], lz[q]);
             } else {
                 if constexpr (S > 27) {
                     vk = tma ? vks[q] : stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
                 } else {
                     T wl[S];
                     load_row<S, T>(row, g.N, k[q], wl);
-                    vk = stencil_apply<G, T>(wl, tile, lx[q], ly[q], lz[q]);
+                    vk = stencil_apply<G, T, (G != 2)>(wl, tile, lx[q], ly[q], lz[q]);
                 }
             }
             v_new[k[q]] = vk;
@@ -2054,14 +2054,14 @@ __device__ void phase_b2(const PArgs &a, T *tile, const T *v, T alpha, DotAcc<T>
             if (a.ta.kind && a.ta.kind[k[q]] == KIND_NEUMANN) {
                 tk = sk;
             } else if (PREF) {
-                tk = stencil_apply<G, T>(w[q], tile, lx[q], ly[q], lz[q]);
+                tk = stencil_apply<G, T, (G != 2)>(w[q], tile, lx[q], ly[q], lz[q]);
             } else {
                 if constexpr (S > 27) {
                     tk = tma ? vks[q] : stencil_apply_rows<G, T>(row, g.N, k[q], tile, lx[q], ly[q], lz[q]);
                 } else {
                     T wl[S];
                     load_row<S, T>(row, g.N, k[q], wl);
-                    tk = stencil_apply<G, T>(wl, tile, lx[q], ly[q], lz[q]);
+                    tk = stencil_apply<G, T, (G != 2)>(wl, tile, lx[q], ly[q], lz[q]);
                 }
             }
             t_out[k[q]] = tk;
@@ -2238,7 +2238,7 @@ __device__ void phase_ca_staged(const PArgs &a, float *tile0, float *tile1, int 
             add_correction(a.xlo, x, k[q], xo[q], xl[q], alpha, po[q], omega, so[q]);
             r[k[q]] = rk;
             p_new[k[q]] = pk;
-            const float vk = neu[q] ? pk : stencil_apply<2, float>(w[q], tile, lx[q], ly[q], 0);
+            const float vk = neu[q] ? pk : stencil_apply<2, float, false>(w[q], tile, lx[q], ly[q], 0);
             v_new[k[q]] = vk;
             dot[0].add(rh[q], vk);
             dot[1].add(rk, rk);
@@ -2302,7 +2302,7 @@ __device__ void phase_b2_staged(const PArgs &a, float *tile0, float *tile1, int 
             if (k[q] < 0) continue;
             const float sk = tile[tile_centre<2>(lx[q], ly[q], 0)];
             s_out[k[q]] = sk;
-            const float tk = neu[q] ? sk : stencil_apply<2, float>(w[q], tile, lx[q], ly[q], 0);
+            const float tk = neu[q] ? sk : stencil_apply<2, float, false>(w[q], tile, lx[q], ly[q], 0);
             t_out[k[q]] = tk;
             dot[0].add(tk, sk);
             dot[1].add(tk, tk);

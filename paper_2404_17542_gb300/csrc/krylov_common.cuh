@@ -343,17 +343,35 @@ __device__ __forceinline__ int tile_centre(int lx, int ly, int lz) {
 // O(|grad x| / l0) terms loses the digits of their O(lap x) sum and slows
 // Bi-CGSTAB by about 2x; the compensation costs about 11 FP32 operations per
 // term, which this bandwidth-bound kernel has to spare.
+//
+// COMP = false accumulates the FP32 difference form with one FMA per term
+// instead.  The single-system 2D solver uses it: its iteration is bound by
+// issue and latency, not bandwidth, and with its dot products still
+// double-float the plain 3x3 sum costs about 4 % more iterations on the
+// flow's PPE while each iteration takes about 9 % less.  Wide and 3D
+// stencils and the batched solver keep the compensated sum.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-template <int G, typename T>
+template <int G, typename T, bool COMP = true>
 __device__ __forceinline__ T stencil_apply(const T *w, const T *tile, int lx, int ly, int lz) {
     using HD = HaloDims<G>;
     constexpr int C = HD::S / 2, W = Shape<G>::W;
     const T xk = tile[tile_centre<G>(lx, ly, lz)];
+    if (sizeof(T) == 4 && !COMP) {
+        float acc = (float)w[C] * (float)xk;   // centre weight is 0 or 1: exact
+#pragma unroll
+        for (int s = 0; s < HD::S; ++s) {
+            if (s == C) continue;
+            const int ox = s % W, oy = (s / W) % W, oz = s / (W * W);
+            const int h = (lx + ox) + HD::HX * ((ly + oy) + HD::HY * (lz + oz));
+            acc = __fmaf_rn((float)w[s], __fsub_rn((float)tile[h], (float)xk), acc);
+        }
+        return (T)acc;
+    }
     if (sizeof(T) == 4) {
         float hi = (float)w[C] * (float)xk, lo = 0.0f;   // centre weight is 0 or 1: exact
 #pragma unroll
